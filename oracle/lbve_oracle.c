@@ -1,0 +1,635 @@
+/*
+ * lbve_oracle.c -- plain, slow, FP64 CPU oracle of the coupled viscoelastic
+ * lattice Boltzmann time step of Yu, Chen, Wang, Yuan & Shu, "An improved
+ * lattice Boltzmann method with a novel conservative boundary scheme for
+ * viscoelastic fluid flows" (arXiv 2508.16997).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA path and never calls it.
+ *
+ * The oracle is written as the paper's algorithm, step by step, with no
+ * blocking, fusion or algebraic shortcut: every Hermite moment is the literal
+ * sum over the nine D2Q9 directions, every tensor contraction runs over all
+ * index tuples, and streaming is an explicit push.  Precomputed tables hold
+ * only the D2Q9 velocities, weights and Hermite polynomials themselves.
+ *
+ * State at the start of a step (time t): the completed post-streaming
+ * populations f_i(x,t) and g^c_i(x,t) (c = xx, xy, yy), plus the history
+ * S^c(x,t-1) and u(x,t-1) needed by the time derivative of the CDE source.
+ *
+ * One step (Sec. 3):
+ *   1. moments:  rho = sum f, rho u = sum e f + F/2 (eq. eq_ev_f0),
+ *                phi^c = sum g^c (Sec. 3.2, last relation)
+ *   2. gradients of u and of rho u_x^3, rho u_y^3 by second-order finite
+ *      differences (the paper does not state the scheme; reading: central
+ *      differences, one-sided second order on wall rows)
+ *   3. Oldroyd-B stress tau = mu_p/lambda (A - I) (eq_kramer, eqb4) and the
+ *      constitutive source S = Phi_ab (Sec. 3.2, expression under eq_cde)
+ *   4. hydrodynamic TRT-RLB collision with G_i, F_i, T_i (eq_ev_f, eq2, eq4,
+ *      eq5, eq6 and the forcing term of Sec. 3.1)
+ *   5. three CDE TRT-RLB collisions with G~_i (eq_p_G_1), F~_i (eq_p_F) and
+ *      the backward difference of F~_i (eq_g0 and the difference formula of
+ *      Sec. 3.2)
+ *   6. push streaming; populations that would come from outside the domain
+ *      are left unknown
+ *   7. hydrodynamic wet-node non-equilibrium bounce-back (Zou-He) on flat
+ *      walls (named in Secs. 4.2, 4.3; formulas are this oracle's reading)
+ *   8. CNEBB completion of each CDE lattice (Sec. 3.3)
+ *   9. history <- S(t), u(t)
+ *
+ * Domain: nx x ny nodes, row-major [y][x], periodic in x.  In y either
+ * periodic, or wet-node walls on rows y = 0 and y = ny-1 (solid beyond).
+ *
+ * Parity status: every function here is pinned by tests under tests/
+ * (closed forms, invariants, special cases); see the per-function comments.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 9
+#define NC 3 /* conformation components: 0 = xx, 1 = xy, 2 = yy */
+
+/* ---------------------------------------------------------------------- */
+/* D2Q9 lattice (Sec. 3.1, velocity set and weights)                        */
+/* ---------------------------------------------------------------------- */
+static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double W[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
+                            1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
+                            1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+static const double CS2 = 1.0 / 3.0; /* c_s^2 with c = 1 */
+
+/* Hermite polynomials of orders 1..3 for every direction (Sec. 3.1):
+ *   H_a    = e_a
+ *   H_ab   = e_a e_b - cs2 d_ab
+ *   H_abc  = e_a e_b e_c - cs2 (e_a d_bc + e_b d_ac + e_c d_ab)         */
+static double H1[Q][2], H2[Q][2][2], H3[Q][2][2][2];
+static int tables_ready = 0;
+
+static void build_tables(void) {
+  if (tables_ready) return;
+  for (int i = 0; i < Q; ++i) {
+    const double e[2] = {(double)EX[i], (double)EY[i]};
+    for (int a = 0; a < 2; ++a) {
+      H1[i][a] = e[a];
+      for (int b = 0; b < 2; ++b) {
+        H2[i][a][b] = e[a] * e[b] - CS2 * (a == b);
+        for (int c = 0; c < 2; ++c)
+          H3[i][a][b][c] = e[a] * e[b] * e[c] -
+                           CS2 * (e[a] * (b == c) + e[b] * (a == c) + e[c] * (a == b));
+      }
+    }
+  }
+  tables_ready = 1;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Parameters                                                               */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t nx, ny;
+  int32_t periodic_y; /* 0: wet-node walls on rows 0 and ny-1          */
+  int32_t reserved;
+  double beta, Wi, Re, Sc, Ma; /* Sec. 2.4-2.5                          */
+  double Lc;                   /* characteristic length, lattice units  */
+  double Lambda_s, Lambda_p;   /* magic parameters (Secs. 3.1, 3.2)      */
+  double Fx, Fy;               /* uniform body force if no field given  */
+} orc_params;
+
+/* Derived lattice coefficients (Sec. 2.4 and the relaxation-time relations
+ * of Secs. 3.1-3.2), rho_0 = 1, dt = dx = 1:
+ *   U_c = Ma c_s                                  (eq_Mach)
+ *   nu_0 = U_c L_c / Re                           (eqb5)
+ *   nu_s = beta nu_0, mu_p = (1-beta) nu_0         (eqb7, mu_0 = mu_s + mu_p)
+ *   tau_s1 = nu_s / cs2 + 1/2                      (mu_s relation, Sec. 3.1)
+ *   tau_s2 = Lambda_s/(tau_s1 - 1/2) + 1/2         (Lambda_s relation)
+ *   kappa = nu_s / Sc                              (eqb8)
+ *   tau_p1 = kappa / cs2 + 1/2                     (kappa relation, Sec. 3.2)
+ *   tau_p2 = Lambda_p/(tau_p1 - 1/2) + 1/2         (tau_p2 relation)
+ *   lambda = Wi L_c / U_c                          (eqb6)                 */
+typedef struct {
+  double Uc, nu0, nus, mup, tau_s1, tau_s2, kappa, tau_p1, tau_p2, lambda;
+} orc_coeffs;
+
+void orc_derive(const orc_params* p, orc_coeffs* c) {
+  c->Uc = p->Ma * sqrt(CS2);
+  c->nu0 = c->Uc * p->Lc / p->Re;
+  c->nus = p->beta * c->nu0;
+  c->mup = (1.0 - p->beta) * c->nu0;
+  c->tau_s1 = c->nus / CS2 + 0.5;
+  c->tau_s2 = p->Lambda_s / (c->tau_s1 - 0.5) + 0.5;
+  c->kappa = c->nus / p->Sc;
+  c->tau_p1 = c->kappa / CS2 + 0.5;
+  c->tau_p2 = p->Lambda_p / (c->tau_p1 - 0.5) + 0.5;
+  c->lambda = p->Wi * p->Lc / c->Uc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Node-level building blocks                                               */
+/* ---------------------------------------------------------------------- */
+
+/* Third-order Hermite equilibrium of the hydrodynamic lattice (eq2). */
+void orc_feq(double rho, double ux, double uy, double* feq) {
+  build_tables();
+  const double u[2] = {ux, uy};
+  for (int i = 0; i < Q; ++i) {
+    double s1 = 0, s2 = 0, s3 = 0;
+    for (int a = 0; a < 2; ++a) {
+      s1 += H1[i][a] * u[a];
+      for (int b = 0; b < 2; ++b) {
+        s2 += H2[i][a][b] * u[a] * u[b];
+        for (int c = 0; c < 2; ++c) s3 += H3[i][a][b][c] * u[a] * u[b] * u[c];
+      }
+    }
+    feq[i] = W[i] * rho *
+             (1.0 + s1 / CS2 + s2 / (2.0 * CS2 * CS2) + s3 / (6.0 * CS2 * CS2 * CS2));
+  }
+}
+
+/* Second-order Hermite equilibrium of a CDE lattice (eq_geq). */
+void orc_geq(double phi, double ux, double uy, double* geq) {
+  build_tables();
+  const double u[2] = {ux, uy};
+  for (int i = 0; i < Q; ++i) {
+    double s1 = 0, s2 = 0;
+    for (int a = 0; a < 2; ++a) {
+      s1 += H1[i][a] * u[a];
+      for (int b = 0; b < 2; ++b) s2 += H2[i][a][b] * u[a] * u[b];
+    }
+    geq[i] = W[i] * phi * (1.0 + s1 / CS2 + s2 / (2.0 * CS2 * CS2));
+  }
+}
+
+/* Hydrodynamic moments (eq_ev_f0): rho = sum f, rho u = sum e f + F/2. */
+void orc_hydro_moments(const double* f, double Fx, double Fy, double* rho, double* ux,
+                       double* uy) {
+  double r = 0, jx = 0, jy = 0;
+  for (int i = 0; i < Q; ++i) {
+    r += f[i];
+    jx += EX[i] * f[i];
+    jy += EY[i] * f[i];
+  }
+  *rho = r;
+  *ux = (jx + 0.5 * Fx) / r;
+  *uy = (jy + 0.5 * Fy) / r;
+}
+
+/* Hydrodynamic TRT-RLB collision (eq_ev_f) with
+ *   off-equilibrium Hermite moments A0, A_a, A_ab, A_abc (eq4a-d),
+ *   Galilean correction G_i (eq5) with d_g Phi_abg given by its two nonzero
+ *     components dPhi[0] = d_x(rho u_x^3), dPhi[1] = d_y(rho u_y^3),
+ *   viscoelastic source T_i (eq6) with tau = {tau_xx, tau_xy, tau_yy},
+ *   first-order Hermite forcing F_i (Sec. 3.1), dt = 1.
+ * Input f is the completed post-streaming population at time t; out is f^dagger. */
+void orc_hydro_collide(const double* f, double Fx, double Fy, const double* tau,
+                       const double* dPhi, double tau_s1, double tau_s2, double* out) {
+  build_tables();
+  double rho, ux, uy;
+  orc_hydro_moments(f, Fx, Fy, &rho, &ux, &uy);
+  double feq[Q];
+  orc_feq(rho, ux, uy, feq);
+
+  double A0 = 0, A1[2] = {0, 0}, A2[2][2] = {{0, 0}, {0, 0}};
+  double A3[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
+  for (int i = 0; i < Q; ++i) {
+    const double fneq = f[i] - feq[i];
+    A0 += fneq;
+    for (int a = 0; a < 2; ++a) {
+      A1[a] += H1[i][a] * fneq;
+      for (int b = 0; b < 2; ++b) {
+        A2[a][b] += H2[i][a][b] * fneq;
+        for (int c = 0; c < 2; ++c) A3[a][b][c] += H3[i][a][b][c] * fneq;
+      }
+    }
+  }
+  const double T2[2][2] = {{tau[0], tau[1]}, {tau[1], tau[2]}};
+  const double dP[2][2] = {{dPhi[0], 0.0}, {0.0, dPhi[1]}}; /* d_g Phi_abg */
+  const double F[2] = {Fx, Fy};
+  const double cs4 = CS2 * CS2, cs6 = CS2 * CS2 * CS2;
+
+  for (int i = 0; i < Q; ++i) {
+    double r1 = A0, r3 = 0, g2 = 0, t2 = 0, f1 = 0;
+    for (int a = 0; a < 2; ++a) {
+      r1 += H1[i][a] * A1[a] / CS2;
+      f1 += H1[i][a] * F[a] / CS2;
+      for (int b = 0; b < 2; ++b) {
+        r1 += H2[i][a][b] * A2[a][b] / (2.0 * cs4);
+        g2 += H2[i][a][b] * dP[a][b];
+        t2 += H2[i][a][b] * T2[a][b];
+        for (int c = 0; c < 2; ++c) r3 += H3[i][a][b][c] * A3[a][b][c];
+      }
+    }
+    const double Gi = -W[i] * (1.0 - 1.0 / (2.0 * tau_s1)) * g2 / (6.0 * cs6);
+    const double Ti = -W[i] * t2 / (2.0 * cs4 * tau_s1);
+    const double Fi = (1.0 - 1.0 / (2.0 * tau_s1)) * W[i] * f1;
+    out[i] = feq[i] + W[i] * (1.0 - 1.0 / tau_s1) * r1 +
+             W[i] * (1.0 - 1.0 / tau_s2) * r3 / (6.0 * cs6) + Gi + Fi + Ti;
+  }
+}
+
+/* CDE source term F~_i (eq_p_F) for source S and velocity u. */
+static void cde_source(double S, double ux, double uy, double tau_p1, double* Ft) {
+  const double u[2] = {ux, uy};
+  for (int i = 0; i < Q; ++i) {
+    double eu = 0;
+    for (int a = 0; a < 2; ++a) eu += H1[i][a] * u[a];
+    Ft[i] = W[i] * S + (1.0 - 1.0 / (2.0 * tau_p1)) * W[i] * eu * S / CS2;
+  }
+}
+
+/* CDE TRT-RLB collision (eq_g0) of one conformation lattice:
+ *   off-equilibrium moments B0, B_a, B_ab (Sec. 3.2, eq_p_neq_m),
+ *   auxiliary term G~_i (eq_p_G_1), source F~_i(t) (eq_p_F) and
+ *   (dt^2/2) d_t F~_i with the backward difference of Sec. 3.2, dt = 1.
+ * u, rho, F are the hydrodynamic velocity, density and body force at t;
+ * S, S_old are the source at t and t-1; uold the velocity at t-1. */
+void orc_cde_collide(const double* g, double rho, double ux, double uy, double Fx,
+                     double Fy, double S, double S_old, double uxo, double uyo,
+                     double tau_p1, double tau_p2, double* out) {
+  build_tables();
+  double phi = 0;
+  for (int i = 0; i < Q; ++i) phi += g[i];
+  double geq[Q];
+  orc_geq(phi, ux, uy, geq);
+  double B0 = 0, B1[2] = {0, 0}, B2[2][2] = {{0, 0}, {0, 0}};
+  for (int i = 0; i < Q; ++i) {
+    const double gneq = g[i] - geq[i];
+    B0 += gneq;
+    for (int a = 0; a < 2; ++a) {
+      B1[a] += H1[i][a] * gneq;
+      for (int b = 0; b < 2; ++b) B2[a][b] += H2[i][a][b] * gneq;
+    }
+  }
+  double Ft[Q], Ft_old[Q];
+  cde_source(S, ux, uy, tau_p1, Ft);
+  cde_source(S_old, uxo, uyo, tau_p1, Ft_old);
+  const double F[2] = {Fx, Fy};
+  const double cs4 = CS2 * CS2;
+  for (int i = 0; i < Q; ++i) {
+    double r1 = B0, r2 = 0, eF = 0;
+    for (int a = 0; a < 2; ++a) {
+      r1 += H1[i][a] * B1[a] / CS2;
+      eF += H1[i][a] * F[a];
+      for (int b = 0; b < 2; ++b) r2 += H2[i][a][b] * B2[a][b] / (2.0 * cs4);
+    }
+    const double Gt = W[i] * (1.0 - 1.0 / (2.0 * tau_p1)) * (eF / CS2) * (phi / rho);
+    out[i] = geq[i] + W[i] * (1.0 - 1.0 / tau_p1) * r1 + W[i] * (1.0 - 1.0 / tau_p2) * r2 +
+             Gt + Ft[i] + 0.5 * (Ft[i] - Ft_old[i]);
+  }
+}
+
+/* Oldroyd-B constitutive source (Sec. 3.2, expression for Phi_ab):
+ *   S_ab = -(A_ab - d_ab)/lambda + A_ag d_g u_b + A_gb d_g u_a + A_ab d_g u_g
+ * grad[g][b] = d_g u_b.  A and S are {xx, xy, yy}. */
+void orc_source(const double* A, const double* grad, double lambda, double* S) {
+  const double A2[2][2] = {{A[0], A[1]}, {A[1], A[2]}};
+  const double (*G)[2] = (const double (*)[2])grad;
+  const int ab[3][2] = {{0, 0}, {0, 1}, {1, 1}};
+  const double div = G[0][0] + G[1][1];
+  for (int c = 0; c < NC; ++c) {
+    const int a = ab[c][0], b = ab[c][1];
+    double s = -(A2[a][b] - (a == b)) / lambda;
+    for (int g = 0; g < 2; ++g) s += A2[a][g] * G[g][b] + A2[g][b] * G[g][a];
+    s += A2[a][b] * div;
+    S[c] = s;
+  }
+}
+
+/* Hydrodynamic wet-node bounce-back of the non-equilibrium part with the
+ * two tangential/normal moment conditions (Zou-He), wall velocity 0, on a
+ * flat wall.  The paper names the hydrodynamic NEBB scheme (Secs. 4.2, 4.3)
+ * without formulas; this oracle's reading: the completed populations satisfy
+ *   sum_i f_i = rho and sum_i e_i f_i = -F/2   (so u = 0 through eq_ev_f0),
+ *   f_n - f_nbar = 0 for the wall-normal pair,
+ * with rho solved from the known populations.  side = 0: bottom wall (unknown
+ * 2, 5, 6), side = 1: top wall (unknown 4, 7, 8). */
+void orc_zou_he(double* f, double Fx, double Fy, int side) {
+  if (side == 0) {
+    /* sum e_y f = f2+f5+f6 - (f4+f7+f8) = -Fy/2  and  sum f = rho          */
+    f[2] = f[4];
+    f[5] = f[7] - 0.5 * (f[1] - f[3]) - 0.25 * Fx - 0.25 * Fy;
+    f[6] = f[8] + 0.5 * (f[1] - f[3]) + 0.25 * Fx - 0.25 * Fy;
+  } else {
+    f[4] = f[2];
+    f[7] = f[5] + 0.5 * (f[1] - f[3]) + 0.25 * Fx + 0.25 * Fy;
+    f[8] = f[6] - 0.5 * (f[1] - f[3]) - 0.25 * Fx + 0.25 * Fy;
+  }
+}
+
+/* CNEBB completion of one CDE lattice at a boundary node (Sec. 3.3).
+ *   known[i]   : 1 if g_i(x_b,t+1) arrived by streaming, 0 if unknown
+ *   g          : post-streaming populations at (x_b,t+1), unknown slots ignored
+ *   gpost      : post-collision populations at (x_b,t)
+ *   ux, uy     : hydrodynamic velocity at (x_b,t+1) after the hydro completion
+ * H is the set of directions pointing toward the solid, i.e. the opposites of
+ * the unknown directions.  Returns the wall "in" and "out" amounts:
+ *   out = sum_{eta in H} g^dagger_eta(x_b,t)   (sent toward the wall),
+ *   in  = what the completion adds back = phi_b - sum_{gamma in Gamma} g_gamma. */
+void orc_cnebb(double* g, const double* gpost, const int* known, double ux, double uy,
+               double* in_amount, double* out_amount) {
+  double phi = 0, out = 0;
+  for (int i = 0; i < Q; ++i)
+    if (known[i]) phi += g[i];
+  double known_sum = phi;
+  for (int i = 0; i < Q; ++i)
+    if (!known[i]) {
+      const int eta = OPP[i]; /* points toward the solid */
+      phi += gpost[eta];
+      out += gpost[eta];
+    }
+  double geq[Q];
+  orc_geq(phi, ux, uy, geq);
+  for (int i = 0; i < Q; ++i)
+    if (!known[i]) g[i] = geq[i] + (g[OPP[i]] - geq[OPP[i]]);
+  double rest = 0;
+  for (int i = 1; i < Q; ++i) rest += g[i];
+  g[0] = phi - rest;
+  *in_amount = phi - known_sum;
+  *out_amount = out;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Whole-domain simulation                                                  */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  orc_params p;
+  orc_coeffs c;
+  int nx, ny, n;
+  double* f;     /* [Q][n]      completed post-streaming, time t          */
+  double* g;     /* [NC][Q][n]                                             */
+  double* fpost; /* [Q][n]      post-collision (scratch)                   */
+  double* gpost; /* [NC][Q][n]                                             */
+  double* Sold;  /* [NC][n]     S(t-1)                                     */
+  double* uold;  /* [2][n]      u(t-1)                                     */
+  double* F;     /* [2][n]      body force                                 */
+  double* mom;   /* [6][n]      rho, ux, uy, phi_xx, phi_xy, phi_yy at t   */
+  double* grad;  /* [6][n]      dxux, dxuy, dyux, dyuy, dx(rho ux^3), dy(rho uy^3) */
+  double* S;     /* [NC][n]                                                */
+  int64_t t;
+  double wall_in[NC], wall_out[NC];
+} orc_sim;
+
+static inline int wrap(int a, int n) { return ((a % n) + n) % n; }
+
+static void compute_moments(orc_sim* s) {
+  const int n = s->n;
+  for (int k = 0; k < n; ++k) {
+    double fk[Q];
+    for (int i = 0; i < Q; ++i) fk[i] = s->f[i * n + k];
+    double rho, ux, uy;
+    orc_hydro_moments(fk, s->F[k], s->F[n + k], &rho, &ux, &uy);
+    s->mom[0 * n + k] = rho;
+    s->mom[1 * n + k] = ux;
+    s->mom[2 * n + k] = uy;
+    for (int c = 0; c < NC; ++c) {
+      double phi = 0;
+      for (int i = 0; i < Q; ++i) phi += s->g[(c * Q + i) * n + k];
+      s->mom[(3 + c) * n + k] = phi;
+    }
+  }
+}
+
+/* Second-order finite difference of field q along x (dir 0) or y (dir 1)
+ * at node (x,y): central in the interior and across periodic boundaries,
+ * one-sided (-3 q0 + 4 q1 - q2)/2 on a wall row (reading of the paper, which
+ * does not state how these gradients are discretised). */
+static double fd(const orc_sim* s, const double* q, int x, int y, int dir) {
+  const int nx = s->nx, ny = s->ny;
+  if (dir == 0) return 0.5 * (q[y * nx + wrap(x + 1, nx)] - q[y * nx + wrap(x - 1, nx)]);
+  if (s->p.periodic_y) return 0.5 * (q[wrap(y + 1, ny) * nx + x] - q[wrap(y - 1, ny) * nx + x]);
+  if (y == 0) return 0.5 * (-3.0 * q[x] + 4.0 * q[nx + x] - q[2 * nx + x]);
+  if (y == ny - 1)
+    return 0.5 * (3.0 * q[y * nx + x] - 4.0 * q[(y - 1) * nx + x] + q[(y - 2) * nx + x]);
+  return 0.5 * (q[(y + 1) * nx + x] - q[(y - 1) * nx + x]);
+}
+
+static void compute_gradients_and_source(orc_sim* s) {
+  const int n = s->n, nx = s->nx, ny = s->ny;
+  double* cube_x = (double*)malloc(sizeof(double) * n);
+  double* cube_y = (double*)malloc(sizeof(double) * n);
+  for (int k = 0; k < n; ++k) {
+    const double rho = s->mom[k], ux = s->mom[n + k], uy = s->mom[2 * n + k];
+    cube_x[k] = rho * ux * ux * ux; /* Phi_xxx (eq5) */
+    cube_y[k] = rho * uy * uy * uy; /* Phi_yyy */
+  }
+  const double* ux = s->mom + n;
+  const double* uy = s->mom + 2 * n;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const int k = y * nx + x;
+      s->grad[0 * n + k] = fd(s, ux, x, y, 0);
+      s->grad[1 * n + k] = fd(s, uy, x, y, 0);
+      s->grad[2 * n + k] = fd(s, ux, x, y, 1);
+      s->grad[3 * n + k] = fd(s, uy, x, y, 1);
+      s->grad[4 * n + k] = fd(s, cube_x, x, y, 0);
+      s->grad[5 * n + k] = fd(s, cube_y, x, y, 1);
+      /* grad[g][b] = d_g u_b */
+      const double G[2][2] = {{s->grad[k], s->grad[n + k]}, {s->grad[2 * n + k], s->grad[3 * n + k]}};
+      const double A[3] = {s->mom[3 * n + k], s->mom[4 * n + k], s->mom[5 * n + k]};
+      double S[3];
+      orc_source(A, &G[0][0], s->c.lambda, S);
+      for (int c = 0; c < NC; ++c) s->S[c * n + k] = S[c];
+    }
+  free(cube_x);
+  free(cube_y);
+}
+
+static void fill_history(orc_sim* s) {
+  const int n = s->n;
+  for (int k = 0; k < n; ++k) {
+    for (int c = 0; c < NC; ++c) s->Sold[c * n + k] = s->S[c * n + k];
+    s->uold[k] = s->mom[n + k];
+    s->uold[n + k] = s->mom[2 * n + k];
+  }
+}
+
+static void free_sim(orc_sim* s) {
+  if (!s) return;
+  free(s->f); free(s->g); free(s->fpost); free(s->gpost); free(s->Sold);
+  free(s->uold); free(s->F); free(s->mom); free(s->grad); free(s->S);
+  free(s);
+}
+
+/* Create a simulation.  force: [2][ny][nx] or NULL (uniform p->Fx, p->Fy).
+ * init: [6][ny][nx] = rho, ux, uy, Axx, Axy, Ayy, or NULL for rho = 1, u = 0,
+ * A = I (Sec. 4.2 initial state).  Populations start at equilibrium (eq2,
+ * eq_geq) of the initial fields; history S(-1) := S(0), u(-1) := u(0), i.e.
+ * the backward difference of F~ is zero on the first step. */
+orc_sim* orc_create(const orc_params* p, const double* force, const double* init) {
+  build_tables();
+  if (p->nx < 1 || p->ny < 1 || (!p->periodic_y && p->ny < 3)) return NULL;
+  orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
+  s->p = *p;
+  orc_derive(p, &s->c);
+  s->nx = p->nx;
+  s->ny = p->ny;
+  s->n = p->nx * p->ny;
+  const int n = s->n;
+  s->f = (double*)calloc((size_t)Q * n, sizeof(double));
+  s->g = (double*)calloc((size_t)NC * Q * n, sizeof(double));
+  s->fpost = (double*)calloc((size_t)Q * n, sizeof(double));
+  s->gpost = (double*)calloc((size_t)NC * Q * n, sizeof(double));
+  s->Sold = (double*)calloc((size_t)NC * n, sizeof(double));
+  s->uold = (double*)calloc((size_t)2 * n, sizeof(double));
+  s->F = (double*)calloc((size_t)2 * n, sizeof(double));
+  s->mom = (double*)calloc((size_t)6 * n, sizeof(double));
+  s->grad = (double*)calloc((size_t)6 * n, sizeof(double));
+  s->S = (double*)calloc((size_t)NC * n, sizeof(double));
+  if (!s->f || !s->g || !s->fpost || !s->gpost || !s->Sold || !s->uold || !s->F || !s->mom ||
+      !s->grad || !s->S) {
+    free_sim(s);
+    return NULL;
+  }
+  for (int k = 0; k < n; ++k) {
+    s->F[k] = force ? force[k] : p->Fx;
+    s->F[n + k] = force ? force[n + k] : p->Fy;
+    const double rho = init ? init[k] : 1.0;
+    const double ux = init ? init[n + k] : 0.0;
+    const double uy = init ? init[2 * n + k] : 0.0;
+    const double A[3] = {init ? init[3 * n + k] : 1.0, init ? init[4 * n + k] : 0.0,
+                         init ? init[5 * n + k] : 1.0};
+    double eq[Q];
+    orc_feq(rho, ux, uy, eq);
+    for (int i = 0; i < Q; ++i) s->f[i * n + k] = eq[i];
+    for (int c = 0; c < NC; ++c) {
+      orc_geq(A[c], ux, uy, eq);
+      for (int i = 0; i < Q; ++i) s->g[(c * Q + i) * n + k] = eq[i];
+    }
+  }
+  compute_moments(s);
+  compute_gradients_and_source(s);
+  fill_history(s);
+  return s;
+}
+
+void orc_destroy(orc_sim* s) { free_sim(s); }
+
+void orc_get_coeffs(const orc_sim* s, orc_coeffs* c) { *c = s->c; }
+
+/* Advance n_steps time steps (steps 1-9 of the header). */
+void orc_step(orc_sim* s, int64_t n_steps) {
+  const int n = s->n, nx = s->nx, ny = s->ny;
+  for (int64_t it = 0; it < n_steps; ++it) {
+    /* 1-3: moments, gradients, stress and source at time t */
+    compute_moments(s);
+    compute_gradients_and_source(s);
+    /* 4-5: collisions */
+    for (int k = 0; k < n; ++k) {
+      const double rho = s->mom[k], ux = s->mom[n + k], uy = s->mom[2 * n + k];
+      const double Fx = s->F[k], Fy = s->F[n + k];
+      const double A[3] = {s->mom[3 * n + k], s->mom[4 * n + k], s->mom[5 * n + k]};
+      const double tau[3] = {s->c.mup / s->c.lambda * (A[0] - 1.0),
+                             s->c.mup / s->c.lambda * A[1],
+                             s->c.mup / s->c.lambda * (A[2] - 1.0)}; /* eq_kramer, eqb4 */
+      const double dPhi[2] = {s->grad[4 * n + k], s->grad[5 * n + k]};
+      double fk[Q], out[Q];
+      for (int i = 0; i < Q; ++i) fk[i] = s->f[i * n + k];
+      orc_hydro_collide(fk, Fx, Fy, tau, dPhi, s->c.tau_s1, s->c.tau_s2, out);
+      for (int i = 0; i < Q; ++i) s->fpost[i * n + k] = out[i];
+      for (int c = 0; c < NC; ++c) {
+        double gk[Q];
+        for (int i = 0; i < Q; ++i) gk[i] = s->g[(c * Q + i) * n + k];
+        orc_cde_collide(gk, rho, ux, uy, Fx, Fy, s->S[c * n + k], s->Sold[c * n + k],
+                        s->uold[k], s->uold[n + k], s->c.tau_p1, s->c.tau_p2, out);
+        for (int i = 0; i < Q; ++i) s->gpost[(c * Q + i) * n + k] = out[i];
+      }
+    }
+    /* 9 (done now, the values are no longer needed): history <- S(t), u(t) */
+    fill_history(s);
+    /* 6: push streaming; unknown slots are overwritten by 7-8 */
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int k = y * nx + x;
+        for (int i = 0; i < Q; ++i) {
+          int yd = y + EY[i];
+          if (s->p.periodic_y) yd = wrap(yd, ny);
+          else if (yd < 0 || yd >= ny) continue; /* leaves toward the wall */
+          const int kd = yd * nx + wrap(x + EX[i], nx);
+          s->f[i * n + kd] = s->fpost[i * n + k];
+          for (int c = 0; c < NC; ++c) s->g[(c * Q + i) * n + kd] = s->gpost[(c * Q + i) * n + k];
+        }
+      }
+    for (int c = 0; c < NC; ++c) s->wall_in[c] = s->wall_out[c] = 0.0;
+    if (!s->p.periodic_y) {
+      /* 7-8 on the two wall rows */
+      for (int side = 0; side < 2; ++side) {
+        const int y = side == 0 ? 0 : ny - 1;
+        int known[Q];
+        for (int i = 0; i < Q; ++i) {
+          const int ys = y - EY[i]; /* source row of direction i */
+          known[i] = (ys >= 0 && ys < ny);
+        }
+        for (int x = 0; x < nx; ++x) {
+          const int k = y * nx + x;
+          const double Fx = s->F[k], Fy = s->F[n + k];
+          double fk[Q];
+          for (int i = 0; i < Q; ++i) fk[i] = s->f[i * n + k];
+          orc_zou_he(fk, Fx, Fy, side);
+          for (int i = 0; i < Q; ++i) s->f[i * n + k] = fk[i];
+          double rho, ux, uy;
+          orc_hydro_moments(fk, Fx, Fy, &rho, &ux, &uy);
+          for (int c = 0; c < NC; ++c) {
+            double gk[Q], gp[Q], win, wout;
+            for (int i = 0; i < Q; ++i) {
+              gk[i] = s->g[(c * Q + i) * n + k];
+              gp[i] = s->gpost[(c * Q + i) * n + k];
+            }
+            orc_cnebb(gk, gp, known, ux, uy, &win, &wout);
+            for (int i = 0; i < Q; ++i) s->g[(c * Q + i) * n + k] = gk[i];
+            s->wall_in[c] += win;
+            s->wall_out[c] += wout;
+          }
+        }
+      }
+    }
+    s->t += 1;
+  }
+}
+
+/* Macroscopic fields at the current time t: [6][ny][nx] =
+ * rho, ux, uy (eq_ev_f0), Axx, Axy, Ayy (phi of each CDE lattice). */
+void orc_fields(orc_sim* s, double* out) {
+  compute_moments(s);
+  memcpy(out, s->mom, sizeof(double) * 6 * (size_t)s->n);
+}
+
+/* Domain totals at time t and the CNEBB wall balance of the last step:
+ * out[0..2]  = sum rho, sum rho ux, sum rho uy
+ * out[3..5]  = sum phi_xx, sum phi_xy, sum phi_yy
+ * out[6..8]  = wall "in" per lattice, out[9..11] = wall "out" per lattice. */
+void orc_totals(orc_sim* s, double* out) {
+  compute_moments(s);
+  const int n = s->n;
+  for (int j = 0; j < 12; ++j) out[j] = 0;
+  for (int k = 0; k < n; ++k) {
+    const double rho = s->mom[k];
+    out[0] += rho;
+    out[1] += rho * s->mom[n + k];
+    out[2] += rho * s->mom[2 * n + k];
+    for (int c = 0; c < NC; ++c) out[3 + c] += s->mom[(3 + c) * n + k];
+  }
+  for (int c = 0; c < NC; ++c) {
+    out[6 + c] = s->wall_in[c];
+    out[9 + c] = s->wall_out[c];
+  }
+}
+
+/* Source S(t) of the last moment/gradient evaluation, and the history. */
+void orc_get_source(const orc_sim* s, double* S_out) {
+  memcpy(S_out, s->S, sizeof(double) * NC * (size_t)s->n);
+}
+
+/* Raw state access for tests: f [Q][n], g [NC][Q][n]. */
+void orc_get_state(const orc_sim* s, double* f, double* g) {
+  memcpy(f, s->f, sizeof(double) * Q * (size_t)s->n);
+  memcpy(g, s->g, sizeof(double) * NC * Q * (size_t)s->n);
+}
+void orc_set_state(orc_sim* s, const double* f, const double* g) {
+  memcpy(s->f, f, sizeof(double) * Q * (size_t)s->n);
+  memcpy(s->g, g, sizeof(double) * NC * Q * (size_t)s->n);
+}
+int64_t orc_time(const orc_sim* s) { return s->t; }

@@ -1,0 +1,16 @@
+"""Small helpers shared by the tests: turn a workload instance into oracle
+parameters and run the oracle.  (Test infrastructure; no method arithmetic.)"""
+from __future__ import annotations
+
+from oracle import oracle as o
+
+
+def oracle_params(inst, **override):
+    d = dict(beta=inst.beta, Wi=inst.Wi, Re=inst.Re, Sc=inst.Sc, Ma=inst.Ma, Lc=inst.Lc,
+             Lambda_s=inst.Lambda_s, Lambda_p=inst.Lambda_p, Fx=inst.Fx, Fy=inst.Fy)
+    d.update(override)
+    return o.make_params(inst.nx, inst.ny, inst.periodic_y, **d)
+
+
+def oracle_sim(inst, init=None, **override):
+    return o.Sim(oracle_params(inst, **override), force=inst.force_field, init=init)
