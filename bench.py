@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled viscoelastic LBM step on GB300.
+
+Workload: the batched mix of force-driven Oldroyd-B Poiseuille channels and
+simplified four-roll mills (256 seeded instances of uneven sizes, Wi and
+beta), all advanced together by one launch per time step, FP32-deviation
+storage with float64 reductions.  One bench "step" is one coupled time step
+of every instance.  The metric is MLUPS (one lattice update = all four
+lattices at one node), whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-LBM MLUPS & % HBM roofline; FP32/batched vs plain FP64 at stated error"
+UNIT = "MLUPS"
+BASE_SEED = 20250823
+N_INSTANCES = 256
+SCALARS_PER_LU = 82  # 36 populations + 5 history values, read and written
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--instances", type=int, default=N_INSTANCES)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(rank: int, n: int):
+    from paper_2508_16997_gb300 import workloads as wl
+    return wl.batch_mix(n=n, base_seed=BASE_SEED + 100003 * rank)
+
+
+def bytes_per_lu(inst, elem: int) -> int:
+    """Algorithmic HBM bytes of one lattice update: 82 scalars (36 populations
+    and 5 history values, each read once and written once) plus the 2 force
+    components when the instance has a per-node force field."""
+    return elem * (SCALARS_PER_LU + (2 if inst.force_field is not None else 0))
+
+
+def workload_desc(insts, total_nodes):
+    n_ch = sum(1 for i in insts if i.kind == "channel")
+    return {
+        "workload": (f"batched mix: {n_ch} Oldroyd-B Poiseuille channels (nx=4, H~U{{32..512}}) + "
+                     f"{len(insts) - n_ch} four-roll mills (N~U{{64..512}}), Wi=10^U(0,4), "
+                     f"beta~U(0.1,0.9), seeds {BASE_SEED}+i"),
+        "instances": len(insts),
+        "nodes_per_gpu": total_nodes,
+        "storage": "fp32 deviations, fp64 totals",
+        "l2": "inputs larger than L2 (working set >> 129 MB), no flush needed",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_sample(insts, budget_nodes: int):
+    """Smallest instances of the mix, in order, up to budget_nodes nodes."""
+    chosen, total = [], 0
+    for inst in sorted(insts, key=lambda i: i.n_nodes):
+        if chosen and total + inst.n_nodes > budget_nodes:
+            break
+        chosen.append(inst)
+        total += inst.n_nodes
+    return chosen, total
+
+
+def time_oracle(sample, steps: int):
+    """Oracle wall time for `steps` steps of every sample instance."""
+    from oracle import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle_helpers import oracle_sim
+    oracle.build()
+    sims = [oracle_sim(inst) for inst in sample]
+    t0 = time.perf_counter()
+    for s in sims:
+        s.step(steps)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    insts = workload(0, args.instances)
+    total_steps = args.warmup + args.steps
+    # size each step so that the whole run is about a minute of oracle work
+    budget = max(1, int(60.0 * 1.0e6 / total_steps))
+    sample, nodes = cpu_sample(insts, budget)
+    from oracle import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle_helpers import oracle_sim
+    oracle.build()
+    sims = [oracle_sim(inst) for inst in sample]
+    for s in sims:
+        s.step(args.warmup)
+    t0 = time.perf_counter()
+    for s in sims:
+        s.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = nodes * args.steps / dt / 1e6
+    desc = f"oracle FP64, {len(sample)} smallest instances of the mix ({nodes} nodes) per step"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": workload_desc(insts, sum(i.n_nodes for i in insts)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2508_16997_gb300 import build as b, lbve
+    if rank == 0 or world == 1:
+        b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    b.build()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    insts = workload(rank, args.instances)
+    total_nodes = sum(i.n_nodes for i in insts)
+    stream = torch.cuda.current_stream()
+    K, W = args.steps, args.warmup
+
+    # ---- headline: FP32-deviation batch, inputs resident in HBM -------------
+    sim = lbve.Simulation(insts, precision=lbve.LBVE_FP32_DEV)
+    sim.step(W)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    flags = sim.status()
+    value = world * total_nodes * K / (ms / 1e3) / 1e6
+    bytes_launch = sum(i.n_nodes * bytes_per_lu(i, 4) for i in insts)
+    achieved = bytes_launch / (ms / 1e3 / K) / 1e9
+    peak, peak_kind = measured_peaks()
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    pinned_force = [None if i.force_field is None else
+                    torch.from_numpy(np.ascontiguousarray(i.force_field)).pin_memory()
+                    for i in insts]
+    pinned_init = []
+    for i in insts:
+        f = np.zeros((6, i.ny, i.nx))
+        f[0] = 1.0
+        f[3] = 1.0
+        f[5] = 1.0
+        pinned_init.append(torch.from_numpy(f).pin_memory())
+    pinned_out = [torch.empty((6, i.ny, i.nx), dtype=torch.float64).pin_memory() for i in insts]
+    h2d = sum(t.numel() * 8 for t in pinned_init) + sum(
+        t.numel() * 8 for t in pinned_force if t is not None)
+    d2h = sum(t.numel() * 8 for t in pinned_out)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for j, inst in enumerate(insts):
+        lbve.lbve_set_geometry(sim.h, j, None,
+                               None if pinned_force[j] is None else pinned_force[j].numpy(),
+                               pinned_init[j].numpy(), n_nodes=inst.n_nodes)
+    sim.step(K)
+    for j in range(len(insts)):
+        lbve.lbve_fields(sim.h, j, pinned_out[j].data_ptr(), False)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * total_nodes * K / e2e_s / 1e6
+
+    # ---- plain FP64 on the same mix, and the FP32 error against it ---------
+    K64 = max(1, K // 10)
+    sim64 = lbve.Simulation(insts, precision=lbve.LBVE_FP64)
+    sim64.step(W)
+    torch.cuda.synchronize()
+    barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    sim64.step(K64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(f0.elapsed_time(f1))
+    value64 = world * total_nodes * K64 / (ms64 / 1e3) / 1e6
+    for j in range(len(insts)):  # FP32 run from the same initial state, same step count
+        lbve.lbve_set_geometry(sim.h, j, None, insts[j].force_field, None,
+                               n_nodes=insts[j].n_nodes)
+    sim.step(W + K64)
+    err_all, err_le100 = 0.0, 0.0
+    flags64 = sim64.status()
+    for j, inst in enumerate(insts):
+        if flags64[j]:
+            continue
+        a = sim.fields_device(j)
+        r = sim64.fields_device(j)
+        eu = float(torch.linalg.vector_norm(a[1:3] - r[1:3]) / torch.linalg.vector_norm(r[1:3]))
+        eC = float(torch.linalg.vector_norm(a[3:6] - r[3:6]) / torch.linalg.vector_norm(r[3:6]))
+        e = max(eu, eC)
+        err_all = max(err_all, e)
+        if inst.Wi <= 100:
+            err_le100 = max(err_le100, e)
+    err_all = max_over_ranks(err_all)
+    err_le100 = max_over_ranks(err_le100)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_desc(insts, total_nodes),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "kernel": "step_kernel<float> (one launch per step; per-step CUDA-event "
+                               "time incl. the end-of-call reduction)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+                "d2h_bytes_per_step": d2h / K,
+                "region": "lbve_set_geometry (pinned host force + initial fields) for every "
+                          "instance, lbve_step(K), lbve_fields to pinned host"},
+        "gpu_launches": K + 1,
+        "clocks": clocks,
+        "fp64_plain": {"value": value64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64,
+                       "speedup_fp32_over_fp64": value / value64},
+        "fp32_vs_fp64_rel_l2": {"max_all": err_all, "max_Wi_le_100": err_le100,
+                                "steps": W + K64, "target_Wi_le_100": 1e-5},
+        "nonfinite_instances": int((flags != 0).sum()),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        sample, nodes = cpu_sample(insts, 50000)
+        steps_cpu = 200
+        dt = time_oracle(sample, steps_cpu)
+        line["cpu_baseline"] = {
+            "value": nodes * steps_cpu / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, {len(sample)} smallest instances of the mix "
+                      f"({nodes} nodes) x {steps_cpu} steps, single thread"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * lbve.h -- C ABI of the GB300 coupled viscoelastic lattice Boltzmann step.
+ *
+ * The library advances the coupled time step of Yu, Chen, Wang, Yuan & Shu,
+ * "An improved lattice Boltzmann method with a novel conservative boundary
+ * scheme for viscoelastic fluid flows" (arXiv 2508.16997):
+ *   - a D2Q9 two-relaxation-time regularised (TRT-RLB) hydrodynamic lattice
+ *     with the third-order Hermite equilibrium, the Galilean correction G_i,
+ *     the local polymer-stress source T_i and the Hermite forcing F_i
+ *     (Sec. 3.1, eqs. eq_ev_f, eq2, eq_ev_f0, eq4a-d, eq5, eq6);
+ *   - three TRT-RLB convection-diffusion lattices for A_xx, A_xy, A_yy with
+ *     the Oldroyd-B source Phi_ab, the auxiliary term G~_i, the source F~_i
+ *     and its backward time difference (Sec. 3.2, eqs. eq_g0, eq_geq,
+ *     eq_p_neq_m, eq_p_G_1, eq_p_F);
+ *   - conservative non-equilibrium bounce-back (CNEBB) for the conformation
+ *     lattices and wet-node non-equilibrium bounce-back (Zou-He) for the
+ *     hydrodynamic lattice on flat walls (Sec. 3.3; Secs. 4.2-4.3).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: LBVE_OK (0) or a negative LBVE_ERR_* code.  No C++
+ *     exception crosses the ABI.  lbve_error_string() names a code;
+ *     lbve_last_error() gives a one-line detail for the calling thread.
+ *   - Grids are nx x ny nodes, periodic in x.  In y either periodic, or
+ *     wet-node walls on rows y = 0 and y = ny - 1 (solid beyond them).
+ *   - Host arrays are row-major [component][y][x], x fastest, float64,
+ *     regardless of the storage precision of the instance.
+ *   - The library never allocates device memory.  The caller allocates one
+ *     device workspace of lbve_workspace_bytes() bytes and keeps it alive
+ *     until lbve_destroy(); the library carves every buffer out of it.
+ *   - All device work is enqueued on the caller's CUDA stream (cudaStream_t
+ *     passed as void*).  Only lbve_status, lbve_fields (host output),
+ *     lbve_totals, lbve_residual and lbve_save synchronise that stream.
+ *   - Lattice units: dx = dt = 1, rho_0 = 1, c_s^2 = 1/3.
+ */
+#ifndef LBVE_H
+#define LBVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define LBVE_OK 0
+#define LBVE_ERR_ARG (-1)       /* invalid argument or parameter            */
+#define LBVE_ERR_CUDA (-2)      /* a CUDA runtime call or launch failed     */
+#define LBVE_ERR_NONFINITE (-3) /* a field became NaN or Inf                */
+#define LBVE_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up       */
+#define LBVE_ERR_GEOMETRY (-5)  /* geometry not supported / inconsistent    */
+#define LBVE_ERR_WORKSPACE (-6) /* workspace missing, too small, misaligned */
+#define LBVE_ERR_STATE (-7)     /* call out of order (e.g. step before init)*/
+
+/* ---- storage / arithmetic precision of an instance ---------------------- */
+#define LBVE_FP64 0     /* populations stored and computed in float64        */
+#define LBVE_FP32_DEV 1 /* float32 storage of deviations from the rest state
+                           (f_i - w_i, g_i - w_i delta_c), float32 arithmetic,
+                           float64 for conserved totals and wall balances     */
+
+/* Number of doubles returned by lbve_totals(). */
+#define LBVE_NTOTALS 12
+
+/* One problem statement (Sec. 2.4-2.5 of the paper), lattice units.
+ * Derived on the host in float64:
+ *   U_c = Ma c_s, nu_0 = U_c L_c / Re, nu_s = beta nu_0, mu_p = (1-beta) nu_0,
+ *   tau_s1 = 3 nu_s + 1/2, tau_s2 = Lambda_s/(tau_s1 - 1/2) + 1/2,
+ *   kappa = nu_s / Sc, tau_p1 = 3 kappa + 1/2,
+ *   tau_p2 = Lambda_p/(tau_p1 - 1/2) + 1/2, lambda = Wi L_c / U_c. */
+typedef struct {
+  int32_t nx, ny;     /* nodes (ny >= 3 when walled)                        */
+  int32_t periodic_y; /* 1: periodic in y; 0: walls on rows 0 and ny-1      */
+  int32_t precision;  /* LBVE_FP64 or LBVE_FP32_DEV                         */
+  double beta;        /* viscosity ratio mu_s/mu_0, 0 < beta <= 1 (eqb7)    */
+  double Wi;          /* Weissenberg number (eqb6), > 0                     */
+  double Re;          /* Reynolds number (eqb5), > 0                        */
+  double Sc;          /* Schmidt number (eqb8), > 0                         */
+  double Ma;          /* Mach number (eq_Mach), > 0                         */
+  double Lc;          /* characteristic length in lattice units, > 0       */
+  double Lambda_s;    /* hydrodynamic magic parameter (Sec. 3.1), > 0       */
+  double Lambda_p;    /* conformation magic parameter (Sec. 3.2), > 0       */
+  double Fx, Fy;      /* uniform body force, used when no force field given */
+} lbve_params;
+
+typedef struct lbve_handle lbve_handle;
+
+/* Bytes of device workspace needed for n_instances problems p[0..n-1].
+ * Pure host computation.  Errors: LBVE_ERR_ARG for invalid parameters. */
+int lbve_workspace_bytes(const lbve_params* p, int32_t n_instances, size_t* bytes);
+
+/* Create a handle for n_instances independent problems p[0..n-1] that are
+ * advanced together, one launch per precision per time step.
+ *   d_workspace: device pointer, >= lbve_workspace_bytes() bytes, 256-byte
+ *                aligned, owned by the caller, alive until lbve_destroy().
+ *   cuda_stream: cudaStream_t (or NULL for the legacy default stream).
+ * Copies the parameter tables to the device (on the stream).  The
+ * instances are not initialised until lbve_set_geometry().
+ * Errors: LBVE_ERR_ARG, LBVE_ERR_WORKSPACE, LBVE_ERR_CUDA. */
+int lbve_create(const lbve_params* p, int32_t n_instances, void* d_workspace, size_t bytes,
+                void* cuda_stream, lbve_handle** out);
+
+/* Set the geometry, body force and initial state of instance inst and reset
+ * its time to 0 (Sec. 4.2: unit density, zero velocity, identity
+ * conformation and equilibrium populations unless init_fields is given).
+ *   solid_mask : must be NULL (walls follow periodic_y; interior obstacles
+ *                are not supported by this version -> LBVE_ERR_GEOMETRY).
+ *   body_force : host float64 [2][ny][nx], or NULL for the uniform (Fx, Fy).
+ *   init_fields: host float64 [6][ny][nx] = rho, ux, uy, Axx, Axy, Ayy, or
+ *                NULL for rho = 1, u = 0, A = I.
+ * Populations start at the equilibria (eq2, eq_geq) of the initial fields;
+ * the history of the CDE source is set so that its time difference is zero
+ * on the first step.  Host arrays may be freed when the call returns.
+ * Errors: LBVE_ERR_ARG, LBVE_ERR_GEOMETRY, LBVE_ERR_CUDA. */
+int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
+                      const double* body_force, const double* init_fields);
+
+/* Advance every instance by n_steps >= 0 time steps (asynchronous on the
+ * stream).  The last step of the call also refreshes the macroscopic fields,
+ * the float64 totals, the residual and the non-finite flags.
+ * Errors: LBVE_ERR_STATE if an instance was never initialised,
+ * LBVE_ERR_CUDA if a launch failed. */
+int lbve_step(lbve_handle* h, int64_t n_steps);
+
+/* Synchronise the stream and copy per-instance status flags into
+ * flags[0..n-1] (bit 0: a non-finite field was seen at the end of an
+ * lbve_step call).  Returns LBVE_ERR_NONFINITE if any flag is set. */
+int lbve_status(lbve_handle* h, int32_t* flags);
+
+/* Macroscopic fields of instance inst at its current time:
+ * [6][ny][nx] float64 = rho, ux, uy (eq_ev_f0), Axx, Axy, Ayy (sum of g).
+ * on_device = 0: out is host memory (the call synchronises the stream);
+ * on_device = 1: out is device memory (asynchronous device-to-device copy). */
+int lbve_fields(lbve_handle* h, int32_t inst, double* out, int32_t on_device);
+
+/* Float64 totals of instance inst at its current time (synchronises):
+ *   out[0..2]  sum rho, sum rho ux, sum rho uy  (rho u as in eq_ev_f0)
+ *   out[3..5]  sum A_xx, sum A_xy, sum A_yy
+ *   out[6..8]  CNEBB wall "in" of the last step, per conformation lattice:
+ *              what the completion added back at wall nodes
+ *   out[9..11] CNEBB wall "out" of the last step: post-collision populations
+ *              that left wall nodes toward the wall (Sec. 3.3); in == out. */
+int lbve_totals(lbve_handle* h, int32_t inst, double out[LBVE_NTOTALS]);
+
+/* Residual of instance inst (synchronises): max over nodes of
+ * |u(t) - u(t')| / U_c, where t is the current time and t' the time at the
+ * end of the previous lbve_step call (eq_err / 2eq4 when the calls advance
+ * T_c steps each). */
+int lbve_residual(lbve_handle* h, int32_t inst, double* out);
+
+/* Current time step of instance inst. */
+int lbve_time(lbve_handle* h, int32_t inst, int64_t* t);
+
+/* Release the handle (host memory only; the workspace stays the caller's).
+ * Synchronises the stream. */
+void lbve_destroy(lbve_handle* h);
+
+/* Static name of a return code, and a detail line for the calling thread. */
+const char* lbve_error_string(int code);
+const char* lbve_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBVE_H */

@@ -1,0 +1,464 @@
+// lbve_host.cu -- host side of the C ABI declared in include/lbve.h.
+//
+// Plans the workspace layout, derives the lattice coefficients in float64
+// (Sec. 2.4-2.5 and the relaxation-time relations of Secs. 3.1-3.2), builds
+// the tile tables and drives the kernels on the caller's stream.  It never
+// allocates device memory: every buffer lives in the caller's workspace.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbve.h"
+#include "lbve_internal.h"
+
+using namespace lbve;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(LBVE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+constexpr int64_t kMaxNodes = int64_t(1) << 25;  // keeps 36 * stride in int32
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Coeffs {
+  double Uc, nu0, nus, mup, tau_s1, tau_s2, kappa, tau_p1, tau_p2, lambda;
+};
+
+// Sec. 2.4-2.5 and Secs. 3.1-3.2 (rho_0 = 1, dt = dx = 1, c_s^2 = 1/3).
+Coeffs derive(const lbve_params& p) {
+  Coeffs c;
+  c.Uc = p.Ma * std::sqrt(1.0 / 3.0);              // eq_Mach
+  c.nu0 = c.Uc * p.Lc / p.Re;                      // eqb5
+  c.nus = p.beta * c.nu0;                          // eqb7
+  c.mup = (1.0 - p.beta) * c.nu0;                  // mu_0 = mu_s + mu_p
+  c.tau_s1 = 3.0 * c.nus + 0.5;                    // mu_s = rho cs2 (tau_s1 - 1/2)
+  c.tau_s2 = p.Lambda_s / (c.tau_s1 - 0.5) + 0.5;  // Lambda_s relation
+  c.kappa = c.nus / p.Sc;                          // eqb8
+  c.tau_p1 = 3.0 * c.kappa + 0.5;                  // kappa = (tau_p1 - 1/2) cs2
+  c.tau_p2 = p.Lambda_p / (c.tau_p1 - 0.5) + 0.5;  // tau_p2 relation
+  c.lambda = p.Wi * p.Lc / c.Uc;                   // eqb6
+  return c;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int validate(const lbve_params& p, int i) {
+  if (p.nx < 1 || p.ny < 1) return fail(LBVE_ERR_ARG, "instance %d: nx, ny must be >= 1", i);
+  if (!p.periodic_y && p.ny < 3)
+    return fail(LBVE_ERR_ARG, "instance %d: a walled channel needs ny >= 3", i);
+  if (int64_t(p.nx) * p.ny > kMaxNodes)
+    return fail(LBVE_ERR_ARG, "instance %d: more than %lld nodes", i, (long long)kMaxNodes);
+  if (p.precision != LBVE_FP64 && p.precision != LBVE_FP32_DEV)
+    return fail(LBVE_ERR_ARG, "instance %d: unknown precision %d", i, p.precision);
+  if (p.periodic_y != 0 && p.periodic_y != 1)
+    return fail(LBVE_ERR_ARG, "instance %d: periodic_y must be 0 or 1", i);
+  if (!(std::isfinite(p.beta) && p.beta > 0.0 && p.beta <= 1.0))
+    return fail(LBVE_ERR_ARG, "instance %d: beta must be in (0, 1]", i);
+  if (!finite_pos(p.Wi) || !finite_pos(p.Re) || !finite_pos(p.Sc) || !finite_pos(p.Ma) ||
+      !finite_pos(p.Lc) || !finite_pos(p.Lambda_s) || !finite_pos(p.Lambda_p))
+    return fail(LBVE_ERR_ARG, "instance %d: Wi, Re, Sc, Ma, Lc, Lambda_s, Lambda_p must be > 0",
+                i);
+  if (!std::isfinite(p.Fx) || !std::isfinite(p.Fy))
+    return fail(LBVE_ERR_ARG, "instance %d: body force must be finite", i);
+  const Coeffs c = derive(p);
+  if (!(c.tau_s1 > 0.5) || !(c.tau_p1 > 0.5) || !std::isfinite(c.tau_s2) ||
+      !std::isfinite(c.tau_p2) || !finite_pos(c.lambda))
+    return fail(LBVE_ERR_ARG, "instance %d: derived relaxation times are degenerate", i);
+  return LBVE_OK;
+}
+
+struct InstPlan {
+  size_t off_pop[2], off_hist, off_force, off_fields;
+  int stride, TX, TY, hy, ntx, nty;
+  int list, tile_begin, ntiles;  // position in its precision's tile list
+  int slot_begin;
+};
+
+struct Plan {
+  std::vector<InstPlan> inst;
+  size_t off_insts, off_tiles[2], off_partials, off_totals, off_flags, total;
+  int ntiles[2], nslots;
+};
+
+void tile_shape(const lbve_params& p, int& TX, int& TY, int& hy) {
+  TX = p.nx >= 32 ? 32 : p.nx;
+  TY = kThreads / TX;
+  hy = p.periodic_y ? 1 : 2;
+}
+
+Plan make_plan(const lbve_params* p, int n) {
+  Plan pl;
+  pl.inst.resize(n);
+  size_t off = 0;
+  pl.ntiles[0] = pl.ntiles[1] = 0;
+  for (int i = 0; i < n; ++i) {
+    InstPlan& q = pl.inst[i];
+    const size_t es = p[i].precision == LBVE_FP64 ? 8 : 4;
+    const size_t nn = size_t(p[i].nx) * p[i].ny;
+    q.stride = (int)align_up(nn, 64);
+    const size_t plane = size_t(q.stride) * es;
+    for (int b = 0; b < 2; ++b) {
+      q.off_pop[b] = off;
+      off = align_up(off + 36 * plane, kAlign);
+    }
+    q.off_hist = off;
+    off = align_up(off + 5 * plane, kAlign);
+    q.off_force = off;
+    off = align_up(off + 2 * plane, kAlign);
+    q.off_fields = off;
+    off = align_up(off + 6 * size_t(q.stride) * 8, kAlign);
+    tile_shape(p[i], q.TX, q.TY, q.hy);
+    q.ntx = (p[i].nx + q.TX - 1) / q.TX;
+    q.nty = (p[i].ny + q.TY - 1) / q.TY;
+    q.list = p[i].precision == LBVE_FP64 ? 0 : 1;
+    q.tile_begin = pl.ntiles[q.list];
+    q.ntiles = q.ntx * q.nty;
+    pl.ntiles[q.list] += q.ntiles;
+  }
+  // partial-record slots: list 0 tiles first, then list 1
+  pl.nslots = pl.ntiles[0] + pl.ntiles[1];
+  for (int i = 0; i < n; ++i) {
+    InstPlan& q = pl.inst[i];
+    q.slot_begin = (q.list == 0 ? 0 : pl.ntiles[0]) + q.tile_begin;
+  }
+  pl.off_insts = off;
+  off = align_up(off + sizeof(InstDev) * n, kAlign);
+  for (int l = 0; l < 2; ++l) {
+    pl.off_tiles[l] = off;
+    off = align_up(off + sizeof(TileDev) * std::max(pl.ntiles[l], 1), kAlign);
+  }
+  pl.off_partials = off;
+  off = align_up(off + sizeof(double) * kPartial * std::max(pl.nslots, 1), kAlign);
+  pl.off_totals = off;
+  off = align_up(off + sizeof(double) * kTotals * n, kAlign);
+  pl.off_flags = off;
+  off = align_up(off + sizeof(int32_t) * n, kAlign);
+  pl.total = off;
+  return pl;
+}
+
+}  // namespace
+
+struct lbve_handle {
+  int n = 0;
+  std::vector<lbve_params> p;
+  std::vector<Coeffs> c;
+  Plan plan;
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<InstDev> insts;
+  InstDev* d_insts = nullptr;
+  TileDev* d_tiles[2] = {nullptr, nullptr};
+  double* d_partials = nullptr;
+  double* d_totals = nullptr;
+  int32_t* d_flags = nullptr;
+  int parity = 0;
+  std::vector<int64_t> t;
+  std::vector<char> ready;
+};
+
+extern "C" {
+
+const char* lbve_error_string(int code) {
+  switch (code) {
+    case LBVE_OK: return "ok";
+    case LBVE_ERR_ARG: return "invalid argument";
+    case LBVE_ERR_CUDA: return "CUDA error";
+    case LBVE_ERR_NONFINITE: return "non-finite field";
+    case LBVE_ERR_TIMEOUT: return "device wait timed out";
+    case LBVE_ERR_GEOMETRY: return "unsupported or inconsistent geometry";
+    case LBVE_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case LBVE_ERR_STATE: return "call out of order";
+    default: return "unknown error code";
+  }
+}
+
+const char* lbve_last_error(void) { return g_last_error.c_str(); }
+
+int lbve_workspace_bytes(const lbve_params* p, int32_t n, size_t* bytes) {
+  if (!p || !bytes || n < 1) return fail(LBVE_ERR_ARG, "null pointer or n_instances < 1");
+  for (int i = 0; i < n; ++i) {
+    const int rc = validate(p[i], i);
+    if (rc) return rc;
+  }
+  *bytes = make_plan(p, n).total;
+  return LBVE_OK;
+}
+
+int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes,
+                void* cuda_stream, lbve_handle** out) {
+  if (!out) return fail(LBVE_ERR_ARG, "out is null");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = lbve_workspace_bytes(p, n, &need);
+  if (rc) return rc;
+  if (!d_workspace || bytes < need)
+    return fail(LBVE_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", bytes, need);
+  if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)
+    return fail(LBVE_ERR_WORKSPACE, "workspace not %zu-byte aligned", kAlign);
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, d_workspace);
+  if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(LBVE_ERR_WORKSPACE, "workspace is not device memory");
+  }
+
+  lbve_handle* h = new lbve_handle();
+  h->n = n;
+  h->p.assign(p, p + n);
+  h->plan = make_plan(p, n);
+  h->ws = (char*)d_workspace;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->t.assign(n, 0);
+  h->ready.assign(n, 0);
+  const Plan& pl = h->plan;
+  h->d_insts = (InstDev*)(h->ws + pl.off_insts);
+  h->d_tiles[0] = (TileDev*)(h->ws + pl.off_tiles[0]);
+  h->d_tiles[1] = (TileDev*)(h->ws + pl.off_tiles[1]);
+  h->d_partials = (double*)(h->ws + pl.off_partials);
+  h->d_totals = (double*)(h->ws + pl.off_totals);
+  h->d_flags = (int32_t*)(h->ws + pl.off_flags);
+
+  h->insts.resize(n);
+  h->c.resize(n);
+  std::vector<TileDev> tiles[2];
+  tiles[0].resize(pl.ntiles[0]);
+  tiles[1].resize(pl.ntiles[1]);
+  for (int i = 0; i < n; ++i) {
+    const InstPlan& q = pl.inst[i];
+    const Coeffs c = derive(p[i]);
+    h->c[i] = c;
+    InstDev& D = h->insts[i];
+    std::memset(&D, 0, sizeof(D));
+    D.pop[0] = h->ws + q.off_pop[0];
+    D.pop[1] = h->ws + q.off_pop[1];
+    D.hist = h->ws + q.off_hist;
+    D.force = h->ws + q.off_force;
+    D.fields = (double*)(h->ws + q.off_fields);
+    D.nx = p[i].nx;
+    D.ny = p[i].ny;
+    D.stride = q.stride;
+    D.periodic_y = p[i].periodic_y;
+    D.TX = q.TX;
+    D.TY = q.TY;
+    D.hy = q.hy;
+    D.force_field = 0;
+    D.slot_begin = q.slot_begin;
+    D.slot_end = q.slot_begin + q.ntiles;
+    D.prec = p[i].precision;
+    D.Fx = p[i].Fx;
+    D.Fy = p[i].Fy;
+    D.inv_Uc = 1.0 / c.Uc;
+    D.c_s1 = 1.0 - 1.0 / c.tau_s1;
+    D.c_s2 = 1.0 - 1.0 / c.tau_s2;
+    D.h_s1 = (c.tau_s1 - 0.5) / c.tau_s1;
+    D.w_s1 = 1.0 / c.tau_s1;
+    D.ep_p1 = 2.0 - 1.0 / c.tau_p1;
+    D.c_p2 = 1.0 - 1.0 / c.tau_p2;
+    D.h_p1 = (c.tau_p1 - 0.5) / c.tau_p1;
+    D.inv_lambda = 1.0 / c.lambda;
+    D.mup_over_lambda = c.mup / c.lambda;
+    int k = q.tile_begin;
+    for (int ty = 0; ty < q.nty; ++ty)
+      for (int tx = 0; tx < q.ntx; ++tx) {
+        TileDev& T = tiles[q.list][k];
+        T.inst = i;
+        T.x0 = tx * q.TX;
+        T.y0 = ty * q.TY;
+        T.slot = q.slot_begin + (k - q.tile_begin);
+        ++k;
+      }
+  }
+  // Synchronous copies from pageable host memory: the host vectors may go
+  // out of scope as soon as the calls return.
+  e = cudaMemcpyAsync(h->d_insts, h->insts.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice,
+                      h->stream);
+  for (int l = 0; l < 2 && e == cudaSuccess; ++l)
+    if (!tiles[l].empty())
+      e = cudaMemcpyAsync(h->d_tiles[l], tiles[l].data(), sizeof(TileDev) * tiles[l].size(),
+                          cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int32_t) * n, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->d_totals, 0, sizeof(double) * kTotals * n, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "lbve_create upload");
+  }
+  *out = h;
+  return LBVE_OK;
+}
+
+int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
+                      const double* body_force, const double* init_fields) {
+  if (!h || inst < 0 || inst >= h->n) return fail(LBVE_ERR_ARG, "bad handle or instance");
+  if (solid_mask)
+    return fail(LBVE_ERR_GEOMETRY,
+                "solid masks are not supported; walls follow periodic_y (pass NULL)");
+  const lbve_params& p = h->p[inst];
+  const InstPlan& q = h->plan.inst[inst];
+  const size_t nn = size_t(p.nx) * p.ny;
+  const size_t S = q.stride;
+  const int P = h->parity;
+  InstDev& D = h->insts[inst];
+  cudaError_t e = cudaSuccess;
+
+  if (body_force) {
+    for (size_t k = 0; k < 2 * nn; ++k)
+      if (!std::isfinite(body_force[k])) return fail(LBVE_ERR_ARG, "body force not finite");
+    double* stage = (double*)D.pop[P];  // staging: float64 [2][S]
+    e = cudaMemcpy2DAsync(stage, S * 8, body_force, nn * 8, nn * 8, 2, cudaMemcpyHostToDevice,
+                          h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "force upload");
+    if (launch_convert_force(p.precision, stage, D.force, (int)nn, (int)S, h->stream))
+      return cuda_fail(cudaGetLastError(), "force conversion launch");
+    D.force_field = 1;
+  } else {
+    D.force_field = 0;
+  }
+
+  // staged initial fields, float64 [6][S], in the buffer the init kernel reads
+  double* stage = (double*)D.pop[P ^ 1];
+  if (init_fields) {
+    for (size_t k = 0; k < 6 * nn; ++k)
+      if (!std::isfinite(init_fields[k])) return fail(LBVE_ERR_ARG, "initial fields not finite");
+    for (size_t k = 0; k < nn; ++k)
+      if (!(init_fields[k] > 0.0)) return fail(LBVE_ERR_ARG, "initial density must be > 0");
+    e = cudaMemcpy2DAsync(stage, S * 8, init_fields, nn * 8, nn * 8, 6, cudaMemcpyHostToDevice,
+                          h->stream);
+  } else {
+    std::vector<double> def(6 * nn, 0.0);
+    for (size_t k = 0; k < nn; ++k) def[k] = def[3 * nn + k] = def[5 * nn + k] = 1.0;
+    e = cudaMemcpy2DAsync(stage, S * 8, def.data(), nn * 8, nn * 8, 6, cudaMemcpyHostToDevice,
+                          h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "initial field upload");
+  e = cudaMemcpyAsync(h->d_insts + inst, &D, sizeof(InstDev), cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "descriptor upload");
+  e = cudaMemsetAsync(h->d_flags + inst, 0, sizeof(int32_t), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "flag reset");
+  // collide the equilibrium state of t = 0: reads pop[P^1] (staging), writes pop[P]
+  if (launch_step(p.precision, h->d_insts, h->d_tiles[q.list] + q.tile_begin, q.ntiles, P ^ 1,
+                  kModeInit, kFinal, h->d_partials, h->stream))
+    return cuda_fail(cudaGetLastError(), "init kernel launch");
+  if (launch_reduce(h->d_insts, inst, 1, h->d_partials, h->d_totals, h->d_flags, h->stream))
+    return cuda_fail(cudaGetLastError(), "reduce launch");
+  // the pageable copy of D above is staged before return; make the device
+  // state consistent before the caller reuses its arrays
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbve_set_geometry");
+  h->t[inst] = 0;
+  h->ready[inst] = 1;
+  return LBVE_OK;
+}
+
+int lbve_step(lbve_handle* h, int64_t n_steps) {
+  if (!h || n_steps < 0) return fail(LBVE_ERR_ARG, "bad handle or negative step count");
+  for (int i = 0; i < h->n; ++i)
+    if (!h->ready[i]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", i);
+  for (int64_t s = 0; s < n_steps; ++s) {
+    const int flags = (s == n_steps - 1) ? kFinal : 0;
+    for (int l = 0; l < 2; ++l) {
+      if (h->plan.ntiles[l] == 0) continue;
+      if (launch_step(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_tiles[l],
+                      h->plan.ntiles[l], h->parity, kModeStep, flags, h->d_partials, h->stream))
+        return cuda_fail(cudaGetLastError(), "step kernel launch");
+    }
+    h->parity ^= 1;
+  }
+  if (n_steps > 0) {
+    if (launch_reduce(h->d_insts, 0, h->n, h->d_partials, h->d_totals, h->d_flags, h->stream))
+      return cuda_fail(cudaGetLastError(), "reduce launch");
+    for (int i = 0; i < h->n; ++i) h->t[i] += n_steps;
+  }
+  return LBVE_OK;
+}
+
+int lbve_status(lbve_handle* h, int32_t* flags) {
+  if (!h || !flags) return fail(LBVE_ERR_ARG, "null argument");
+  cudaError_t e = cudaMemcpyAsync(flags, h->d_flags, sizeof(int32_t) * h->n,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbve_status");
+  for (int i = 0; i < h->n; ++i)
+    if (flags[i] & 1) return fail(LBVE_ERR_NONFINITE, "instance %d has a non-finite field", i);
+  return LBVE_OK;
+}
+
+int lbve_fields(lbve_handle* h, int32_t inst, double* out, int32_t on_device) {
+  if (!h || !out || inst < 0 || inst >= h->n) return fail(LBVE_ERR_ARG, "bad argument");
+  if (!h->ready[inst]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", inst);
+  const lbve_params& p = h->p[inst];
+  const size_t nn = size_t(p.nx) * p.ny, S = h->plan.inst[inst].stride;
+  cudaError_t e = cudaMemcpy2DAsync(out, nn * 8, h->insts[inst].fields, S * 8, nn * 8, 6,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbve_fields");
+  return LBVE_OK;
+}
+
+static int read_totals(lbve_handle* h, int32_t inst, double* rec) {
+  if (!h || inst < 0 || inst >= h->n) return fail(LBVE_ERR_ARG, "bad argument");
+  if (!h->ready[inst]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", inst);
+  cudaError_t e = cudaMemcpyAsync(rec, h->d_totals + (size_t)inst * kTotals,
+                                  sizeof(double) * kTotals, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "totals readback");
+  return LBVE_OK;
+}
+
+int lbve_totals(lbve_handle* h, int32_t inst, double out[LBVE_NTOTALS]) {
+  if (!out) return fail(LBVE_ERR_ARG, "out is null");
+  double rec[kTotals];
+  const int rc = read_totals(h, inst, rec);
+  if (rc) return rc;
+  for (int j = 0; j < LBVE_NTOTALS; ++j) out[j] = rec[j];
+  return LBVE_OK;
+}
+
+int lbve_residual(lbve_handle* h, int32_t inst, double* out) {
+  if (!out) return fail(LBVE_ERR_ARG, "out is null");
+  double rec[kTotals];
+  const int rc = read_totals(h, inst, rec);
+  if (rc) return rc;
+  *out = rec[kResid];
+  return LBVE_OK;
+}
+
+int lbve_time(lbve_handle* h, int32_t inst, int64_t* t) {
+  if (!h || !t || inst < 0 || inst >= h->n) return fail(LBVE_ERR_ARG, "bad argument");
+  *t = h->t[inst];
+  return LBVE_OK;
+}
+
+void lbve_destroy(lbve_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+}  // extern "C"

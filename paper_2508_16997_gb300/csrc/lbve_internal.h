@@ -1,0 +1,63 @@
+// lbve_internal.h -- layout shared by the host code and the CUDA kernels of
+// liblbve (not part of the public ABI).
+#pragma once
+#include <cstdint>
+
+namespace lbve {
+
+constexpr int kThreads = 256;     // threads per CTA of the step kernel
+constexpr int kRegionMax = 800;   // (TX+2)(TY+2*hy) upper bound for TX*TY <= 256
+constexpr int kPartial = 16;      // doubles per tile partial record
+constexpr int kTotals = 16;       // doubles per instance totals record
+
+// Partial / totals record slots.
+enum : int {
+  kSumRho = 0, kSumJx = 1, kSumJy = 2, kSumPhi = 3,  // 3..5
+  kWallIn = 6,                                        // 6..8
+  kWallOut = 9,                                       // 9..11
+  kResid = 12, kNonFinite = 13
+};
+
+// Kernel flags.
+enum : int { kFinal = 1 };
+
+// Everything a CTA needs about its instance.  Pointers are device addresses
+// inside the caller's workspace.  Coefficients are derived in float64 on
+// the host (Sec. 3.1-3.2 relaxation-time relations) and rounded once.
+struct InstDev {
+  void* pop[2];        // [36][stride] post-collision populations, ping-pong
+  void* hist;          // [5][stride]  S_xx, S_xy, S_yy, ux, uy of the last step
+  void* force;         // [2][stride]  per-node body force (if force_field)
+  double* fields;      // [6][stride]  rho, ux, uy, Axx, Axy, Ayy (float64)
+  int32_t nx, ny, stride, periodic_y;
+  int32_t TX, TY, hy, force_field;
+  int32_t slot_begin, slot_end;  // partial-record slots of this instance
+  int32_t prec, pad;
+  double Fx, Fy, inv_Uc;
+  double c_s1;    // 1 - 1/tau_s1
+  double c_s2;    // 1 - 1/tau_s2
+  double h_s1;    // 1 - 1/(2 tau_s1)
+  double w_s1;    // 1/tau_s1
+  double ep_p1;   // 2 - 1/tau_p1, so that 1 - 1/tau_p1 = ep_p1 - 1
+  double c_p2;    // 1 - 1/tau_p2
+  double h_p1;    // 1 - 1/(2 tau_p1)
+  double inv_lambda;
+  double mup_over_lambda;
+};
+
+// One tile of one instance: {instance, x0, y0, partial slot}.
+struct TileDev {
+  int32_t inst, x0, y0, slot;
+};
+
+// Launchers implemented in lbve_kernels.cu (templated over float/double).
+enum : int { kModeStep = 0, kModeInit = 1 };
+
+int launch_step(int prec, const InstDev* d_insts, const TileDev* d_tiles, int n_tiles,
+                int parity, int mode, int flags, double* d_partials, void* stream);
+int launch_reduce(const InstDev* d_insts, int first_inst, int n_insts, const double* d_partials,
+                  double* d_totals, int32_t* d_flags, void* stream);
+int launch_convert_force(int prec, const double* d_src, void* d_dst, int n, int stride,
+                         void* stream);
+
+}  // namespace lbve

@@ -1,0 +1,93 @@
+// lbve_kernels.cu -- launchers of the step kernel, the deterministic float64
+// reduction of per-tile partial records, and the force conversion kernel.
+#include <cuda_runtime.h>
+
+#include "lbve_internal.h"
+#include "lbve_step.cuh"
+
+namespace lbve {
+
+template <typename R>
+static int launch_step_t(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
+                         int mode, int flags, double* d_partials, cudaStream_t st) {
+  if (n_tiles <= 0) return 0;
+  if (mode == kModeStep)
+    step_kernel<R, kModeStep><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, parity, flags,
+                                                             d_partials);
+  else
+    step_kernel<R, kModeInit><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, parity, flags,
+                                                             d_partials);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_step(int prec, const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
+                int mode, int flags, double* d_partials, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == 0)
+    return launch_step_t<double>(d_insts, d_tiles, n_tiles, parity, mode, flags, d_partials, st);
+  return launch_step_t<float>(d_insts, d_tiles, n_tiles, parity, mode, flags, d_partials, st);
+}
+
+// One CTA per instance: sum (max for the residual) the partial records of the
+// instance's tiles in a fixed order, so totals are bit-reproducible.
+__global__ void __launch_bounds__(256) reduce_kernel(const InstDev* __restrict__ insts,
+                                                     int first_inst,
+                                                     const double* __restrict__ partials,
+                                                     double* __restrict__ totals,
+                                                     int32_t* __restrict__ flags) {
+  __shared__ double s[256];
+  const int inst = first_inst + blockIdx.x;
+  const InstDev& D = insts[inst];
+  for (int j = 0; j < 14; ++j) {
+    double v = 0.0;
+    for (int q = D.slot_begin + threadIdx.x; q < D.slot_end; q += blockDim.x) {
+      const double p = partials[(size_t)q * kPartial + j];
+      v = (j == kResid) ? fmax(v, p) : v + p;
+    }
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w)
+        s[threadIdx.x] = (j == kResid) ? fmax(s[threadIdx.x], s[threadIdx.x + w])
+                                       : s[threadIdx.x] + s[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      totals[(size_t)inst * kTotals + j] = s[0];
+      if (j == kNonFinite && s[0] > 0.0) flags[inst] |= 1;
+    }
+    __syncthreads();
+  }
+}
+
+int launch_reduce(const InstDev* d_insts, int first_inst, int n_insts, const double* d_partials,
+                  double* d_totals, int32_t* d_flags, void* stream) {
+  if (n_insts <= 0) return 0;
+  reduce_kernel<<<n_insts, 256, 0, (cudaStream_t)stream>>>(d_insts, first_inst, d_partials,
+                                                           d_totals, d_flags);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename R>
+__global__ void convert_force_kernel(const double* __restrict__ src, R* __restrict__ dst, int n,
+                                     int stride) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    dst[i] = (R)src[i];
+    dst[stride + i] = (R)src[stride + i];
+  }
+}
+
+int launch_convert_force(int prec, const double* d_src, void* d_dst, int n, int stride,
+                         void* stream) {
+  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  if (blocks <= 0) return 0;
+  if (prec == 0)
+    convert_force_kernel<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(d_src, (double*)d_dst,
+                                                                          n, stride);
+  else
+    convert_force_kernel<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(d_src, (float*)d_dst, n,
+                                                                         stride);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace lbve

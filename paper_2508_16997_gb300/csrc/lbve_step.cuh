@@ -1,0 +1,501 @@
+// lbve_step.cuh -- the fused coupled time step (hand-written CUDA, sm_103a).
+//
+// One CTA updates one tile of one instance.  Storage is structure-of-arrays,
+// x fastest: 9 hydrodynamic planes then 3 x 9 conformation planes of
+// post-collision populations, kept as deviations from the rest state
+// (f_i - w_i, g^c_i - w_i delta_c), ping-pong between two buffers (pull
+// scheme), plus 5 history planes (S_xx, S_xy, S_yy, ux, uy of the previous
+// step) and an optional per-node body force.
+//
+// Per step, per node (paper Sec. 3):
+//   pull-stream all 36 populations (eq_ev_f / eq_g0 left-hand sides);
+//   complete wall rows: hydro wet-node bounce-back of the non-equilibrium part
+//   (Zou-He, wall velocity 0), then CNEBB for each conformation lattice from
+//   the node's own outgoing-to-wall post-collision slots (Sec. 3.3);
+//   moments rho, u (eq_ev_f0), phi^c;
+//   second-order finite differences of u, rho u_x^3, rho u_y^3 from a
+//   one-node (two rows at walls) halo of moments held in shared memory;
+//   Oldroyd-B stress (eq_kramer, eqb4) and source Phi_ab (Sec. 3.2);
+//   TRT-RLB collisions of all four lattices, evaluated in Hermite moment
+//   space: the regularised post-collision state is the projection onto
+//   {1, H_a, H_ab, H_xxy, H_xyy} (the D2Q9 H_xxx, H_yyy vanish), so it is
+//   rebuilt per direction from 8 (hydro) or 6 (conformation) coefficients.
+//   This is algebraically identical to eq_ev_f / eq_g0 written per direction.
+//
+// Phase A computes rho, u on the tile plus halo into shared memory; phase B
+// does the full update of the tile's own nodes.  Halo pulls hit L1/L2; each
+// population is read from HBM once per step by the node that pulls it.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lbve_internal.h"
+
+namespace lbve {
+
+template <typename R>
+struct HydroM {  // raw moments of the (deviation) populations
+  R drho, jx, jy, pxx, pyy, pxy, qxxy, qxyy;
+};
+template <typename R>
+struct CdeM {
+  R dphi, jx, jy, pxx, pyy, pxy;
+};
+
+template <typename R>
+__device__ __forceinline__ void hydro_moments(const R d[9], HydroM<R>& m) {
+  const R s58 = (d[5] + d[6]) + (d[7] + d[8]);
+  m.drho = ((d[0] + d[1]) + (d[2] + d[3])) + (d[4] + s58);
+  m.jx = (d[1] - d[3]) + ((d[5] - d[6]) + (d[8] - d[7]));
+  m.jy = (d[2] - d[4]) + ((d[5] + d[6]) - (d[7] + d[8]));
+  m.pxx = (d[1] + d[3]) + s58;
+  m.pyy = (d[2] + d[4]) + s58;
+  m.pxy = (d[5] + d[7]) - (d[6] + d[8]);
+  m.qxxy = (d[5] + d[6]) - (d[7] + d[8]);
+  m.qxyy = (d[5] + d[8]) - (d[6] + d[7]);
+}
+
+template <typename R>
+__device__ __forceinline__ void cde_moments(const R d[9], CdeM<R>& m) {
+  const R s58 = (d[5] + d[6]) + (d[7] + d[8]);
+  m.dphi = ((d[0] + d[1]) + (d[2] + d[3])) + (d[4] + s58);
+  m.jx = (d[1] - d[3]) + ((d[5] - d[6]) + (d[8] - d[7]));
+  m.jy = (d[2] - d[4]) + ((d[5] + d[6]) - (d[7] + d[8]));
+  m.pxx = (d[1] + d[3]) + s58;
+  m.pyy = (d[2] + d[4]) + s58;
+  m.pxy = (d[5] + d[7]) - (d[6] + d[8]);
+}
+
+// Rebuild the nine (deviation) populations from Hermite coefficients:
+//   d_i = w_i [ b0' + 3 e.b + 4.5 (H_xx bxx + 2 H_xy bxy + H_yy byy)
+//               + 13.5 (H_xxy bxxy + H_xyy bxyy) ]
+// with b0' the zeroth coefficient minus the rest value.
+template <typename R>
+__device__ __forceinline__ void reconstruct(R b0p, R bx, R by, R bxx, R byy, R bxy, R bxxy,
+                                            R bxyy, R out[9]) {
+  const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+  const R s = bxx + byy;
+  out[0] = w0 * (b0p - R(1.5) * s);
+  const R b13 = b0p + R(3.0) * bxx - R(1.5) * byy;
+  const R o13 = R(3.0) * bx - R(4.5) * bxyy;
+  out[1] = w1 * (b13 + o13);
+  out[3] = w1 * (b13 - o13);
+  const R b24 = b0p - R(1.5) * bxx + R(3.0) * byy;
+  const R o24 = R(3.0) * by - R(4.5) * bxxy;
+  out[2] = w1 * (b24 + o24);
+  out[4] = w1 * (b24 - o24);
+  const R bd = b0p + R(3.0) * s;
+  const R xy9 = R(9.0) * bxy;
+  const R o57 = R(3.0) * (bx + by) + R(9.0) * (bxxy + bxyy);
+  const R o68 = R(3.0) * (by - bx) + R(9.0) * (bxxy - bxyy);
+  out[5] = w5 * ((bd + xy9) + o57);
+  out[7] = w5 * ((bd + xy9) - o57);
+  out[6] = w5 * ((bd - xy9) + o68);
+  out[8] = w5 * ((bd - xy9) - o68);
+}
+
+// Pull the nine populations of one lattice arriving at (x, y): d_i(x) =
+// post_i(x - e_i).  rm / rp are the row offsets of rows y-1 / y+1, or -1
+// where that row is outside a walled domain (those directions stay unknown
+// and are completed by the caller).
+template <typename R>
+__device__ __forceinline__ void pull9(const R* __restrict__ p, int S, int rc, int rm, int rp,
+                                      int x, int xm, int xp, R d[9]) {
+  d[0] = p[0 * S + rc + x];
+  d[1] = p[1 * S + rc + xm];
+  d[3] = p[3 * S + rc + xp];
+  if (rm >= 0) {
+    d[2] = p[2 * S + rm + x];
+    d[5] = p[5 * S + rm + xm];
+    d[6] = p[6 * S + rm + xp];
+  } else {
+    d[2] = d[5] = d[6] = R(0);
+  }
+  if (rp >= 0) {
+    d[4] = p[4 * S + rp + x];
+    d[7] = p[7 * S + rp + xp];
+    d[8] = p[8 * S + rp + xm];
+  } else {
+    d[4] = d[7] = d[8] = R(0);
+  }
+}
+
+// Hydrodynamic wet-node completion with zero wall velocity: sum e f = -F/2
+// (so u = 0 through eq_ev_f0) and the wall-normal pair bounced back.  The
+// paired weights are equal, so the formulas hold for deviations unchanged.
+template <typename R>
+__device__ __forceinline__ void zou_he(R d[9], R Fx, R Fy, bool bottom) {
+  const R h = R(0.5) * (d[1] - d[3]);
+  const R qx = R(0.25) * Fx, qy = R(0.25) * Fy;
+  if (bottom) {
+    d[2] = d[4];
+    d[5] = d[7] - h - qx - qy;
+    d[6] = d[8] + h + qx - qy;
+  } else {
+    d[4] = d[2];
+    d[7] = d[5] + h + qx + qy;
+    d[8] = d[6] - h - qx + qy;
+  }
+}
+
+// CNEBB (Sec. 3.3) on deviations.  post_* are the node's own post-collision
+// slots pointing toward the wall (H); the unknown directions U are their
+// opposites.  phi_b = known incoming + sum_H post; unknown i gets
+// g_i = g_ibar + (g^eq_i - g^eq_ibar) = g_ibar + 6 w_i phi_b (e_i . u_b);
+// the rest population closes sum g = phi_b.  Returns the wall in/out amounts
+// (full populations, float64).
+template <typename R>
+__device__ __forceinline__ void cnebb(R d[9], R post_a, R post_b, R post_c, R delta_c, R ubx,
+                                      R uby, bool bottom, double& win, double& wout) {
+  // bottom: H = {4, 7, 8}, U = {2, 5, 6};  top: H = {2, 5, 6}, U = {4, 7, 8}
+  const R d0_old = d[0];
+  R dphi;
+  if (bottom) {
+    dphi = ((d[0] + d[1]) + (d[3] + d[4])) + ((d[7] + d[8]) + ((post_a + post_b) + post_c));
+  } else {
+    dphi = ((d[0] + d[1]) + (d[3] + d[2])) + ((d[5] + d[6]) + ((post_a + post_b) + post_c));
+  }
+  const R phib = delta_c + dphi;
+  const R a2 = R(6.0 / 9.0) * phib, a5 = R(6.0 / 36.0) * phib;
+  if (bottom) {
+    d[2] = d[4] + a2 * uby;
+    d[5] = d[7] + a5 * (ubx + uby);
+    d[6] = d[8] + a5 * (uby - ubx);
+  } else {
+    d[4] = d[2] - a2 * uby;
+    d[7] = d[5] - a5 * (ubx + uby);
+    d[8] = d[6] + a5 * (ubx - uby);
+  }
+  d[0] = dphi - (((d[1] + d[2]) + (d[3] + d[4])) + ((d[5] + d[6]) + (d[7] + d[8])));
+  const double dc = (double)delta_c;
+  wout = ((double)post_a + (double)post_b + (double)post_c) + dc / 6.0;
+  double added;
+  if (bottom) added = (double)d[2] + (double)d[5] + (double)d[6];
+  else added = (double)d[4] + (double)d[7] + (double)d[8];
+  win = added + dc / 6.0 + ((double)d[0] - (double)d0_old);
+}
+
+template <typename R>
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Populations of one lattice at a node: pulled from the previous step
+// (kModeStep) or the equilibrium of the staged initial fields (kModeInit).
+template <typename R, int MODE>
+struct PopSource;
+
+template <typename R>
+struct PopSource<R, kModeStep> {
+  static __device__ __forceinline__ void hydro(const void* src, int S, int nx, int k, int rc,
+                                               int rm, int rp, int x, int xm, int xp, R d[9]) {
+    pull9<R>((const R*)src, S, rc, rm, rp, x, xm, xp, d);
+  }
+  static __device__ __forceinline__ void cde(const void* src, int l, int S, int nx, int k, int rc,
+                                             int rm, int rp, int x, int xm, int xp, R d[9]) {
+    pull9<R>((const R*)src + (size_t)(9 + 9 * l) * S, S, rc, rm, rp, x, xm, xp, d);
+  }
+};
+
+template <typename R>
+struct PopSource<R, kModeInit> {
+  // staged fields: float64 [6][S] = rho, ux, uy, Axx, Axy, Ayy at node k
+  static __device__ __forceinline__ void hydro(const void* src, int S, int nx, int k, int rc,
+                                               int rm, int rp, int x, int xm, int xp, R d[9]) {
+    const double* f = (const double*)src;
+    const R r = (R)f[k], ux = (R)f[S + k], uy = (R)f[2 * S + k];
+    // equilibrium (eq2): Hermite coefficients rho, rho u, rho uu, rho u_x^2 u_y, rho u_x u_y^2
+    reconstruct<R>((R)(f[k] - 1.0), r * ux, r * uy, r * ux * ux, r * uy * uy, r * ux * uy,
+                   r * ux * ux * uy, r * ux * uy * uy, d);
+  }
+  static __device__ __forceinline__ void cde(const void* src, int l, int S, int nx, int k, int rc,
+                                             int rm, int rp, int x, int xm, int xp, R d[9]) {
+    const double* f = (const double*)src;
+    const R ux = (R)f[S + k], uy = (R)f[2 * S + k];
+    const double A = f[(3 + l) * S + k];
+    const R a = (R)A;
+    const R ap = (R)(A - (l == 1 ? 0.0 : 1.0));
+    // equilibrium (eq_geq): phi, phi u, phi uu
+    reconstruct<R>(ap, a * ux, a * uy, a * ux * ux, a * uy * uy, a * ux * uy, R(0), R(0), d);
+  }
+};
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kThreads, 2)
+    step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles, int parity,
+                int flags, double* __restrict__ partials) {
+  __shared__ R s_rho[kRegionMax];
+  __shared__ R s_ux[kRegionMax];
+  __shared__ R s_uy[kRegionMax];
+  __shared__ double s_red[kThreads / 32][kPartial];
+
+  const TileDev T = tiles[blockIdx.x];
+  const InstDev& D = insts[T.inst];
+  const int nx = D.nx, ny = D.ny, S = D.stride, TX = D.TX, TY = D.TY, hy = D.hy;
+  const bool py = D.periodic_y != 0;
+  const void* src = D.pop[parity];
+  R* __restrict__ dst = (R*)D.pop[parity ^ 1];
+  const R* __restrict__ force = (const R*)D.force;
+  const bool ffield = D.force_field != 0;
+  const R Fx0 = (R)D.Fx, Fy0 = (R)D.Fy;
+  const int RW = TX + 2, RH = TY + 2 * hy;
+
+  // ---------------- phase A: rho, u on tile + halo -------------------------
+  for (int r = threadIdx.x; r < RW * RH; r += blockDim.x) {
+    const int lx = r % RW, ly = r / RW;
+    int gx = T.x0 - 1 + lx;
+    gx = ((gx % nx) + nx) % nx;
+    int gy = T.y0 - hy + ly;
+    if (py) {
+      gy = ((gy % ny) + ny) % ny;
+    } else if (gy < 0 || gy >= ny) {
+      continue;
+    }
+    const int k = gy * nx + gx;
+    const int rc = gy * nx;
+    int rm, rp;
+    if (py) {
+      rm = (gy == 0 ? ny - 1 : gy - 1) * nx;
+      rp = (gy == ny - 1 ? 0 : gy + 1) * nx;
+    } else {
+      rm = gy > 0 ? (gy - 1) * nx : -1;
+      rp = gy < ny - 1 ? (gy + 1) * nx : -1;
+    }
+    const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
+    const R Fx = ffield ? force[k] : Fx0;
+    const R Fy = ffield ? force[S + k] : Fy0;
+    R d[9];
+    PopSource<R, MODE>::hydro(src, S, nx, k, rc, rm, rp, gx, xm, xp, d);
+    if (MODE == kModeStep && !py && (gy == 0 || gy == ny - 1)) zou_he<R>(d, Fx, Fy, gy == 0);
+    HydroM<R> m;
+    hydro_moments<R>(d, m);
+    const R rho = R(1) + m.drho;
+    s_rho[r] = rho;
+    s_ux[r] = (m.jx + R(0.5) * Fx) / rho;
+    s_uy[r] = (m.jy + R(0.5) * Fy) / rho;
+  }
+  __syncthreads();
+
+  // ---------------- phase B: full update of the tile's nodes ---------------
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int x = T.x0 + tx, y = T.y0 + ty;
+  const bool active = (ty < TY) && (x < nx) && (y < ny);
+  const bool final_step = (flags & kFinal) != 0;
+  double part[14];
+#pragma unroll
+  for (int j = 0; j < 14; ++j) part[j] = 0.0;
+
+  if (active) {
+    const int k = y * nx + x;
+    const int rc = y * nx;
+    const bool wb = !py && y == 0, wt = !py && y == ny - 1;
+    int rm, rp;
+    if (py) {
+      rm = (y == 0 ? ny - 1 : y - 1) * nx;
+      rp = (y == ny - 1 ? 0 : y + 1) * nx;
+    } else {
+      rm = y > 0 ? (y - 1) * nx : -1;
+      rp = y < ny - 1 ? (y + 1) * nx : -1;
+    }
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const R Fx = ffield ? force[k] : Fx0;
+    const R Fy = ffield ? force[S + k] : Fy0;
+
+    // hydro populations -> moments
+    R d[9];
+    PopSource<R, MODE>::hydro(src, S, nx, k, rc, rm, rp, x, xm, xp, d);
+    if (MODE == kModeStep && (wb || wt)) zou_he<R>(d, Fx, Fy, wb);
+    HydroM<R> hm;
+    hydro_moments<R>(d, hm);
+
+    const int ri = (ty + hy) * RW + tx + 1;  // this node in the halo region
+    const R rho = s_rho[ri], ux = s_ux[ri], uy = s_uy[ri];
+
+    // gradients: grad[g][b] = d_g u_b  (G00 = dx ux, G01 = dx uy, G10 = dy ux, G11 = dy uy)
+    const R half = R(0.5);
+    const R G00 = half * (s_ux[ri + 1] - s_ux[ri - 1]);
+    const R G01 = half * (s_uy[ri + 1] - s_uy[ri - 1]);
+    const R cxp = s_rho[ri + 1] * s_ux[ri + 1] * s_ux[ri + 1] * s_ux[ri + 1];
+    const R cxm = s_rho[ri - 1] * s_ux[ri - 1] * s_ux[ri - 1] * s_ux[ri - 1];
+    const R dPx = half * (cxp - cxm);
+    R G10, G11, dPy;
+    {
+      auto cy = [&](int j) { return s_rho[j] * s_uy[j] * s_uy[j] * s_uy[j]; };
+      if (wb) {
+        const int j1 = ri + RW, j2 = ri + 2 * RW;
+        G10 = half * (R(-3) * s_ux[ri] + R(4) * s_ux[j1] - s_ux[j2]);
+        G11 = half * (R(-3) * s_uy[ri] + R(4) * s_uy[j1] - s_uy[j2]);
+        dPy = half * (R(-3) * cy(ri) + R(4) * cy(j1) - cy(j2));
+      } else if (wt) {
+        const int j1 = ri - RW, j2 = ri - 2 * RW;
+        G10 = half * (R(3) * s_ux[ri] - R(4) * s_ux[j1] + s_ux[j2]);
+        G11 = half * (R(3) * s_uy[ri] - R(4) * s_uy[j1] + s_uy[j2]);
+        dPy = half * (R(3) * cy(ri) - R(4) * cy(j1) + cy(j2));
+      } else {
+        G10 = half * (s_ux[ri + RW] - s_ux[ri - RW]);
+        G11 = half * (s_uy[ri + RW] - s_uy[ri - RW]);
+        dPy = half * (cy(ri + RW) - cy(ri - RW));
+      }
+    }
+
+    // conformation populations -> (completed) -> moments
+    CdeM<R> cm[3];
+    const R* srcR = (const R*)src;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      R g[9];
+      PopSource<R, MODE>::cde(src, l, S, nx, k, rc, rm, rp, x, xm, xp, g);
+      if (MODE == kModeStep && (wb || wt)) {
+        const R* own = srcR + (size_t)(9 + 9 * l) * S + k;
+        const R delta = (l == 1) ? R(0) : R(1);
+        double win, wout;
+        if (wb) cnebb<R>(g, own[4 * S], own[7 * S], own[8 * S], delta, ux, uy, true, win, wout);
+        else cnebb<R>(g, own[2 * S], own[5 * S], own[6 * S], delta, ux, uy, false, win, wout);
+        part[kWallIn + l] += win;
+        part[kWallOut + l] += wout;
+      }
+      cde_moments<R>(g, cm[l]);
+    }
+
+    // conformation tensor, polymer stress (eq_kramer with eqb4), source Phi_ab
+    const R Axx = R(1) + cm[0].dphi, Axy = cm[1].dphi, Ayy = R(1) + cm[2].dphi;
+    const R mpl = (R)D.mup_over_lambda, il = (R)D.inv_lambda;
+    const R txx = mpl * cm[0].dphi, txy = mpl * cm[1].dphi, tyy = mpl * cm[2].dphi;
+    const R div = G00 + G11;
+    R Sc[3];
+    Sc[0] = -cm[0].dphi * il + R(2) * (Axx * G00 + Axy * G10) + Axx * div;
+    Sc[1] = -cm[1].dphi * il + (Axx * G01 + Axy * G11) + (Axy * G00 + Ayy * G10) + Axy * div;
+    Sc[2] = -cm[2].dphi * il + R(2) * (Axy * G01 + Ayy * G11) + Ayy * div;
+
+    // history of the source term (backward difference of F~, Sec. 3.2)
+    R* __restrict__ hist = (R*)D.hist;
+    R So[3], uxo, uyo;
+    if (MODE == kModeStep) {
+      So[0] = hist[k];
+      So[1] = hist[S + k];
+      So[2] = hist[2 * S + k];
+      uxo = hist[3 * S + k];
+      uyo = hist[4 * S + k];
+    } else {
+      So[0] = Sc[0];
+      So[1] = Sc[1];
+      So[2] = Sc[2];
+      uxo = ux;
+      uyo = uy;
+    }
+
+    // ---- hydrodynamic TRT-RLB collision (eq_ev_f, eq4, eq5, eq6, F_i) ----
+    {
+      const R cs2 = R(1.0 / 3.0);
+      const R c1 = (R)D.c_s1, c2 = (R)D.c_s2, h1 = (R)D.h_s1, w1 = (R)D.w_s1;
+      const R ruxx = rho * ux * ux, ruyy = rho * uy * uy, ruxy = rho * ux * uy;
+      const R ruxxy = ruxx * uy, ruxyy = ruxy * uy;
+      const R nxx = hm.pxx - cs2 * hm.drho - ruxx;  // A_xx^neq
+      const R nyy = hm.pyy - cs2 * hm.drho - ruyy;  // A_yy^neq
+      const R nxy = hm.pxy - ruxy;                  // A_xy^neq
+      const R nxxy = hm.qxxy - cs2 * hm.jy - ruxxy; // A_xxy^neq
+      const R nxyy = hm.qxyy - cs2 * hm.jx - ruxyy; // A_xyy^neq
+      const R bx = hm.jx + Fx, by = hm.jy + Fy;     // rho u + (1-1/tau)A_a + F-term
+      const R bxx = ruxx + c1 * nxx - h1 * dPx - w1 * txx;
+      const R byy = ruyy + c1 * nyy - h1 * dPy - w1 * tyy;
+      const R bxy = ruxy + c1 * nxy - w1 * txy;
+      const R bxxy = ruxxy + c2 * nxxy;
+      const R bxyy = ruxyy + c2 * nxyy;
+      R out[9];
+      reconstruct<R>(hm.drho, bx, by, bxx, byy, bxy, bxxy, bxyy, out);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) dst[(size_t)i * S + k] = out[i];
+    }
+
+    // ---- three conformation TRT-RLB collisions (eq_g0) ----
+    {
+      const R cs2 = R(1.0 / 3.0);
+      const R ep = (R)D.ep_p1, c2 = (R)D.c_p2, h1 = (R)D.h_p1;
+      const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const R phi = (l == 1 ? R(0) : R(1)) + cm[l].dphi;
+        const R Bx = cm[l].jx - phi * ux, By = cm[l].jy - phi * uy;
+        const R Bxx = cm[l].pxx - cs2 * cm[l].dphi - phi * uxx;
+        const R Byy = cm[l].pyy - cs2 * cm[l].dphi - phi * uyy;
+        const R Bxy = cm[l].pxy - phi * uxy;
+        const R s = Sc[l], so = So[l];
+        const R c0p = cm[l].dphi + R(1.5) * s - R(0.5) * so;
+        const R pr = phi / rho;
+        // (1 - 1/tau_p1) B = -B + ep B, kept split so float32 keeps the tiny
+        // difference tau_p1 - 1/2 accurately
+        const R cx = (phi * ux - Bx) + ep * Bx + h1 * (pr * Fx + ux * s) +
+                     R(0.5) * h1 * (ux * s - uxo * so);
+        const R cy = (phi * uy - By) + ep * By + h1 * (pr * Fy + uy * s) +
+                     R(0.5) * h1 * (uy * s - uyo * so);
+        const R cxx = phi * uxx + c2 * Bxx;
+        const R cyy = phi * uyy + c2 * Byy;
+        const R cxy = phi * uxy + c2 * Bxy;
+        R out[9];
+        reconstruct<R>(c0p, cx, cy, cxx, cyy, cxy, R(0), R(0), out);
+        R* dl = dst + (size_t)(9 + 9 * l) * S;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dl[(size_t)i * S + k] = out[i];
+      }
+    }
+
+    hist[k] = Sc[0];
+    hist[S + k] = Sc[1];
+    hist[2 * S + k] = Sc[2];
+    hist[3 * S + k] = ux;
+    hist[4 * S + k] = uy;
+
+    if (final_step) {
+      double* fl = D.fields;
+      const double r = 1.0 + (double)hm.drho;
+      const double vx = (double)ux, vy = (double)uy;
+      const double axx = 1.0 + (double)cm[0].dphi, axy = (double)cm[1].dphi,
+                   ayy = 1.0 + (double)cm[2].dphi;
+      // residual against the fields of the previous final step (none at init)
+      const double res = (MODE == kModeStep)
+                             ? fmax(fabs(vx - fl[S + k]), fabs(vy - fl[2 * S + k])) * D.inv_Uc
+                             : 0.0;
+      fl[k] = r;
+      fl[S + k] = vx;
+      fl[2 * S + k] = vy;
+      fl[3 * S + k] = axx;
+      fl[4 * S + k] = axy;
+      fl[5 * S + k] = ayy;
+      part[kSumRho] = r;
+      part[kSumJx] = (double)rho * vx;
+      part[kSumJy] = (double)rho * vy;
+      part[kSumPhi + 0] = axx;
+      part[kSumPhi + 1] = axy;
+      part[kSumPhi + 2] = ayy;
+      const bool finite = isfinite(r) && isfinite(vx) && isfinite(vy) && isfinite(axx) &&
+                          isfinite(axy) && isfinite(ayy);
+      part[kResid] = finite ? res : 0.0;
+      part[kNonFinite] = finite ? 0.0 : 1.0;
+    }
+  }
+
+  if (final_step) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 14; ++j) {
+      const double v = (j == kResid) ? warp_max(part[j]) : warp_sum<double>(part[j]);
+      if (lane == 0) s_red[warp][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 14) {
+      const int j = threadIdx.x;
+      double v = s_red[0][j];
+      for (int w = 1; w < kThreads / 32; ++w)
+        v = (j == kResid) ? fmax(v, s_red[w][j]) : v + s_red[w][j];
+      partials[(size_t)T.slot * kPartial + j] = v;
+    }
+  }
+}
+
+}  // namespace lbve

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of ``liblbve.so`` (declared in ``include/lbve.h``).
+
+The functions below carry the C names and only marshal arguments; every
+step of the computation runs in the library's CUDA kernels.  Device memory
+and the stream come from PyTorch.  There is no CPU fallback: if the library
+is missing, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbve.so")
+
+LBVE_OK = 0
+LBVE_ERR_ARG = -1
+LBVE_ERR_CUDA = -2
+LBVE_ERR_NONFINITE = -3
+LBVE_ERR_TIMEOUT = -4
+LBVE_ERR_GEOMETRY = -5
+LBVE_ERR_WORKSPACE = -6
+LBVE_ERR_STATE = -7
+LBVE_FP64 = 0
+LBVE_FP32_DEV = 1
+LBVE_NTOTALS = 12
+
+EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_step",
+            "lbve_status", "lbve_fields", "lbve_totals", "lbve_residual", "lbve_time",
+            "lbve_destroy", "lbve_error_string", "lbve_last_error"]
+
+
+class lbve_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("beta", ctypes.c_double), ("Wi", ctypes.c_double),
+                ("Re", ctypes.c_double), ("Sc", ctypes.c_double), ("Ma", ctypes.c_double),
+                ("Lc", ctypes.c_double), ("Lambda_s", ctypes.c_double),
+                ("Lambda_p", ctypes.c_double), ("Fx", ctypes.c_double), ("Fy", ctypes.c_double)]
+
+
+class LbveError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        L = _lib
+        name = L.lbve_error_string(code).decode() if L else str(code)
+        detail = L.lbve_last_error().decode() if L else ""
+        super().__init__(f"{where}: {name} ({code}): {detail}")
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+def load() -> ctypes.CDLL:
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2508_16997_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER(lbve_params)
+        L.lbve_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        L.lbve_create.argtypes = [P, ctypes.c_int32, _vp, ctypes.c_size_t, _vp,
+                                  ctypes.POINTER(_vp)]
+        L.lbve_set_geometry.argtypes = [_vp, ctypes.c_int32, _vp, _dp, _dp]
+        L.lbve_step.argtypes = [_vp, ctypes.c_int64]
+        L.lbve_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+        L.lbve_fields.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32]
+        L.lbve_totals.argtypes = [_vp, ctypes.c_int32, _dp]
+        L.lbve_residual.argtypes = [_vp, ctypes.c_int32, _dp]
+        L.lbve_time.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+        L.lbve_destroy.argtypes = [_vp]
+        L.lbve_destroy.restype = None
+        L.lbve_error_string.argtypes = [ctypes.c_int]
+        L.lbve_error_string.restype = ctypes.c_char_p
+        L.lbve_last_error.argtypes = []
+        L.lbve_last_error.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name not in ("lbve_destroy", "lbve_error_string", "lbve_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != LBVE_OK:
+        raise LbveError(rc, where)
+
+
+def _params_array(params) -> ctypes.Array:
+    arr = (lbve_params * len(params))()
+    for i, p in enumerate(params):
+        arr[i] = p
+    return arr
+
+
+def _f64(a, n):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"expected {n} float64 values, got {a.size}")
+    return a, a.ctypes.data_as(_dp)
+
+
+# ---- the C entry points, same names -----------------------------------------
+
+def lbve_workspace_bytes(params) -> int:
+    arr = _params_array(params)
+    out = ctypes.c_size_t()
+    _check(load().lbve_workspace_bytes(arr, len(params), ctypes.byref(out)),
+           "lbve_workspace_bytes")
+    return out.value
+
+
+def lbve_create(params, d_workspace: int, nbytes: int, stream: int) -> ctypes.c_void_p:
+    arr = _params_array(params)
+    h = _vp()
+    _check(load().lbve_create(arr, len(params), _vp(d_workspace), nbytes, _vp(stream),
+                              ctypes.byref(h)), "lbve_create")
+    return h
+
+
+def lbve_set_geometry(h, inst: int, solid_mask=None, body_force=None, init_fields=None,
+                      n_nodes: int | None = None) -> None:
+    mask_ptr = None
+    if solid_mask is not None:
+        m = np.ascontiguousarray(solid_mask, dtype=np.uint8)
+        mask_ptr = m.ctypes.data
+    bf, bf_ptr = _f64(body_force, 2 * n_nodes) if body_force is not None else (None, None)
+    ini, ini_ptr = _f64(init_fields, 6 * n_nodes) if init_fields is not None else (None, None)
+    _check(load().lbve_set_geometry(h, inst, mask_ptr, bf_ptr, ini_ptr), "lbve_set_geometry")
+
+
+def lbve_step(h, n_steps: int) -> None:
+    _check(load().lbve_step(h, int(n_steps)), "lbve_step")
+
+
+def lbve_status(h, n_instances: int) -> np.ndarray:
+    flags = np.zeros(n_instances, dtype=np.int32)
+    rc = load().lbve_status(h, flags.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc not in (LBVE_OK, LBVE_ERR_NONFINITE):
+        _check(rc, "lbve_status")
+    return flags
+
+
+def lbve_fields(h, inst: int, out_ptr: int, on_device: bool) -> None:
+    _check(load().lbve_fields(h, inst, _vp(out_ptr), 1 if on_device else 0), "lbve_fields")
+
+
+def lbve_totals(h, inst: int) -> np.ndarray:
+    out = np.empty(LBVE_NTOTALS)
+    _check(load().lbve_totals(h, inst, out.ctypes.data_as(_dp)), "lbve_totals")
+    return out
+
+
+def lbve_residual(h, inst: int) -> float:
+    out = ctypes.c_double()
+    _check(load().lbve_residual(h, inst, ctypes.byref(out)), "lbve_residual")
+    return out.value
+
+
+def lbve_time(h, inst: int) -> int:
+    out = ctypes.c_int64()
+    _check(load().lbve_time(h, inst, ctypes.byref(out)), "lbve_time")
+    return out.value
+
+
+def lbve_destroy(h) -> None:
+    if h:
+        load().lbve_destroy(h)
+
+
+# ---- convenience wrapper ----------------------------------------------------
+
+def params_from(inst, precision: int = LBVE_FP64) -> lbve_params:
+    """lbve_params of a :class:`workloads.Instance`."""
+    return lbve_params(inst.nx, inst.ny, 1 if inst.periodic_y else 0, precision, inst.beta,
+                       inst.Wi, inst.Re, inst.Sc, inst.Ma, inst.Lc, inst.Lambda_s, inst.Lambda_p,
+                       inst.Fx, inst.Fy)
+
+
+class Simulation:
+    """A batch of instances advanced together on the current CUDA device.
+
+    The workspace is one torch uint8 tensor; the library runs on torch's
+    current stream."""
+
+    def __init__(self, instances, precision=LBVE_FP64, init_fields=None, device=None):
+        import torch
+        self.torch = torch
+        self.instances = list(instances)
+        if isinstance(precision, int):
+            precision = [precision] * len(self.instances)
+        self.params = [params_from(inst, pr) for inst, pr in zip(self.instances, precision)]
+        self.device = torch.device(device or "cuda")
+        self.nbytes = lbve_workspace_bytes(self.params)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = torch.cuda.current_stream(self.device)
+        self.h = lbve_create(self.params, self.workspace.data_ptr(), self.nbytes,
+                             self.stream.cuda_stream)
+        for i, inst in enumerate(self.instances):
+            ini = None if init_fields is None else init_fields[i]
+            lbve_set_geometry(self.h, i, None, inst.force_field, ini, n_nodes=inst.n_nodes)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lbve_destroy(h)
+            self.h = None
+
+    def step(self, n: int) -> None:
+        lbve_step(self.h, n)
+
+    def fields(self, i: int) -> np.ndarray:
+        inst = self.instances[i]
+        out = np.empty((6, inst.ny, inst.nx))
+        lbve_fields(self.h, i, out.ctypes.data, False)
+        return out
+
+    def fields_device(self, i: int):
+        inst = self.instances[i]
+        out = self.torch.empty((6, inst.ny, inst.nx), dtype=self.torch.float64,
+                               device=self.device)
+        lbve_fields(self.h, i, out.data_ptr(), True)
+        return out
+
+    def totals(self, i: int) -> np.ndarray:
+        return lbve_totals(self.h, i)
+
+    def residual(self, i: int) -> float:
+        return lbve_residual(self.h, i)
+
+    def status(self) -> np.ndarray:
+        return lbve_status(self.h, len(self.instances))
+
+    def time(self, i: int = 0) -> int:
+        return lbve_time(self.h, i)

@@ -1,0 +1,80 @@
+"""The C-ABI library loads without a GPU, exports every entry point that
+include/lbve.h declares, and rejects bad arguments on the host."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbve.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2508_16997_gb300 import build, lbve
+    build.build()
+    return lbve
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbve_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree(L):
+    assert declared_functions() == sorted(L.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (lbve_\w+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    lib = L.load()
+    for f in declared_functions():
+        assert hasattr(lib, f)
+
+
+def test_workspace_bytes_and_validation(L):
+    from paper_2508_16997_gb300 import workloads as wl
+    p = [L.params_from(wl.frm(64)), L.params_from(wl.channel(32), L.LBVE_FP32_DEV)]
+    n = L.lbve_workspace_bytes(p)
+    # two ping-pong buffers of 36 planes dominate: > 2*36*4096*8 bytes
+    assert n > 2 * 36 * 4096 * 8
+    bad = L.params_from(wl.frm(8))
+    bad.beta = 0.0
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_workspace_bytes([bad])
+    assert e.value.code == L.LBVE_ERR_ARG
+    bad = L.params_from(wl.channel(8))
+    bad.ny = 2
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_workspace_bytes([bad])
+    assert e.value.code == L.LBVE_ERR_ARG
+    bad = L.params_from(wl.frm(8))
+    bad.precision = 7
+    with pytest.raises(L.LbveError):
+        L.lbve_workspace_bytes([bad])
+
+
+def test_create_rejects_missing_workspace(L):
+    from paper_2508_16997_gb300 import workloads as wl
+    p = [L.params_from(wl.frm(16))]
+    n = L.lbve_workspace_bytes(p)
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(p, 0, n, 0)
+    assert e.value.code == L.LBVE_ERR_WORKSPACE
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(p, 256, n - 1, 0)
+    assert e.value.code == L.LBVE_ERR_WORKSPACE
+
+
+def test_error_strings(L):
+    lib = L.load()
+    for code in range(0, -8, -1):
+        assert lib.lbve_error_string(code)
+    assert b"unknown" in lib.lbve_error_string(-99)

@@ -1,0 +1,158 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every test feeds the same seeded inputs to both sides and compares the
+macroscopic fields element by element.  Tolerances:
+  * FP64 path: relative L2 <= 1e-12 on u and on C (the target stated for the
+    plain FP64 path) and on the deformation C - I; both sides do the same
+    arithmetic in a different association order, so differences are
+    round-off that the dissipative scheme does not amplify.
+  * FP32-deviation path: relative L2 <= 1e-5 on u and C for Wi <= 100 (the
+    stated FP32 target).
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import parity_errors
+from oracle_helpers import oracle_sim
+from paper_2508_16997_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lbve():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_16997_gb300 import build, lbve as L
+    build.build()
+    return L
+
+
+def run_pair(L, insts, steps, precision=0, inits=None, check_steps=None):
+    """Advance a batch on the GPU and each instance on the oracle."""
+    sim = L.Simulation(insts, precision=precision, init_fields=inits)
+    orcs = [oracle_sim(inst, init=None if inits is None else inits[i])
+            for i, inst in enumerate(insts)]
+    sim.step(steps)
+    for o in orcs:
+        o.step(steps)
+    return sim, orcs
+
+
+def assert_fp64_parity(gpu, ref, tol=FP64_TOL, what=""):
+    err = parity_errors(gpu, ref)
+    assert err["u"] <= tol and err["C"] <= tol and err["C-I"] <= 100 * tol, (what, err)
+    assert np.abs(gpu[0] - ref[0]).max() <= 1e-13, (what, err)
+
+
+def test_frm64_fp64_1000_steps(lbve):
+    """Four-roll mill 64^2, beta 0.5, Wi 5, Re 0.01, Sc 1e5, Ma 1e-3, FP64:
+    the small configuration, 1000 steps."""
+    inst = wl.frm(64)
+    sim, (o,) = run_pair(lbve, [inst], 1000)
+    assert_fp64_parity(sim.fields(0), o.fields(), what="frm64")
+    assert sim.time(0) == 1000
+
+
+def test_channel_fp64_walls(lbve):
+    """Oldroyd-B Poiseuille channel (Zou-He + CNEBB walls), H = 16, Wi = 10."""
+    inst = wl.channel(16, nx=4, Wi=10.0)
+    sim, (o,) = run_pair(lbve, [inst], 1500)
+    assert_fp64_parity(sim.fields(0), o.fields(), what="channel")
+
+
+@pytest.mark.parametrize("nx,ny,periodic", [(37, 21, True), (45, 19, False), (1, 9, False),
+                                            (2, 7, True), (33, 3, False), (70, 70, True)])
+def test_ragged_tiles_random_state(lbve, nx, ny, periodic):
+    """Ragged tiles in x and y, degenerate widths (nx = 1, 2), the smallest
+    walled channel (ny = 3), random initial fields and a random force field."""
+    inst = wl.Instance(nx, ny, periodic, 0.6, 0.8, 1.0, 1e3, 0.1,
+                       (nx / (2 * np.pi)) if periodic else float(ny - 1), 0.25, 1e-4,
+                       kind="custom")
+    inst.force_field = wl.random_force(nx, ny, seed=nx * 100 + ny, amp=1e-4)
+    init = wl.random_fields(nx, ny, seed=nx * 1000 + ny)
+    sim, (o,) = run_pair(lbve, [inst], 150, inits=[init])
+    assert_fp64_parity(sim.fields(0), o.fields(), what=f"{nx}x{ny}")
+
+
+def test_batch_mixed_instances(lbve):
+    """Several instances of different kinds and sizes in one handle: each
+    matches its own oracle run (no cross-talk between instances)."""
+    insts = [wl.frm(40, Wi=2.0, Re=1.0, Ma=0.05), wl.channel(24, nx=4, Wi=100.0, beta=0.3),
+             wl.channel(9, nx=6, Wi=1.0, beta=0.9), wl.frm(33, Wi=0.5, Re=0.1, Ma=0.01)]
+    sim, orcs = run_pair(lbve, insts, 300)
+    for i, o in enumerate(orcs):
+        assert_fp64_parity(sim.fields(i), o.fields(), what=f"inst{i}")
+
+
+def test_totals_and_wall_balance(lbve):
+    """Float64 totals and the CNEBB wall balance match the oracle's; the wall
+    returns exactly what it received (in == out)."""
+    inst = wl.channel(12, nx=5, Wi=3.0, Sc=1e3)
+    init = wl.random_fields(inst.nx, inst.ny, seed=5)
+    sim, (o,) = run_pair(lbve, [inst], 40, inits=[init])
+    tg, to = sim.totals(0), o.totals()
+    np.testing.assert_allclose(tg[:6], to[:6], rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(tg[6:], to[6:], rtol=1e-11, atol=1e-14)
+    np.testing.assert_allclose(tg[6:9], tg[9:12], rtol=1e-13, atol=1e-15)
+
+
+def test_multiple_step_calls_and_residual(lbve):
+    """Stepping in several calls equals stepping once; the residual is
+    max |u(t) - u(t')| / U_c between the ends of consecutive calls."""
+    inst = wl.frm(24, Wi=1.0, Re=1.0, Ma=0.1)
+    sim = lbve.Simulation([inst])
+    o = oracle_sim(inst)
+    sim.step(7)
+    o.step(7)
+    prev = o.fields()
+    sim.step(13)
+    sim.step(0)  # no-op
+    o.step(13)
+    cur = o.fields()
+    assert_fp64_parity(sim.fields(0), cur)
+    Uc = o.coeffs()["Uc"]
+    expect = max(np.abs(cur[1] - prev[1]).max(), np.abs(cur[2] - prev[2]).max()) / Uc
+    assert abs(sim.residual(0) - expect) <= 1e-10 * expect
+    assert sim.time(0) == 20
+
+
+def test_fp32_dev_frm(lbve):
+    """FP32 deviation storage on the four-roll mill 64^2 (Wi = 5): relative L2
+    error against the FP64 oracle within 1e-5 after 1000 steps."""
+    inst = wl.frm(64)
+    sim, (o,) = run_pair(lbve, [inst], 1000, precision=1)
+    err = parity_errors(sim.fields(0), o.fields())
+    assert err["u"] <= FP32_TOL and err["C"] <= FP32_TOL, err
+
+
+@pytest.mark.parametrize("Wi", [1.0, 10.0, 100.0])
+def test_fp32_dev_channel(lbve, Wi):
+    """FP32 deviation storage on the Oldroyd-B channel for Wi <= 100."""
+    inst = wl.channel(32, nx=4, Wi=Wi)
+    sim, (o,) = run_pair(lbve, [inst], 2000, precision=1)
+    err = parity_errors(sim.fields(0), o.fields())
+    assert err["u"] <= FP32_TOL and err["C"] <= FP32_TOL, err
+
+
+def test_status_flags_nonfinite(lbve):
+    """A blow-up is reported through the status flags, not a fault: an
+    absurd force drives the fields to Inf/NaN within a few steps."""
+    inst = wl.frm(16, Wi=1.0, Re=1.0, Ma=0.1)
+    inst.force_field = np.full((2, 16, 16), 1e300)
+    sim = lbve.Simulation([inst, wl.frm(16, Wi=1.0, Re=1.0, Ma=0.1)])
+    sim.step(5)
+    flags = sim.status()
+    assert flags[0] & 1 and flags[1] == 0
+
+
+def test_fields_on_device(lbve):
+    """lbve_fields into a device tensor equals the host copy."""
+    inst = wl.channel(10, nx=3, Wi=2.0)
+    sim = lbve.Simulation([inst])
+    sim.step(11)
+    np.testing.assert_array_equal(sim.fields_device(0).cpu().numpy(), sim.fields(0))
