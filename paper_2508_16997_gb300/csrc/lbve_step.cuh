@@ -226,6 +226,40 @@ struct PopSource<R, kModeInit> {
   }
 };
 
+// Row offsets of the rows y-1 and y+1 feeding the pull at row y (-1 outside
+// a walled domain).
+__device__ __forceinline__ void neighbour_rows(int y, int nx, int ny, bool py, int& rm, int& rp) {
+  if (py) {
+    rm = (y == 0 ? ny - 1 : y - 1) * nx;
+    rp = (y == ny - 1 ? 0 : y + 1) * nx;
+  } else {
+    rm = y > 0 ? (y - 1) * nx : -1;
+    rp = y < ny - 1 ? (y + 1) * nx : -1;
+  }
+}
+
+// rho, u of node (gx, gy) at the current time: pull (or equilibrium at
+// init), hydro wall completion, moments (eq_ev_f0).
+template <typename R, int MODE>
+__device__ __forceinline__ void node_rho_u(const void* src, const R* __restrict__ force,
+                                           bool ffield, R Fx0, R Fy0, int S, int nx, int ny,
+                                           bool py, int gx, int gy, R& rho, R& ux, R& uy) {
+  const int k = gy * nx + gx;
+  int rm, rp;
+  neighbour_rows(gy, nx, ny, py, rm, rp);
+  const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
+  const R Fx = ffield ? force[k] : Fx0;
+  const R Fy = ffield ? force[S + k] : Fy0;
+  R d[9];
+  PopSource<R, MODE>::hydro(src, S, nx, k, gy * nx, rm, rp, gx, xm, xp, d);
+  if (MODE == kModeStep && !py && (gy == 0 || gy == ny - 1)) zou_he<R>(d, Fx, Fy, gy == 0);
+  HydroM<R> m;
+  hydro_moments<R>(d, m);
+  rho = R(1) + m.drho;
+  ux = (m.jx + R(0.5) * Fx) / rho;
+  uy = (m.jy + R(0.5) * Fy) / rho;
+}
+
 template <typename R, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
     step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles, int parity,
@@ -240,15 +274,96 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int nx = D.nx, ny = D.ny, S = D.stride, TX = D.TX, TY = D.TY, hy = D.hy;
   const bool py = D.periodic_y != 0;
   const void* src = D.pop[parity];
+  const R* __restrict__ srcR = (const R*)src;
   R* __restrict__ dst = (R*)D.pop[parity ^ 1];
   const R* __restrict__ force = (const R*)D.force;
+  R* __restrict__ hist = (R*)D.hist;
   const bool ffield = D.force_field != 0;
   const R Fx0 = (R)D.Fx, Fy0 = (R)D.Fy;
-  const int RW = TX + 2, RH = TY + 2 * hy;
+  const int RW = TX + 2;
 
-  // ---------------- phase A: rho, u on tile + halo -------------------------
-  for (int r = threadIdx.x; r < RW * RH; r += blockDim.x) {
-    const int lx = r % RW, ly = r / RW;
+  // ---- phase A: every load of the thread's own node is issued here, before
+  // the barrier, so that the whole tile's HBM traffic is in flight at once;
+  // rho and u of the node go to shared memory --------------------------------
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const bool in_tile = ty < TY;
+  const int x = T.x0 + tx, y = T.y0 + ty;
+  const bool active = in_tile && (x < nx) && (y < ny);
+  const int ri = (ty + hy) * RW + tx + 1;  // this slot in the halo region
+  const bool wb = active && !py && y == 0, wt = active && !py && y == ny - 1;
+
+  R d[9], g[3][9], So[3], uxo = R(0), uyo = R(0), Fx = Fx0, Fy = Fy0;
+  R post[3][3];  // own outgoing-to-wall post-collision slots (wall rows only)
+  int k = 0;
+  if (active) {
+    k = y * nx + x;
+    int rm, rp;
+    neighbour_rows(y, nx, ny, py, rm, rp);
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int rc = y * nx;
+    PopSource<R, MODE>::hydro(src, S, nx, k, rc, rm, rp, x, xm, xp, d);
+    if (ffield) {
+      Fx = force[k];
+      Fy = force[S + k];
+    }
+#pragma unroll
+    for (int l = 0; l < 3; ++l) PopSource<R, MODE>::cde(src, l, S, nx, k, rc, rm, rp, x, xm, xp, g[l]);
+    if (MODE == kModeStep) {
+      So[0] = hist[k];
+      So[1] = hist[S + k];
+      So[2] = hist[2 * S + k];
+      uxo = hist[3 * S + k];
+      uyo = hist[4 * S + k];
+      if (wb || wt) {
+        // bottom wall: H = {4, 7, 8}; top wall: H = {2, 5, 6}
+        const int h0 = wb ? 4 : 2, h1 = wb ? 7 : 5, h2 = wb ? 8 : 6;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          const R* own = srcR + (size_t)(9 + 9 * l) * S + k;
+          post[l][0] = own[h0 * S];
+          post[l][1] = own[h1 * S];
+          post[l][2] = own[h2 * S];
+        }
+      }
+    }
+    if (MODE == kModeStep && (wb || wt)) zou_he<R>(d, Fx, Fy, wb);
+    HydroM<R> m;
+    hydro_moments<R>(d, m);
+    const R rho = R(1) + m.drho;
+    s_rho[ri] = rho;
+    s_ux[ri] = (m.jx + R(0.5) * Fx) / rho;
+    s_uy[ri] = (m.jy + R(0.5) * Fy) / rho;
+  } else if (in_tile) {
+    // slot outside the domain (ragged tile): it may still be a periodic
+    // neighbour of an active node, so fill it with the wrapped node
+    int gx = x % nx, gy = y;
+    if (py) gy = gy % ny;
+    if (gy < ny) {
+      R r, vx, vy;
+      node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
+      s_rho[ri] = r;
+      s_ux[ri] = vx;
+      s_uy[ri] = vy;
+    }
+  }
+  // halo ring: hy rows above and below, one column left and right
+  const int nring = 2 * hy * RW + 2 * TY;
+  for (int q = threadIdx.x; q < nring; q += blockDim.x) {
+    int lx, ly, qq = q;
+    if (qq < hy * RW) {
+      ly = qq / RW;
+      lx = qq % RW;
+    } else if ((qq -= hy * RW) < hy * RW) {
+      ly = hy + TY + qq / RW;
+      lx = qq % RW;
+    } else if ((qq -= hy * RW) < TY) {
+      lx = 0;
+      ly = hy + qq;
+    } else {
+      qq -= TY;
+      lx = RW - 1;
+      ly = hy + qq;
+    }
     int gx = T.x0 - 1 + lx;
     gx = ((gx % nx) + nx) % nx;
     int gy = T.y0 - hy + ly;
@@ -257,64 +372,24 @@ __global__ void __launch_bounds__(kThreads, 2)
     } else if (gy < 0 || gy >= ny) {
       continue;
     }
-    const int k = gy * nx + gx;
-    const int rc = gy * nx;
-    int rm, rp;
-    if (py) {
-      rm = (gy == 0 ? ny - 1 : gy - 1) * nx;
-      rp = (gy == ny - 1 ? 0 : gy + 1) * nx;
-    } else {
-      rm = gy > 0 ? (gy - 1) * nx : -1;
-      rp = gy < ny - 1 ? (gy + 1) * nx : -1;
-    }
-    const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
-    const R Fx = ffield ? force[k] : Fx0;
-    const R Fy = ffield ? force[S + k] : Fy0;
-    R d[9];
-    PopSource<R, MODE>::hydro(src, S, nx, k, rc, rm, rp, gx, xm, xp, d);
-    if (MODE == kModeStep && !py && (gy == 0 || gy == ny - 1)) zou_he<R>(d, Fx, Fy, gy == 0);
-    HydroM<R> m;
-    hydro_moments<R>(d, m);
-    const R rho = R(1) + m.drho;
-    s_rho[r] = rho;
-    s_ux[r] = (m.jx + R(0.5) * Fx) / rho;
-    s_uy[r] = (m.jy + R(0.5) * Fy) / rho;
+    R r, vx, vy;
+    node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
+    const int rr = ly * RW + lx;
+    s_rho[rr] = r;
+    s_ux[rr] = vx;
+    s_uy[rr] = vy;
   }
   __syncthreads();
 
-  // ---------------- phase B: full update of the tile's nodes ---------------
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int x = T.x0 + tx, y = T.y0 + ty;
-  const bool active = (ty < TY) && (x < nx) && (y < ny);
+  // ---- phase B: full update of the tile's own nodes ------------------------
   const bool final_step = (flags & kFinal) != 0;
   double part[14];
 #pragma unroll
   for (int j = 0; j < 14; ++j) part[j] = 0.0;
 
   if (active) {
-    const int k = y * nx + x;
-    const int rc = y * nx;
-    const bool wb = !py && y == 0, wt = !py && y == ny - 1;
-    int rm, rp;
-    if (py) {
-      rm = (y == 0 ? ny - 1 : y - 1) * nx;
-      rp = (y == ny - 1 ? 0 : y + 1) * nx;
-    } else {
-      rm = y > 0 ? (y - 1) * nx : -1;
-      rp = y < ny - 1 ? (y + 1) * nx : -1;
-    }
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const R Fx = ffield ? force[k] : Fx0;
-    const R Fy = ffield ? force[S + k] : Fy0;
-
-    // hydro populations -> moments
-    R d[9];
-    PopSource<R, MODE>::hydro(src, S, nx, k, rc, rm, rp, x, xm, xp, d);
-    if (MODE == kModeStep && (wb || wt)) zou_he<R>(d, Fx, Fy, wb);
     HydroM<R> hm;
     hydro_moments<R>(d, hm);
-
-    const int ri = (ty + hy) * RW + tx + 1;  // this node in the halo region
     const R rho = s_rho[ri], ux = s_ux[ri], uy = s_uy[ri];
 
     // gradients: grad[g][b] = d_g u_b  (G00 = dx ux, G01 = dx uy, G10 = dy ux, G11 = dy uy)
@@ -344,23 +419,18 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
 
-    // conformation populations -> (completed) -> moments
+    // conformation populations: CNEBB at wall rows, then moments
     CdeM<R> cm[3];
-    const R* srcR = (const R*)src;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      R g[9];
-      PopSource<R, MODE>::cde(src, l, S, nx, k, rc, rm, rp, x, xm, xp, g);
       if (MODE == kModeStep && (wb || wt)) {
-        const R* own = srcR + (size_t)(9 + 9 * l) * S + k;
         const R delta = (l == 1) ? R(0) : R(1);
         double win, wout;
-        if (wb) cnebb<R>(g, own[4 * S], own[7 * S], own[8 * S], delta, ux, uy, true, win, wout);
-        else cnebb<R>(g, own[2 * S], own[5 * S], own[6 * S], delta, ux, uy, false, win, wout);
+        cnebb<R>(g[l], post[l][0], post[l][1], post[l][2], delta, ux, uy, wb, win, wout);
         part[kWallIn + l] += win;
         part[kWallOut + l] += wout;
       }
-      cde_moments<R>(g, cm[l]);
+      cde_moments<R>(g[l], cm[l]);
     }
 
     // conformation tensor, polymer stress (eq_kramer with eqb4), source Phi_ab
@@ -372,17 +442,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     Sc[0] = -cm[0].dphi * il + R(2) * (Axx * G00 + Axy * G10) + Axx * div;
     Sc[1] = -cm[1].dphi * il + (Axx * G01 + Axy * G11) + (Axy * G00 + Ayy * G10) + Axy * div;
     Sc[2] = -cm[2].dphi * il + R(2) * (Axy * G01 + Ayy * G11) + Ayy * div;
-
-    // history of the source term (backward difference of F~, Sec. 3.2)
-    R* __restrict__ hist = (R*)D.hist;
-    R So[3], uxo, uyo;
-    if (MODE == kModeStep) {
-      So[0] = hist[k];
-      So[1] = hist[S + k];
-      So[2] = hist[2 * S + k];
-      uxo = hist[3 * S + k];
-      uyo = hist[4 * S + k];
-    } else {
+    if (MODE != kModeStep) {
+      // first step: the backward difference of the CDE source is zero
       So[0] = Sc[0];
       So[1] = Sc[1];
       So[2] = Sc[2];
@@ -426,7 +487,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         const R Byy = cm[l].pyy - cs2 * cm[l].dphi - phi * uyy;
         const R Bxy = cm[l].pxy - phi * uxy;
         const R s = Sc[l], so = So[l];
-        const R c0p = cm[l].dphi + R(1.5) * s - R(0.5) * so;
+        // small source terms first, one rounding at the magnitude of phi
+        const R c0p = cm[l].dphi + (R(1.5) * s - R(0.5) * so);
         const R pr = phi / rho;
         // (1 - 1/tau_p1) B = -B + ep B, kept split so float32 keeps the tiny
         // difference tau_p1 - 1/2 accurately
