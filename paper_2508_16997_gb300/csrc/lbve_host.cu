@@ -90,21 +90,25 @@ int validate(const lbve_params& p, int i) {
   return LBVE_OK;
 }
 
+// Tile lists: 0 = float64 instances, 1 = float32 instances.
+constexpr int kLists = 2;
+
 struct InstPlan {
   size_t off_pop[2], off_hist, off_force, off_fields;
   int stride, TX, TY, hy, ntx, nty;
-  int list, tile_begin, ntiles;  // position in its precision's tile list
-  int slot_begin;
+  int list;                  // tile list of this instance
+  int tile_begin, ntiles;    // range in the list's tile table
+  int slot_begin, nslots;    // partial-record slots
 };
 
 struct Plan {
   std::vector<InstPlan> inst;
-  size_t off_insts, off_tiles[2], off_partials, off_totals, off_flags, total;
-  int ntiles[2], nslots;
+  size_t off_insts, off_tiles[kLists], off_partials, off_totals, off_flags, total;
+  int ntiles[kLists], nslots;
 };
 
 void tile_shape(const lbve_params& p, int& TX, int& TY, int& hy) {
-  TX = p.nx >= 32 ? 32 : p.nx;
+  TX = p.nx >= kTileTX ? kTileTX : p.nx;
   TY = kThreads / TX;
   hy = p.periodic_y ? 1 : 2;
 }
@@ -113,7 +117,7 @@ Plan make_plan(const lbve_params* p, int n) {
   Plan pl;
   pl.inst.resize(n);
   size_t off = 0;
-  pl.ntiles[0] = pl.ntiles[1] = 0;
+  for (int l = 0; l < kLists; ++l) pl.ntiles[l] = 0;
   for (int i = 0; i < n; ++i) {
     InstPlan& q = pl.inst[i];
     const size_t es = p[i].precision == LBVE_FP64 ? 8 : 4;
@@ -131,22 +135,26 @@ Plan make_plan(const lbve_params* p, int n) {
     q.off_fields = off;
     off = align_up(off + 6 * size_t(q.stride) * 8, kAlign);
     tile_shape(p[i], q.TX, q.TY, q.hy);
+    q.list = p[i].precision == LBVE_FP64 ? 0 : 1;
     q.ntx = (p[i].nx + q.TX - 1) / q.TX;
     q.nty = (p[i].ny + q.TY - 1) / q.TY;
-    q.list = p[i].precision == LBVE_FP64 ? 0 : 1;
     q.tile_begin = pl.ntiles[q.list];
     q.ntiles = q.ntx * q.nty;
     pl.ntiles[q.list] += q.ntiles;
   }
-  // partial-record slots: list 0 tiles first, then list 1
-  pl.nslots = pl.ntiles[0] + pl.ntiles[1];
+  // partial-record slots: [list 0 | list 1]
+  pl.nslots = 0;
+  for (int l = 0; l < kLists; ++l) pl.nslots += pl.ntiles[l];
   for (int i = 0; i < n; ++i) {
     InstPlan& q = pl.inst[i];
-    q.slot_begin = (q.list == 0 ? 0 : pl.ntiles[0]) + q.tile_begin;
+    int base = 0;
+    for (int l = 0; l < q.list; ++l) base += pl.ntiles[l];
+    q.slot_begin = base + q.tile_begin;
+    q.nslots = q.ntiles;
   }
   pl.off_insts = off;
   off = align_up(off + sizeof(InstDev) * n, kAlign);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = 0; l < kLists; ++l) {
     pl.off_tiles[l] = off;
     off = align_up(off + sizeof(TileDev) * std::max(pl.ntiles[l], 1), kAlign);
   }
@@ -171,7 +179,7 @@ struct lbve_handle {
   cudaStream_t stream = nullptr;
   std::vector<InstDev> insts;
   InstDev* d_insts = nullptr;
-  TileDev* d_tiles[2] = {nullptr, nullptr};
+  TileDev* d_tiles[kLists] = {nullptr, nullptr};
   double* d_partials = nullptr;
   double* d_totals = nullptr;
   int32_t* d_flags = nullptr;
@@ -236,17 +244,15 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
   h->ready.assign(n, 0);
   const Plan& pl = h->plan;
   h->d_insts = (InstDev*)(h->ws + pl.off_insts);
-  h->d_tiles[0] = (TileDev*)(h->ws + pl.off_tiles[0]);
-  h->d_tiles[1] = (TileDev*)(h->ws + pl.off_tiles[1]);
+  for (int l = 0; l < kLists; ++l) h->d_tiles[l] = (TileDev*)(h->ws + pl.off_tiles[l]);
   h->d_partials = (double*)(h->ws + pl.off_partials);
   h->d_totals = (double*)(h->ws + pl.off_totals);
   h->d_flags = (int32_t*)(h->ws + pl.off_flags);
 
   h->insts.resize(n);
   h->c.resize(n);
-  std::vector<TileDev> tiles[2];
-  tiles[0].resize(pl.ntiles[0]);
-  tiles[1].resize(pl.ntiles[1]);
+  std::vector<TileDev> tiles[kLists];
+  for (int l = 0; l < kLists; ++l) tiles[l].resize(pl.ntiles[l]);
   for (int i = 0; i < n; ++i) {
     const InstPlan& q = pl.inst[i];
     const Coeffs c = derive(p[i]);
@@ -267,20 +273,21 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     D.hy = q.hy;
     D.force_field = 0;
     D.slot_begin = q.slot_begin;
-    D.slot_end = q.slot_begin + q.ntiles;
+    D.slot_end = q.slot_begin + q.nslots;
     D.prec = p[i].precision;
-    D.Fx = p[i].Fx;
-    D.Fy = p[i].Fy;
     D.inv_Uc = 1.0 / c.Uc;
-    D.c_s1 = 1.0 - 1.0 / c.tau_s1;
-    D.c_s2 = 1.0 - 1.0 / c.tau_s2;
-    D.h_s1 = (c.tau_s1 - 0.5) / c.tau_s1;
-    D.w_s1 = 1.0 / c.tau_s1;
-    D.ep_p1 = 2.0 - 1.0 / c.tau_p1;
-    D.c_p2 = 1.0 - 1.0 / c.tau_p2;
-    D.h_p1 = (c.tau_p1 - 0.5) / c.tau_p1;
-    D.inv_lambda = 1.0 / c.lambda;
-    D.mup_over_lambda = c.mup / c.lambda;
+    D.cd[kCoefFx] = p[i].Fx;
+    D.cd[kCoefFy] = p[i].Fy;
+    D.cd[kCoefCs1] = 1.0 - 1.0 / c.tau_s1;
+    D.cd[kCoefCs2] = 1.0 - 1.0 / c.tau_s2;
+    D.cd[kCoefHs1] = (c.tau_s1 - 0.5) / c.tau_s1;
+    D.cd[kCoefWs1] = 1.0 / c.tau_s1;
+    D.cd[kCoefEp1] = 2.0 - 1.0 / c.tau_p1;
+    D.cd[kCoefCp2] = 1.0 - 1.0 / c.tau_p2;
+    D.cd[kCoefHp1] = (c.tau_p1 - 0.5) / c.tau_p1;
+    D.cd[kCoefInvLam] = 1.0 / c.lambda;
+    D.cd[kCoefMupLam] = c.mup / c.lambda;
+    for (int j = 0; j < kNumCoef; ++j) D.cf[j] = (float)D.cd[j];
     int k = q.tile_begin;
     for (int ty = 0; ty < q.nty; ++ty)
       for (int tx = 0; tx < q.ntx; ++tx) {
@@ -296,7 +303,7 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
   // out of scope as soon as the calls return.
   e = cudaMemcpyAsync(h->d_insts, h->insts.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice,
                       h->stream);
-  for (int l = 0; l < 2 && e == cudaSuccess; ++l)
+  for (int l = 0; l < kLists && e == cudaSuccess; ++l)
     if (!tiles[l].empty())
       e = cudaMemcpyAsync(h->d_tiles[l], tiles[l].data(), sizeof(TileDev) * tiles[l].size(),
                           cudaMemcpyHostToDevice, h->stream);
@@ -381,12 +388,11 @@ int lbve_step(lbve_handle* h, int64_t n_steps) {
     if (!h->ready[i]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", i);
   for (int64_t s = 0; s < n_steps; ++s) {
     const int flags = (s == n_steps - 1) ? kFinal : 0;
-    for (int l = 0; l < 2; ++l) {
-      if (h->plan.ntiles[l] == 0) continue;
-      if (launch_step(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_tiles[l],
+    for (int l = 0; l < kLists; ++l)
+      if (h->plan.ntiles[l] > 0 &&
+          launch_step(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_tiles[l],
                       h->plan.ntiles[l], h->parity, kModeStep, flags, h->d_partials, h->stream))
         return cuda_fail(cudaGetLastError(), "step kernel launch");
-    }
     h->parity ^= 1;
   }
   if (n_steps > 0) {

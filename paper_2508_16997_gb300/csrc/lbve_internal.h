@@ -5,8 +5,16 @@
 
 namespace lbve {
 
-constexpr int kThreads = 256;     // threads per CTA of the step kernel
-constexpr int kRegionMax = 800;   // (TX+2)(TY+2*hy) upper bound for TX*TY <= 256
+#ifndef LBVE_THREADS
+#define LBVE_THREADS 256
+#endif
+#ifndef LBVE_TILE_TX
+#define LBVE_TILE_TX 32
+#endif
+constexpr int kThreads = LBVE_THREADS;  // threads per CTA of the step kernel
+constexpr int kTileTX = LBVE_TILE_TX;   // tile width (nodes along x) for nx >= kTileTX
+// (TX+2)(TY+2*hy) <= 3 (kThreads + 4) for every TX >= 1, TY = kThreads / TX, hy <= 2
+constexpr int kRegionMax = 3 * (kThreads + 4);
 constexpr int kPartial = 16;      // doubles per tile partial record
 constexpr int kTotals = 16;       // doubles per instance totals record
 
@@ -21,6 +29,21 @@ enum : int {
 // Kernel flags.
 enum : int { kFinal = 1 };
 
+// Coefficient slots of InstDev::cd / InstDev::cf.
+enum : int {
+  kCoefFx = 0, kCoefFy,
+  kCoefCs1,     // 1 - 1/tau_s1
+  kCoefCs2,     // 1 - 1/tau_s2
+  kCoefHs1,     // 1 - 1/(2 tau_s1)
+  kCoefWs1,     // 1/tau_s1
+  kCoefEp1,     // 2 - 1/tau_p1, so that 1 - 1/tau_p1 = ep - 1
+  kCoefCp2,     // 1 - 1/tau_p2
+  kCoefHp1,     // 1 - 1/(2 tau_p1)
+  kCoefInvLam,  // 1/lambda
+  kCoefMupLam,  // mu_p/lambda
+  kNumCoef
+};
+
 // Everything a CTA needs about its instance.  Pointers are device addresses
 // inside the caller's workspace.  Coefficients are derived in float64 on
 // the host (Sec. 3.1-3.2 relaxation-time relations) and rounded once.
@@ -33,16 +56,11 @@ struct InstDev {
   int32_t TX, TY, hy, force_field;
   int32_t slot_begin, slot_end;  // partial-record slots of this instance
   int32_t prec, pad;
-  double Fx, Fy, inv_Uc;
-  double c_s1;    // 1 - 1/tau_s1
-  double c_s2;    // 1 - 1/tau_s2
-  double h_s1;    // 1 - 1/(2 tau_s1)
-  double w_s1;    // 1/tau_s1
-  double ep_p1;   // 2 - 1/tau_p1, so that 1 - 1/tau_p1 = ep_p1 - 1
-  double c_p2;    // 1 - 1/tau_p2
-  double h_p1;    // 1 - 1/(2 tau_p1)
-  double inv_lambda;
-  double mup_over_lambda;
+  double inv_Uc;
+  // Collision coefficients, in float64 and rounded once to float32, so that
+  // neither kernel converts precision per node.
+  double cd[16];
+  float cf[16];
 };
 
 // One tile of one instance: {instance, x0, y0, partial slot}.

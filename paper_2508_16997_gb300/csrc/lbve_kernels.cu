@@ -7,16 +7,23 @@
 
 namespace lbve {
 
+template <typename R, int MODE, bool FINAL>
+static void launch_step_k(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
+                          double* d_partials, cudaStream_t st) {
+  step_kernel<R, MODE, FINAL><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, parity, d_partials);
+}
+
 template <typename R>
 static int launch_step_t(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
                          int mode, int flags, double* d_partials, cudaStream_t st) {
   if (n_tiles <= 0) return 0;
-  if (mode == kModeStep)
-    step_kernel<R, kModeStep><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, parity, flags,
-                                                             d_partials);
-  else
-    step_kernel<R, kModeInit><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, parity, flags,
-                                                             d_partials);
+  const bool fin = (flags & kFinal) != 0;
+  if (mode == kModeStep) {
+    if (fin) launch_step_k<R, kModeStep, true>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
+    else launch_step_k<R, kModeStep, false>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
+  } else {
+    launch_step_k<R, kModeInit, true>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -30,6 +30,10 @@
 
 #include "lbve_internal.h"
 
+#ifndef LBVE_FP32_MIN_BLOCKS
+#define LBVE_FP32_MIN_BLOCKS 3
+#endif
+
 namespace lbve {
 
 template <typename R>
@@ -260,10 +264,208 @@ __device__ __forceinline__ void node_rho_u(const void* src, const R* __restrict_
   uy = (m.jy + R(0.5) * Fy) / rho;
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+template <typename R>
+__device__ __forceinline__ R coef(const InstDev& D, int i);
+template <>
+__device__ __forceinline__ double coef<double>(const InstDev& D, int i) {
+  return D.cd[i];
+}
+template <>
+__device__ __forceinline__ float coef<float>(const InstDev& D, int i) {
+  return D.cf[i];
+}
+
+// Position of halo-ring slot q in the (TX+2) x (TY+2hy) region: hy rows
+// above, hy rows below, one column left and one right of the tile.
+__device__ __forceinline__ void ring_slot(int q, int RW, int TY, int hy, int& lx, int& ly) {
+  if (q < hy * RW) {
+    ly = q / RW;
+    lx = q % RW;
+  } else if ((q -= hy * RW) < hy * RW) {
+    ly = hy + TY + q / RW;
+    lx = q % RW;
+  } else if ((q -= hy * RW) < TY) {
+    lx = 0;
+    ly = hy + q;
+  } else {
+    lx = RW - 1;
+    ly = hy + q - TY;
+  }
+}
+
+// Global node of region slot (lx, ly); false if it lies outside a walled domain.
+__device__ __forceinline__ bool region_node(int lx, int ly, int x0, int y0, int hy, int nx,
+                                            int ny, bool py, int& gx, int& gy) {
+  gx = x0 - 1 + lx;
+  gx = ((gx % nx) + nx) % nx;
+  gy = y0 - hy + ly;
+  if (py) {
+    gy = ((gy % ny) + ny) % ny;
+    return true;
+  }
+  return gy >= 0 && gy < ny;
+}
+
+// Source, both collisions, stores and final-step bookkeeping of one node
+// whose populations are already reduced to (wall-completed) moments:
+//   hm      raw hydro moments, cm[3] raw conformation moments
+//   rho, u  eq_ev_f0 moments; G** = d_g u_b; dPx, dPy = d_x(rho ux^3), d_y(rho uy^3)
+//   So, uo  source and velocity of the previous step (ignored at init)
+// Writes the 36 post-collision populations and the 5 history values of node k;
+// on the final step also the float64 fields and this node's partial sums.
+template <typename R, int MODE, bool FINAL>
+__device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* __restrict__ dst,
+                                             R* __restrict__ hist, const HydroM<R>& hm,
+                                             const CdeM<R>* cm, R rho, R ux, R uy, R G00, R G01,
+                                             R G10, R G11, R dPx, R dPy, R Fx, R Fy, R So0,
+                                             R So1, R So2, R uxo, R uyo, double* part) {
+  // conformation tensor, polymer stress (eq_kramer with eqb4), source Phi_ab
+  const R Axx = R(1) + cm[0].dphi, Axy = cm[1].dphi, Ayy = R(1) + cm[2].dphi;
+  const R mpl = coef<R>(D, kCoefMupLam), il = coef<R>(D, kCoefInvLam);
+  const R txx = mpl * cm[0].dphi, txy = mpl * cm[1].dphi, tyy = mpl * cm[2].dphi;
+  const R div = G00 + G11;
+  R Sc[3], So[3] = {So0, So1, So2};
+  Sc[0] = -cm[0].dphi * il + R(2) * (Axx * G00 + Axy * G10) + Axx * div;
+  Sc[1] = -cm[1].dphi * il + (Axx * G01 + Axy * G11) + (Axy * G00 + Ayy * G10) + Axy * div;
+  Sc[2] = -cm[2].dphi * il + R(2) * (Axy * G01 + Ayy * G11) + Ayy * div;
+  if (MODE != kModeStep) {
+    // first step: the backward difference of the CDE source is zero
+    So[0] = Sc[0];
+    So[1] = Sc[1];
+    So[2] = Sc[2];
+    uxo = ux;
+    uyo = uy;
+  }
+
+  // ---- hydrodynamic TRT-RLB collision (eq_ev_f, eq4, eq5, eq6, F_i) ----
+  {
+    const R cs2 = R(1.0 / 3.0);
+    const R c1 = coef<R>(D, kCoefCs1), c2 = coef<R>(D, kCoefCs2);
+    const R h1 = coef<R>(D, kCoefHs1), w1 = coef<R>(D, kCoefWs1);
+    const R ruxx = rho * ux * ux, ruyy = rho * uy * uy, ruxy = rho * ux * uy;
+    const R ruxxy = ruxx * uy, ruxyy = ruxy * uy;
+    const R nxx = hm.pxx - cs2 * hm.drho - ruxx;  // A_xx^neq
+    const R nyy = hm.pyy - cs2 * hm.drho - ruyy;  // A_yy^neq
+    const R nxy = hm.pxy - ruxy;                  // A_xy^neq
+    const R nxxy = hm.qxxy - cs2 * hm.jy - ruxxy; // A_xxy^neq
+    const R nxyy = hm.qxyy - cs2 * hm.jx - ruxyy; // A_xyy^neq
+    const R bx = hm.jx + Fx, by = hm.jy + Fy;     // rho u + (1-1/tau)A_a + F-term
+    const R bxx = ruxx + c1 * nxx - h1 * dPx - w1 * txx;
+    const R byy = ruyy + c1 * nyy - h1 * dPy - w1 * tyy;
+    const R bxy = ruxy + c1 * nxy - w1 * txy;
+    const R bxxy = ruxxy + c2 * nxxy;
+    const R bxyy = ruxyy + c2 * nxyy;
+    R out[9];
+    reconstruct<R>(hm.drho, bx, by, bxx, byy, bxy, bxxy, bxyy, out);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dst[(size_t)i * S + k] = out[i];
+  }
+
+  // ---- three conformation TRT-RLB collisions (eq_g0) ----
+  {
+    const R cs2 = R(1.0 / 3.0);
+    const R ep = coef<R>(D, kCoefEp1), c2 = coef<R>(D, kCoefCp2), h1 = coef<R>(D, kCoefHp1);
+    const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const R phi = (l == 1 ? R(0) : R(1)) + cm[l].dphi;
+      const R Bx = cm[l].jx - phi * ux, By = cm[l].jy - phi * uy;
+      const R Bxx = cm[l].pxx - cs2 * cm[l].dphi - phi * uxx;
+      const R Byy = cm[l].pyy - cs2 * cm[l].dphi - phi * uyy;
+      const R Bxy = cm[l].pxy - phi * uxy;
+      const R sl = Sc[l], so = So[l];
+      // small source terms first, one rounding at the magnitude of phi
+      const R c0p = cm[l].dphi + (R(1.5) * sl - R(0.5) * so);
+      const R pr = phi / rho;
+      // (1 - 1/tau_p1) B = -B + ep B, kept split so float32 keeps the tiny
+      // difference tau_p1 - 1/2 accurately
+      const R cx = (phi * ux - Bx) + ep * Bx + h1 * (pr * Fx + ux * sl) +
+                   R(0.5) * h1 * (ux * sl - uxo * so);
+      const R cy = (phi * uy - By) + ep * By + h1 * (pr * Fy + uy * sl) +
+                   R(0.5) * h1 * (uy * sl - uyo * so);
+      const R cxx = phi * uxx + c2 * Bxx;
+      const R cyy = phi * uyy + c2 * Byy;
+      const R cxy = phi * uxy + c2 * Bxy;
+      R out[9];
+      reconstruct<R>(c0p, cx, cy, cxx, cyy, cxy, R(0), R(0), out);
+      R* dl = dst + (size_t)(9 + 9 * l) * S;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) dl[(size_t)i * S + k] = out[i];
+    }
+  }
+
+  hist[k] = Sc[0];
+  hist[S + k] = Sc[1];
+  hist[2 * S + k] = Sc[2];
+  hist[3 * S + k] = ux;
+  hist[4 * S + k] = uy;
+
+  if (FINAL) {
+    double* fl = D.fields;
+    const double r = 1.0 + (double)hm.drho;
+    const double vx = (double)ux, vy = (double)uy;
+    const double axx = 1.0 + (double)cm[0].dphi, axy = (double)cm[1].dphi,
+                 ayy = 1.0 + (double)cm[2].dphi;
+    // residual against the fields of the previous final step (none at init)
+    const double res = (MODE == kModeStep)
+                           ? fmax(fabs(vx - fl[S + k]), fabs(vy - fl[2 * S + k])) * D.inv_Uc
+                           : 0.0;
+    fl[k] = r;
+    fl[S + k] = vx;
+    fl[2 * S + k] = vy;
+    fl[3 * S + k] = axx;
+    fl[4 * S + k] = axy;
+    fl[5 * S + k] = ayy;
+    part[kSumRho] += r;
+    part[kSumJx] += (double)rho * vx;
+    part[kSumJy] += (double)rho * vy;
+    part[kSumPhi + 0] += axx;
+    part[kSumPhi + 1] += axy;
+    part[kSumPhi + 2] += ayy;
+    const bool finite = isfinite(r) && isfinite(vx) && isfinite(vy) && isfinite(axx) &&
+                        isfinite(axy) && isfinite(ayy);
+    part[kResid] = fmax(part[kResid], finite ? res : 0.0);
+    part[kNonFinite] += finite ? 0.0 : 1.0;
+  }
+}
+
+// Second-order differences in y of u and rho u_y^3 at a node, from the
+// moments of rows y-2..y+2 (central inside, one-sided on wall rows).
+template <typename R>
+__device__ __forceinline__ void y_gradients(bool wb, bool wt, R rm2, R uxm2, R uym2, R rm1,
+                                            R uxm1, R uym1, R r0, R ux0, R uy0, R rp1, R uxp1,
+                                            R uyp1, R rp2, R uxp2, R uyp2, R& G10, R& G11,
+                                            R& dPy) {
+  const R half = R(0.5);
+  if (wb) {
+    G10 = half * (R(-3) * ux0 + R(4) * uxp1 - uxp2);
+    G11 = half * (R(-3) * uy0 + R(4) * uyp1 - uyp2);
+    dPy = half * (R(-3) * (r0 * uy0 * uy0 * uy0) + R(4) * (rp1 * uyp1 * uyp1 * uyp1) -
+                  rp2 * uyp2 * uyp2 * uyp2);
+  } else if (wt) {
+    G10 = half * (R(3) * ux0 - R(4) * uxm1 + uxm2);
+    G11 = half * (R(3) * uy0 - R(4) * uym1 + uym2);
+    dPy = half * (R(3) * (r0 * uy0 * uy0 * uy0) - R(4) * (rm1 * uym1 * uym1 * uym1) +
+                  rm2 * uym2 * uym2 * uym2);
+  } else {
+    G10 = half * (uxp1 - uxm1);
+    G11 = half * (uyp1 - uym1);
+    dPy = half * (rp1 * uyp1 * uyp1 * uyp1 - rm1 * uym1 * uym1 * uym1);
+  }
+}
+
+// Resident CTAs per SM the register budget is sized for: the float32 step
+// is HBM-bound and wants more loads in flight; the float64 step is bound by
+// the FP64 pipe.
+template <typename R>
+struct MinBlocks {
+  static constexpr int value = sizeof(R) == 4 ? LBVE_FP32_MIN_BLOCKS : (kThreads <= 256 ? 2 : 1);
+};
+
+template <typename R, int MODE, bool FINAL>
+__global__ void __launch_bounds__(kThreads, MinBlocks<R>::value)
     step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles, int parity,
-                int flags, double* __restrict__ partials) {
+                double* __restrict__ partials) {
   __shared__ R s_rho[kRegionMax];
   __shared__ R s_ux[kRegionMax];
   __shared__ R s_uy[kRegionMax];
@@ -279,20 +481,40 @@ __global__ void __launch_bounds__(kThreads, 2)
   const R* __restrict__ force = (const R*)D.force;
   R* __restrict__ hist = (R*)D.hist;
   const bool ffield = D.force_field != 0;
-  const R Fx0 = (R)D.Fx, Fy0 = (R)D.Fy;
+  const R Fx0 = coef<R>(D, kCoefFx), Fy0 = coef<R>(D, kCoefFy);
   const int RW = TX + 2;
 
-  // ---- phase A: every load of the thread's own node is issued here, before
-  // the barrier, so that the whole tile's HBM traffic is in flight at once;
-  // rho and u of the node go to shared memory --------------------------------
+  // ---- phase A --------------------------------------------------------------
+  // Every load this thread needs -- one halo-ring node's hydro populations
+  // and all of its own node's populations, history and force -- is issued
+  // before any of them is used, so the tile's whole HBM traffic is in flight
+  // together.  Own hydro and conformation populations are then reduced to
+  // moments (walls completed first); rho and u go to shared memory.
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const bool in_tile = ty < TY;
   const int x = T.x0 + tx, y = T.y0 + ty;
   const bool active = in_tile && (x < nx) && (y < ny);
   const int ri = (ty + hy) * RW + tx + 1;  // this slot in the halo region
   const bool wb = active && !py && y == 0, wt = active && !py && y == ny - 1;
+  const int nring = 2 * hy * RW + 2 * TY;
 
-  R d[9], g[3][9], So[3], uxo = R(0), uyo = R(0), Fx = Fx0, Fy = Fy0;
+  // (1) first halo-ring node of this thread: issue its pull
+  int ring_r = -1, rgx = 0, rgy = 0;
+  R dr[9];
+  if (threadIdx.x < nring) {
+    int lx, ly;
+    ring_slot(threadIdx.x, RW, TY, hy, lx, ly);
+    if (region_node(lx, ly, T.x0, T.y0, hy, nx, ny, py, rgx, rgy)) {
+      ring_r = ly * RW + lx;
+      int rm, rp;
+      neighbour_rows(rgy, nx, ny, py, rm, rp);
+      const int xm = rgx == 0 ? nx - 1 : rgx - 1, xp = rgx == nx - 1 ? 0 : rgx + 1;
+      PopSource<R, MODE>::hydro(src, S, nx, rgy * nx + rgx, rgy * nx, rm, rp, rgx, xm, xp, dr);
+    }
+  }
+
+  // (2) own node: all 36 populations, force, history, wall slots
+  R d[9], g[3][9], So[3] = {R(0), R(0), R(0)}, uxo = R(0), uyo = R(0), Fx = Fx0, Fy = Fy0;
   R post[3][3];  // own outgoing-to-wall post-collision slots (wall rows only)
   int k = 0;
   if (active) {
@@ -326,18 +548,49 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       }
     }
-    if (MODE == kModeStep && (wb || wt)) zou_he<R>(d, Fx, Fy, wb);
+  }
+
+  // (3) ring node moments
+  if (ring_r >= 0) {
+    const int rk = rgy * nx + rgx;
+    const R rFx = ffield ? force[rk] : Fx0;
+    const R rFy = ffield ? force[S + rk] : Fy0;
+    if (MODE == kModeStep && !py && (rgy == 0 || rgy == ny - 1)) zou_he<R>(dr, rFx, rFy, rgy == 0);
     HydroM<R> m;
-    hydro_moments<R>(d, m);
+    hydro_moments<R>(dr, m);
     const R rho = R(1) + m.drho;
+    s_rho[ring_r] = rho;
+    s_ux[ring_r] = (m.jx + R(0.5) * rFx) / rho;
+    s_uy[ring_r] = (m.jy + R(0.5) * rFy) / rho;
+  }
+
+  // (4) own moments; conformation walls completed with the node's own u
+  HydroM<R> hm;
+  CdeM<R> cm[3];
+  R rho = R(1), ux = R(0), uy = R(0);
+  double wall_io[6] = {0, 0, 0, 0, 0, 0};
+  if (active) {
+    if (MODE == kModeStep && (wb || wt)) zou_he<R>(d, Fx, Fy, wb);
+    hydro_moments<R>(d, hm);
+    rho = R(1) + hm.drho;
+    ux = (hm.jx + R(0.5) * Fx) / rho;
+    uy = (hm.jy + R(0.5) * Fy) / rho;
     s_rho[ri] = rho;
-    s_ux[ri] = (m.jx + R(0.5) * Fx) / rho;
-    s_uy[ri] = (m.jy + R(0.5) * Fy) / rho;
+    s_ux[ri] = ux;
+    s_uy[ri] = uy;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      if (MODE == kModeStep && (wb || wt)) {
+        const R delta = (l == 1) ? R(0) : R(1);
+        cnebb<R>(g[l], post[l][0], post[l][1], post[l][2], delta, ux, uy, wb, wall_io[l],
+                 wall_io[3 + l]);
+      }
+      cde_moments<R>(g[l], cm[l]);
+    }
   } else if (in_tile) {
     // slot outside the domain (ragged tile): it may still be a periodic
     // neighbour of an active node, so fill it with the wrapped node
-    int gx = x % nx, gy = y;
-    if (py) gy = gy % ny;
+    const int gx = x % nx, gy = py ? y % ny : y;
     if (gy < ny) {
       R r, vx, vy;
       node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
@@ -346,32 +599,12 @@ __global__ void __launch_bounds__(kThreads, 2)
       s_uy[ri] = vy;
     }
   }
-  // halo ring: hy rows above and below, one column left and right
-  const int nring = 2 * hy * RW + 2 * TY;
-  for (int q = threadIdx.x; q < nring; q += blockDim.x) {
-    int lx, ly, qq = q;
-    if (qq < hy * RW) {
-      ly = qq / RW;
-      lx = qq % RW;
-    } else if ((qq -= hy * RW) < hy * RW) {
-      ly = hy + TY + qq / RW;
-      lx = qq % RW;
-    } else if ((qq -= hy * RW) < TY) {
-      lx = 0;
-      ly = hy + qq;
-    } else {
-      qq -= TY;
-      lx = RW - 1;
-      ly = hy + qq;
-    }
-    int gx = T.x0 - 1 + lx;
-    gx = ((gx % nx) + nx) % nx;
-    int gy = T.y0 - hy + ly;
-    if (py) {
-      gy = ((gy % ny) + ny) % ny;
-    } else if (gy < 0 || gy >= ny) {
-      continue;
-    }
+
+  // (5) remaining ring nodes (only when the ring outnumbers the threads)
+  for (int q = threadIdx.x + blockDim.x; q < nring; q += blockDim.x) {
+    int lx, ly, gx, gy;
+    ring_slot(q, RW, TY, hy, lx, ly);
+    if (!region_node(lx, ly, T.x0, T.y0, hy, nx, ny, py, gx, gy)) continue;
     R r, vx, vy;
     node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
     const int rr = ly * RW + lx;
@@ -381,17 +614,12 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   __syncthreads();
 
-  // ---- phase B: full update of the tile's own nodes ------------------------
-  const bool final_step = (flags & kFinal) != 0;
-  double part[14];
+  // ---- phase B: gradients, source, collisions, stores ----------------------
+  double part[FINAL ? 14 : 1];
 #pragma unroll
-  for (int j = 0; j < 14; ++j) part[j] = 0.0;
+  for (int j = 0; j < (FINAL ? 14 : 1); ++j) part[j] = 0.0;
 
   if (active) {
-    HydroM<R> hm;
-    hydro_moments<R>(d, hm);
-    const R rho = s_rho[ri], ux = s_ux[ri], uy = s_uy[ri];
-
     // gradients: grad[g][b] = d_g u_b  (G00 = dx ux, G01 = dx uy, G10 = dy ux, G11 = dy uy)
     const R half = R(0.5);
     const R G00 = half * (s_ux[ri + 1] - s_ux[ri - 1]);
@@ -401,148 +629,21 @@ __global__ void __launch_bounds__(kThreads, 2)
     const R dPx = half * (cxp - cxm);
     R G10, G11, dPy;
     {
-      auto cy = [&](int j) { return s_rho[j] * s_uy[j] * s_uy[j] * s_uy[j]; };
-      if (wb) {
-        const int j1 = ri + RW, j2 = ri + 2 * RW;
-        G10 = half * (R(-3) * s_ux[ri] + R(4) * s_ux[j1] - s_ux[j2]);
-        G11 = half * (R(-3) * s_uy[ri] + R(4) * s_uy[j1] - s_uy[j2]);
-        dPy = half * (R(-3) * cy(ri) + R(4) * cy(j1) - cy(j2));
-      } else if (wt) {
-        const int j1 = ri - RW, j2 = ri - 2 * RW;
-        G10 = half * (R(3) * s_ux[ri] - R(4) * s_ux[j1] + s_ux[j2]);
-        G11 = half * (R(3) * s_uy[ri] - R(4) * s_uy[j1] + s_uy[j2]);
-        dPy = half * (R(3) * cy(ri) - R(4) * cy(j1) + cy(j2));
-      } else {
-        G10 = half * (s_ux[ri + RW] - s_ux[ri - RW]);
-        G11 = half * (s_uy[ri + RW] - s_uy[ri - RW]);
-        dPy = half * (cy(ri + RW) - cy(ri - RW));
-      }
+      // rows y-2..y+2 of this column (only those a wall row needs are read)
+      const int a = wb ? ri : (wt ? ri - 2 * RW : ri), b = wb ? ri : (wt ? ri - RW : ri - RW);
+      const int c = wb ? ri + RW : (wt ? ri : ri + RW), e = wb ? ri + 2 * RW : ri;
+      y_gradients<R>(wb, wt, s_rho[a], s_ux[a], s_uy[a], s_rho[b], s_ux[b], s_uy[b], rho, ux,
+                     uy, s_rho[c], s_ux[c], s_uy[c], s_rho[e], s_ux[e], s_uy[e], G10, G11, dPy);
     }
-
-    // conformation populations: CNEBB at wall rows, then moments
-    CdeM<R> cm[3];
+    if (FINAL) {
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      if (MODE == kModeStep && (wb || wt)) {
-        const R delta = (l == 1) ? R(0) : R(1);
-        double win, wout;
-        cnebb<R>(g[l], post[l][0], post[l][1], post[l][2], delta, ux, uy, wb, win, wout);
-        part[kWallIn + l] += win;
-        part[kWallOut + l] += wout;
-      }
-      cde_moments<R>(g[l], cm[l]);
+      for (int j = 0; j < 6; ++j) part[kWallIn + j] = wall_io[j];
     }
-
-    // conformation tensor, polymer stress (eq_kramer with eqb4), source Phi_ab
-    const R Axx = R(1) + cm[0].dphi, Axy = cm[1].dphi, Ayy = R(1) + cm[2].dphi;
-    const R mpl = (R)D.mup_over_lambda, il = (R)D.inv_lambda;
-    const R txx = mpl * cm[0].dphi, txy = mpl * cm[1].dphi, tyy = mpl * cm[2].dphi;
-    const R div = G00 + G11;
-    R Sc[3];
-    Sc[0] = -cm[0].dphi * il + R(2) * (Axx * G00 + Axy * G10) + Axx * div;
-    Sc[1] = -cm[1].dphi * il + (Axx * G01 + Axy * G11) + (Axy * G00 + Ayy * G10) + Axy * div;
-    Sc[2] = -cm[2].dphi * il + R(2) * (Axy * G01 + Ayy * G11) + Ayy * div;
-    if (MODE != kModeStep) {
-      // first step: the backward difference of the CDE source is zero
-      So[0] = Sc[0];
-      So[1] = Sc[1];
-      So[2] = Sc[2];
-      uxo = ux;
-      uyo = uy;
-    }
-
-    // ---- hydrodynamic TRT-RLB collision (eq_ev_f, eq4, eq5, eq6, F_i) ----
-    {
-      const R cs2 = R(1.0 / 3.0);
-      const R c1 = (R)D.c_s1, c2 = (R)D.c_s2, h1 = (R)D.h_s1, w1 = (R)D.w_s1;
-      const R ruxx = rho * ux * ux, ruyy = rho * uy * uy, ruxy = rho * ux * uy;
-      const R ruxxy = ruxx * uy, ruxyy = ruxy * uy;
-      const R nxx = hm.pxx - cs2 * hm.drho - ruxx;  // A_xx^neq
-      const R nyy = hm.pyy - cs2 * hm.drho - ruyy;  // A_yy^neq
-      const R nxy = hm.pxy - ruxy;                  // A_xy^neq
-      const R nxxy = hm.qxxy - cs2 * hm.jy - ruxxy; // A_xxy^neq
-      const R nxyy = hm.qxyy - cs2 * hm.jx - ruxyy; // A_xyy^neq
-      const R bx = hm.jx + Fx, by = hm.jy + Fy;     // rho u + (1-1/tau)A_a + F-term
-      const R bxx = ruxx + c1 * nxx - h1 * dPx - w1 * txx;
-      const R byy = ruyy + c1 * nyy - h1 * dPy - w1 * tyy;
-      const R bxy = ruxy + c1 * nxy - w1 * txy;
-      const R bxxy = ruxxy + c2 * nxxy;
-      const R bxyy = ruxyy + c2 * nxyy;
-      R out[9];
-      reconstruct<R>(hm.drho, bx, by, bxx, byy, bxy, bxxy, bxyy, out);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) dst[(size_t)i * S + k] = out[i];
-    }
-
-    // ---- three conformation TRT-RLB collisions (eq_g0) ----
-    {
-      const R cs2 = R(1.0 / 3.0);
-      const R ep = (R)D.ep_p1, c2 = (R)D.c_p2, h1 = (R)D.h_p1;
-      const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
-#pragma unroll
-      for (int l = 0; l < 3; ++l) {
-        const R phi = (l == 1 ? R(0) : R(1)) + cm[l].dphi;
-        const R Bx = cm[l].jx - phi * ux, By = cm[l].jy - phi * uy;
-        const R Bxx = cm[l].pxx - cs2 * cm[l].dphi - phi * uxx;
-        const R Byy = cm[l].pyy - cs2 * cm[l].dphi - phi * uyy;
-        const R Bxy = cm[l].pxy - phi * uxy;
-        const R s = Sc[l], so = So[l];
-        // small source terms first, one rounding at the magnitude of phi
-        const R c0p = cm[l].dphi + (R(1.5) * s - R(0.5) * so);
-        const R pr = phi / rho;
-        // (1 - 1/tau_p1) B = -B + ep B, kept split so float32 keeps the tiny
-        // difference tau_p1 - 1/2 accurately
-        const R cx = (phi * ux - Bx) + ep * Bx + h1 * (pr * Fx + ux * s) +
-                     R(0.5) * h1 * (ux * s - uxo * so);
-        const R cy = (phi * uy - By) + ep * By + h1 * (pr * Fy + uy * s) +
-                     R(0.5) * h1 * (uy * s - uyo * so);
-        const R cxx = phi * uxx + c2 * Bxx;
-        const R cyy = phi * uyy + c2 * Byy;
-        const R cxy = phi * uxy + c2 * Bxy;
-        R out[9];
-        reconstruct<R>(c0p, cx, cy, cxx, cyy, cxy, R(0), R(0), out);
-        R* dl = dst + (size_t)(9 + 9 * l) * S;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) dl[(size_t)i * S + k] = out[i];
-      }
-    }
-
-    hist[k] = Sc[0];
-    hist[S + k] = Sc[1];
-    hist[2 * S + k] = Sc[2];
-    hist[3 * S + k] = ux;
-    hist[4 * S + k] = uy;
-
-    if (final_step) {
-      double* fl = D.fields;
-      const double r = 1.0 + (double)hm.drho;
-      const double vx = (double)ux, vy = (double)uy;
-      const double axx = 1.0 + (double)cm[0].dphi, axy = (double)cm[1].dphi,
-                   ayy = 1.0 + (double)cm[2].dphi;
-      // residual against the fields of the previous final step (none at init)
-      const double res = (MODE == kModeStep)
-                             ? fmax(fabs(vx - fl[S + k]), fabs(vy - fl[2 * S + k])) * D.inv_Uc
-                             : 0.0;
-      fl[k] = r;
-      fl[S + k] = vx;
-      fl[2 * S + k] = vy;
-      fl[3 * S + k] = axx;
-      fl[4 * S + k] = axy;
-      fl[5 * S + k] = ayy;
-      part[kSumRho] = r;
-      part[kSumJx] = (double)rho * vx;
-      part[kSumJy] = (double)rho * vy;
-      part[kSumPhi + 0] = axx;
-      part[kSumPhi + 1] = axy;
-      part[kSumPhi + 2] = ayy;
-      const bool finite = isfinite(r) && isfinite(vx) && isfinite(vy) && isfinite(axx) &&
-                          isfinite(axy) && isfinite(ayy);
-      part[kResid] = finite ? res : 0.0;
-      part[kNonFinite] = finite ? 0.0 : 1.0;
-    }
+    collide_node<R, MODE, FINAL>(D, k, S, dst, hist, hm, cm, rho, ux, uy, G00, G01, G10, G11,
+                                 dPx, dPy, Fx, Fy, So[0], So[1], So[2], uxo, uyo, part);
   }
 
-  if (final_step) {
+  if (FINAL) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < 14; ++j) {
