@@ -150,6 +150,32 @@ int lbve_residual(lbve_handle* h, int32_t inst, double* out);
 /* Current time step of instance inst. */
 int lbve_time(lbve_handle* h, int32_t inst, int64_t* t);
 
+/* Float64 sums of a macroscopic field array, computed WITHOUT ALLOCATING any
+ * device memory.  The paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc -- a framework whose own allocator owns all device
+ * memory and forbids side allocations, a latency-critical loop that cannot
+ * afford the device synchronisation of cudaMalloc/cudaFree, or a caller that
+ * holds a field array but no lbve workspace.
+ *   d_fields: device float64 [6][ny][nx] = rho, ux, uy, Axx, Axy, Ayy (the
+ *             layout lbve_fields() writes with on_device = 1); read only.
+ *   d_out   : device float64 [6], written: sum rho, sum rho ux, sum rho uy,
+ *             sum Axx, sum Axy, sum Ayy (the quantities of lbve_totals()
+ *             out[0..5], summed in a different fixed order).
+ * Asynchronous on cuda_stream (a cudaStream_t, NULL for the default stream).
+ * Scratch: one file-scope static device array of 16384 partial records
+ * (1 MiB) that every GPU loading the library keeps until the process exits;
+ * it limits a call to nx * ny <= 16,777,216 nodes (LBVE_ERR_ARG beyond, with
+ * a message on stderr).  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the array and
+ * leaves its records behind; each call overwrites the records it reads, so
+ * nothing needs clearing, but calls that overlap on the GPU (other streams,
+ * other threads) race on it and must be serialised by the caller.
+ * Errors: LBVE_ERR_ARG (null pointer, bad size, over the limit),
+ * LBVE_ERR_CUDA (device query, symbol lookup or launch failed). */
+int lbve_field_totals_noalloc(const double* d_fields, int32_t nx, int32_t ny, double* d_out,
+                              void* cuda_stream);
+
 /* Release the handle (host memory only; the workspace stays the caller's).
  * Synchronises the stream. */
 void lbve_destroy(lbve_handle* h);

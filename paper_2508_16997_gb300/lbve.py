@@ -29,7 +29,7 @@ LBVE_NTOTALS = 12
 
 EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_step",
             "lbve_status", "lbve_fields", "lbve_totals", "lbve_residual", "lbve_time",
-            "lbve_destroy", "lbve_error_string", "lbve_last_error"]
+            "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc"]
 
 
 class lbve_params(ctypes.Structure):
@@ -73,6 +73,7 @@ def load() -> ctypes.CDLL:
         L.lbve_totals.argtypes = [_vp, ctypes.c_int32, _dp]
         L.lbve_residual.argtypes = [_vp, ctypes.c_int32, _dp]
         L.lbve_time.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+        L.lbve_field_totals_noalloc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
         L.lbve_destroy.argtypes = [_vp]
         L.lbve_destroy.restype = None
         L.lbve_error_string.argtypes = [ctypes.c_int]
@@ -168,6 +169,13 @@ def lbve_time(h, inst: int) -> int:
     out = ctypes.c_int64()
     _check(load().lbve_time(h, inst, ctypes.byref(out)), "lbve_time")
     return out.value
+
+
+def lbve_field_totals_noalloc(d_fields: int, nx: int, ny: int, d_out: int, stream: int) -> None:
+    """Sums of a device field array [6][ny][nx] into a device array of 6
+    doubles, using only the library's static scratch (no allocation)."""
+    _check(load().lbve_field_totals_noalloc(_vp(d_fields), nx, ny, _vp(d_out), _vp(stream)),
+           "lbve_field_totals_noalloc")
 
 
 def lbve_destroy(h) -> None:
