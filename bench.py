@@ -135,6 +135,33 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("lbve_step.cuh", "lbve_kernels.cu", "lbve_internal.h"):
+        with open(os.path.join(ROOT, "paper_2508_16997_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    capture, or None when the kernel sources changed since the capture."""
+    try:
+        vals = {}
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")) as f:
+            for line in f:
+                if line.startswith("#") or not line.strip():
+                    continue
+                k, v = line.split(None, 1)
+                vals[k] = v.strip()
+        if vals.get("sources_sha256") != kernel_sources_sha256():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,7 +354,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_desc(insts, total_nodes),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": measured_traffic(),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "kernel": "step_kernel<float> (one launch per step; per-step CUDA-event "
