@@ -150,6 +150,35 @@ int lbve_residual(lbve_handle* h, int32_t inst, double* out);
 /* Current time step of instance inst. */
 int lbve_time(lbve_handle* h, int32_t inst, int64_t* t);
 
+/* Bytes of device workspace lbve_adjoint_step() needs for instance inst and
+ * a trajectory of n_steps >= 1 steps (sqrt(n_steps) checkpoints and one
+ * recomputed segment of stored states, plus the adjoint fields).  Host only. */
+int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps, size_t* bytes);
+
+/* Gradient of a loss L on the fields at time n_steps with respect to the
+ * per-node body force of instance inst, by a discrete adjoint of every step
+ * (the reverse of each stage of the coupled step of Secs. 3.1-3.3: collisions,
+ * source, finite-difference gradients, Zou-He and CNEBB completions, pull
+ * streaming) with sqrt(n_steps) checkpointing and recomputation.
+ * The trajectory is the one that lbve_set_geometry(h, inst, NULL, <current
+ * force of inst>, init_fields) followed by lbve_step(n_steps) produces; the
+ * forward states are recomputed in the adjoint workspace (the instance's own
+ * state is not touched).
+ *   init_fields  : host float64 [6][ny][nx] initial fields, or NULL for rho = 1,
+ *                  u = 0, A = I (as in lbve_set_geometry)
+ *   d_dL_dfields : device float64 [6][ny][nx], dL/d(rho, ux, uy, Axx, Axy, Ayy)
+ *                  at time n_steps
+ *   d_ws, bytes  : device workspace >= lbve_adjoint_workspace_bytes(), 256-byte
+ *                  aligned, owned by the caller
+ *   d_dL_dforce  : device float64 [2][ny][nx], overwritten with dL/dF (the
+ *                  derivative with respect to a per-node force, also when the
+ *                  instance uses a uniform force)
+ * Computed in the instance's precision.  Synchronises the stream.
+ * Errors: LBVE_ERR_ARG, LBVE_ERR_STATE, LBVE_ERR_WORKSPACE, LBVE_ERR_CUDA. */
+int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* init_fields,
+                      const double* d_dL_dfields, int64_t n_steps, void* d_ws, size_t bytes,
+                      double* d_dL_dforce);
+
 /* Float64 sums of a macroscopic field array, computed WITHOUT ALLOCATING any
  * device memory.  The paper has no counterpart: this serves callers that
  * cannot call cudaMalloc -- a framework whose own allocator owns all device

@@ -1,0 +1,55 @@
+// lbve_adjoint.cu -- launchers of the adjoint passes (see lbve_adjoint.cuh).
+#include <cuda_runtime.h>
+
+#include "lbve_adjoint.cuh"
+#include "lbve_internal.h"
+
+namespace lbve {
+
+template <typename R>
+static AdjArgs<R> cast_args(const AdjArgsRaw& a) {
+  AdjArgs<R> A;
+  A.X = (const R*)a.X;
+  A.init = a.init;
+  A.force = (const R*)a.force;
+  A.M = (R*)a.M;
+  A.lam_next = (const R*)a.lam_next;
+  A.lam_fields = a.lam_fields;
+  A.lam_pulled = (R*)a.lam_pulled;
+  A.lam_G = (R*)a.lam_G;
+  A.lam_dir = (R*)a.lam_dir;
+  A.lam_mh = (R*)a.lam_mh;
+  A.lam_cur = (R*)a.lam_cur;
+  A.dF = a.dF;
+  return A;
+}
+
+template <typename R, int MODE>
+static void run_pass(int pass, const InstDev* d, const AdjArgs<R>& A, int blocks, cudaStream_t st) {
+  switch (pass) {
+    case 0: adj_moments<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
+    case 1: adj_local<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
+    case 2: adj_gather<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
+    default: adj_pull<R><<<blocks, 256, 0, st>>>(d, A); break;
+  }
+}
+
+template <typename R>
+static void run_mode(int mode, int pass, const InstDev* d, const AdjArgs<R>& A, int blocks,
+                     cudaStream_t st) {
+  if (mode == kAdjStep) run_pass<R, kAdjStep>(pass, d, A, blocks, st);
+  else if (mode == kAdjFields) run_pass<R, kAdjFields>(pass, d, A, blocks, st);
+  else run_pass<R, kAdjInit>(pass, d, A, blocks, st);
+}
+
+int launch_adjoint(int prec, int mode, int pass, const InstDev* d_desc, const AdjArgsRaw& a,
+                   int n_nodes, void* stream) {
+  const int blocks = (n_nodes + 255) / 256;
+  if (blocks <= 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == 0) run_mode<double>(mode, pass, d_desc, cast_args<double>(a), blocks, st);
+  else run_mode<float>(mode, pass, d_desc, cast_args<float>(a), blocks, st);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace lbve

@@ -1,0 +1,618 @@
+// lbve_adjoint.cuh -- hand-written discrete adjoint of the coupled step.
+//
+// The forward step maps the stored state X_t (36 post-collision populations
+// and 5 history values per node) and the body force F to X_{t+1}.  Its
+// adjoint maps lambda_{t+1} = dL/dX_{t+1} to lambda_t = dL/dX_t and adds the
+// step's contribution to dL/dF.  Every stage of the forward step (see
+// lbve_step.cuh) is reversed by hand, in reverse order:
+//   reconstruction (linear)          -> weighted moments of lambda
+//   collision coefficients b, c      -> lambda of moments, u, rho, F, S, dPhi, tau
+//   Oldroyd-B source Phi_ab          -> lambda of A and of the velocity gradient
+//   finite-difference gradients      -> transposed stencils (a gather)
+//   u = (j + F/2)/rho, moments       -> lambda of the completed populations
+//   Zou-He and CNEBB completions     -> lambda of pulled populations, own wall slots, u_b
+//   pull streaming                   -> reverse pull (a gather from x + e_i)
+// Three passes per step, each one thread per node:
+//   adj_local   collision/source/CNEBB reverse at the node; writes lambda of the
+//               conformation pulls, the gradient adjoints and the direct
+//               adjoints of rho and u; writes lambda_t's history part
+//   adj_gather  transposed gradient stencils + u/rho chain + Zou-He reverse;
+//               writes lambda of the hydro pulls, accumulates dL/dF
+//   adj_pull    reverse pull into lambda_t's populations
+// A fourth kernel (adj_moments) recomputes rho, u of the forward state so the
+// gather can read its neighbours.  Modes: a normal step; the final fields
+// (the loss enters through rho, u, A of the last step); the initial collision
+// (equilibrium populations do not depend on F; history = current values).
+#pragma once
+#include "lbve_step.cuh"
+
+namespace lbve {
+
+// Plane counts of the adjoint buffers (all with the instance's stride).
+constexpr int kStateVals = 41;  // 36 populations + 5 history
+
+template <typename R>
+struct AdjArgs {
+  const R* X;         // [41][S] forward state X_t (pops, then history); kAdjInit: unused
+  const double* init; // kAdjInit: staged initial fields float64 [6][S]
+  const R* force;     // [2][S] per-node force or null (uniform)
+  R* M;               // [3][S] rho, ux, uy of the forward state at time t+1 moments
+  const R* lam_next;  // [41][S] lambda_{t+1}; kAdjFields: null
+  const double* lam_fields;  // kAdjFields: dL/d(rho, ux, uy, Axx, Axy, Ayy) [6][n] (n = nx*ny)
+  R* lam_pulled;      // [36][S] lambda of the pulled (pre-completion) populations
+  R* lam_G;           // [6][S]  lambda of G00, G01, G10, G11, dPx, dPy
+  R* lam_dir;         // [3][S]  direct lambda of rho, ux, uy
+  R* lam_mh;          // [8][S]  direct lambda of the raw hydro moments
+  R* lam_cur;         // [41][S] lambda_t
+  double* dF;         // [2][n]  accumulated dL/dF
+};
+
+// Forward recompute at one node: completed hydro populations (deviations),
+// force, raw moments and rho, u.  kAdjInit takes the equilibria of the
+// staged initial fields instead of a pull and completes no wall.
+template <typename R, int MODE>
+__device__ __forceinline__ void adj_hydro_node(const InstDev& D, const AdjArgs<R>& A, int x, int y,
+                                               R d[9], R& Fx, R& Fy, HydroM<R>& hm, R& rho, R& ux,
+                                               R& uy) {
+  const int nx = D.nx, ny = D.ny, S = D.stride;
+  const bool py = D.periodic_y != 0;
+  const int k = y * nx + x;
+  int rm, rp;
+  neighbour_rows(y, nx, ny, py, rm, rp);
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  Fx = A.force ? A.force[k] : coef<R>(D, kCoefFx);
+  Fy = A.force ? A.force[S + k] : coef<R>(D, kCoefFy);
+  if (MODE == kAdjInit) {
+    PopSource<R, kModeInit>::hydro(A.init, S, nx, k, y * nx, rm, rp, x, xm, xp, d);
+  } else {
+    pull9<R>(A.X, S, y * nx, rm, rp, x, xm, xp, d);
+    if (!py && (y == 0 || y == ny - 1)) zou_he<R>(d, Fx, Fy, y == 0);
+  }
+  hydro_moments<R>(d, hm);
+  rho = R(1) + hm.drho;
+  ux = (hm.jx + R(0.5) * Fx) / rho;
+  uy = (hm.jy + R(0.5) * Fy) / rho;
+}
+
+// rho, u of every node of the forward state (for the neighbours' gradients).
+template <typename R, int MODE>
+__global__ void adj_moments(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
+  const InstDev& D = *Dp;
+  const int n = D.nx * D.ny;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int x = k % D.nx, y = k / D.nx, S = D.stride;
+  R d[9], Fx, Fy, rho, ux, uy;
+  HydroM<R> hm;
+  adj_hydro_node<R, MODE>(D, A, x, y, d, Fx, Fy, hm, rho, ux, uy);
+  A.M[k] = rho;
+  A.M[S + k] = ux;
+  A.M[2 * S + k] = uy;
+}
+
+// Transpose of reconstruct(): lambda of the Hermite coefficients from the
+// lambda of the nine rebuilt populations (weighted moments).
+template <typename R>
+__device__ __forceinline__ void reconstruct_T(const R l[9], R& b0, R& bx, R& by, R& bxx, R& byy,
+                                              R& bxy, R& bxxy, R& bxyy) {
+  const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+  const R a0 = w0 * l[0], a1 = w1 * l[1], a2 = w1 * l[2], a3 = w1 * l[3], a4 = w1 * l[4];
+  const R a5 = w5 * l[5], a6 = w5 * l[6], a7 = w5 * l[7], a8 = w5 * l[8];
+  const R s58 = (a5 + a6) + (a7 + a8);
+  b0 = ((a0 + a1) + (a2 + a3)) + (a4 + s58);
+  bx = R(3) * ((a1 - a3) + ((a5 - a6) + (a8 - a7)));
+  by = R(3) * ((a2 - a4) + ((a5 + a6) - (a7 + a8)));
+  // H_xx = e_x^2 - 1/3, H_yy = e_y^2 - 1/3, 2 H_xy = 2 e_x e_y
+  const R sall = b0;
+  bxx = R(4.5) * (((a1 + a3) + s58) - sall / R(3));
+  byy = R(4.5) * (((a2 + a4) + s58) - sall / R(3));
+  bxy = R(9) * ((a5 + a7) - (a6 + a8));
+  // H_xxy = e_y (e_x^2 - 1/3), H_xyy = e_x (e_y^2 - 1/3)
+  const R ey_all = (a2 - a4) + ((a5 + a6) - (a7 + a8));
+  const R ex_all = (a1 - a3) + ((a5 - a6) + (a8 - a7));
+  bxxy = R(13.5) * (((a5 + a6) - (a7 + a8)) - ey_all / R(3));
+  bxyy = R(13.5) * (((a5 + a8) - (a6 + a7)) - ex_all / R(3));
+}
+
+// Transpose of hydro_moments / cde_moments: lambda of the nine populations
+// from lambda of (drho, jx, jy, pxx, pyy, pxy, qxxy, qxyy).
+template <typename R>
+__device__ __forceinline__ void moments_T(R l0, R lx, R ly, R lxx, R lyy, R lxy, R lxxy, R lxyy,
+                                          R out[9]) {
+  out[0] = l0;
+  out[1] = l0 + lx + lxx;
+  out[3] = l0 - lx + lxx;
+  out[2] = l0 + ly + lyy;
+  out[4] = l0 - ly + lyy;
+  // diagonals: e_x^2 = e_y^2 = 1
+  out[5] = l0 + lx + ly + lxx + lyy + lxy + lxxy + lxyy;
+  out[6] = l0 - lx + ly + lxx + lyy - lxy + lxxy - lxyy;
+  out[7] = l0 - lx - ly + lxx + lyy + lxy - lxxy - lxyy;
+  out[8] = l0 + lx - ly + lxx + lyy - lxy - lxxy + lxyy;
+}
+
+// Reverse of cnebb() at a wall node: given lambda of the completed
+// populations lg[9], add to lambda of the pulled known populations (ld),
+// of the node's own outgoing-to-wall slots (lpost[3], in H order) and of u_b.
+template <typename R>
+__device__ __forceinline__ void cnebb_T(const R d[9], R pa, R pb, R pc, R delta, R ubx, R uby,
+                                        bool bottom, const R lg[9], R ld[9], R lpost[3], R& lubx,
+                                        R& luby) {
+  // forward intermediates
+  R dphi;
+  if (bottom) dphi = ((d[0] + d[1]) + (d[3] + d[4])) + ((d[7] + d[8]) + ((pa + pb) + pc));
+  else dphi = ((d[0] + d[1]) + (d[3] + d[2])) + ((d[5] + d[6]) + ((pa + pb) + pc));
+  const R phib = delta + dphi;
+  const R a2 = R(6.0 / 9.0) * phib, a5 = R(6.0 / 36.0) * phib;
+  // g0 = dphi - sum_{i != 0} g_i, so every other completed slot also feeds -lg[0]
+  R lt[9];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) lt[i] = lg[i] - lg[0];
+  R ldphi = lg[0];
+  R la2 = R(0), la5 = R(0);
+  if (bottom) {
+    // known: 0? (g0 is rebuilt), 1, 3, 4, 7, 8; unknown rebuilt: 2, 5, 6
+    ld[1] += lt[1];
+    ld[3] += lt[3];
+    ld[4] += lt[4] + lt[2];
+    ld[7] += lt[7] + lt[5];
+    ld[8] += lt[8] + lt[6];
+    la2 += uby * lt[2];
+    luby += a2 * lt[2];
+    la5 += (ubx + uby) * lt[5] + (uby - ubx) * lt[6];
+    lubx += a5 * (lt[5] - lt[6]);
+    luby += a5 * (lt[5] + lt[6]);
+  } else {
+    // known: 1, 2, 3, 5, 6; rebuilt: 4 = d2 - a2 uy, 7 = d5 - a5 (ux+uy), 8 = d6 + a5 (ux-uy)
+    ld[1] += lt[1];
+    ld[3] += lt[3];
+    ld[2] += lt[2] + lt[4];
+    ld[5] += lt[5] + lt[7];
+    ld[6] += lt[6] + lt[8];
+    la2 += -uby * lt[4];
+    luby += -a2 * lt[4];
+    la5 += -(ubx + uby) * lt[7] + (ubx - uby) * lt[8];
+    lubx += a5 * (lt[8] - lt[7]);
+    luby += -a5 * (lt[7] + lt[8]);
+  }
+  ldphi += R(6.0 / 9.0) * la2 + R(6.0 / 36.0) * la5;
+  // dphi = sum of the known slots (0 included) and the three own post slots
+  ld[0] += ldphi;
+  if (bottom) {
+    ld[1] += ldphi;
+    ld[3] += ldphi;
+    ld[4] += ldphi;
+    ld[7] += ldphi;
+    ld[8] += ldphi;
+  } else {
+    ld[1] += ldphi;
+    ld[3] += ldphi;
+    ld[2] += ldphi;
+    ld[5] += ldphi;
+    ld[6] += ldphi;
+  }
+  lpost[0] += ldphi;
+  lpost[1] += ldphi;
+  lpost[2] += ldphi;
+}
+
+// Pass 1: local reverse of the collision, source, history and CNEBB.
+template <typename R, int MODE>
+__global__ void adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
+  const InstDev& D = *Dp;
+  const int nx = D.nx, ny = D.ny, S = D.stride, n = nx * ny;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int x = k % nx, y = k / nx;
+  const bool py = D.periodic_y != 0;
+  const bool wb = !py && y == 0, wt = !py && y == ny - 1;
+  const bool walls = (MODE != kAdjInit) && (wb || wt);
+
+  // ---- forward recompute ----
+  R d[9], Fx, Fy, rho, ux, uy;
+  HydroM<R> hm;
+  adj_hydro_node<R, MODE>(D, A, x, y, d, Fx, Fy, hm, rho, ux, uy);
+  int rm, rp;
+  neighbour_rows(y, nx, ny, py, rm, rp);
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  R g[3][9], gp[3][9], post[3][3];
+  CdeM<R> cm[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    if (MODE == kAdjInit) {
+      PopSource<R, kModeInit>::cde(A.init, l, S, nx, k, y * nx, rm, rp, x, xm, xp, g[l]);
+    } else {
+      pull9<R>(A.X + (size_t)(9 + 9 * l) * S, S, y * nx, rm, rp, x, xm, xp, g[l]);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gp[l][i] = g[l][i];  // pulled, before completion
+    post[l][0] = post[l][1] = post[l][2] = R(0);
+    if (walls) {
+      const R* own = A.X + (size_t)(9 + 9 * l) * S + k;
+      post[l][0] = own[(wb ? 4 : 2) * S];
+      post[l][1] = own[(wb ? 7 : 5) * S];
+      post[l][2] = own[(wb ? 8 : 6) * S];
+      double wi, wo;
+      cnebb<R>(g[l], post[l][0], post[l][1], post[l][2], (l == 1) ? R(0) : R(1), ux, uy, wb, wi,
+               wo);
+    }
+    cde_moments<R>(g[l], cm[l]);
+  }
+
+  R lrho = R(0), lux = R(0), luy = R(0);         // direct lambdas of rho, u
+  R lm[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};  // raw hydro moments
+  R lG[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};                // G00 G01 G10 G11 dPx dPy
+  R lcm[3][6];                                                   // raw CDE moments
+  R lFx = R(0), lFy = R(0);
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) lcm[l][j] = R(0);
+
+  if (MODE == kAdjFields) {
+    // the loss enters through the fields of this step; nothing flows to the history
+    R* lh = A.lam_cur + (size_t)36 * S;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) lh[(size_t)j * S + k] = R(0);
+    lrho = (R)A.lam_fields[k];
+    lux = (R)A.lam_fields[n + k];
+    luy = (R)A.lam_fields[2 * n + k];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) lcm[l][0] = (R)A.lam_fields[(3 + l) * n + k];
+  } else {
+    // ---- forward recompute of gradients, source, coefficients ----
+    const R* Mr = A.M;
+    const R* Mx = A.M + S;
+    const R* My = A.M + 2 * S;
+    const int kxm = y * nx + xm, kxp = y * nx + xp;
+    const R half = R(0.5);
+    const R G00 = half * (Mx[kxp] - Mx[kxm]);
+    const R G01 = half * (My[kxp] - My[kxm]);
+    const R dPx = half * (Mr[kxp] * Mx[kxp] * Mx[kxp] * Mx[kxp] -
+                          Mr[kxm] * Mx[kxm] * Mx[kxm] * Mx[kxm]);
+    R G10, G11, dPy;
+    {
+      auto at = [&](int yy) { return ((yy % ny) + ny) % ny * nx + x; };
+      const int km2 = at(y - 2), km1 = at(y - 1), kp1 = at(y + 1), kp2 = at(y + 2);
+      y_gradients<R>(wb, wt, Mr[km2], Mx[km2], My[km2], Mr[km1], Mx[km1], My[km1], rho, ux, uy,
+                     Mr[kp1], Mx[kp1], My[kp1], Mr[kp2], Mx[kp2], My[kp2], G10, G11, dPy);
+    }
+    const R Axx = R(1) + cm[0].dphi, Axy = cm[1].dphi, Ayy = R(1) + cm[2].dphi;
+    const R mpl = coef<R>(D, kCoefMupLam), il = coef<R>(D, kCoefInvLam);
+    const R div = G00 + G11;
+    R Sc[3];
+    Sc[0] = -cm[0].dphi * il + R(2) * (Axx * G00 + Axy * G10) + Axx * div;
+    Sc[1] = -cm[1].dphi * il + (Axx * G01 + Axy * G11) + (Axy * G00 + Ayy * G10) + Axy * div;
+    Sc[2] = -cm[2].dphi * il + R(2) * (Axy * G01 + Ayy * G11) + Ayy * div;
+    R So[3], uxo, uyo;
+    if (MODE == kAdjInit) {
+      So[0] = Sc[0];
+      So[1] = Sc[1];
+      So[2] = Sc[2];
+      uxo = ux;
+      uyo = uy;
+    } else {
+      const R* h = A.X + (size_t)36 * S;
+      So[0] = h[k];
+      So[1] = h[S + k];
+      So[2] = h[2 * S + k];
+      uxo = h[3 * S + k];
+      uyo = h[4 * S + k];
+    }
+
+    // ---- lambda of the step outputs ----
+    R lout[4][9], lH[5];
+#pragma unroll
+    for (int q = 0; q < 36; ++q) lout[q / 9][q % 9] = A.lam_next[(size_t)q * S + k];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) lH[j] = A.lam_next[(size_t)(36 + j) * S + k];
+    // history out = (S, u)
+    R lS[3] = {lH[0], lH[1], lH[2]};
+    lux += lH[3];
+    luy += lH[4];
+    R lSo[3] = {R(0), R(0), R(0)}, luxo = R(0), luyo = R(0);
+
+    // ---- hydro collision reverse ----
+    {
+      const R cs2 = R(1.0 / 3.0);
+      const R c1 = coef<R>(D, kCoefCs1), c2 = coef<R>(D, kCoefCs2);
+      const R h1 = coef<R>(D, kCoefHs1), w1 = coef<R>(D, kCoefWs1);
+      R lb0, lbx, lby, lbxx, lbyy, lbxy, lbxxy, lbxyy;
+      reconstruct_T<R>(lout[0], lb0, lbx, lby, lbxx, lbyy, lbxy, lbxxy, lbxyy);
+      // b0' = drho; bx = jx + Fx; by = jy + Fy
+      lm[0] += lb0;
+      lm[1] += lbx;
+      lm[2] += lby;
+      lFx += lbx;
+      lFy += lby;
+      // bxx = (1-c1) rho ux^2 + c1 pxx - c1 cs2 drho - h1 dPx - w1 mpl dphi_xx, etc.
+      lm[3] += c1 * lbxx;
+      lm[4] += c1 * lbyy;
+      lm[5] += c1 * lbxy;
+      lm[0] += -c1 * cs2 * (lbxx + lbyy);
+      lG[4] += -h1 * lbxx;
+      lG[5] += -h1 * lbyy;
+      lcm[0][0] += -w1 * mpl * lbxx;
+      lcm[1][0] += -w1 * mpl * lbxy;
+      lcm[2][0] += -w1 * mpl * lbyy;
+      // bxxy = (1-c2) rho ux^2 uy + c2 qxxy - c2 cs2 jy; bxyy likewise with jx
+      lm[6] += c2 * lbxxy;
+      lm[7] += c2 * lbxyy;
+      lm[2] += -c2 * cs2 * lbxxy;
+      lm[1] += -c2 * cs2 * lbxyy;
+      const R q1 = (R(1) - c1) * lbxx, q2 = (R(1) - c1) * lbyy, q3 = (R(1) - c1) * lbxy;
+      const R q4 = (R(1) - c2) * lbxxy, q5 = (R(1) - c2) * lbxyy;
+      // Q1 = rho ux^2, Q2 = rho uy^2, Q3 = rho ux uy, Q4 = rho ux^2 uy, Q5 = rho ux uy^2
+      lrho += ux * ux * q1 + uy * uy * q2 + ux * uy * q3 + ux * ux * uy * q4 + ux * uy * uy * q5;
+      lux += R(2) * rho * ux * q1 + rho * uy * q3 + R(2) * rho * ux * uy * q4 + rho * uy * uy * q5;
+      luy += R(2) * rho * uy * q2 + rho * ux * q3 + rho * ux * ux * q4 + R(2) * rho * ux * uy * q5;
+    }
+
+    // ---- conformation collision reverse ----
+    {
+      const R cs2 = R(1.0 / 3.0);
+      const R ep = coef<R>(D, kCoefEp1), c2 = coef<R>(D, kCoefCp2), h1 = coef<R>(D, kCoefHp1);
+      const R e1 = ep - R(1);  // 1 - 1/tau_p1
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const R phi = (l == 1 ? R(0) : R(1)) + cm[l].dphi;
+        R lc0, lcx, lcy, lcxx, lcyy, lcxy, u1, u2;
+        reconstruct_T<R>(lout[1 + l], lc0, lcx, lcy, lcxx, lcyy, lcxy, u1, u2);
+        R lphi = R(0);
+        // c0p = dphi + 1.5 S - 0.5 So
+        lcm[l][0] += lc0;
+        lS[l] += R(1.5) * lc0;
+        lSo[l] += R(-0.5) * lc0;
+        // cx = (1-e1) phi ux + e1 jx + h1 phi Fx / rho + 1.5 h1 ux S - 0.5 h1 uxo So
+        lphi += ((R(1) - e1) * ux + h1 * Fx / rho) * lcx + ((R(1) - e1) * uy + h1 * Fy / rho) * lcy;
+        lux += ((R(1) - e1) * phi + R(1.5) * h1 * Sc[l]) * lcx;
+        luy += ((R(1) - e1) * phi + R(1.5) * h1 * Sc[l]) * lcy;
+        lcm[l][1] += e1 * lcx;
+        lcm[l][2] += e1 * lcy;
+        lFx += h1 * phi / rho * lcx;
+        lFy += h1 * phi / rho * lcy;
+        lrho += -h1 * phi * (Fx * lcx + Fy * lcy) / (rho * rho);
+        lS[l] += R(1.5) * h1 * (ux * lcx + uy * lcy);
+        luxo += R(-0.5) * h1 * So[l] * lcx;
+        luyo += R(-0.5) * h1 * So[l] * lcy;
+        lSo[l] += R(-0.5) * h1 * (uxo * lcx + uyo * lcy);
+        // cxx = (1-c2) phi ux^2 + c2 pxx - c2 cs2 dphi, cyy, cxy = (1-c2) phi ux uy + c2 pxy
+        const R k2 = R(1) - c2;
+        lphi += k2 * (ux * ux * lcxx + uy * uy * lcyy + ux * uy * lcxy);
+        lux += k2 * phi * (R(2) * ux * lcxx + uy * lcxy);
+        luy += k2 * phi * (R(2) * uy * lcyy + ux * lcxy);
+        lcm[l][3] += c2 * lcxx;
+        lcm[l][4] += c2 * lcyy;
+        lcm[l][5] += c2 * lcxy;
+        lcm[l][0] += -c2 * cs2 * (lcxx + lcyy) + lphi;
+      }
+    }
+    if (MODE == kAdjInit) {
+      // history = current values: So = S, uo = u
+#pragma unroll
+      for (int l = 0; l < 3; ++l) lS[l] += lSo[l];
+      lux += luxo;
+      luy += luyo;
+    } else {
+      // lambda_t's history part
+      R* lh = A.lam_cur + (size_t)36 * S;
+      lh[k] = lSo[0];
+      lh[S + k] = lSo[1];
+      lh[2 * S + k] = lSo[2];
+      lh[3 * S + k] = luxo;
+      lh[4 * S + k] = luyo;
+    }
+
+    // ---- source reverse: S(A, grad u) ----
+    {
+      // S0
+      lcm[0][0] += (-il + R(3) * G00 + G11) * lS[0];
+      lcm[1][0] += R(2) * G10 * lS[0];
+      lG[0] += R(3) * Axx * lS[0];
+      lG[2] += R(2) * Axy * lS[0];
+      lG[3] += Axx * lS[0];
+      // S1
+      lcm[0][0] += G01 * lS[1];
+      lcm[1][0] += (-il + R(2) * G00 + R(2) * G11) * lS[1];
+      lcm[2][0] += G10 * lS[1];
+      lG[1] += Axx * lS[1];
+      lG[3] += R(2) * Axy * lS[1];
+      lG[0] += R(2) * Axy * lS[1];
+      lG[2] += Ayy * lS[1];
+      // S2
+      lcm[1][0] += R(2) * G01 * lS[2];
+      lcm[2][0] += (-il + G00 + R(3) * G11) * lS[2];
+      lG[1] += R(2) * Axy * lS[2];
+      lG[3] += R(3) * Ayy * lS[2];
+      lG[0] += Ayy * lS[2];
+    }
+  }
+
+  // ---- conformation moments -> completed populations -> CNEBB -> pulls ----
+  if (MODE != kAdjInit) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      R lg[9];
+      moments_T<R>(lcm[l][0], lcm[l][1], lcm[l][2], lcm[l][3], lcm[l][4], lcm[l][5], R(0), R(0),
+                   lg);
+      R ld[9];
+      if (walls) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ld[i] = R(0);
+        R lpost[3] = {R(0), R(0), R(0)};
+        cnebb_T<R>(gp[l], post[l][0], post[l][1], post[l][2], (l == 1) ? R(0) : R(1), ux, uy,
+                   wb, lg, ld, lpost, lux, luy);
+        // unknown slots carry lambda of the own outgoing-to-wall slots (opposites)
+        if (wb) {  // U = {2, 5, 6} <- H = {4, 7, 8}
+          ld[2] = lpost[0];
+          ld[5] = lpost[1];
+          ld[6] = lpost[2];
+        } else {  // U = {4, 7, 8} <- H = {2, 5, 6}
+          ld[4] = lpost[0];
+          ld[7] = lpost[1];
+          ld[8] = lpost[2];
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ld[i] = lg[i];
+      }
+      R* lp = A.lam_pulled + (size_t)(9 + 9 * l) * S + k;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) lp[(size_t)i * S] = ld[i];
+    }
+  }
+  A.lam_G[k] = lG[0];
+  A.lam_G[S + k] = lG[1];
+  A.lam_G[2 * S + k] = lG[2];
+  A.lam_G[3 * S + k] = lG[3];
+  A.lam_G[4 * S + k] = lG[4];
+  A.lam_G[5 * S + k] = lG[5];
+  A.lam_dir[k] = lrho;
+  A.lam_dir[S + k] = lux;
+  A.lam_dir[2 * S + k] = luy;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) A.lam_mh[(size_t)j * S + k] = lm[j];
+  A.dF[k] += (double)lFx;
+  A.dF[n + k] += (double)lFy;
+}
+
+// Coefficient with which q(row yq) enters the y-derivative at row y of a
+// column (central inside, one-sided on wall rows).
+__device__ __forceinline__ double ycoef(int y, int yq, int ny, bool py) {
+  if (py) {
+    const int up = (y + 1) % ny, dn = (y - 1 + ny) % ny;
+    double c = 0.0;
+    if (yq == up) c += 0.5;
+    if (yq == dn) c -= 0.5;
+    return c;
+  }
+  if (y == 0) return yq == 0 ? -1.5 : (yq == 1 ? 2.0 : (yq == 2 ? -0.5 : 0.0));
+  if (y == ny - 1) return yq == y ? 1.5 : (yq == y - 1 ? -2.0 : (yq == y - 2 ? 0.5 : 0.0));
+  return yq == y + 1 ? 0.5 : (yq == y - 1 ? -0.5 : 0.0);
+}
+
+// Pass 2: gather the transposed gradient stencils, reverse u = (j + F/2)/rho
+// and the hydro moments, reverse Zou-He; writes lambda of the hydro pulls and
+// accumulates dL/dF.
+template <typename R, int MODE>
+__global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
+  const InstDev& D = *Dp;
+  const int nx = D.nx, ny = D.ny, S = D.stride, n = nx * ny;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int x = k % nx, y = k / nx;
+  const bool py = D.periodic_y != 0;
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const R rho = A.M[k], ux = A.M[S + k], uy = A.M[2 * S + k];
+  R lrho = A.lam_dir[k], lux = A.lam_dir[S + k], luy = A.lam_dir[2 * S + k];
+  // x stencils of the nodes left and right of this one: d/dx q(x) = (q(x+1) - q(x-1))/2
+  {
+    const int kl = y * nx + xm, kr = y * nx + xp;
+    // this node is the right neighbour of kl (+1/2) and the left neighbour of kr (-1/2)
+    R lc = R(0);
+    lux += R(0.5) * (A.lam_G[kl] - A.lam_G[kr]);
+    luy += R(0.5) * (A.lam_G[S + kl] - A.lam_G[S + kr]);
+    lc += R(0.5) * (A.lam_G[4 * S + kl] - A.lam_G[4 * S + kr]);
+    // c = rho ux^3
+    lrho += ux * ux * ux * lc;
+    lux += R(3) * rho * ux * ux * lc;
+  }
+  // y stencils of the nodes of this column that read this row
+  {
+    R lcy = R(0);
+    for (int dy = -2; dy <= 2; ++dy) {
+      int yy = y + dy;
+      if (py) {
+        yy = ((yy % ny) + ny) % ny;
+      } else if (yy < 0 || yy >= ny) {
+        continue;
+      }
+      if (py && dy != -1 && dy != 1) continue;  // periodic: central only
+      const double c = ycoef(yy, y, ny, py);
+      if (c == 0.0) continue;
+      const int kk = yy * nx + x;
+      lux += (R)c * A.lam_G[2 * S + kk];
+      luy += (R)c * A.lam_G[3 * S + kk];
+      lcy += (R)c * A.lam_G[5 * S + kk];
+    }
+    // cy = rho uy^3
+    lrho += uy * uy * uy * lcy;
+    luy += R(3) * rho * uy * uy * lcy;
+  }
+  // u = (j + F/2) / rho, rho = 1 + drho
+  R lm[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) lm[j] = (MODE == kAdjFields) ? R(0) : A.lam_mh[(size_t)j * S + k];
+  lm[1] += lux / rho;
+  lm[2] += luy / rho;
+  lm[0] += lrho - (ux * lux + uy * luy) / rho;
+  R lFx = R(0.5) * lux / rho, lFy = R(0.5) * luy / rho;
+  if (MODE != kAdjInit) {
+    R ld[9];
+    moments_T<R>(lm[0], lm[1], lm[2], lm[3], lm[4], lm[5], lm[6], lm[7], ld);
+    const bool wb = !py && y == 0, wt = !py && y == ny - 1;
+    if (wb) {
+      // d2 = d4; d5 = d7 - h - Fx/4 - Fy/4; d6 = d8 + h + Fx/4 - Fy/4, h = (d1 - d3)/2
+      ld[4] += ld[2];
+      ld[7] += ld[5];
+      ld[8] += ld[6];
+      ld[1] += R(0.5) * (ld[6] - ld[5]);
+      ld[3] += R(0.5) * (ld[5] - ld[6]);
+      lFx += R(0.25) * (ld[6] - ld[5]);
+      lFy += R(-0.25) * (ld[5] + ld[6]);
+      ld[2] = ld[5] = ld[6] = R(0);
+    } else if (wt) {
+      // d4 = d2; d7 = d5 + h + Fx/4 + Fy/4; d8 = d6 - h - Fx/4 + Fy/4
+      ld[2] += ld[4];
+      ld[5] += ld[7];
+      ld[6] += ld[8];
+      ld[1] += R(0.5) * (ld[7] - ld[8]);
+      ld[3] += R(0.5) * (ld[8] - ld[7]);
+      lFx += R(0.25) * (ld[7] - ld[8]);
+      lFy += R(0.25) * (ld[7] + ld[8]);
+      ld[4] = ld[7] = ld[8] = R(0);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) A.lam_pulled[(size_t)i * S + k] = ld[i];
+  }
+  A.dF[k] += (double)lFx;
+  A.dF[n + k] += (double)lFy;
+}
+
+// Pass 3: reverse pull.  lambda_t(y, i) = lambda_pulled(y + e_i, i); at a wall
+// node the CDE slots that point at the wall take the lambda CNEBB stored in
+// the opposite (unknown) slot, and the hydro ones get nothing.
+template <typename R>
+__global__ void adj_pull(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
+  const InstDev& D = *Dp;
+  const int nx = D.nx, ny = D.ny, S = D.stride, n = nx * ny;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int x = k % nx, y = k / nx;
+  const bool py = D.periodic_y != 0;
+  const int EXd[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int EYd[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const int OPPd[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      int xd = x + EXd[i];
+      xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
+      int yd = y + EYd[i];
+      R v = R(0);
+      if (py) {
+        yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
+        v = A.lam_pulled[(size_t)(9 * l + i) * S + yd * nx + xd];
+      } else if (yd >= 0 && yd < ny) {
+        v = A.lam_pulled[(size_t)(9 * l + i) * S + yd * nx + xd];
+      } else if (l > 0) {
+        // direction i leaves the domain at this wall node: CNEBB's own slot
+        v = A.lam_pulled[(size_t)(9 * l + OPPd[i]) * S + k];
+      }
+      A.lam_cur[(size_t)(9 * l + i) * S + k] = v;
+    }
+  }
+}
+
+}  // namespace lbve

@@ -468,3 +468,222 @@ void lbve_destroy(lbve_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Adjoint: gradient of a loss on the final fields with respect to the
+// per-node body force, by a hand-written discrete adjoint of every step
+// (lbve_adjoint.cuh) with sqrt(T) checkpointing.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjPlan {
+  int64_t T, s, nck;             // steps, checkpoint interval, checkpoints
+  size_t state_bytes;            // one stored state: 41 planes
+  size_t off_desc, off_tiles, off_partials, off_fields, off_stage, off_ck, off_seg, off_lam[2],
+      off_pulled, off_G, off_dir, off_mh, off_M, total;
+};
+
+AdjPlan make_adj_plan(const lbve_params& p, const InstPlan& q, int64_t T) {
+  AdjPlan a;
+  a.T = T;
+  a.s = 1;
+  while (a.s * a.s < T) ++a.s;
+  a.nck = (T + a.s - 1) / a.s;
+  const size_t es = p.precision == LBVE_FP64 ? 8 : 4;
+  const size_t plane = size_t(q.stride) * es;
+  a.state_bytes = 41 * plane;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1), kAlign);
+    return o;
+  };
+  a.off_desc = take(sizeof(InstDev));
+  a.off_tiles = take(sizeof(TileDev) * q.ntiles);
+  a.off_partials = take(sizeof(double) * kPartial * q.ntiles);
+  a.off_fields = take(sizeof(double) * 6 * q.stride);
+  a.off_stage = take(sizeof(double) * 6 * q.stride);
+  a.off_ck = take(a.state_bytes * a.nck);
+  a.off_seg = take(a.state_bytes * (a.s + 1));
+  a.off_lam[0] = take(a.state_bytes);
+  a.off_lam[1] = take(a.state_bytes);
+  a.off_pulled = take(36 * plane);
+  a.off_G = take(6 * plane);
+  a.off_dir = take(3 * plane);
+  a.off_mh = take(8 * plane);
+  a.off_M = take(3 * plane);
+  a.total = off;
+  return a;
+}
+
+}  // namespace
+
+extern "C" int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps,
+                                            size_t* bytes) {
+  if (!h || !bytes || inst < 0 || inst >= h->n || n_steps < 1)
+    return fail(LBVE_ERR_ARG, "bad handle, instance, step count or output pointer");
+  *bytes = make_adj_plan(h->p[inst], h->plan.inst[inst], n_steps).total;
+  return LBVE_OK;
+}
+
+extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* init_fields,
+                                 const double* d_dL_dfields, int64_t n_steps, void* d_ws,
+                                 size_t bytes, double* d_dL_dforce) {
+  if (!h || inst < 0 || inst >= h->n || !d_dL_dfields || !d_dL_dforce || n_steps < 1)
+    return fail(LBVE_ERR_ARG, "bad handle, instance, pointer or step count");
+  if (!h->ready[inst]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", inst);
+  const lbve_params& p = h->p[inst];
+  const InstPlan& q = h->plan.inst[inst];
+  const AdjPlan a = make_adj_plan(p, q, n_steps);
+  if (!d_ws || bytes < a.total)
+    return fail(LBVE_ERR_WORKSPACE, "adjoint workspace of %zu bytes given, %zu needed", bytes,
+                a.total);
+  if (reinterpret_cast<uintptr_t>(d_ws) % kAlign)
+    return fail(LBVE_ERR_WORKSPACE, "adjoint workspace not %zu-byte aligned", kAlign);
+  char* ws = (char*)d_ws;
+  cudaStream_t st = h->stream;
+  const int prec = p.precision;
+  const size_t nn = size_t(p.nx) * p.ny, S = q.stride;
+  const size_t es = prec == LBVE_FP64 ? 8 : 4;
+  const size_t plane = S * es;
+  cudaError_t e = cudaSuccess;
+
+  // single-instance descriptor and tile table (instance index 0)
+  InstDev D = h->insts[inst];
+  D.fields = (double*)(ws + a.off_fields);
+  D.slot_begin = 0;
+  D.slot_end = q.ntiles;
+  std::vector<TileDev> tiles(q.ntiles);
+  for (int ty = 0, k = 0; ty < q.nty; ++ty)
+    for (int tx = 0; tx < q.ntx; ++tx, ++k) tiles[k] = TileDev{0, tx * q.TX, ty * q.TY, k};
+  InstDev* d_desc = (InstDev*)(ws + a.off_desc);
+  TileDev* d_tiles = (TileDev*)(ws + a.off_tiles);
+  double* d_partials = (double*)(ws + a.off_partials);
+  e = cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TileDev) * q.ntiles, cudaMemcpyHostToDevice,
+                      st);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint tile upload");
+  auto set_desc = [&](void* pop0, void* pop1, void* hist) -> cudaError_t {
+    D.pop[0] = pop0;
+    D.pop[1] = pop1;
+    D.hist = hist;
+    // ordered on the stream; a pageable source is staged before the call
+    // returns, so D may change right after
+    return cudaMemcpyAsync(d_desc, &D, sizeof(InstDev), cudaMemcpyHostToDevice, st);
+  };
+  auto state = [&](char* base) { return base; };
+  auto hist_of = [&](char* st_) { return st_ + 36 * plane; };
+  char* ck = ws + a.off_ck;
+  char* seg = ws + a.off_seg;
+
+  // staged initial fields (float64 [6][S])
+  double* stage = (double*)(ws + a.off_stage);
+  if (init_fields) {
+    e = cudaMemcpy2DAsync(stage, S * 8, init_fields, nn * 8, nn * 8, 6, cudaMemcpyHostToDevice,
+                          st);
+  } else {
+    std::vector<double> def(6 * nn, 0.0);
+    for (size_t k = 0; k < nn; ++k) def[k] = def[3 * nn + k] = def[5 * nn + k] = 1.0;
+    e = cudaMemcpy2DAsync(stage, S * 8, def.data(), nn * 8, nn * 8, 6, cudaMemcpyHostToDevice,
+                          st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint initial-field upload");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "adjoint set-up");
+
+  // one forward step from state `from` into state `to` (history copied, then updated in place)
+  auto fwd = [&](char* from, char* to) -> int {
+    cudaError_t ee = cudaMemcpyAsync(hist_of(to), hist_of(from), 5 * plane,
+                                     cudaMemcpyDeviceToDevice, st);
+    if (ee != cudaSuccess) return cuda_fail(ee, "adjoint history copy");
+    if ((ee = set_desc(state(from), state(to), hist_of(to))) != cudaSuccess)
+      return cuda_fail(ee, "adjoint descriptor");
+    if (launch_step(prec, d_desc, d_tiles, q.ntiles, 0, kModeStep, 0, d_partials, st))
+      return cuda_fail(cudaGetLastError(), "adjoint forward step");
+    return LBVE_OK;
+  };
+
+  // ---- forward sweep: X_0 from the initial fields, checkpoints every s steps ----
+  if ((e = set_desc(stage, state(ck), hist_of(ck))) != cudaSuccess)
+    return cuda_fail(e, "adjoint descriptor");
+  if (launch_step(prec, d_desc, d_tiles, q.ntiles, 0, kModeInit, kFinal, d_partials, st))
+    return cuda_fail(cudaGetLastError(), "adjoint init step");
+  for (int64_t j = 1; j < a.nck; ++j) {
+    // X_{j s} from X_{(j-1) s}: s steps through two rolling buffers of the segment area
+    char* cur = ck + (j - 1) * a.state_bytes;
+    for (int64_t m = 0; m < a.s; ++m) {
+      char* nxt = (m == a.s - 1) ? ck + j * a.state_bytes : seg + (m % 2) * a.state_bytes;
+      const int rc = fwd(cur, nxt);
+      if (rc) return rc;
+      cur = nxt;
+    }
+  }
+
+  // ---- reverse sweep ----
+  AdjArgsRaw A;
+  std::memset(&A, 0, sizeof(A));
+  A.init = stage;
+  A.force = D.force_field ? D.force : nullptr;
+  A.M = ws + a.off_M;
+  A.lam_pulled = ws + a.off_pulled;
+  A.lam_G = ws + a.off_G;
+  A.lam_dir = ws + a.off_dir;
+  A.lam_mh = ws + a.off_mh;
+  A.dF = d_dL_dforce;
+  if ((e = cudaMemsetAsync(d_dL_dforce, 0, sizeof(double) * 2 * nn, st)) != cudaSuccess)
+    return cuda_fail(e, "gradient reset");
+  char* lam[2] = {ws + a.off_lam[0], ws + a.off_lam[1]};
+  int li = 0;  // lam[li] holds lambda of the most recent (later) state
+  const int n_nodes = (int)nn;
+  auto pass = [&](int mode, int which) -> int {
+    if (launch_adjoint(prec, mode, which, d_desc, A, n_nodes, st))
+      return cuda_fail(cudaGetLastError(), "adjoint pass launch");
+    return LBVE_OK;
+  };
+  bool first = true;  // the last state carries the loss
+  for (int64_t j = a.nck - 1; j >= 0; --j) {
+    const int64_t m0 = j * a.s, m1 = std::min<int64_t>((j + 1) * a.s, a.T);  // states m0..m1-1
+    // recompute the segment's states into seg[0 .. m1-m0-1]
+    e = cudaMemcpyAsync(seg, ck + j * a.state_bytes, a.state_bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint checkpoint copy");
+    for (int64_t m = m0 + 1; m < m1; ++m) {
+      const int rc = fwd(seg + (m - 1 - m0) * a.state_bytes, seg + (m - m0) * a.state_bytes);
+      if (rc) return rc;
+    }
+    for (int64_t m = m1 - 1; m >= m0; --m) {
+      char* X = seg + (m - m0) * a.state_bytes;
+      if ((e = set_desc(state(X), state(X), hist_of(X))) != cudaSuccess)
+        return cuda_fail(e, "adjoint descriptor");
+      A.X = X;
+      A.lam_cur = lam[li ^ 1];
+      int mode;
+      if (first) {
+        mode = kAdjFields;
+        A.lam_next = nullptr;
+        A.lam_fields = d_dL_dfields;
+        first = false;
+      } else {
+        mode = kAdjStep;
+        A.lam_next = lam[li];
+        A.lam_fields = nullptr;
+      }
+      int rc = pass(mode, 0);
+      if (!rc) rc = pass(mode, 1);
+      if (!rc) rc = pass(mode, 2);
+      if (!rc) rc = pass(mode, 3);
+      if (rc) return rc;
+      li ^= 1;
+    }
+  }
+  // the initial collision (X_0 from the equilibrium of the initial fields)
+  if ((e = set_desc(stage, ck, hist_of(ck))) != cudaSuccess)
+    return cuda_fail(e, "adjoint descriptor");
+  A.X = nullptr;
+  A.lam_next = lam[li];
+  A.lam_fields = nullptr;
+  A.lam_cur = lam[li ^ 1];
+  int rc = pass(kAdjInit, 0);
+  if (!rc) rc = pass(kAdjInit, 1);
+  if (!rc) rc = pass(kAdjInit, 2);
+  if (rc) return rc;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "lbve_adjoint_step");
+  return LBVE_OK;
+}

@@ -73,6 +73,28 @@ enum : int { kModeStep = 0, kModeInit = 1 };
 
 int launch_step(int prec, const InstDev* d_insts, const TileDev* d_tiles, int n_tiles,
                 int parity, int mode, int flags, double* d_partials, void* stream);
+// Adjoint pass modes: a normal step, the final fields (the loss), the initial collision.
+enum : int { kAdjStep = 0, kAdjFields = 1, kAdjInit = 2 };
+
+// Untyped pointers of one adjoint pass (see AdjArgs in lbve_adjoint.cuh).
+struct AdjArgsRaw {
+  const void* X;
+  const double* init;
+  const void* force;
+  void* M;
+  const void* lam_next;
+  const double* lam_fields;
+  void* lam_pulled;
+  void* lam_G;
+  void* lam_dir;
+  void* lam_mh;
+  void* lam_cur;
+  double* dF;
+};
+// pass: 0 moments, 1 local reverse, 2 gather, 3 reverse pull; mode: kAdjStep,
+// kAdjFields, kAdjInit (lbve_adjoint.cuh).
+int launch_adjoint(int prec, int mode, int pass, const InstDev* d_desc, const AdjArgsRaw& a,
+                   int n_nodes, void* stream);
 int launch_reduce(const InstDev* d_insts, int first_inst, int n_insts, const double* d_partials,
                   double* d_totals, int32_t* d_flags, void* stream);
 int launch_convert_force(int prec, const double* d_src, void* d_dst, int n, int stride,

@@ -29,7 +29,8 @@ LBVE_NTOTALS = 12
 
 EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_step",
             "lbve_status", "lbve_fields", "lbve_totals", "lbve_residual", "lbve_time",
-            "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc"]
+            "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc",
+            "lbve_adjoint_workspace_bytes", "lbve_adjoint_step"]
 
 
 class lbve_params(ctypes.Structure):
@@ -74,6 +75,10 @@ def load() -> ctypes.CDLL:
         L.lbve_residual.argtypes = [_vp, ctypes.c_int32, _dp]
         L.lbve_time.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
         L.lbve_field_totals_noalloc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
+        L.lbve_adjoint_workspace_bytes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64,
+                                                    ctypes.POINTER(ctypes.c_size_t)]
+        L.lbve_adjoint_step.argtypes = [_vp, ctypes.c_int32, _dp, _vp, ctypes.c_int64, _vp,
+                                        ctypes.c_size_t, _vp]
         L.lbve_destroy.argtypes = [_vp]
         L.lbve_destroy.restype = None
         L.lbve_error_string.argtypes = [ctypes.c_int]
@@ -178,6 +183,20 @@ def lbve_field_totals_noalloc(d_fields: int, nx: int, ny: int, d_out: int, strea
            "lbve_field_totals_noalloc")
 
 
+def lbve_adjoint_workspace_bytes(h, inst: int, n_steps: int) -> int:
+    out = ctypes.c_size_t()
+    _check(load().lbve_adjoint_workspace_bytes(h, inst, int(n_steps), ctypes.byref(out)),
+           "lbve_adjoint_workspace_bytes")
+    return out.value
+
+
+def lbve_adjoint_step(h, inst: int, init_fields, d_dL_dfields: int, n_steps: int, d_ws: int,
+                      nbytes: int, d_dL_dforce: int, n_nodes: int) -> None:
+    ini, ini_ptr = _f64(init_fields, 6 * n_nodes) if init_fields is not None else (None, None)
+    _check(load().lbve_adjoint_step(h, inst, ini_ptr, _vp(d_dL_dfields), int(n_steps), _vp(d_ws),
+                                    nbytes, _vp(d_dL_dforce)), "lbve_adjoint_step")
+
+
 def lbve_destroy(h) -> None:
     if h:
         load().lbve_destroy(h)
@@ -248,3 +267,37 @@ class Simulation:
 
     def time(self, i: int = 0) -> int:
         return lbve_time(self.h, i)
+
+
+def force_to_fields(sim: "Simulation", inst: int, force, n_steps: int, init_fields=None):
+    """Differentiable map per-node body force -> fields after n_steps steps.
+
+    ``force`` is a float64 torch tensor [2, ny, nx] (requires_grad allowed);
+    the result is the float64 device tensor [6, ny, nx] of (rho, ux, uy, Axx,
+    Axy, Ayy).  The backward pass calls lbve_adjoint_step (hand-written
+    adjoint with sqrt(T) checkpointing)."""
+    import torch
+
+    class _ForceToFields(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, f):
+            ctx.in_device = f.device
+            inst_obj = sim.instances[inst]
+            host = f.detach().to("cpu", torch.float64).contiguous().numpy()
+            lbve_set_geometry(sim.h, inst, None, host, init_fields, n_nodes=inst_obj.n_nodes)
+            sim.step(n_steps)
+            return sim.fields_device(inst)
+
+        @staticmethod
+        def backward(ctx, grad_fields):
+            inst_obj = sim.instances[inst]
+            g = grad_fields.to(sim.device, torch.float64).contiguous()
+            nbytes = lbve_adjoint_workspace_bytes(sim.h, inst, n_steps)
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=sim.device)
+            out = torch.empty((2, inst_obj.ny, inst_obj.nx), dtype=torch.float64,
+                              device=sim.device)
+            lbve_adjoint_step(sim.h, inst, init_fields, g.data_ptr(), n_steps, ws.data_ptr(),
+                              nbytes, out.data_ptr(), inst_obj.n_nodes)
+            return out.to(ctx.in_device)
+
+    return _ForceToFields.apply(force)
