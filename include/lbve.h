@@ -116,7 +116,9 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
 
 /* Advance every instance by n_steps >= 0 time steps (asynchronous on the
  * stream).  The last step of the call also refreshes the macroscopic fields,
- * the float64 totals, the residual and the non-finite flags.
+ * the float64 totals, the residual and the non-finite flags.  Runs of 32
+ * non-final steps are replayed from a CUDA graph captured on first use (a
+ * driver-managed object owned by the handle, released by lbve_destroy).
  * Errors: LBVE_ERR_STATE if an instance was never initialised,
  * LBVE_ERR_CUDA if a launch failed. */
 int lbve_step(lbve_handle* h, int64_t n_steps);
@@ -149,6 +151,21 @@ int lbve_residual(lbve_handle* h, int32_t inst, double* out);
 
 /* Current time step of instance inst. */
 int lbve_time(lbve_handle* h, int32_t inst, int64_t* t);
+
+/* Host bytes of a saved state of every instance of h (lbve_save/lbve_load). */
+int lbve_state_bytes(lbve_handle* h, size_t* bytes);
+
+/* Checkpoint: copy every instance's current state -- 36 post-collision
+ * populations, 5 history values and the force (storage precision), the
+ * float64 fields, the time and the set-up flags -- into host_buf
+ * (>= lbve_state_bytes()).  Synchronises the stream. */
+int lbve_save(lbve_handle* h, void* host_buf, size_t bytes);
+
+/* Resume: restore a state saved by lbve_save() into a handle created with the
+ * same parameters (checked: instance count, grid, precision, walls).  The
+ * continuation is bit-identical to the saved run's.  Synchronises.
+ * Errors: LBVE_ERR_ARG on a size or parameter mismatch, LBVE_ERR_CUDA. */
+int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes);
 
 /* Bytes of device workspace lbve_adjoint_step() needs for instance inst and
  * a trajectory of n_steps >= 1 steps (sqrt(n_steps) checkpoints and one

@@ -186,7 +186,53 @@ struct lbve_handle {
   int parity = 0;
   std::vector<int64_t> t;
   std::vector<char> ready;
+  // CUDA graph of kGraphSteps non-final steps starting at parity 0, captured
+  // on a private stream on first use and replayed on the caller's stream
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
 };
+
+namespace {
+
+constexpr int kGraphSteps = 32;  // even, so a replay leaves the parity unchanged
+
+// Launch one time step of every tile list on stream st with the given parity.
+int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
+  for (int l = 0; l < kLists; ++l)
+    if (h->plan.ntiles[l] > 0 &&
+        launch_step(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_tiles[l],
+                    h->plan.ntiles[l], parity, kModeStep, flags, h->d_partials, st))
+      return cuda_fail(cudaGetLastError(), "step kernel launch");
+  return LBVE_OK;
+}
+
+int ensure_graph(lbve_handle* h) {
+  if (h->graph_exec) return LBVE_OK;
+  cudaError_t e = cudaSuccess;
+  if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture start");
+  int rc = LBVE_OK;
+  for (int s = 0; s < kGraphSteps && rc == LBVE_OK; ++s) rc = launch_one_step(h, s & 1, 0, h->cap_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+  e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    h->graph_exec = nullptr;
+    return cuda_fail(e, "graph instantiation");
+  }
+  h->graph = g;
+  return LBVE_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -386,20 +432,36 @@ int lbve_step(lbve_handle* h, int64_t n_steps) {
   if (!h || n_steps < 0) return fail(LBVE_ERR_ARG, "bad handle or negative step count");
   for (int i = 0; i < h->n; ++i)
     if (!h->ready[i]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", i);
-  for (int64_t s = 0; s < n_steps; ++s) {
-    const int flags = (s == n_steps - 1) ? kFinal : 0;
-    for (int l = 0; l < kLists; ++l)
-      if (h->plan.ntiles[l] > 0 &&
-          launch_step(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_tiles[l],
-                      h->plan.ntiles[l], h->parity, kModeStep, flags, h->d_partials, h->stream))
-        return cuda_fail(cudaGetLastError(), "step kernel launch");
+  if (n_steps == 0) return LBVE_OK;
+  int64_t left = n_steps - 1;  // non-final steps
+  // non-final steps: whole graphs where possible (they start at parity 0)
+  if (left >= kGraphSteps + (h->parity ? 1 : 0)) {
+    if (h->parity) {
+      const int rc = launch_one_step(h, 1, 0, h->stream);
+      if (rc) return rc;
+      h->parity = 0;
+      --left;
+    }
+    int rc = ensure_graph(h);
+    if (rc) return rc;
+    while (left >= kGraphSteps) {
+      const cudaError_t e = cudaGraphLaunch(h->graph_exec, h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+      left -= kGraphSteps;
+    }
+  }
+  for (; left > 0; --left) {
+    const int rc = launch_one_step(h, h->parity, 0, h->stream);
+    if (rc) return rc;
     h->parity ^= 1;
   }
-  if (n_steps > 0) {
-    if (launch_reduce(h->d_insts, 0, h->n, h->d_partials, h->d_totals, h->d_flags, h->stream))
-      return cuda_fail(cudaGetLastError(), "reduce launch");
-    for (int i = 0; i < h->n; ++i) h->t[i] += n_steps;
-  }
+  // the final step also writes fields and partial records
+  int rc = launch_one_step(h, h->parity, kFinal, h->stream);
+  if (rc) return rc;
+  h->parity ^= 1;
+  if (launch_reduce(h->d_insts, 0, h->n, h->d_partials, h->d_totals, h->d_flags, h->stream))
+    return cuda_fail(cudaGetLastError(), "reduce launch");
+  for (int i = 0; i < h->n; ++i) h->t[i] += n_steps;
   return LBVE_OK;
 }
 
@@ -461,9 +523,133 @@ int lbve_time(lbve_handle* h, int32_t inst, int64_t* t) {
   return LBVE_OK;
 }
 
+// ---- checkpoint / resume -------------------------------------------------
+namespace {
+constexpr uint32_t kStateMagic = 0x4556424cu;  // "LBVE"
+constexpr uint32_t kStateVersion = 1;
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t n, reserved;
+};
+struct InstHeader {
+  int64_t t;
+  int32_t nx, ny, precision, periodic_y, force_field, ready;
+};
+size_t inst_state_bytes(const lbve_params& p) {
+  const size_t nn = size_t(p.nx) * p.ny, es = p.precision == LBVE_FP64 ? 8 : 4;
+  return sizeof(InstHeader) + (36 + 5 + 2) * nn * es + 6 * nn * 8;
+}
+}  // namespace
+
+int lbve_state_bytes(lbve_handle* h, size_t* bytes) {
+  if (!h || !bytes) return fail(LBVE_ERR_ARG, "null argument");
+  size_t b = sizeof(StateHeader);
+  for (int i = 0; i < h->n; ++i) b += inst_state_bytes(h->p[i]);
+  *bytes = b;
+  return LBVE_OK;
+}
+
+int lbve_save(lbve_handle* h, void* host_buf, size_t bytes) {
+  size_t need = 0;
+  int rc = lbve_state_bytes(h, &need);
+  if (rc) return rc;
+  if (!host_buf || bytes < need) return fail(LBVE_ERR_ARG, "state buffer of %zu bytes, %zu needed", bytes, need);
+  char* out = (char*)host_buf;
+  StateHeader H{kStateMagic, kStateVersion, h->n, 0};
+  std::memcpy(out, &H, sizeof(H));
+  out += sizeof(H);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < h->n && e == cudaSuccess; ++i) {
+    const lbve_params& p = h->p[i];
+    const InstDev& D = h->insts[i];
+    const size_t nn = size_t(p.nx) * p.ny, S = D.stride, es = p.precision == LBVE_FP64 ? 8 : 4;
+    InstHeader I{h->t[i], p.nx, p.ny, p.precision, p.periodic_y, D.force_field, h->ready[i]};
+    std::memcpy(out, &I, sizeof(I));
+    out += sizeof(I);
+    // current populations (36), history (5), force (2): planes of nn values
+    e = cudaMemcpy2DAsync(out, nn * es, D.pop[h->parity], S * es, nn * es, 36,
+                          cudaMemcpyDeviceToHost, h->stream);
+    out += 36 * nn * es;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(out, nn * es, D.hist, S * es, nn * es, 5, cudaMemcpyDeviceToHost,
+                            h->stream);
+    out += 5 * nn * es;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(out, nn * es, D.force, S * es, nn * es, 2, cudaMemcpyDeviceToHost,
+                            h->stream);
+    out += 2 * nn * es;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(out, nn * 8, D.fields, S * 8, nn * 8, 6, cudaMemcpyDeviceToHost,
+                            h->stream);
+    out += 6 * nn * 8;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbve_save");
+  return LBVE_OK;
+}
+
+int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes) {
+  size_t need = 0;
+  int rc = lbve_state_bytes(h, &need);
+  if (rc) return rc;
+  if (!host_buf || bytes < need) return fail(LBVE_ERR_ARG, "state buffer of %zu bytes, %zu needed", bytes, need);
+  const char* in = (const char*)host_buf;
+  StateHeader H;
+  std::memcpy(&H, in, sizeof(H));
+  in += sizeof(H);
+  if (H.magic != kStateMagic || H.version != kStateVersion || H.n != h->n)
+    return fail(LBVE_ERR_ARG, "state was not saved by lbve_save for this instance count");
+  // validate every instance header before touching the device
+  const char* scan = in;
+  for (int i = 0; i < h->n; ++i) {
+    InstHeader I;
+    std::memcpy(&I, scan, sizeof(I));
+    const lbve_params& p = h->p[i];
+    if (I.nx != p.nx || I.ny != p.ny || I.precision != p.precision || I.periodic_y != p.periodic_y)
+      return fail(LBVE_ERR_ARG, "saved instance %d does not match this handle's parameters", i);
+    scan += inst_state_bytes(p);
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < h->n && e == cudaSuccess; ++i) {
+    InstHeader I;
+    std::memcpy(&I, in, sizeof(I));
+    in += sizeof(I);
+    const lbve_params& p = h->p[i];
+    InstDev& D = h->insts[i];
+    const size_t nn = size_t(p.nx) * p.ny, S = D.stride, es = p.precision == LBVE_FP64 ? 8 : 4;
+    e = cudaMemcpy2DAsync(D.pop[h->parity], S * es, in, nn * es, nn * es, 36,
+                          cudaMemcpyHostToDevice, h->stream);
+    in += 36 * nn * es;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(D.hist, S * es, in, nn * es, nn * es, 5, cudaMemcpyHostToDevice,
+                            h->stream);
+    in += 5 * nn * es;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(D.force, S * es, in, nn * es, nn * es, 2, cudaMemcpyHostToDevice,
+                            h->stream);
+    in += 2 * nn * es;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(D.fields, S * 8, in, nn * 8, nn * 8, 6, cudaMemcpyHostToDevice,
+                            h->stream);
+    in += 6 * nn * 8;
+    D.force_field = I.force_field;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->d_insts + i, &D, sizeof(InstDev), cudaMemcpyHostToDevice, h->stream);
+    h->t[i] = I.t;
+    h->ready[i] = (char)I.ready;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int32_t) * h->n, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbve_load");
+  return LBVE_OK;
+}
+
 void lbve_destroy(lbve_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 

@@ -30,7 +30,8 @@ LBVE_NTOTALS = 12
 EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_step",
             "lbve_status", "lbve_fields", "lbve_totals", "lbve_residual", "lbve_time",
             "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc",
-            "lbve_adjoint_workspace_bytes", "lbve_adjoint_step"]
+            "lbve_adjoint_workspace_bytes", "lbve_adjoint_step", "lbve_state_bytes", "lbve_save",
+            "lbve_load"]
 
 
 class lbve_params(ctypes.Structure):
@@ -79,6 +80,9 @@ def load() -> ctypes.CDLL:
                                                     ctypes.POINTER(ctypes.c_size_t)]
         L.lbve_adjoint_step.argtypes = [_vp, ctypes.c_int32, _dp, _vp, ctypes.c_int64, _vp,
                                         ctypes.c_size_t, _vp]
+        L.lbve_state_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.lbve_save.argtypes = [_vp, _vp, ctypes.c_size_t]
+        L.lbve_load.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.lbve_destroy.argtypes = [_vp]
         L.lbve_destroy.restype = None
         L.lbve_error_string.argtypes = [ctypes.c_int]
@@ -195,6 +199,24 @@ def lbve_adjoint_step(h, inst: int, init_fields, d_dL_dfields: int, n_steps: int
     ini, ini_ptr = _f64(init_fields, 6 * n_nodes) if init_fields is not None else (None, None)
     _check(load().lbve_adjoint_step(h, inst, ini_ptr, _vp(d_dL_dfields), int(n_steps), _vp(d_ws),
                                     nbytes, _vp(d_dL_dforce)), "lbve_adjoint_step")
+
+
+def lbve_state_bytes(h) -> int:
+    out = ctypes.c_size_t()
+    _check(load().lbve_state_bytes(h, ctypes.byref(out)), "lbve_state_bytes")
+    return out.value
+
+
+def lbve_save(h) -> bytes:
+    n = lbve_state_bytes(h)
+    buf = ctypes.create_string_buffer(n)
+    _check(load().lbve_save(h, buf, n), "lbve_save")
+    return buf.raw
+
+
+def lbve_load(h, state: bytes) -> None:
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(load().lbve_load(h, buf, len(state)), "lbve_load")
 
 
 def lbve_destroy(h) -> None:
