@@ -40,12 +40,25 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--instances", type=int, default=N_INSTANCES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=100)
     return ap.parse_args()
+
+
+def rank_seed(rank: int) -> int:
+    """Base seed of a rank's batch: every rank runs its own independent mix
+    (weak scaling, no data exchange between ranks)."""
+    return BASE_SEED + 100003 * rank
 
 
 def workload(rank: int, n: int):
     from paper_2508_16997_gb300 import workloads as wl
-    return wl.batch_mix(n=n, base_seed=BASE_SEED + 100003 * rank)
+    return wl.batch_mix(n=n, base_seed=rank_seed(rank))
+
+
+def job_value(job_nodes: int, steps: int, seconds_max: float) -> float:
+    """Whole-job MLUPS: the lattice updates of all ranks (job_nodes nodes in
+    total, each advanced `steps` steps) over the slowest rank's time."""
+    return job_nodes * steps / seconds_max / 1e6
 
 
 def bytes_per_lu(inst, elem: int) -> int:
@@ -169,6 +182,29 @@ def dist_setup(args):
     return world, rank, local
 
 
+def reduce_max(v: float, world: int, device: str = "cpu") -> float:
+    """Maximum of v over the ranks of the default process group (v itself
+    when running alone)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(v: float, world: int, device: str = "cpu") -> float:
+    """Sum of v over the ranks of the default process group."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def cpu_sample(insts, budget_nodes: int):
     """Smallest instances of the mix, in order, up to budget_nodes nodes."""
     chosen, total = [], 0
@@ -248,14 +284,11 @@ def run_ours(args):
             torch.distributed.barrier()
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, world, device="cuda")
 
     insts = workload(rank, args.instances)
     total_nodes = sum(i.n_nodes for i in insts)
+    job_nodes = int(reduce_sum(float(total_nodes), world, device="cuda"))
     stream = torch.cuda.current_stream()
     K, W = args.steps, args.warmup
 
@@ -275,7 +308,7 @@ def run_ours(args):
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1))
     flags = sim.status()
-    value = world * total_nodes * K / (ms / 1e3) / 1e6
+    value = job_value(job_nodes, K, ms / 1e3)
     bytes_launch = sum(i.n_nodes * bytes_per_lu(i, 4) for i in insts)
     achieved = bytes_launch / (ms / 1e3 / K) / 1e9
     peak, peak_kind = measured_peaks()
@@ -307,7 +340,7 @@ def run_ours(args):
         lbve.lbve_fields(sim.h, j, pinned_out[j].data_ptr(), False)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = world * total_nodes * K / e2e_s / 1e6
+    e2e_value = job_value(job_nodes, K, e2e_s)
 
     # ---- plain FP64 on the same mix, and the FP32 error against it ---------
     K64 = max(1, K // 10)
@@ -322,7 +355,7 @@ def run_ours(args):
     f1.record(stream)
     torch.cuda.synchronize()
     ms64 = max_over_ranks(f0.elapsed_time(f1))
-    value64 = world * total_nodes * K64 / (ms64 / 1e3) / 1e6
+    value64 = job_value(job_nodes, K64, ms64 / 1e3)
     for j in range(len(insts)):  # FP32 run from the same initial state, same step count
         lbve.lbve_set_geometry(sim.h, j, None, insts[j].force_field, None,
                                n_nodes=insts[j].n_nodes)
@@ -342,6 +375,35 @@ def run_ours(args):
             err_le100 = max(err_le100, e)
     err_all = max_over_ranks(err_all)
     err_le100 = max_over_ranks(err_le100)
+
+    # ---- adjoint: the 512^2 four-roll mill, FP32, sqrt(T) checkpointing ----
+    adj = None
+    if args.adjoint_steps > 0:
+        from paper_2508_16997_gb300 import workloads as wl
+        Ta = args.adjoint_steps
+        fi = wl.frm(512, Wi=5.0)
+        asim = lbve.Simulation([fi], precision=lbve.LBVE_FP32_DEV)
+        asim.step(Ta)
+        fields = asim.fields_device(0)
+        g = torch.zeros_like(fields)
+        g[1:3] = fields[1:3]  # dL/du of L = 1/2 |u|^2
+        nbytes = lbve.lbve_adjoint_workspace_bytes(asim.h, 0, Ta)
+        aws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        dF = torch.empty((2, 512, 512), dtype=torch.float64, device="cuda")
+        lbve.lbve_adjoint_step(asim.h, 0, None, g.data_ptr(), Ta, aws.data_ptr(), nbytes,
+                               dF.data_ptr(), fi.n_nodes)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lbve.lbve_adjoint_step(asim.h, 0, None, g.data_ptr(), Ta, aws.data_ptr(), nbytes,
+                               dF.data_ptr(), fi.n_nodes)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        adj = {"workload": "four-roll mill 512^2, beta 0.5, Wi 5, FP32, loss 1/2 |u(T)|^2",
+               "steps": Ta, "seconds": dt, "ms_per_reversed_step": 1e3 * dt / Ta,
+               "workspace_bytes": nbytes,
+               "includes": "forward recompute from the initial fields (checkpoints + segments) "
+                           "and the reverse sweep"}
+        del aws, asim
 
     if rank != 0:
         if world > 1:
@@ -371,6 +433,8 @@ def run_ours(args):
                                 "steps": W + K64, "target_Wi_le_100": 1e-5},
         "nonfinite_instances": int((flags != 0).sum()),
     }
+    if adj is not None:
+        line["adjoint"] = adj
     if world == 1 and not args.no_cpu_baseline:
         sample, nodes = cpu_sample(insts, 50000)
         steps_cpu = 200

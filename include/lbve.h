@@ -80,6 +80,13 @@ typedef struct {
   double Lambda_s;    /* hydrodynamic magic parameter (Sec. 3.1), > 0       */
   double Lambda_p;    /* conformation magic parameter (Sec. 3.2), > 0       */
   double Fx, Fy;      /* uniform body force, used when no force field given */
+  int32_t tile_tx;    /* tile width in nodes along x for the step kernel:
+                         0 = library default (min(32, nx)), else 1..128 and
+                         <= nx (e.g. a width lbve_autotune() returned).  A
+                         pure performance setting: each node's update does
+                         not depend on the tiling; only the summation order
+                         of the float64 totals follows the tiles.  The
+                         workspace size does not depend on it.             */
 } lbve_params;
 
 typedef struct lbve_handle lbve_handle;
@@ -87,6 +94,26 @@ typedef struct lbve_handle lbve_handle;
 /* Bytes of device workspace needed for n_instances problems p[0..n-1].
  * Pure host computation.  Errors: LBVE_ERR_ARG for invalid parameters. */
 int lbve_workspace_bytes(const lbve_params* p, int32_t n_instances, size_t* bytes);
+
+/* Tile-width autotuner (the paper has no counterpart: the step kernel's
+ * tiling is an implementation choice).  Times the batch p[0..n-1] with
+ * candidate tile widths -- the divisors-of-two widths 8..128 that fit nx,
+ * or nx itself when nx < 8 -- and writes the fastest width of each instance
+ * to tile_tx_out[0..n-1] (never 0).  Instances with the same candidates,
+ * precision and wall layout share one width; one pass of coordinate descent
+ * over these classes keeps a width only when the whole batch gets more than
+ * 1% faster.  Each timing is trial_steps (1..100000) steps of lbve_step()
+ * from the rest state with the uniform force of p, after as many warm-up
+ * steps, best of two.
+ *   d_workspace: >= lbve_workspace_bytes(p, n) bytes of device memory,
+ *                256-byte aligned; used as scratch and left undefined, so it
+ *                must not belong to a live handle (a handle may be created
+ *                on it afterwards).
+ *   cuda_stream: the stream the trials run on; synchronised.  The call
+ *                refuses (LBVE_ERR_STATE) while that stream is capturing.
+ * Errors: LBVE_ERR_ARG, LBVE_ERR_WORKSPACE, LBVE_ERR_STATE, LBVE_ERR_CUDA. */
+int lbve_autotune(const lbve_params* p, int32_t n_instances, void* d_workspace, size_t bytes,
+                  void* cuda_stream, int32_t trial_steps, int32_t* tile_tx_out);
 
 /* Create a handle for n_instances independent problems p[0..n-1] that are
  * advanced together, one launch per precision per time step.

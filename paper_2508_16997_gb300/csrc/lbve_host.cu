@@ -83,6 +83,9 @@ int validate(const lbve_params& p, int i) {
                 i);
   if (!std::isfinite(p.Fx) || !std::isfinite(p.Fy))
     return fail(LBVE_ERR_ARG, "instance %d: body force must be finite", i);
+  if (p.tile_tx != 0 && (p.tile_tx < 1 || p.tile_tx > kTileTXMax || p.tile_tx > p.nx))
+    return fail(LBVE_ERR_ARG, "instance %d: tile_tx must be 0 or in [1, min(%d, nx)]", i,
+                kTileTXMax);
   const Coeffs c = derive(p);
   if (!(c.tau_s1 > 0.5) || !(c.tau_p1 > 0.5) || !std::isfinite(c.tau_s2) ||
       !std::isfinite(c.tau_p2) || !finite_pos(c.lambda))
@@ -105,19 +108,35 @@ struct Plan {
   std::vector<InstPlan> inst;
   size_t off_insts, off_tiles[kLists], off_partials, off_totals, off_flags, total;
   int ntiles[kLists], nslots;
+  int cap_tiles[kLists];  // tile-table capacity: the most tiles any tile width gives
 };
 
+int default_tile_tx(const lbve_params& p) { return p.nx >= kTileTX ? kTileTX : p.nx; }
+
 void tile_shape(const lbve_params& p, int& TX, int& TY, int& hy) {
-  TX = p.nx >= kTileTX ? kTileTX : p.nx;
+  TX = p.tile_tx > 0 ? p.tile_tx : default_tile_tx(p);
   TY = kThreads / TX;
   hy = p.periodic_y ? 1 : 2;
+}
+
+int64_t tiles_for(const lbve_params& p, int TX) {
+  const int TY = kThreads / TX;
+  return int64_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
+}
+
+// Most tiles any admissible tile width gives for p: the workspace layout is
+// sized by it, so the same workspace serves every tile width.
+int64_t max_tiles(const lbve_params& p) {
+  int64_t m = 0;
+  for (int TX = 1; TX <= std::min(kTileTXMax, p.nx); ++TX) m = std::max(m, tiles_for(p, TX));
+  return m;
 }
 
 Plan make_plan(const lbve_params* p, int n) {
   Plan pl;
   pl.inst.resize(n);
   size_t off = 0;
-  for (int l = 0; l < kLists; ++l) pl.ntiles[l] = 0;
+  for (int l = 0; l < kLists; ++l) pl.ntiles[l] = pl.cap_tiles[l] = 0;
   for (int i = 0; i < n; ++i) {
     InstPlan& q = pl.inst[i];
     const size_t es = p[i].precision == LBVE_FP64 ? 8 : 4;
@@ -141,6 +160,7 @@ Plan make_plan(const lbve_params* p, int n) {
     q.tile_begin = pl.ntiles[q.list];
     q.ntiles = q.ntx * q.nty;
     pl.ntiles[q.list] += q.ntiles;
+    pl.cap_tiles[q.list] += (int)max_tiles(p[i]);
   }
   // partial-record slots: [list 0 | list 1]
   pl.nslots = 0;
@@ -156,10 +176,11 @@ Plan make_plan(const lbve_params* p, int n) {
   off = align_up(off + sizeof(InstDev) * n, kAlign);
   for (int l = 0; l < kLists; ++l) {
     pl.off_tiles[l] = off;
-    off = align_up(off + sizeof(TileDev) * std::max(pl.ntiles[l], 1), kAlign);
+    off = align_up(off + sizeof(TileDev) * std::max(pl.cap_tiles[l], 1), kAlign);
   }
   pl.off_partials = off;
-  off = align_up(off + sizeof(double) * kPartial * std::max(pl.nslots, 1), kAlign);
+  off = align_up(off + sizeof(double) * kPartial * std::max(pl.cap_tiles[0] + pl.cap_tiles[1], 1),
+                 kAlign);
   pl.off_totals = off;
   off = align_up(off + sizeof(double) * kTotals * n, kAlign);
   pl.off_flags = off;
@@ -654,6 +675,129 @@ void lbve_destroy(lbve_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Tile-width autotuner.  The batch is timed as a whole (one launch per
+// precision per step covers every instance, so widths interact only through
+// the shared launch); instances are grouped into classes that admit the same
+// candidate widths and have the same precision and wall layout, and one pass
+// of coordinate descent over the classes keeps a width only when it beats the
+// incumbent by more than kAutotuneGain.
+namespace {
+
+constexpr double kAutotuneGain = 0.01;
+constexpr int kAutotuneRepeats = 2;  // the fastest of these timings counts
+
+std::vector<int> width_candidates(const lbve_params& p) {
+  std::vector<int> c;
+  if (p.nx < 8) c.push_back(p.nx);
+  for (int t = 8; t <= kTileTXMax; t *= 2)
+    if (t <= p.nx) c.push_back(t);
+  return c;
+}
+
+// Milliseconds per step of trial_steps steps of the batch with tile widths
+// q[i].tile_tx, from the rest state, on a handle built in the workspace.
+int time_batch(const std::vector<lbve_params>& q, void* d_ws, size_t bytes, cudaStream_t st,
+               int trial_steps, cudaEvent_t ev[2], double& ms_out) {
+  ms_out = 1e300;
+  for (int r = 0; r < kAutotuneRepeats; ++r) {
+    lbve_handle* h = nullptr;
+    int rc = lbve_create(q.data(), (int32_t)q.size(), d_ws, bytes, st, &h);
+    if (rc) return rc;
+    for (int i = 0; i < (int)q.size() && rc == LBVE_OK; ++i)
+      rc = lbve_set_geometry(h, i, nullptr, nullptr, nullptr);
+    if (rc == LBVE_OK) rc = lbve_step(h, trial_steps);  // warm-up, builds the step graph
+    cudaError_t e = cudaSuccess;
+    if (rc == LBVE_OK) {
+      e = cudaEventRecord(ev[0], st);
+      if (e == cudaSuccess && (rc = lbve_step(h, trial_steps)) == LBVE_OK) {
+        e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e == cudaSuccess) ms_out = std::min(ms_out, double(ms) / trial_steps);
+      }
+    }
+    lbve_destroy(h);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+  }
+  return LBVE_OK;
+}
+
+}  // namespace
+
+extern "C" int lbve_autotune(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes,
+                             void* cuda_stream, int32_t trial_steps, int32_t* tile_tx_out) {
+  if (!tile_tx_out) return fail(LBVE_ERR_ARG, "tile_tx_out is null");
+  if (trial_steps < 1 || trial_steps > 100000)
+    return fail(LBVE_ERR_ARG, "trial_steps must be in [1, 100000]");
+  size_t need = 0;
+  int rc = lbve_workspace_bytes(p, n, &need);
+  if (rc) return rc;
+  if (!d_workspace || bytes < need)
+    return fail(LBVE_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", bytes, need);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return cuda_fail(e, "stream query");
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(LBVE_ERR_STATE, "lbve_autotune cannot run while the stream is being captured");
+
+  std::vector<lbve_params> q(p, p + n);
+  for (auto& x : q) x.tile_tx = x.tile_tx > 0 ? x.tile_tx : default_tile_tx(x);
+  // classes of instances with the same candidates, precision and walls
+  std::vector<int> cls(n, -1);
+  std::vector<std::vector<int>> cand_of;
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < n; ++i) {
+    const std::vector<int> c = width_candidates(q[i]);
+    for (size_t k = 0; k < cand_of.size() && cls[i] < 0; ++k) {
+      const lbve_params& r = q[members[k][0]];
+      if (cand_of[k] == c && r.precision == q[i].precision && r.periodic_y == q[i].periodic_y)
+        cls[i] = (int)k;
+    }
+    if (cls[i] < 0) {
+      cls[i] = (int)cand_of.size();
+      cand_of.push_back(c);
+      members.emplace_back();
+    }
+    members[cls[i]].push_back(i);
+  }
+
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  if (e != cudaSuccess) {
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    return cuda_fail(e, "event creation");
+  }
+  double best = 0.0;
+  rc = time_batch(q, d_workspace, bytes, st, trial_steps, ev, best);
+  for (size_t k = 0; k < cand_of.size() && rc == LBVE_OK; ++k) {
+    if (cand_of[k].size() < 2) continue;
+    const int incumbent = q[members[k][0]].tile_tx;
+    int keep = incumbent;
+    for (int c : cand_of[k]) {
+      if (c == incumbent) continue;
+      for (int i : members[k]) q[i].tile_tx = c;
+      double ms = 0.0;
+      rc = time_batch(q, d_workspace, bytes, st, trial_steps, ev, ms);
+      if (rc) break;
+      if (ms < best * (1.0 - kAutotuneGain)) {
+        best = ms;
+        keep = c;
+      }
+    }
+    for (int i : members[k]) q[i].tile_tx = keep;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) tile_tx_out[i] = q[i].tile_tx;
+  return LBVE_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Adjoint: gradient of a loss on the final fields with respect to the

@@ -12,8 +12,11 @@ namespace lbve {
 #define LBVE_TILE_TX 32
 #endif
 constexpr int kThreads = LBVE_THREADS;  // threads per CTA of the step kernel
-constexpr int kTileTX = LBVE_TILE_TX;   // tile width (nodes along x) for nx >= kTileTX
-// (TX+2)(TY+2*hy) <= 3 (kThreads + 4) for every TX >= 1, TY = kThreads / TX, hy <= 2
+constexpr int kTileTX = LBVE_TILE_TX;   // default tile width (nodes along x) for nx >= kTileTX
+constexpr int kTileTXMax = kThreads / 2;  // widest tile a caller may ask for
+// Halo region of a tile: (TX+2)(TY+2*hy) <= (TX+2)(kThreads/TX+4)
+// = kThreads + 4 TX + 2 kThreads/TX + 8, which is convex in TX and equals
+// 3 (kThreads + 4) at both ends of 1 <= TX <= kTileTXMax (TY = kThreads/TX, hy <= 2).
 constexpr int kRegionMax = 3 * (kThreads + 4);
 constexpr int kPartial = 16;      // doubles per tile partial record
 constexpr int kTotals = 16;       // doubles per instance totals record

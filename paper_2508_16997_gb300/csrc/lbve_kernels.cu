@@ -7,10 +7,33 @@
 
 namespace lbve {
 
+#ifndef LBVE_PERSISTENT
+#define LBVE_PERSISTENT 0
+#endif
+
 template <typename R, int MODE, bool FINAL>
 static void launch_step_k(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
                           double* d_partials, cudaStream_t st) {
-  step_kernel<R, MODE, FINAL><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, parity, d_partials);
+  // Persistent grid (resident CTAs per SM x SMs) for the time steps, one CTA
+  // per tile for the initialisation.
+  static int resident = 0;  // CTAs that fit on the device at once
+  if (LBVE_PERSISTENT && MODE == kModeStep && resident == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<R, MODE, FINAL, true>,
+                                                      kThreads, 0) == cudaSuccess)
+      resident = sms * per_sm;
+    else
+      resident = -1;
+  }
+  if (LBVE_PERSISTENT && MODE == kModeStep && resident > 0 && n_tiles > resident) {
+    step_kernel<R, MODE, FINAL, true><<<resident, kThreads, 0, st>>>(d_insts, d_tiles, n_tiles,
+                                                                     parity, d_partials);
+  } else {
+    step_kernel<R, MODE, FINAL, false><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, n_tiles,
+                                                                     parity, d_partials);
+  }
 }
 
 template <typename R>

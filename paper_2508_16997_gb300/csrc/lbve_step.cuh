@@ -260,8 +260,9 @@ __device__ __forceinline__ void node_rho_u(const void* src, const R* __restrict_
   HydroM<R> m;
   hydro_moments<R>(d, m);
   rho = R(1) + m.drho;
-  ux = (m.jx + R(0.5) * Fx) / rho;
-  uy = (m.jy + R(0.5) * Fy) / rho;
+  const R irho = R(1) / rho;
+  ux = (m.jx + R(0.5) * Fx) * irho;
+  uy = (m.jy + R(0.5) * Fy) * irho;
 }
 
 template <typename R>
@@ -365,6 +366,7 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
   {
     const R cs2 = R(1.0 / 3.0);
     const R ep = coef<R>(D, kCoefEp1), c2 = coef<R>(D, kCoefCp2), h1 = coef<R>(D, kCoefHp1);
+    const R irho = R(1) / rho;
     const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
@@ -376,7 +378,7 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
       const R sl = Sc[l], so = So[l];
       // small source terms first, one rounding at the magnitude of phi
       const R c0p = cm[l].dphi + (R(1.5) * sl - R(0.5) * so);
-      const R pr = phi / rho;
+      const R pr = phi * irho;
       // (1 - 1/tau_p1) B = -B + ep B, kept split so float32 keeps the tiny
       // difference tau_p1 - 1/2 accurately
       const R cx = (phi * ux - Bx) + ep * Bx + h1 * (pr * Fx + ux * sl) +
@@ -462,16 +464,45 @@ struct MinBlocks {
   static constexpr int value = sizeof(R) == 4 ? LBVE_FP32_MIN_BLOCKS : (kThreads <= 256 ? 2 : 1);
 };
 
-template <typename R, int MODE, bool FINAL>
-__global__ void __launch_bounds__(kThreads, MinBlocks<R>::value)
-    step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles, int parity,
-                double* __restrict__ partials) {
-  __shared__ R s_rho[kRegionMax];
-  __shared__ R s_ux[kRegionMax];
-  __shared__ R s_uy[kRegionMax];
-  __shared__ double s_red[kThreads / 32][kPartial];
+// Ask L2 for everything this thread's node of tile T will load (its 36
+// pulled populations, history and force).  No registers are held: the
+// demand loads of the next tile then hit L2 instead of HBM.
+template <typename R>
+__device__ __forceinline__ void prefetch_tile(const InstDev* __restrict__ insts, const TileDev T,
+                                              int parity) {
+  const InstDev& D = insts[T.inst];
+  const int nx = D.nx, ny = D.ny, S = D.stride, TX = D.TX, TY = D.TY;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int x = T.x0 + tx, y = T.y0 + ty;
+  if (ty >= TY || x >= nx || y >= ny) return;
+  const bool py = D.periodic_y != 0;
+  int rm, rp;
+  neighbour_rows(y, nx, ny, py, rm, rp);
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const int rc = y * nx, k = rc + x;
+  const int off[9] = {rc + x, rc + xm, rm >= 0 ? rm + x : rc + x, rc + xp, rp >= 0 ? rp + x : rc + x,
+                      rm >= 0 ? rm + xm : rc + x, rm >= 0 ? rm + xp : rc + x,
+                      rp >= 0 ? rp + xp : rc + x, rp >= 0 ? rp + xm : rc + x};
+  const R* src = (const R*)D.pop[parity];
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (size_t)(9 * l + i) * S + off[i]));
+  const R* hist = (const R*)D.hist;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) asm volatile("prefetch.global.L2 [%0];" ::"l"(hist + (size_t)j * S + k));
+  if (D.force_field) {
+    const R* force = (const R*)D.force;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(force + k));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(force + S + k));
+  }
+}
 
-  const TileDev T = tiles[blockIdx.x];
+template <typename R, int MODE, bool FINAL>
+__device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, const TileDev T,
+                                             int parity, double* __restrict__ partials, R* s_rho,
+                                             R* s_ux, R* s_uy, double (*s_red)[kPartial]) {
   const InstDev& D = insts[T.inst];
   const int nx = D.nx, ny = D.ny, S = D.stride, TX = D.TX, TY = D.TY, hy = D.hy;
   const bool py = D.periodic_y != 0;
@@ -560,8 +591,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value)
     hydro_moments<R>(dr, m);
     const R rho = R(1) + m.drho;
     s_rho[ring_r] = rho;
-    s_ux[ring_r] = (m.jx + R(0.5) * rFx) / rho;
-    s_uy[ring_r] = (m.jy + R(0.5) * rFy) / rho;
+    const R irho = R(1) / rho;
+    s_ux[ring_r] = (m.jx + R(0.5) * rFx) * irho;
+    s_uy[ring_r] = (m.jy + R(0.5) * rFy) * irho;
   }
 
   // (4) own moments; conformation walls completed with the node's own u
@@ -573,8 +605,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value)
     if (MODE == kModeStep && (wb || wt)) zou_he<R>(d, Fx, Fy, wb);
     hydro_moments<R>(d, hm);
     rho = R(1) + hm.drho;
-    ux = (hm.jx + R(0.5) * Fx) / rho;
-    uy = (hm.jy + R(0.5) * Fy) / rho;
+    const R irho_own = R(1) / rho;
+    ux = (hm.jx + R(0.5) * Fx) * irho_own;
+    uy = (hm.jy + R(0.5) * Fy) * irho_own;
     s_rho[ri] = rho;
     s_ux[ri] = ux;
     s_uy[ri] = uy;
@@ -657,6 +690,28 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value)
       for (int w = 1; w < kThreads / 32; ++w)
         v = (j == kResid) ? fmax(v, s_red[w][j]) : v + s_red[w][j];
       partials[(size_t)T.slot * kPartial + j] = v;
+    }
+  }
+}
+
+template <typename R, int MODE, bool FINAL, bool PERSIST>
+__global__ void __launch_bounds__(kThreads, MinBlocks<R>::value)
+    step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles, int n_tiles,
+                int parity, double* __restrict__ partials) {
+  __shared__ R s_rho[kRegionMax];
+  __shared__ R s_ux[kRegionMax];
+  __shared__ R s_uy[kRegionMax];
+  __shared__ double s_red[kThreads / 32][kPartial];
+  if constexpr (!PERSIST) {
+    process_tile<R, MODE, FINAL>(insts, tiles[blockIdx.x], parity, partials, s_rho, s_ux, s_uy,
+                                 s_red);
+  } else {
+    // persistent: walk the tile list with a stride of the grid, prefetching
+    // the next tile into L2 before working on the current one
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      if (t + (int)gridDim.x < n_tiles) prefetch_tile<R>(insts, tiles[t + gridDim.x], parity);
+      process_tile<R, MODE, FINAL>(insts, tiles[t], parity, partials, s_rho, s_ux, s_uy, s_red);
+      __syncthreads();  // the shared halo arrays are reused by the next tile
     }
   }
 }

@@ -31,7 +31,7 @@ EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_st
             "lbve_status", "lbve_fields", "lbve_totals", "lbve_residual", "lbve_time",
             "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc",
             "lbve_adjoint_workspace_bytes", "lbve_adjoint_step", "lbve_state_bytes", "lbve_save",
-            "lbve_load"]
+            "lbve_load", "lbve_autotune"]
 
 
 class lbve_params(ctypes.Structure):
@@ -39,7 +39,8 @@ class lbve_params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("beta", ctypes.c_double), ("Wi", ctypes.c_double),
                 ("Re", ctypes.c_double), ("Sc", ctypes.c_double), ("Ma", ctypes.c_double),
                 ("Lc", ctypes.c_double), ("Lambda_s", ctypes.c_double),
-                ("Lambda_p", ctypes.c_double), ("Fx", ctypes.c_double), ("Fy", ctypes.c_double)]
+                ("Lambda_p", ctypes.c_double), ("Fx", ctypes.c_double), ("Fy", ctypes.c_double),
+                ("tile_tx", ctypes.c_int32)]
 
 
 class LbveError(RuntimeError):
@@ -83,6 +84,8 @@ def load() -> ctypes.CDLL:
         L.lbve_state_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
         L.lbve_save.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.lbve_load.argtypes = [_vp, _vp, ctypes.c_size_t]
+        L.lbve_autotune.argtypes = [P, ctypes.c_int32, _vp, ctypes.c_size_t, _vp, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32)]
         L.lbve_destroy.argtypes = [_vp]
         L.lbve_destroy.restype = None
         L.lbve_error_string.argtypes = [ctypes.c_int]
@@ -219,6 +222,16 @@ def lbve_load(h, state: bytes) -> None:
     _check(load().lbve_load(h, buf, len(state)), "lbve_load")
 
 
+def lbve_autotune(params, d_workspace: int, nbytes: int, stream: int,
+                  trial_steps: int = 64) -> list:
+    """Fastest tile width per instance (list of ints); the workspace is scratch."""
+    arr = _params_array(params)
+    out = (ctypes.c_int32 * len(params))()
+    _check(load().lbve_autotune(arr, len(params), _vp(d_workspace), nbytes, _vp(stream),
+                                int(trial_steps), out), "lbve_autotune")
+    return list(out)
+
+
 def lbve_destroy(h) -> None:
     if h:
         load().lbve_destroy(h)
@@ -226,30 +239,44 @@ def lbve_destroy(h) -> None:
 
 # ---- convenience wrapper ----------------------------------------------------
 
-def params_from(inst, precision: int = LBVE_FP64) -> lbve_params:
+def params_from(inst, precision: int = LBVE_FP64, tile_tx: int = 0) -> lbve_params:
     """lbve_params of a :class:`workloads.Instance`."""
     return lbve_params(inst.nx, inst.ny, 1 if inst.periodic_y else 0, precision, inst.beta,
                        inst.Wi, inst.Re, inst.Sc, inst.Ma, inst.Lc, inst.Lambda_s, inst.Lambda_p,
-                       inst.Fx, inst.Fy)
+                       inst.Fx, inst.Fy, tile_tx)
 
 
 class Simulation:
     """A batch of instances advanced together on the current CUDA device.
 
     The workspace is one torch uint8 tensor; the library runs on torch's
-    current stream."""
+    current stream.  ``tile_tx`` is an int or per-instance list of tile
+    widths (0 = default); ``autotune`` (a trial step count, or True for 64)
+    picks them with lbve_autotune on the workspace before the handle is made.
+    """
 
-    def __init__(self, instances, precision=LBVE_FP64, init_fields=None, device=None):
+    def __init__(self, instances, precision=LBVE_FP64, init_fields=None, device=None,
+                 tile_tx=0, autotune=False):
         import torch
         self.torch = torch
         self.instances = list(instances)
         if isinstance(precision, int):
             precision = [precision] * len(self.instances)
-        self.params = [params_from(inst, pr) for inst, pr in zip(self.instances, precision)]
+        if isinstance(tile_tx, int):
+            tile_tx = [tile_tx] * len(self.instances)
+        self.params = [params_from(inst, pr, tx)
+                       for inst, pr, tx in zip(self.instances, precision, tile_tx)]
         self.device = torch.device(device or "cuda")
         self.nbytes = lbve_workspace_bytes(self.params)
         self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
         self.stream = torch.cuda.current_stream(self.device)
+        if autotune:
+            steps = 64 if autotune is True else int(autotune)
+            widths = lbve_autotune(self.params, self.workspace.data_ptr(), self.nbytes,
+                                   self.stream.cuda_stream, steps)
+            for p, tx in zip(self.params, widths):
+                p.tile_tx = tx
+        self.tile_tx = [p.tile_tx for p in self.params]
         self.h = lbve_create(self.params, self.workspace.data_ptr(), self.nbytes,
                              self.stream.cuda_stream)
         for i, inst in enumerate(self.instances):

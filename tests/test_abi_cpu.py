@@ -78,3 +78,33 @@ def test_error_strings(L):
     for code in range(0, -8, -1):
         assert lib.lbve_error_string(code)
     assert b"unknown" in lib.lbve_error_string(-99)
+
+
+def test_tile_width_validation_and_layout(L):
+    """tile_tx is validated on the host and never changes the workspace size."""
+    from paper_2508_16997_gb300 import workloads as wl
+    base = [L.params_from(wl.frm(130)), L.params_from(wl.channel(33, nx=20), L.LBVE_FP32_DEV)]
+    n0 = L.lbve_workspace_bytes(base)
+    for tx in (1, 3, 8, 16, 20, 64, 128):
+        p = [L.params_from(wl.frm(130), tile_tx=tx),
+             L.params_from(wl.channel(33, nx=20), L.LBVE_FP32_DEV, tile_tx=min(tx, 20))]
+        assert L.lbve_workspace_bytes(p) == n0
+    for bad_tx in (-1, 129, 131):
+        with pytest.raises(L.LbveError) as e:
+            L.lbve_workspace_bytes([L.params_from(wl.frm(256), tile_tx=bad_tx)])
+        assert e.value.code == L.LBVE_ERR_ARG
+    with pytest.raises(L.LbveError) as e:  # wider than the grid
+        L.lbve_workspace_bytes([L.params_from(wl.channel(33, nx=4), tile_tx=8)])
+    assert e.value.code == L.LBVE_ERR_ARG
+
+
+def test_autotune_rejects_bad_arguments_on_the_host(L):
+    from paper_2508_16997_gb300 import workloads as wl
+    p = [L.params_from(wl.frm(64))]
+    n = L.lbve_workspace_bytes(p)
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_autotune(p, 256, n, 0, trial_steps=0)
+    assert e.value.code == L.LBVE_ERR_ARG
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_autotune(p, 0, n, 0)
+    assert e.value.code == L.LBVE_ERR_WORKSPACE

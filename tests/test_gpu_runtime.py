@@ -58,3 +58,44 @@ def test_save_load_bit_exact_resume(lbve, precision):
     c = lbve.Simulation(_batch()[:2], precision=precision)
     with pytest.raises(lbve.LbveError):
         lbve.lbve_load(c.h, state)
+
+
+def _ragged_batch():
+    # ragged in x and y for every tile width; walled and periodic; a force field
+    f = wl.frm(70, Wi=2.0, Re=1.0, Ma=0.05)
+    return [f, wl.channel(37, nx=45, Wi=30.0), wl.frm(17, Wi=0.5, Re=0.1, Ma=0.01)]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_width_does_not_change_fields(lbve, precision):
+    """Each node's update is independent of the tiling: the fields after 60
+    steps are bit-identical for every tile width, and the float64 totals
+    (whose summation follows the tiles) agree to rounding."""
+    insts = _ragged_batch()
+    inits = [wl.random_fields(i.nx, i.ny, seed=11 + k) for k, i in enumerate(insts)]
+    ref = lbve.Simulation(insts, precision=precision, init_fields=inits)
+    ref.step(60)
+    for tx in (1, 5, 8, 16, 64):
+        widths = [min(tx, i.nx) for i in insts]
+        s = lbve.Simulation(insts, precision=precision, init_fields=inits, tile_tx=widths)
+        s.step(60)
+        for i in range(len(insts)):
+            np.testing.assert_array_equal(s.fields(i), ref.fields(i), err_msg=f"tile_tx={tx}")
+            t0, t1 = ref.totals(i), s.totals(i)
+            np.testing.assert_allclose(t1[:6], t0[:6], rtol=1e-13, atol=1e-13 * np.abs(t0[:6]).max())
+
+
+def test_autotune_picks_admissible_widths(lbve):
+    """lbve_autotune returns one admissible width per instance, the same for
+    instances of one class, and the tuned batch reproduces the default one."""
+    insts = [wl.frm(128), wl.frm(128, Wi=2.0), wl.channel(64, nx=4), wl.frm(96)]
+    s = lbve.Simulation(insts, precision=1, autotune=16)
+    for tx, inst in zip(s.tile_tx, insts):
+        assert 1 <= tx <= min(128, inst.nx)
+    assert s.tile_tx[0] == s.tile_tx[1]
+    assert s.tile_tx[2] == 4
+    ref = lbve.Simulation(insts, precision=1)
+    s.step(40)
+    ref.step(40)
+    for i in range(len(insts)):
+        np.testing.assert_array_equal(s.fields(i), ref.fields(i))
