@@ -35,11 +35,19 @@
  *      are left unknown
  *   7. hydrodynamic wet-node non-equilibrium bounce-back (Zou-He) on flat
  *      walls (named in Secs. 4.2, 4.3; formulas are this oracle's reading)
- *   8. CNEBB completion of each CDE lattice (Sec. 3.3)
+ *  7b. at fluid nodes next to a solid-mask node: interpolated bounce-back of
+ *      each unknown hydrodynamic population (the linear scheme of Bouzidi,
+ *      Firdaouss & Lallemand 2001, standing in for the curved-wall scheme
+ *      the paper cites in Sec. 4.3 without formulas; q = 1/2 is half-way
+ *      bounce-back) and the momentum-exchange force on the solid (eq_F_x)
+ *   8. CNEBB completion of each CDE lattice (Sec. 3.3) on the flat walls and
+ *      at the solid-mask boundary nodes
  *   9. history <- S(t), u(t)
  *
  * Domain: nx x ny nodes, row-major [y][x], periodic in x.  In y either
  * periodic, or wet-node walls on rows y = 0 and y = ny-1 (solid beyond).
+ * Optionally a solid mask (orc_set_mask): solid nodes take no part in the
+ * update and report zero fields; gradients next to them are one-sided.
  *
  * Parity status: every function here is pinned by tests under tests/
  * (closed forms, invariants, special cases); see the per-function comments.
@@ -371,13 +379,43 @@ typedef struct {
   double* S;     /* [NC][n]                                                */
   int64_t t;
   double wall_in[NC], wall_out[NC];
+  uint8_t* solid; /* [n] 1 = solid node, or NULL (no mask)                 */
+  double* qlink;  /* [Q][n] wall distance fraction of link (x, i), i unknown */
+  double drag[2]; /* momentum-exchange force on the solid mask, last step   */
 } orc_sim;
 
 static inline int wrap(int a, int n) { return ((a % n) + n) % n; }
 
+/* 1 if (x, y) is a solid node of the mask.  x wraps; y wraps when periodic;
+ * rows outside a walled domain are not mask nodes. */
+static int is_solid(const orc_sim* s, int x, int y) {
+  if (!s->solid) return 0;
+  x = wrap(x, s->nx);
+  if (s->p.periodic_y) y = wrap(y, s->ny);
+  else if (y < 0 || y >= s->ny) return 0;
+  return s->solid[y * s->nx + x] != 0;
+}
+
+/* 1 if (x, y) is a fluid node inside the domain. */
+static int is_fluid(const orc_sim* s, int x, int y) {
+  if (!s->p.periodic_y && (y < 0 || y >= s->ny)) return 0;
+  return !is_solid(s, x, y);
+}
+
+/* Value of field q at (x, y) with the periodic wraps. */
+static double at(const orc_sim* s, const double* q, int x, int y) {
+  x = wrap(x, s->nx);
+  if (s->p.periodic_y) y = wrap(y, s->ny);
+  return q[y * s->nx + x];
+}
+
 static void compute_moments(orc_sim* s) {
   const int n = s->n;
   for (int k = 0; k < n; ++k) {
+    if (s->solid && s->solid[k]) {
+      for (int j = 0; j < 6; ++j) s->mom[j * n + k] = 0.0;
+      continue;
+    }
     double fk[Q];
     for (int i = 0; i < Q; ++i) fk[i] = s->f[i * n + k];
     double rho, ux, uy;
@@ -394,17 +432,29 @@ static void compute_moments(orc_sim* s) {
 }
 
 /* Second-order finite difference of field q along x (dir 0) or y (dir 1)
- * at node (x,y): central in the interior and across periodic boundaries,
- * one-sided (-3 q0 + 4 q1 - q2)/2 on a wall row (reading of the paper, which
- * does not state how these gradients are discretised). */
+ * at fluid node (x,y) (reading of the paper, which does not state how these
+ * gradients are discretised):
+ *   - central, (q(+1) - q(-1))/2, in the interior and across periodic wraps;
+ *   - one-sided (-3 q0 + 4 q1 - q2)/2 on a wall row, toward the interior;
+ *   - next to a solid-mask node on one side: the one-sided second-order
+ *     difference toward the fluid side when two fluid nodes lie there, else
+ *     the first-order difference with the one fluid neighbour;
+ *   - zero when both neighbours along the axis are solid. */
 static double fd(const orc_sim* s, const double* q, int x, int y, int dir) {
-  const int nx = s->nx, ny = s->ny;
-  if (dir == 0) return 0.5 * (q[y * nx + wrap(x + 1, nx)] - q[y * nx + wrap(x - 1, nx)]);
-  if (s->p.periodic_y) return 0.5 * (q[wrap(y + 1, ny) * nx + x] - q[wrap(y - 1, ny) * nx + x]);
-  if (y == 0) return 0.5 * (-3.0 * q[x] + 4.0 * q[nx + x] - q[2 * nx + x]);
-  if (y == ny - 1)
-    return 0.5 * (3.0 * q[y * nx + x] - 4.0 * q[(y - 1) * nx + x] + q[(y - 2) * nx + x]);
-  return 0.5 * (q[(y + 1) * nx + x] - q[(y - 1) * nx + x]);
+  const int ny = s->ny, dx = dir == 0, dy = dir == 1;
+  if (dir == 1 && !s->p.periodic_y && (y == 0 || y == ny - 1)) {
+    const int t = y == 0 ? 1 : -1; /* toward the interior */
+    return 0.5 * t * (-3.0 * at(s, q, x, y) + 4.0 * at(s, q, x, y + t) - at(s, q, x, y + 2 * t));
+  }
+  const int sp = is_solid(s, x + dx, y + dy), sm = is_solid(s, x - dx, y - dy);
+  if (!sp && !sm) return 0.5 * (at(s, q, x + dx, y + dy) - at(s, q, x - dx, y - dy));
+  if (sp && sm) return 0.0;
+  const int t = sp ? -1 : 1; /* toward the fluid side */
+  if (is_fluid(s, x + 2 * t * dx, y + 2 * t * dy))
+    return 0.5 * t *
+           (-3.0 * at(s, q, x, y) + 4.0 * at(s, q, x + t * dx, y + t * dy) -
+            at(s, q, x + 2 * t * dx, y + 2 * t * dy));
+  return t * (at(s, q, x + t * dx, y + t * dy) - at(s, q, x, y));
 }
 
 static void compute_gradients_and_source(orc_sim* s) {
@@ -421,6 +471,11 @@ static void compute_gradients_and_source(orc_sim* s) {
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       const int k = y * nx + x;
+      if (s->solid && s->solid[k]) {
+        for (int j = 0; j < 6; ++j) s->grad[j * n + k] = 0.0;
+        for (int c = 0; c < NC; ++c) s->S[c * n + k] = 0.0;
+        continue;
+      }
       s->grad[0 * n + k] = fd(s, ux, x, y, 0);
       s->grad[1 * n + k] = fd(s, uy, x, y, 0);
       s->grad[2 * n + k] = fd(s, ux, x, y, 1);
@@ -451,6 +506,7 @@ static void free_sim(orc_sim* s) {
   if (!s) return;
   free(s->f); free(s->g); free(s->fpost); free(s->gpost); free(s->Sold);
   free(s->uold); free(s->F); free(s->mom); free(s->grad); free(s->S);
+  free(s->solid); free(s->qlink);
   free(s);
 }
 
@@ -517,8 +573,9 @@ void orc_step(orc_sim* s, int64_t n_steps) {
     /* 1-3: moments, gradients, stress and source at time t */
     compute_moments(s);
     compute_gradients_and_source(s);
-    /* 4-5: collisions */
+    /* 4-5: collisions (fluid nodes only) */
     for (int k = 0; k < n; ++k) {
+      if (s->solid && s->solid[k]) continue;
       const double rho = s->mom[k], ux = s->mom[n + k], uy = s->mom[2 * n + k];
       const double Fx = s->F[k], Fy = s->F[n + k];
       const double A[3] = {s->mom[3 * n + k], s->mom[4 * n + k], s->mom[5 * n + k]};
@@ -540,15 +597,18 @@ void orc_step(orc_sim* s, int64_t n_steps) {
     }
     /* 9 (done now, the values are no longer needed): history <- S(t), u(t) */
     fill_history(s);
-    /* 6: push streaming; unknown slots are overwritten by 7-8 */
+    /* 6: push streaming between fluid nodes; unknown slots are overwritten
+     * by 7-8 */
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         const int k = y * nx + x;
+        if (s->solid && s->solid[k]) continue;
         for (int i = 0; i < Q; ++i) {
           int yd = y + EY[i];
           if (s->p.periodic_y) yd = wrap(yd, ny);
           else if (yd < 0 || yd >= ny) continue; /* leaves toward the wall */
           const int kd = yd * nx + wrap(x + EX[i], nx);
+          if (s->solid && s->solid[kd]) continue; /* leaves toward the mask */
           s->f[i * n + kd] = s->fpost[i * n + k];
           for (int c = 0; c < NC; ++c) s->g[(c * Q + i) * n + kd] = s->gpost[(c * Q + i) * n + k];
         }
@@ -586,8 +646,118 @@ void orc_step(orc_sim* s, int64_t n_steps) {
         }
       }
     }
+    s->drag[0] = s->drag[1] = 0.0;
+    if (s->solid) {
+      /* 7b and 8 at the fluid nodes next to the solid mask */
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          const int k = y * nx + x;
+          if (s->solid[k]) continue;
+          int known[Q], any = 0;
+          for (int i = 0; i < Q; ++i) {
+            known[i] = !(i != 0 && is_solid(s, x - EX[i], y - EY[i]));
+            any |= !known[i];
+          }
+          if (!any) continue;
+          for (int i = 1; i < Q; ++i) {
+            if (known[i]) continue;
+            const int ib = OPP[i]; /* points toward the wall */
+            const double q = s->qlink[i * n + k];
+            const double fb = s->fpost[ib * n + k];
+            double v;
+            if (q < 0.5) {
+              if (is_fluid(s, x + EX[i], y + EY[i])) {
+                const int kf = wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+                v = 2.0 * q * fb + (1.0 - 2.0 * q) * s->fpost[ib * n + kf];
+              } else {
+                v = fb; /* no second fluid node: half-way bounce-back */
+              }
+            } else {
+              v = fb / (2.0 * q) + (1.0 - 1.0 / (2.0 * q)) * s->fpost[i * n + k];
+            }
+            s->f[i * n + k] = v;
+            /* eq_F_x: e_ib (f^dagger_ib(x,t) + f_i(x,t+1)) over links to the wall */
+            s->drag[0] += EX[ib] * (fb + v);
+            s->drag[1] += EY[ib] * (fb + v);
+          }
+          const double Fx = s->F[k], Fy = s->F[n + k];
+          double fk[Q], rho, ux, uy;
+          for (int i = 0; i < Q; ++i) fk[i] = s->f[i * n + k];
+          orc_hydro_moments(fk, Fx, Fy, &rho, &ux, &uy);
+          for (int c = 0; c < NC; ++c) {
+            double gk[Q], gp[Q], win, wout;
+            for (int i = 0; i < Q; ++i) {
+              gk[i] = s->g[(c * Q + i) * n + k];
+              gp[i] = s->gpost[(c * Q + i) * n + k];
+            }
+            orc_cnebb(gk, gp, known, ux, uy, &win, &wout);
+            for (int i = 0; i < Q; ++i) s->g[(c * Q + i) * n + k] = gk[i];
+            s->wall_in[c] += win;
+            s->wall_out[c] += wout;
+          }
+        }
+    }
     s->t += 1;
   }
+}
+
+/* Install a solid mask before the first step.  solid: [ny][nx], nonzero =
+ * solid node.  q: [Q][ny][nx] or NULL; q[i][k] in (0, 1] is the fraction of
+ * the link from fluid node k toward its solid neighbour k - e_i at which the
+ * wall lies (used only where k is fluid and k - e_i solid; NULL = 1/2
+ * everywhere, the staircase wall).  The moments, gradients, source and
+ * history of the initial state are recomputed with the mask.
+ * Returns 0, or -1 if the simulation already stepped, -2 if a walled domain
+ * has solid nodes on rows 0..2 or ny-3..ny-1, -3 if a fluid node has solid
+ * neighbours on both ends of one lattice line, -4 for q outside (0, 1]. */
+int orc_set_mask(orc_sim* s, const uint8_t* solid, const double* q) {
+  const int n = s->n, nx = s->nx, ny = s->ny;
+  if (s->t != 0) return -1;
+  uint8_t* m = (uint8_t*)malloc((size_t)n);
+  double* ql = (double*)malloc(sizeof(double) * Q * (size_t)n);
+  if (!m || !ql) {
+    free(m);
+    free(ql);
+    return -5;
+  }
+  for (int k = 0; k < n; ++k) m[k] = solid[k] ? 1 : 0;
+  for (int k = 0; k < Q * n; ++k) ql[k] = 0.5;
+  uint8_t* old_solid = s->solid;
+  double* old_q = s->qlink;
+  s->solid = m;
+  s->qlink = ql;
+  int rc = 0;
+  if (!s->p.periodic_y)
+    for (int x = 0; x < nx && !rc; ++x)
+      for (int r = 0; r < 3 && !rc; ++r)
+        if (m[r * nx + x] || m[(ny - 1 - r) * nx + x]) rc = -2;
+  for (int y = 0; y < ny && !rc; ++y)
+    for (int x = 0; x < nx && !rc; ++x) {
+      const int k = y * nx + x;
+      if (m[k]) continue;
+      for (int i = 1; i < Q && !rc; ++i) {
+        if (!is_solid(s, x - EX[i], y - EY[i])) continue;
+        if (is_solid(s, x + EX[i], y + EY[i])) rc = -3;
+        if (q) {
+          const double v = q[i * n + k];
+          if (!(v > 0.0 && v <= 1.0)) rc = -4;
+          ql[i * n + k] = v;
+        }
+      }
+    }
+  if (rc) {
+    s->solid = old_solid;
+    s->qlink = old_q;
+    free(m);
+    free(ql);
+    return rc;
+  }
+  free(old_solid);
+  free(old_q);
+  compute_moments(s);
+  compute_gradients_and_source(s);
+  fill_history(s);
+  return 0;
 }
 
 /* Macroscopic fields at the current time t: [6][ny][nx] =
@@ -597,14 +767,17 @@ void orc_fields(orc_sim* s, double* out) {
   memcpy(out, s->mom, sizeof(double) * 6 * (size_t)s->n);
 }
 
-/* Domain totals at time t and the CNEBB wall balance of the last step:
- * out[0..2]  = sum rho, sum rho ux, sum rho uy
+/* Domain totals at time t and the wall balances of the last step:
+ * out[0..2]  = sum rho, sum rho ux, sum rho uy      (fluid nodes)
  * out[3..5]  = sum phi_xx, sum phi_xy, sum phi_yy
- * out[6..8]  = wall "in" per lattice, out[9..11] = wall "out" per lattice. */
+ * out[6..8]  = CNEBB wall "in" per lattice, out[9..11] = wall "out"
+ * out[12..13] = momentum-exchange force on the solid mask (eq_F_x). */
 void orc_totals(orc_sim* s, double* out) {
   compute_moments(s);
   const int n = s->n;
-  for (int j = 0; j < 12; ++j) out[j] = 0;
+  for (int j = 0; j < 14; ++j) out[j] = 0;
+  out[12] = s->drag[0];
+  out[13] = s->drag[1];
   for (int k = 0; k < n; ++k) {
     const double rho = s->mom[k];
     out[0] += rho;

@@ -70,6 +70,8 @@ def lib():
         L.orc_get_state.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.orc_set_state.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.orc_get_coeffs.argtypes = [ctypes.c_void_p, ctypes.POINTER(Coeffs)]
+        L.orc_set_mask.restype = ctypes.c_int
+        L.orc_set_mask.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8), _dp]
         L.orc_time.restype = ctypes.c_int64
         L.orc_time.argtypes = [ctypes.c_void_p]
         L.orc_derive.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Coeffs)]
@@ -143,9 +145,21 @@ class Sim:
         return out
 
     def totals(self) -> np.ndarray:
-        out = np.empty(12)
+        """[0:3] sum rho, rho ux, rho uy; [3:6] sum phi; [6:9] / [9:12] CNEBB wall
+        in / out per lattice; [12:14] force on the solid mask (last step)."""
+        out = np.empty(14)
         lib().orc_totals(self._h, _ptr(out))
         return out
+
+    def set_mask(self, solid: np.ndarray, q: np.ndarray | None = None) -> None:
+        """Solid mask [ny][nx] (nonzero = solid) and optional link fractions
+        q [9][ny][nx]; before the first step."""
+        m = np.ascontiguousarray(solid, dtype=np.uint8).reshape(self.ny * self.nx)
+        qq = None if q is None else np.ascontiguousarray(q, np.float64).reshape(9, -1)
+        rc = lib().orc_set_mask(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                _ptr(qq) if qq is not None else None)
+        if rc != 0:
+            raise ValueError(f"oracle rejected the mask ({rc})")
 
     def source(self) -> np.ndarray:
         out = np.empty((3, self.ny, self.nx))

@@ -17,6 +17,10 @@ Workloads (Sec. 4 of the paper; sizes as used by this project):
   y = 0 and y = H (ny = H + 1), L_c = H, uniform force
   F_x = 8 (nu_s + nu_p) U_c / L_c^2.
 * batched mix: instances of both kinds with seeded random sizes, Wi and beta.
+* solid obstacles (Sec. 4.3 geometry): a solid mask and, for curved walls,
+  the fraction q of each wall link at which the wall lies; a cylinder in a
+  periodic channel, a rectangular block in a periodic box, and a channel
+  bounded by a solid row at a chosen wall distance.
 """
 from __future__ import annotations
 
@@ -26,6 +30,11 @@ from dataclasses import dataclass, field, asdict
 import numpy as np
 
 CS = 1.0 / math.sqrt(3.0)  # lattice speed of sound for c = 1 (D2Q9)
+
+# D2Q9 directions in the order both implementations use; the geometry below
+# needs them to name wall links (link (k, i): fluid node k, solid k - e_i).
+EX = (0, 1, 0, -1, 0, 1, -1, -1, 1)
+EY = (0, 0, 1, 0, -1, 1, 1, -1, -1)
 
 
 @dataclass
@@ -47,6 +56,8 @@ class Instance:
     kind: str = "custom"     # "frm" | "channel" | "custom"
     force_field: np.ndarray | None = field(default=None, repr=False)  # (2, ny, nx) or None
     seed: int = 0
+    solid: np.ndarray | None = field(default=None, repr=False)   # (ny, nx) uint8, 1 = solid
+    wall_q: np.ndarray | None = field(default=None, repr=False)  # (9, ny, nx) link fractions
 
     @property
     def n_nodes(self) -> int:
@@ -54,8 +65,31 @@ class Instance:
 
     def scalars(self) -> dict:
         d = asdict(self)
-        d.pop("force_field")
+        for k in ("force_field", "solid", "wall_q"):
+            d.pop(k)
         return d
+
+    def wall_links(self):
+        """Wall links of the mask as (node k, direction i, q): fluid node k
+        whose neighbour k - e_i is solid, q from ``wall_q`` (1/2 if None)."""
+        if self.solid is None:
+            return []
+        out = []
+        nx, ny = self.nx, self.ny
+        for y in range(ny):
+            for x in range(nx):
+                if self.solid[y, x]:
+                    continue
+                for i in range(1, 9):
+                    ys = y - EY[i]
+                    if self.periodic_y:
+                        ys %= ny
+                    elif not 0 <= ys < ny:
+                        continue
+                    if self.solid[ys, (x - EX[i]) % nx]:
+                        q = 0.5 if self.wall_q is None else float(self.wall_q[i, y, x])
+                        out.append((y * nx + x, i, q))
+        return out
 
 
 def velocity_scale(Ma: float) -> float:
@@ -143,3 +177,106 @@ def random_force(nx: int, ny: int, seed: int, amp: float = 1e-5) -> np.ndarray:
     """Random per-node body force (2, ny, nx), uniform in [-amp, amp]."""
     rng = np.random.default_rng(seed)
     return amp * rng.uniform(-1, 1, (2, ny, nx))
+
+
+def _circle_links(solid: np.ndarray, cx: float, cy: float, R: float, periodic_y: bool):
+    """Link fractions q (9, ny, nx) for a circle of radius R centred at
+    (cx, cy): for fluid node x_b and solid neighbour x_b - e_i, the first
+    crossing x_b + t (x_s - x_b) of the circle, t in (0, 1]."""
+    ny, nx = solid.shape
+    q = np.full((9, ny, nx), 0.5)
+    for y in range(ny):
+        for x in range(nx):
+            if solid[y, x]:
+                continue
+            for i in range(1, 9):
+                ys, xs = y - EY[i], (x - EX[i]) % nx
+                if periodic_y:
+                    ys %= ny
+                elif not 0 <= ys < ny:
+                    continue
+                if not solid[ys, xs]:
+                    continue
+                px, py = x - cx, y - cy
+                dx, dy = -EX[i], -EY[i]
+                a = dx * dx + dy * dy
+                b = px * dx + py * dy
+                c = px * px + py * py - R * R
+                t = (-b - math.sqrt(max(b * b - a * c, 0.0))) / a
+                q[i, y, x] = min(max(t, 1e-6), 1.0)
+    return q
+
+
+def cylinder_channel(R: int, L: int | None = None, H: int | None = None, beta=0.59, Wi=0.5,
+                     Re=1.0, Sc=1e6, Ma=0.01, Lambda_s=0.25, Lambda_p=2.5e-7,
+                     curved: bool = True, seed: int = 0) -> Instance:
+    """Cylinder of radius R in a channel periodic in x (Sec. 4.3 geometry):
+    L x (H + 1) nodes, wet-node walls on rows 0 and H, cylinder centred at
+    (L/2, H/2), solid where (x - cx)^2 + (y - cy)^2 <= R^2, L_c = R,
+    uniform force F_x = 8 nu_0 U_max / H^2 with U_max = 1.5 U_c (the empty
+    channel's profile of the paper's inlet).  curved: exact link fractions of
+    the circle, else staircase (q = 1/2)."""
+    L = 30 * R if L is None else L
+    H = 4 * R if H is None else H
+    ny = H + 1
+    cx, cy = 0.5 * L, 0.5 * H
+    Y, X = np.mgrid[0:ny, 0:L]
+    solid = (((X - cx) ** 2 + (Y - cy) ** 2) <= R * R).astype(np.uint8)
+    Lc = float(R)
+    nu0 = total_viscosity(Ma, Lc, Re)
+    Fx = 8.0 * nu0 * 1.5 * velocity_scale(Ma) / float(H) ** 2
+    inst = Instance(L, ny, False, beta, Wi, Re, Sc, Ma, Lc, Lambda_s, Lambda_p, Fx, 0.0,
+                    "cylinder", None, seed)
+    inst.solid = solid
+    inst.wall_q = _circle_links(solid, cx, cy, R, False) if curved else None
+    return inst
+
+
+def obstacle_box(nx: int, ny: int, block=(0.25, 0.5, 0.375, 0.625), Fx=1e-5, Fy=0.0,
+                 beta=0.5, Wi=1.0, Re=1.0, Sc=1e4, Ma=0.1, Lambda_s=0.25, Lambda_p=1e-6,
+                 seed: int = 0) -> Instance:
+    """Doubly periodic nx x ny box with a solid rectangle covering the
+    fractions block = (x0, x1, y0, y1) of the box, uniform force (Fx, Fy),
+    L_c = ny (half-way walls, q = 1/2)."""
+    x0, x1 = int(round(block[0] * nx)), int(round(block[1] * nx))
+    y0, y1 = int(round(block[2] * ny)), int(round(block[3] * ny))
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[y0:y1, x0:x1] = 1
+    inst = Instance(nx, ny, True, beta, Wi, Re, Sc, Ma, float(ny), Lambda_s, Lambda_p, Fx, Fy,
+                    "obstacle", None, seed)
+    inst.solid = solid
+    return inst
+
+
+def staircase_channel(H: int, q: float = 0.5, nx: int = 3, beta=1.0, Wi=1.0, Re=1.0,
+                      Sc=1e6, Ma=0.1, Lambda_s=0.25, Lambda_p=2.5e-7) -> Instance:
+    """Channel bounded by one solid row: doubly periodic nx x (H + 1) grid,
+    row 0 solid, fluid rows 1..H; every wall link crosses the wall at
+    fraction q, so the walls lie at y = 1 - q and y = H + q and the channel
+    width is W = H - 1 + 2q (= L_c).  Uniform force F_x = 8 nu_0 U_c / W^2."""
+    ny = H + 1
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = 1
+    W = H - 1 + 2.0 * q
+    nu0 = total_viscosity(Ma, W, Re)
+    Fx = 8.0 * nu0 * velocity_scale(Ma) / W ** 2
+    inst = Instance(nx, ny, True, beta, Wi, Re, Sc, Ma, W, Lambda_s, Lambda_p, Fx, 0.0,
+                    "staircase", None, 0)
+    inst.solid = solid
+    inst.wall_q = np.full((9, ny, nx), float(q))
+    return inst
+
+
+def circle_box(nx: int, ny: int, R: float, cx: float, cy: float, Fx=1e-5, Fy=0.0, beta=0.5,
+               Wi=1.0, Re=1.0, Sc=1e4, Ma=0.1, Lambda_s=0.25, Lambda_p=1e-6,
+               curved: bool = True) -> Instance:
+    """Doubly periodic nx x ny box with a solid disc of radius R centred at
+    (cx, cy), uniform force (Fx, Fy), L_c = 2R; curved: exact link
+    fractions of the circle, else q = 1/2."""
+    Y, X = np.mgrid[0:ny, 0:nx]
+    solid = (((X - cx) ** 2 + (Y - cy) ** 2) <= R * R).astype(np.uint8)
+    inst = Instance(nx, ny, True, beta, Wi, Re, Sc, Ma, 2.0 * R, Lambda_s, Lambda_p, Fx, Fy,
+                    "obstacle", None, 0)
+    inst.solid = solid
+    inst.wall_q = _circle_links(solid, cx, cy, R, True) if curved else None
+    return inst

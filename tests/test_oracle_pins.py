@@ -417,3 +417,189 @@ def test_cde_fourier_mode():
     assert np.abs(F[4] - exy).max() < 1e-2 * 0.5 * a * dxy
     assert np.abs(F[5] - 1).max() < 1e-14
     assert np.abs(F[1] - U).max() < 1e-15  # uniform flow is untouched
+
+
+# --------------------------------------------------------------------------
+# Solid mask: interpolated bounce-back, CNEBB at mask walls, drag (Sec. 4.3)
+# --------------------------------------------------------------------------
+
+def _masked(inst, init=None):
+    s = oracle_sim(inst, init=init)
+    s.set_mask(inst.solid, inst.wall_q)
+    return s
+
+
+def _fluid_force_sum(inst):
+    fluid = inst.solid == 0
+    if inst.force_field is not None:
+        return np.array([inst.force_field[0][fluid].sum(), inst.force_field[1][fluid].sum()])
+    return fluid.sum() * np.array([inst.Fx, inst.Fy])
+
+
+def test_mask_halfway_bounce_back_conserves_mass():
+    """q = 1/2 returns to each boundary node exactly what it sent toward the
+    solid, so sum rho over the fluid nodes stays constant; solid nodes report
+    zero fields."""
+    inst = wl.obstacle_box(16, 12, Fx=2e-4, Fy=-1e-4, Wi=0.8)
+    s = _masked(inst, wl.random_fields(16, 12, seed=21))
+    m0 = s.totals()[0]
+    for _ in range(20):
+        s.step(1)
+        assert abs(s.totals()[0] - m0) < 1e-13 * m0
+    assert np.all(s.fields()[:, inst.solid == 1] == 0.0)
+
+
+@pytest.mark.parametrize("curved", [False, True])
+def test_mask_momentum_budget_exact(curved):
+    """Every step the fluid momentum changes by the body force on the fluid
+    minus the force handed to the solid (eq_F_x counts exactly the momentum
+    the wall links exchange), for staircase and interpolated walls alike:
+    sum rho u(t+1) - sum rho u(t) = sum_fluid F - F_solid."""
+    inst = wl.circle_box(22, 18, R=4.3, cx=10.2, cy=8.6, Fx=3e-4, Fy=1e-4, curved=curved)
+    s = _masked(inst, wl.random_fields(22, 18, seed=22))
+    Fs = _fluid_force_sum(inst)
+    t0 = s.totals()
+    for _ in range(12):
+        s.step(1)
+        t1 = s.totals()
+        np.testing.assert_allclose(t1[1:3] - t0[1:3], Fs - t1[12:14], rtol=0, atol=1e-14)
+        assert np.abs(t1[12:14]).max() > 1e-3
+        t0 = t1
+
+
+def test_mask_conformation_budget_and_wall_balance():
+    """CNEBB at mask walls returns to each boundary node what it sent toward
+    the solid: sum_fluid phi(t+1) - sum_fluid phi(t) = sum_fluid [S(t) +
+    (S(t) - S(t-1))/2] per component, and wall in = wall out."""
+    inst = wl.circle_box(20, 16, R=3.7, cx=9.4, cy=7.9, Fx=2e-4, Wi=1.5, Sc=1e3)
+    s = _masked(inst, wl.random_fields(20, 16, seed=23))
+    s.step(1)
+    S_prev = s.source().reshape(3, -1).sum(axis=1)
+    phi_prev = s.totals()[3:6]
+    for _ in range(6):
+        s.step(1)
+        S_now = s.source().reshape(3, -1).sum(axis=1)
+        tot = s.totals()
+        phi = tot[3:6]
+        np.testing.assert_allclose(phi, phi_prev + S_now + 0.5 * (S_now - S_prev), rtol=0,
+                                   atol=1e-12 * max(1.0, np.abs(phi).max()))
+        np.testing.assert_allclose(tot[6:9], tot[9:12], rtol=0, atol=1e-13)
+        assert np.all(np.abs(tot[9:12]) > 0)
+        S_prev, phi_prev = S_now, phi
+
+
+def test_mask_mirror_symmetry():
+    """A disc symmetric about the line y = 9.5 of a 20-row periodic box,
+    driven along x from rest: rho, u_x, A_xx, A_yy are even and u_y, A_xy odd
+    under y -> 19 - y (a transposed direction, sign or index in the mask
+    code breaks this)."""
+    inst = wl.circle_box(23, 20, R=4.6, cx=9.3, cy=9.5, Fx=5e-4, Wi=2.0)
+    s = _masked(inst)
+    s.step(150)
+    F = s.fields()
+    M = F[:, ::-1, :]
+    scale = np.abs(F).reshape(6, -1).max(axis=1)[:, None, None]
+    for c, sign in zip(range(6), (1, 1, -1, 1, -1, 1)):
+        np.testing.assert_allclose(F[c], sign * M[c], rtol=0, atol=1e-12 * scale[c].item())
+    assert np.abs(F[2]).max() > 1e-4 * np.abs(F[1]).max()
+
+
+def _staircase_profile(H, q, Lambda_s, Re=1.0, steps=6000):
+    """Steady Newtonian channel between solid rows (walls at y = 1 - q and
+    y = H + q): numerical u minus the parabola through the walls, and F/nu."""
+    inst = wl.staircase_channel(H, q=q, Lambda_s=Lambda_s, Re=Re)
+    s = _masked(inst)
+    s.step(steps)
+    u = s.fields()[1][1:, 0]
+    y = np.arange(1, H + 1)
+    W = inst.Lc
+    Uc = wl.velocity_scale(inst.Ma)
+    ana = 4.0 * Uc * (y - (1.0 - q)) * (H + q - y) / W ** 2
+    return u - ana, inst.Fx / wl.total_viscosity(inst.Ma, W, inst.Re), Uc
+
+
+@pytest.mark.parametrize("Lambda_s", [3.0 / 16.0, 0.25, 0.5])
+def test_mask_halfway_wall_poiseuille_trt_slip(Lambda_s):
+    """Half-way bounce-back (q = 1/2) of a TRT scheme puts the Poiseuille
+    parabola's zeros half-way between the last fluid and the first solid row,
+    up to the uniform slip (16 Lambda - 3)/24 F/nu -- exact for the magic
+    Lambda = 3/16 (Ginzburg & d'Humieres' bounce-back analysis).  The
+    oracle's staircase channel must reproduce that closed form."""
+    d, Fnu, Uc = _staircase_profile(10, 0.5, Lambda_s)
+    slip = (16.0 * Lambda_s - 3.0) / 24.0 * Fnu
+    assert np.abs(d - slip).max() < 1e-11 * Uc, (np.abs(d - slip).max() / Uc)
+
+
+@pytest.mark.parametrize("q", [0.1, 0.3, 0.75, 0.95])
+def test_mask_interpolated_wall_poiseuille(q):
+    """Linear interpolated bounce-back at wall fraction q: the steady profile
+    is the parabola through the walls at y = 1 - q and y = H + q shifted by a
+    uniform slip (no distortion near the walls: any misplaced interpolation
+    operand bends the profile), the slip does not depend on Lambda_s beyond
+    the half-way term, and in units of F/nu it depends only on q and nu, so
+    two resolutions at equal nu give the same slip (second-order walls)."""
+    d1, Fnu1, Uc = _staircase_profile(10, q, 3.0 / 16.0)
+    assert np.ptp(d1) < 1e-11 * Uc
+    d2, _, _ = _staircase_profile(10, q, 0.5)
+    slip_half = (16.0 * 0.5 - 3.0) / 24.0 * Fnu1
+    np.testing.assert_allclose(d2.mean() - slip_half, d1.mean(), rtol=1e-9)
+    W1, W2 = 9.0 + 2.0 * q, 19.0 + 2.0 * q
+    d3, Fnu3, _ = _staircase_profile(20, q, 3.0 / 16.0, Re=W2 / W1, steps=12000)
+    assert np.ptp(d3) < 1e-11 * Uc
+    np.testing.assert_allclose(d3.mean() / Fnu3, d1.mean() / Fnu1, rtol=1e-8)
+    assert abs(d1.mean()) > 1e-3 * Uc  # q != 1/2 does leave a slip
+
+
+def test_mask_rejections():
+    """The mask is refused after stepping, on the three rows next to a flat
+    wall, with solid on both ends of a lattice line through a fluid node, and
+    with q outside (0, 1]."""
+    inst = wl.obstacle_box(12, 12)
+    s = oracle_sim(inst)
+    s.step(1)
+    with pytest.raises(ValueError):
+        s.set_mask(inst.solid)
+    ch = wl.channel(12, nx=6)
+    m = np.zeros((ch.ny, ch.nx), np.uint8)
+    m[2, 3] = 1
+    with pytest.raises(ValueError):
+        oracle_sim(ch).set_mask(m)
+    m = np.zeros((12, 12), np.uint8)
+    m[5, 4] = m[5, 6] = 1  # fluid node (5, 5) between two solids along x
+    with pytest.raises(ValueError):
+        oracle_sim(inst).set_mask(m)
+    q = np.full((9, 12, 12), 1.5)
+    with pytest.raises(ValueError):
+        oracle_sim(inst).set_mask(inst.solid, q)
+
+
+def test_mask_gradients_exact_on_linear_fields():
+    """Every difference rule the oracle uses next to solid nodes (central,
+    one-sided second order, one-sided first order in two-node gaps, and the
+    wall-row rule) is exact on a linear field.  With A = I and the
+    divergence-free u = (a y' + b x', c x' - b y') the source of the initial
+    state is S_xy = a + c, S_xx = 2b, S_yy = -2b at every fluid node whose
+    stencil does not cross the periodic seam in x."""
+    nx, ny = 26, 20
+    inst = wl.channel(ny - 1, nx=nx, Wi=1e6)  # lambda ~ 1e8: the relaxation term is negligible
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[6:13, 8] = solid[6:13, 11] = 1      # fluid columns 9, 10: a two-node gap in x
+    solid[7, 14:19] = solid[10, 14:19] = 1    # fluid rows 8, 9: a two-node gap in y
+    solid[3:5, 21:24] = 1                     # a block: second-order one-sided rules
+    a, b, c = 2e-3, 7e-4, -1.3e-3
+    Y, X = np.mgrid[0:ny, 0:nx].astype(float)
+    init = np.zeros((6, ny, nx))
+    init[0] = 1.0
+    init[1] = a * (Y - 9.5) + b * (X - 12.0)
+    init[2] = c * (X - 12.0) - b * (Y - 9.5)
+    init[3] = init[5] = 1.0
+    s = oracle_sim(inst, init=init)
+    s.set_mask(solid)
+    S = s.source()
+    lam = s.coeffs()["lambda"]
+    check = (solid == 0)
+    check[:, :3] = check[:, nx - 3:] = False
+    np.testing.assert_allclose(S[1][check], a + c, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(S[0][check], 2 * b, rtol=0, atol=1e-15 + 2 * abs(b) / lam)
+    np.testing.assert_allclose(S[2][check], -2 * b, rtol=0, atol=1e-15 + 2 * abs(b) / lam)
+    assert np.all(S[:, solid == 1] == 0.0)
