@@ -14,14 +14,20 @@
  *     eq_p_neq_m, eq_p_G_1, eq_p_F);
  *   - conservative non-equilibrium bounce-back (CNEBB) for the conformation
  *     lattices and wet-node non-equilibrium bounce-back (Zou-He) for the
- *     hydrodynamic lattice on flat walls (Sec. 3.3; Secs. 4.2-4.3).
+ *     hydrodynamic lattice on flat walls (Sec. 3.3; Secs. 4.2-4.3);
+ *   - optional solid masks (obstacles such as the cylinder of Sec. 4.3):
+ *     CNEBB for the conformation lattices and linear interpolated
+ *     bounce-back, at a per-link wall fraction q, for the hydrodynamic
+ *     lattice, from a compact list of the fluid nodes next to the mask, with
+ *     the momentum-exchange force on the solid (eq_F_x).
  *
  * Conventions shared by every entry point
  *   - Return value: LBVE_OK (0) or a negative LBVE_ERR_* code.  No C++
  *     exception crosses the ABI.  lbve_error_string() names a code;
  *     lbve_last_error() gives a one-line detail for the calling thread.
  *   - Grids are nx x ny nodes, periodic in x.  In y either periodic, or
- *     wet-node walls on rows y = 0 and y = ny - 1 (solid beyond them).
+ *     wet-node walls on rows y = 0 and y = ny - 1 (solid beyond them).  A
+ *     solid mask may add interior solid nodes.
  *   - Host arrays are row-major [component][y][x], x fastest, float64,
  *     regardless of the storage precision of the instance.
  *   - The library never allocates device memory.  The caller allocates one
@@ -59,7 +65,7 @@ extern "C" {
                            float64 for conserved totals and wall balances     */
 
 /* Number of doubles returned by lbve_totals(). */
-#define LBVE_NTOTALS 12
+#define LBVE_NTOTALS 14
 
 /* One problem statement (Sec. 2.4-2.5 of the paper), lattice units.
  * Derived on the host in float64:
@@ -87,6 +93,11 @@ typedef struct {
                          not depend on the tiling; only the summation order
                          of the float64 totals follows the tiles.  The
                          workspace size does not depend on it.             */
+  int32_t max_wall_nodes; /* capacity for a solid mask: the most fluid nodes
+                         next to solid nodes (nodes with a solid neighbour
+                         along any lattice direction) lbve_set_geometry may
+                         install; 0 = no mask.  Costs nx*ny bytes plus 144
+                         bytes per wall node of workspace.                 */
 } lbve_params;
 
 typedef struct lbve_handle lbve_handle;
@@ -129,8 +140,21 @@ int lbve_create(const lbve_params* p, int32_t n_instances, void* d_workspace, si
 /* Set the geometry, body force and initial state of instance inst and reset
  * its time to 0 (Sec. 4.2: unit density, zero velocity, identity
  * conformation and equilibrium populations unless init_fields is given).
- *   solid_mask : must be NULL (walls follow periodic_y; interior obstacles
- *                are not supported by this version -> LBVE_ERR_GEOMETRY).
+ *   solid_mask : host uint8 [ny][nx], nonzero = solid node, or NULL for
+ *                none.  Solid nodes take no part in the update and report
+ *                zero fields; they are left out of the totals.  At each
+ *                fluid node x next to the mask, every link i with x - e_i
+ *                solid is a wall link: its hydrodynamic population is
+ *                completed by linear interpolated bounce-back at wall
+ *                fraction q (1/2, i.e. half-way bounce-back, until
+ *                lbve_set_wall_distances() sets it), its three conformation
+ *                populations by CNEBB (Sec. 3.3) with u at x; velocity
+ *                gradients next to solid nodes are one-sided.
+ *                LBVE_ERR_GEOMETRY if the instance has max_wall_nodes = 0
+ *                or fewer than the mask's wall nodes, if a walled domain
+ *                has solid nodes on rows 0-2 or ny-3..ny-1, if a fluid node
+ *                has solid nodes on both ends of one lattice line, or if no
+ *                fluid node is left.
  *   body_force : host float64 [2][ny][nx], or NULL for the uniform (Fx, Fy).
  *   init_fields: host float64 [6][ny][nx] = rho, ux, uy, Axx, Axy, Ayy, or
  *                NULL for rho = 1, u = 0, A = I.
@@ -140,6 +164,20 @@ int lbve_create(const lbve_params* p, int32_t n_instances, void* d_workspace, si
  * Errors: LBVE_ERR_ARG, LBVE_ERR_GEOMETRY, LBVE_ERR_CUDA. */
 int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
                       const double* body_force, const double* init_fields);
+
+/* Wall fractions of curved walls (Sec. 4.3): for each of the n_links links
+ * (node[j] = y nx + x of a fluid node, dir[j] in 1..8 with x - e_dir a solid
+ * node of the mask), the fraction q[j] in (0, 1] of the link from the node
+ * toward the solid node at which the wall lies.  Links not named keep their
+ * fraction (1/2 after lbve_set_geometry).  q < 1/2 interpolates with the
+ * fluid node x + e_dir (half-way bounce-back where that node is solid).
+ * D2Q9 directions: e_1 = (1,0), e_2 = (0,1), e_3 = (-1,0), e_4 = (0,-1),
+ * e_5 = (1,1), e_6 = (-1,1), e_7 = (-1,-1), e_8 = (1,-1).  Host arrays,
+ * synchronises the stream.
+ * Errors: LBVE_ERR_ARG (ranges, q), LBVE_ERR_GEOMETRY (no mask, not a wall
+ * link), LBVE_ERR_CUDA. */
+int lbve_set_wall_distances(lbve_handle* h, int32_t inst, int32_t n_links, const int32_t* node,
+                            const int32_t* dir, const double* q);
 
 /* Advance every instance by n_steps >= 0 time steps (asynchronous on the
  * stream).  The last step of the call also refreshes the macroscopic fields,
@@ -167,7 +205,11 @@ int lbve_fields(lbve_handle* h, int32_t inst, double* out, int32_t on_device);
  *   out[6..8]  CNEBB wall "in" of the last step, per conformation lattice:
  *              what the completion added back at wall nodes
  *   out[9..11] CNEBB wall "out" of the last step: post-collision populations
- *              that left wall nodes toward the wall (Sec. 3.3); in == out. */
+ *              that left wall nodes toward the wall (Sec. 3.3); in == out
+ *   out[12..13] force of the fluid on the solid mask over the last step by
+ *              momentum exchange (eq_F_x), x and y; 0 without a mask.
+ * Sums run over fluid nodes; flat walls and mask walls both count in
+ * out[6..11]. */
 int lbve_totals(lbve_handle* h, int32_t inst, double out[LBVE_NTOTALS]);
 
 /* Residual of instance inst (synchronises): max over nodes of
@@ -204,6 +246,7 @@ int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps, 
  * (the reverse of each stage of the coupled step of Secs. 3.1-3.3: collisions,
  * source, finite-difference gradients, Zou-He and CNEBB completions, pull
  * streaming) with sqrt(n_steps) checkpointing and recomputation.
+ * Instances with a solid mask are refused (LBVE_ERR_GEOMETRY).
  * The trajectory is the one that lbve_set_geometry(h, inst, NULL, <current
  * force of inst>, init_fields) followed by lbve_step(n_steps) produces; the
  * forward states are recomputed in the adjoint workspace (the instance's own

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbve.so")
-SOURCES = ["lbve_host.cu", "lbve_kernels.cu", "lbve_noalloc.cu", "lbve_adjoint.cu"]
+SOURCES = ["lbve_host.cu", "lbve_kernels.cu", "lbve_noalloc.cu", "lbve_adjoint.cu", "lbve_wall.cu"]
 HEADERS = ["lbve_internal.h", "lbve_step.cuh", "lbve_adjoint.cuh", os.path.join("..", "..", "include", "lbve.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -83,6 +83,8 @@ int validate(const lbve_params& p, int i) {
                 i);
   if (!std::isfinite(p.Fx) || !std::isfinite(p.Fy))
     return fail(LBVE_ERR_ARG, "instance %d: body force must be finite", i);
+  if (p.max_wall_nodes < 0 || int64_t(p.max_wall_nodes) > int64_t(p.nx) * p.ny)
+    return fail(LBVE_ERR_ARG, "instance %d: max_wall_nodes must be in [0, nx*ny]", i);
   if (p.tile_tx != 0 && (p.tile_tx < 1 || p.tile_tx > kTileTXMax || p.tile_tx > p.nx))
     return fail(LBVE_ERR_ARG, "instance %d: tile_tx must be 0 or in [1, min(%d, nx)]", i,
                 kTileTXMax);
@@ -97,7 +99,8 @@ int validate(const lbve_params& p, int i) {
 constexpr int kLists = 2;
 
 struct InstPlan {
-  size_t off_pop[2], off_hist, off_force, off_fields;
+  size_t off_pop[2], off_hist, off_force, off_fields, off_mask;
+  int wall_begin, wall_cap;  // wall-node records of this instance in its list
   int stride, TX, TY, hy, ntx, nty;
   int list;                  // tile list of this instance
   int tile_begin, ntiles;    // range in the list's tile table
@@ -109,6 +112,8 @@ struct Plan {
   size_t off_insts, off_tiles[kLists], off_partials, off_totals, off_flags, total;
   int ntiles[kLists], nslots;
   int cap_tiles[kLists];  // tile-table capacity: the most tiles any tile width gives
+  size_t off_mtiles[kLists], off_walls[kLists], off_wrec[kLists];
+  int wall_cap[kLists];   // wall-node records per list
 };
 
 int default_tile_tx(const lbve_params& p) { return p.nx >= kTileTX ? kTileTX : p.nx; }
@@ -136,7 +141,7 @@ Plan make_plan(const lbve_params* p, int n) {
   Plan pl;
   pl.inst.resize(n);
   size_t off = 0;
-  for (int l = 0; l < kLists; ++l) pl.ntiles[l] = pl.cap_tiles[l] = 0;
+  for (int l = 0; l < kLists; ++l) pl.ntiles[l] = pl.cap_tiles[l] = pl.wall_cap[l] = 0;
   for (int i = 0; i < n; ++i) {
     InstPlan& q = pl.inst[i];
     const size_t es = p[i].precision == LBVE_FP64 ? 8 : 4;
@@ -153,8 +158,13 @@ Plan make_plan(const lbve_params* p, int n) {
     off = align_up(off + 2 * plane, kAlign);
     q.off_fields = off;
     off = align_up(off + 6 * size_t(q.stride) * 8, kAlign);
+    q.off_mask = off;
+    if (p[i].max_wall_nodes > 0) off = align_up(off + size_t(q.stride), kAlign);
     tile_shape(p[i], q.TX, q.TY, q.hy);
     q.list = p[i].precision == LBVE_FP64 ? 0 : 1;
+    q.wall_begin = pl.wall_cap[q.list];
+    q.wall_cap = p[i].max_wall_nodes;
+    pl.wall_cap[q.list] += q.wall_cap;
     q.ntx = (p[i].nx + q.TX - 1) / q.TX;
     q.nty = (p[i].ny + q.TY - 1) / q.TY;
     q.tile_begin = pl.ntiles[q.list];
@@ -177,6 +187,14 @@ Plan make_plan(const lbve_params* p, int n) {
   for (int l = 0; l < kLists; ++l) {
     pl.off_tiles[l] = off;
     off = align_up(off + sizeof(TileDev) * std::max(pl.cap_tiles[l], 1), kAlign);
+  }
+  for (int l = 0; l < kLists; ++l) {
+    pl.off_mtiles[l] = off;
+    off = align_up(off + sizeof(TileDev) * std::max(pl.cap_tiles[l], 1), kAlign);
+    pl.off_walls[l] = off;
+    off = align_up(off + sizeof(WallDev) * std::max(pl.wall_cap[l], 1), kAlign);
+    pl.off_wrec[l] = off;
+    off = align_up(off + sizeof(double) * kWallRec * std::max(pl.wall_cap[l], 1), kAlign);
   }
   pl.off_partials = off;
   off = align_up(off + sizeof(double) * kPartial * std::max(pl.cap_tiles[0] + pl.cap_tiles[1], 1),
@@ -207,6 +225,20 @@ struct lbve_handle {
   int parity = 0;
   std::vector<int64_t> t;
   std::vector<char> ready;
+  // solid masks: host copies of the tile tables (their masked flags), the
+  // masked-tile tables run by the masked kernel, and the wall-node records
+  TileDev* d_mtiles[kLists] = {nullptr, nullptr};
+  WallDev* d_walls[kLists] = {nullptr, nullptr};
+  double* d_wrec[kLists] = {nullptr, nullptr};
+  std::vector<TileDev> tiles_h[kLists];
+  int nmasked[kLists] = {0, 0};
+  int nmasked_inst[kLists] = {0, 0};  // instances of the list that carry a mask
+  std::vector<std::vector<TileDev>> mtiles_of;  // masked tiles of each instance
+  std::vector<int> mbegin;                      // first entry of each in its masked table
+  std::vector<std::vector<WallDev>> walls_of;   // wall-node records of each instance
+  std::vector<std::vector<int32_t>> wall_index; // node -> record, per masked instance
+  std::vector<uint64_t> geom_hash;              // mask + wall fractions, 0 = no mask
+  std::vector<std::vector<uint8_t>> mask_h;     // host copy of each mask
   // CUDA graph of kGraphSteps non-final steps starting at parity 0, captured
   // on a private stream on first use and replayed on the caller's stream
   cudaStream_t cap_stream = nullptr;
@@ -220,11 +252,23 @@ constexpr int kGraphSteps = 32;  // even, so a replay leaves the parity unchange
 
 // Launch one time step of every tile list on stream st with the given parity.
 int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
+  // wall pass first: it completes the populations the step pulls from solid nodes
   for (int l = 0; l < kLists; ++l)
+    if (h->nmasked_inst[l] > 0 &&
+        launch_wall(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_walls[l], h->d_wrec[l],
+                    h->plan.wall_cap[l], parity, flags, st))
+      return cuda_fail(cudaGetLastError(), "wall pass launch");
+  for (int l = 0; l < kLists; ++l) {
+    const int prec = l == 0 ? LBVE_FP64 : LBVE_FP32_DEV;
     if (h->plan.ntiles[l] > 0 &&
-        launch_step(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_tiles[l],
-                    h->plan.ntiles[l], parity, kModeStep, flags, h->d_partials, st))
+        launch_step(prec, h->d_insts, h->d_tiles[l], h->plan.ntiles[l], parity, kModeStep, flags,
+                    h->d_partials, st))
       return cuda_fail(cudaGetLastError(), "step kernel launch");
+    if (h->nmasked[l] > 0 &&
+        launch_step(prec, h->d_insts, h->d_mtiles[l], h->nmasked[l], parity, kModeStep, flags,
+                    h->d_partials, st, 1))
+      return cuda_fail(cudaGetLastError(), "masked step kernel launch");
+  }
   return LBVE_OK;
 }
 
@@ -250,6 +294,166 @@ int ensure_graph(lbve_handle* h) {
     return cuda_fail(e, "graph instantiation");
   }
   h->graph = g;
+  return LBVE_OK;
+}
+
+// Drop the captured step graph (its launch configuration changed).
+void drop_graph(lbve_handle* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->graph_exec = nullptr;
+  h->graph = nullptr;
+}
+
+constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+constexpr int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// FNV-1a over the mask and the wall links: identifies the geometry a saved
+// state belongs to.
+uint64_t geometry_hash(const std::vector<uint8_t>& m, const std::vector<WallDev>& walls) {
+  uint64_t x = 1469598103934665603ull;
+  auto mix = [&x](const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) {
+      x ^= c[i];
+      x *= 1099511628211ull;
+    }
+  };
+  mix(m.data(), m.size());
+  for (const WallDev& W : walls) {
+    mix(&W.k, sizeof(W.k));
+    mix(&W.umask, sizeof(W.umask));
+    mix(W.q, sizeof(W.q));
+  }
+  return m.empty() ? 0 : (x | 1);
+}
+
+// Upload the wall-node records of instance i (unused capacity: inst = -1)
+// and clear its final-step wall sums.
+cudaError_t upload_walls(lbve_handle* h, int i) {
+  const InstPlan& q = h->plan.inst[i];
+  if (q.wall_cap <= 0) return cudaSuccess;
+  std::vector<WallDev> blk(q.wall_cap);
+  for (auto& W : blk) {
+    std::memset(&W, 0, sizeof(W));
+    W.inst = -1;
+  }
+  std::copy(h->walls_of[i].begin(), h->walls_of[i].end(), blk.begin());
+  cudaError_t e = cudaMemcpyAsync(h->d_walls[q.list] + q.wall_begin, blk.data(),
+                                  sizeof(WallDev) * q.wall_cap, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->d_wrec[q.list] + size_t(q.wall_begin) * kWallRec, 0,
+                        sizeof(double) * kWallRec * q.wall_cap, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // blk is pageable and local
+  return e;
+}
+
+// Install (mask != null) or remove the solid mask of instance i: validate
+// it, build the wall-node records (wall fraction 1/2), flag the tiles the
+// masked kernel must run, rebuild the list's masked-tile table, upload.
+int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
+  const lbve_params& p = h->p[i];
+  const InstPlan& q = h->plan.inst[i];
+  const int nx = p.nx, ny = p.ny, l = q.list;
+  const bool py = p.periodic_y != 0;
+  const size_t nn = size_t(nx) * ny;
+  InstDev& D = h->insts[i];
+  const bool had = D.mask != nullptr;
+  std::vector<uint8_t> m;
+  if (mask) {
+    if (p.max_wall_nodes <= 0)
+      return fail(LBVE_ERR_GEOMETRY, "instance %d: max_wall_nodes is 0, so no mask fits", i);
+    m.assign(nn, 0);
+    size_t nsolid = 0;
+    for (size_t k = 0; k < nn; ++k) nsolid += (m[k] = mask[k] ? 1 : 0);
+    if (nsolid == nn) return fail(LBVE_ERR_GEOMETRY, "instance %d: the mask leaves no fluid", i);
+    if (nsolid == 0) m.clear();  // an empty mask is no mask
+  }
+  if (m.empty() && !had) return LBVE_OK;  // no mask before or after: nothing to change
+  auto solid_at = [&](int x, int y) -> bool {
+    if (m.empty()) return false;
+    x = ((x % nx) + nx) % nx;
+    if (py) y = ((y % ny) + ny) % ny;
+    else if (y < 0 || y >= ny) return false;
+    return m[size_t(y) * nx + x] != 0;
+  };
+  std::vector<WallDev> walls;
+  std::vector<int32_t> index;
+  if (!m.empty()) {
+    if (!py)
+      for (int x = 0; x < nx; ++x)
+        for (int r = 0; r < 3; ++r)
+          if (m[size_t(r) * nx + x] || m[size_t(ny - 1 - r) * nx + x])
+            return fail(LBVE_ERR_GEOMETRY,
+                        "instance %d: rows 0-2 and ny-3..ny-1 of a walled domain must be fluid", i);
+    index.assign(nn, -1);
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const size_t k = size_t(y) * nx + x;
+        if (m[k]) continue;
+        int umask = 0, fmask = 0;
+        for (int d = 1; d < 9; ++d) {
+          if (!solid_at(x - kEx[d], y - kEy[d])) continue;
+          if (solid_at(x + kEx[d], y + kEy[d]))
+            return fail(LBVE_ERR_GEOMETRY,
+                        "instance %d: fluid node (%d, %d) has solid on both ends of link %d", i,
+                        x, y, d);
+          umask |= 1 << d;
+          const int yf = y + kEy[d];
+          if ((py || (yf >= 0 && yf < ny)) && !solid_at(x + kEx[d], yf)) fmask |= 1 << d;
+        }
+        if (!umask) continue;
+        if ((int)walls.size() >= p.max_wall_nodes)
+          return fail(LBVE_ERR_GEOMETRY, "instance %d: more wall nodes than max_wall_nodes (%d)",
+                      i, p.max_wall_nodes);
+        WallDev W;
+        std::memset(&W, 0, sizeof(W));
+        W.inst = i;
+        W.k = (int32_t)k;
+        W.umask = umask;
+        W.fmask = fmask;
+        for (int d = 0; d < 8; ++d) W.q[d] = 0.5;
+        index[k] = (int32_t)walls.size();
+        walls.push_back(W);
+      }
+  }
+  // flag the tiles holding a solid node or a node with a solid axis neighbour
+  std::vector<TileDev>& T = h->tiles_h[l];
+  std::vector<TileDev> mt;
+  for (int j = q.tile_begin; j < q.tile_begin + q.ntiles; ++j) {
+    TileDev& t = T[j];
+    t.masked = 0;
+    for (int y = t.y0; y < std::min(t.y0 + q.TY, ny) && !t.masked && !m.empty(); ++y)
+      for (int x = t.x0; x < std::min(t.x0 + q.TX, nx) && !t.masked; ++x)
+        if (solid_at(x, y) || solid_at(x + 1, y) || solid_at(x - 1, y) || solid_at(x, y + 1) ||
+            solid_at(x, y - 1))
+          t.masked = 1;
+    if (t.masked) mt.push_back(t);
+  }
+  h->mtiles_of[i] = std::move(mt);
+  std::vector<TileDev> table;
+  for (int j = 0; j < h->n; ++j)
+    if (h->plan.inst[j].list == l) {
+      h->mbegin[j] = (int)table.size();
+      table.insert(table.end(), h->mtiles_of[j].begin(), h->mtiles_of[j].end());
+    }
+  h->walls_of[i] = std::move(walls);
+  h->wall_index[i] = std::move(index);
+  cudaError_t e = cudaMemcpyAsync(h->d_tiles[l] + q.tile_begin, T.data() + q.tile_begin,
+                                  sizeof(TileDev) * q.ntiles, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && !table.empty())
+    e = cudaMemcpyAsync(h->d_mtiles[l], table.data(), sizeof(TileDev) * table.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && !m.empty())
+    e = cudaMemcpyAsync(h->ws + q.off_mask, m.data(), nn, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = upload_walls(h, i);  // synchronises: the local tables may go
+  if (e != cudaSuccess) return cuda_fail(e, "mask upload");
+  D.mask = m.empty() ? nullptr : (const uint8_t*)(h->ws + q.off_mask);
+  h->nmasked[l] = (int)table.size();
+  h->nmasked_inst[l] += (D.mask ? 1 : 0) - (had ? 1 : 0);
+  h->geom_hash[i] = geometry_hash(m, h->walls_of[i]);
+  h->mask_h[i] = std::move(m);
+  drop_graph(h);
   return LBVE_OK;
 }
 
@@ -312,6 +516,17 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
   const Plan& pl = h->plan;
   h->d_insts = (InstDev*)(h->ws + pl.off_insts);
   for (int l = 0; l < kLists; ++l) h->d_tiles[l] = (TileDev*)(h->ws + pl.off_tiles[l]);
+  for (int l = 0; l < kLists; ++l) {
+    h->d_mtiles[l] = (TileDev*)(h->ws + pl.off_mtiles[l]);
+    h->d_walls[l] = (WallDev*)(h->ws + pl.off_walls[l]);
+    h->d_wrec[l] = (double*)(h->ws + pl.off_wrec[l]);
+  }
+  h->mtiles_of.assign(n, {});
+  h->mbegin.assign(n, 0);
+  h->walls_of.assign(n, {});
+  h->wall_index.assign(n, {});
+  h->geom_hash.assign(n, 0);
+  h->mask_h.assign(n, {});
   h->d_partials = (double*)(h->ws + pl.off_partials);
   h->d_totals = (double*)(h->ws + pl.off_totals);
   h->d_flags = (int32_t*)(h->ws + pl.off_flags);
@@ -342,6 +557,9 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     D.slot_begin = q.slot_begin;
     D.slot_end = q.slot_begin + q.nslots;
     D.prec = p[i].precision;
+    D.mask = nullptr;
+    D.wall_rec = (double*)(h->ws + pl.off_wrec[q.list]) + size_t(q.wall_begin) * kWallRec;
+    D.wall_cap = q.wall_cap;
     D.inv_Uc = 1.0 / c.Uc;
     D.cd[kCoefFx] = p[i].Fx;
     D.cd[kCoefFy] = p[i].Fy;
@@ -363,8 +581,18 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
         T.x0 = tx * q.TX;
         T.y0 = ty * q.TY;
         T.slot = q.slot_begin + (k - q.tile_begin);
+        T.masked = 0;
         ++k;
       }
+  }
+  // unused wall-node records: inst = -1, zero wall sums
+  std::vector<WallDev> no_walls[kLists];
+  for (int l = 0; l < kLists; ++l) {
+    no_walls[l].resize(pl.wall_cap[l]);
+    for (auto& W : no_walls[l]) {
+      std::memset(&W, 0, sizeof(W));
+      W.inst = -1;
+    }
   }
   // Synchronous copies from pageable host memory: the host vectors may go
   // out of scope as soon as the calls return.
@@ -374,6 +602,14 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     if (!tiles[l].empty())
       e = cudaMemcpyAsync(h->d_tiles[l], tiles[l].data(), sizeof(TileDev) * tiles[l].size(),
                           cudaMemcpyHostToDevice, h->stream);
+  for (int l = 0; l < kLists && e == cudaSuccess; ++l)
+    if (pl.wall_cap[l] > 0) {
+      e = cudaMemcpyAsync(h->d_walls[l], no_walls[l].data(), sizeof(WallDev) * pl.wall_cap[l],
+                          cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->d_wrec[l], 0, sizeof(double) * kWallRec * pl.wall_cap[l],
+                            h->stream);
+    }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int32_t) * n, h->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(h->d_totals, 0, sizeof(double) * kTotals * n, h->stream);
@@ -382,6 +618,7 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     delete h;
     return cuda_fail(e, "lbve_create upload");
   }
+  for (int l = 0; l < kLists; ++l) h->tiles_h[l] = std::move(tiles[l]);
   *out = h;
   return LBVE_OK;
 }
@@ -389,9 +626,22 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
 int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
                       const double* body_force, const double* init_fields) {
   if (!h || inst < 0 || inst >= h->n) return fail(LBVE_ERR_ARG, "bad handle or instance");
-  if (solid_mask)
-    return fail(LBVE_ERR_GEOMETRY,
-                "solid masks are not supported; walls follow periodic_y (pass NULL)");
+  {
+    // every host-side check before anything changes
+    const size_t nn = size_t(h->p[inst].nx) * h->p[inst].ny;
+    if (body_force)
+      for (size_t k = 0; k < 2 * nn; ++k)
+        if (!std::isfinite(body_force[k])) return fail(LBVE_ERR_ARG, "body force not finite");
+    if (init_fields) {
+      for (size_t k = 0; k < 6 * nn; ++k)
+        if (!std::isfinite(init_fields[k]))
+          return fail(LBVE_ERR_ARG, "initial fields not finite");
+      for (size_t k = 0; k < nn; ++k)
+        if (!(init_fields[k] > 0.0)) return fail(LBVE_ERR_ARG, "initial density must be > 0");
+    }
+    const int rc = install_mask(h, inst, solid_mask);
+    if (rc) return rc;
+  }
   const lbve_params& p = h->p[inst];
   const InstPlan& q = h->plan.inst[inst];
   const size_t nn = size_t(p.nx) * p.ny;
@@ -401,8 +651,6 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
   cudaError_t e = cudaSuccess;
 
   if (body_force) {
-    for (size_t k = 0; k < 2 * nn; ++k)
-      if (!std::isfinite(body_force[k])) return fail(LBVE_ERR_ARG, "body force not finite");
     double* stage = (double*)D.pop[P];  // staging: float64 [2][S]
     e = cudaMemcpy2DAsync(stage, S * 8, body_force, nn * 8, nn * 8, 2, cudaMemcpyHostToDevice,
                           h->stream);
@@ -417,10 +665,6 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
   // staged initial fields, float64 [6][S], in the buffer the init kernel reads
   double* stage = (double*)D.pop[P ^ 1];
   if (init_fields) {
-    for (size_t k = 0; k < 6 * nn; ++k)
-      if (!std::isfinite(init_fields[k])) return fail(LBVE_ERR_ARG, "initial fields not finite");
-    for (size_t k = 0; k < nn; ++k)
-      if (!(init_fields[k] > 0.0)) return fail(LBVE_ERR_ARG, "initial density must be > 0");
     e = cudaMemcpy2DAsync(stage, S * 8, init_fields, nn * 8, nn * 8, 6, cudaMemcpyHostToDevice,
                           h->stream);
   } else {
@@ -438,6 +682,11 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
   if (launch_step(p.precision, h->d_insts, h->d_tiles[q.list] + q.tile_begin, q.ntiles, P ^ 1,
                   kModeInit, kFinal, h->d_partials, h->stream))
     return cuda_fail(cudaGetLastError(), "init kernel launch");
+  if (!h->mtiles_of[inst].empty() &&
+      launch_step(p.precision, h->d_insts, h->d_mtiles[q.list] + h->mbegin[inst],
+                  (int)h->mtiles_of[inst].size(), P ^ 1, kModeInit, kFinal, h->d_partials,
+                  h->stream, 1))
+    return cuda_fail(cudaGetLastError(), "masked init kernel launch");
   if (launch_reduce(h->d_insts, inst, 1, h->d_partials, h->d_totals, h->d_flags, h->stream))
     return cuda_fail(cudaGetLastError(), "reduce launch");
   // the pageable copy of D above is staged before return; make the device
@@ -525,7 +774,9 @@ int lbve_totals(lbve_handle* h, int32_t inst, double out[LBVE_NTOTALS]) {
   double rec[kTotals];
   const int rc = read_totals(h, inst, rec);
   if (rc) return rc;
-  for (int j = 0; j < LBVE_NTOTALS; ++j) out[j] = rec[j];
+  for (int j = 0; j < 12; ++j) out[j] = rec[j];
+  out[12] = rec[kDrag];
+  out[13] = rec[kDrag + 1];
   return LBVE_OK;
 }
 
@@ -547,7 +798,7 @@ int lbve_time(lbve_handle* h, int32_t inst, int64_t* t) {
 // ---- checkpoint / resume -------------------------------------------------
 namespace {
 constexpr uint32_t kStateMagic = 0x4556424cu;  // "LBVE"
-constexpr uint32_t kStateVersion = 1;
+constexpr uint32_t kStateVersion = 2;
 struct StateHeader {
   uint32_t magic, version;
   int32_t n, reserved;
@@ -555,6 +806,7 @@ struct StateHeader {
 struct InstHeader {
   int64_t t;
   int32_t nx, ny, precision, periodic_y, force_field, ready;
+  uint64_t geometry;  // hash of the solid mask and wall fractions, 0 = none
 };
 size_t inst_state_bytes(const lbve_params& p) {
   const size_t nn = size_t(p.nx) * p.ny, es = p.precision == LBVE_FP64 ? 8 : 4;
@@ -584,7 +836,8 @@ int lbve_save(lbve_handle* h, void* host_buf, size_t bytes) {
     const lbve_params& p = h->p[i];
     const InstDev& D = h->insts[i];
     const size_t nn = size_t(p.nx) * p.ny, S = D.stride, es = p.precision == LBVE_FP64 ? 8 : 4;
-    InstHeader I{h->t[i], p.nx, p.ny, p.precision, p.periodic_y, D.force_field, h->ready[i]};
+    InstHeader I{h->t[i], p.nx, p.ny, p.precision, p.periodic_y, D.force_field, h->ready[i],
+                 h->geom_hash[i]};
     std::memcpy(out, &I, sizeof(I));
     out += sizeof(I);
     // current populations (36), history (5), force (2): planes of nn values
@@ -628,6 +881,9 @@ int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes) {
     const lbve_params& p = h->p[i];
     if (I.nx != p.nx || I.ny != p.ny || I.precision != p.precision || I.periodic_y != p.periodic_y)
       return fail(LBVE_ERR_ARG, "saved instance %d does not match this handle's parameters", i);
+    if (I.geometry != h->geom_hash[i])
+      return fail(LBVE_ERR_GEOMETRY,
+                  "saved instance %d was run on another solid mask (set it before loading)", i);
     scan += inst_state_bytes(p);
   }
   cudaError_t e = cudaSuccess;
@@ -662,6 +918,31 @@ int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int32_t) * h->n, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbve_load");
+  return LBVE_OK;
+}
+
+int lbve_set_wall_distances(lbve_handle* h, int32_t inst, int32_t n_links, const int32_t* node,
+                            const int32_t* dir, const double* q) {
+  if (!h || inst < 0 || inst >= h->n || n_links < 0 || (n_links > 0 && (!node || !dir || !q)))
+    return fail(LBVE_ERR_ARG, "bad handle, instance, count or pointer");
+  if (!h->insts[inst].mask) return fail(LBVE_ERR_GEOMETRY, "instance %d has no solid mask", inst);
+  const lbve_params& p = h->p[inst];
+  const int64_t nn = int64_t(p.nx) * p.ny;
+  std::vector<WallDev>& W = h->walls_of[inst];
+  const std::vector<int32_t>& idx = h->wall_index[inst];
+  for (int32_t j = 0; j < n_links; ++j) {
+    if (node[j] < 0 || node[j] >= nn || dir[j] < 1 || dir[j] > 8)
+      return fail(LBVE_ERR_ARG, "link %d: node or direction out of range", j);
+    const int32_t r = idx[node[j]];
+    if (r < 0 || !((W[r].umask >> dir[j]) & 1))
+      return fail(LBVE_ERR_GEOMETRY, "link %d (node %d, direction %d) is not a wall link", j,
+                  node[j], dir[j]);
+    if (!(q[j] > 0.0 && q[j] <= 1.0)) return fail(LBVE_ERR_ARG, "link %d: q must be in (0, 1]", j);
+  }
+  for (int32_t j = 0; j < n_links; ++j) W[idx[node[j]]].q[dir[j] - 1] = q[j];
+  const cudaError_t e = upload_walls(h, inst);
+  if (e != cudaSuccess) return cuda_fail(e, "wall upload");
+  h->geom_hash[inst] = geometry_hash(h->mask_h[inst], W);
   return LBVE_OK;
 }
 
@@ -862,6 +1143,8 @@ extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* ini
   if (!h || inst < 0 || inst >= h->n || !d_dL_dfields || !d_dL_dforce || n_steps < 1)
     return fail(LBVE_ERR_ARG, "bad handle, instance, pointer or step count");
   if (!h->ready[inst]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", inst);
+  if (h->insts[inst].mask)
+    return fail(LBVE_ERR_GEOMETRY, "the adjoint does not cover solid masks (instance %d)", inst);
   const lbve_params& p = h->p[inst];
   const InstPlan& q = h->plan.inst[inst];
   const AdjPlan a = make_adj_plan(p, q, n_steps);

@@ -26,7 +26,8 @@ enum : int {
   kSumRho = 0, kSumJx = 1, kSumJy = 2, kSumPhi = 3,  // 3..5
   kWallIn = 6,                                        // 6..8
   kWallOut = 9,                                       // 9..11
-  kResid = 12, kNonFinite = 13
+  kResid = 12, kNonFinite = 13,
+  kDrag = 14                                          // 14..15 (totals only)
 };
 
 // Kernel flags.
@@ -58,7 +59,9 @@ struct InstDev {
   int32_t nx, ny, stride, periodic_y;
   int32_t TX, TY, hy, force_field;
   int32_t slot_begin, slot_end;  // partial-record slots of this instance
-  int32_t prec, pad;
+  int32_t prec, wall_cap;        // wall_cap: wall-node records of this instance
+  const uint8_t* mask;           // [stride] 1 = solid node, or null (no mask)
+  double* wall_rec;              // [wall_cap][kWallRec] final-step wall sums
   double inv_Uc;
   // Collision coefficients, in float64 and rounded once to float32, so that
   // neither kernel converts precision per node.
@@ -66,16 +69,36 @@ struct InstDev {
   float cf[16];
 };
 
-// One tile of one instance: {instance, x0, y0, partial slot}.
+// One tile of one instance: {instance, x0, y0, partial slot, masked}.
+// masked: the tile holds a solid node or a node with a solid neighbour along
+// x or y; such tiles are run by the masked variant of the step kernel.
 struct TileDev {
-  int32_t inst, x0, y0, slot;
+  int32_t inst, x0, y0, slot, masked;
 };
+
+// One fluid node next to the solid mask (the compact link list of the wall
+// pass).  inst < 0 marks an unused record.
+//   umask bit i: link i is a wall link (node k - e_i is solid)
+//   fmask bit i: node k + e_i is fluid (second operand of the interpolation)
+//   q[i-1]:      wall fraction of link i, in (0, 1]
+struct WallDev {
+  int32_t inst, k, umask, fmask;
+  double q[8];
+};
+constexpr int kWallRec = 8;  // drag x, drag y, wall in x3, wall out x3
 
 // Launchers implemented in lbve_kernels.cu (templated over float/double).
 enum : int { kModeStep = 0, kModeInit = 1 };
 
+// masked = 0 runs the plain kernel (which skips masked tiles), 1 the masked variant.
 int launch_step(int prec, const InstDev* d_insts, const TileDev* d_tiles, int n_tiles,
-                int parity, int mode, int flags, double* d_partials, void* stream);
+                int parity, int mode, int flags, double* d_partials, void* stream,
+                int masked = 0);
+// Wall pass before a step: completes the populations of the wall links of
+// n_walls records in the buffer pop[parity]; on the final step it writes one
+// kWallRec record per wall node to d_rec (lbve_wall.cu).
+int launch_wall(int prec, const InstDev* d_insts, const WallDev* d_walls, double* d_rec,
+                int n_walls, int parity, int flags, void* stream);
 // Adjoint pass modes: a normal step, the final fields (the loss), the initial collision.
 enum : int { kAdjStep = 0, kAdjFields = 1, kAdjInit = 2 };
 

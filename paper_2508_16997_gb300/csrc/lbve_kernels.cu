@@ -7,59 +7,46 @@
 
 namespace lbve {
 
-#ifndef LBVE_PERSISTENT
-#define LBVE_PERSISTENT 0
-#endif
-
-template <typename R, int MODE, bool FINAL>
+template <typename R, int MODE, bool FINAL, bool MASKED>
 static void launch_step_k(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
                           double* d_partials, cudaStream_t st) {
-  // Persistent grid (resident CTAs per SM x SMs) for the time steps, one CTA
-  // per tile for the initialisation.
-  static int resident = 0;  // CTAs that fit on the device at once
-  if (LBVE_PERSISTENT && MODE == kModeStep && resident == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<R, MODE, FINAL, true>,
-                                                      kThreads, 0) == cudaSuccess)
-      resident = sms * per_sm;
-    else
-      resident = -1;
-  }
-  if (LBVE_PERSISTENT && MODE == kModeStep && resident > 0 && n_tiles > resident) {
-    step_kernel<R, MODE, FINAL, true><<<resident, kThreads, 0, st>>>(d_insts, d_tiles, n_tiles,
-                                                                     parity, d_partials);
-  } else {
-    step_kernel<R, MODE, FINAL, false><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, n_tiles,
-                                                                     parity, d_partials);
-  }
+  step_kernel<R, MODE, FINAL, MASKED><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, parity,
+                                                                    d_partials);
 }
 
-template <typename R>
+template <typename R, bool MASKED>
 static int launch_step_t(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
                          int mode, int flags, double* d_partials, cudaStream_t st) {
   if (n_tiles <= 0) return 0;
   const bool fin = (flags & kFinal) != 0;
   if (mode == kModeStep) {
-    if (fin) launch_step_k<R, kModeStep, true>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
-    else launch_step_k<R, kModeStep, false>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
+    if (fin)
+      launch_step_k<R, kModeStep, true, MASKED>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
+    else
+      launch_step_k<R, kModeStep, false, MASKED>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
   } else {
-    launch_step_k<R, kModeInit, true>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
+    launch_step_k<R, kModeInit, true, MASKED>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_step(int prec, const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
-                int mode, int flags, double* d_partials, void* stream) {
+                int mode, int flags, double* d_partials, void* stream, int masked) {
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == 0)
-    return launch_step_t<double>(d_insts, d_tiles, n_tiles, parity, mode, flags, d_partials, st);
-  return launch_step_t<float>(d_insts, d_tiles, n_tiles, parity, mode, flags, d_partials, st);
+    return masked ? launch_step_t<double, true>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                                                d_partials, st)
+                  : launch_step_t<double, false>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                                                 d_partials, st);
+  return masked ? launch_step_t<float, true>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                                             d_partials, st)
+                : launch_step_t<float, false>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                                              d_partials, st);
 }
 
 // One CTA per instance: sum (max for the residual) the partial records of the
-// instance's tiles in a fixed order, so totals are bit-reproducible.
+// instance's tiles, and the wall-pass records of its mask walls, in a fixed
+// order, so totals are bit-reproducible.
 __global__ void __launch_bounds__(256) reduce_kernel(const InstDev* __restrict__ insts,
                                                      int first_inst,
                                                      const double* __restrict__ partials,
@@ -68,12 +55,17 @@ __global__ void __launch_bounds__(256) reduce_kernel(const InstDev* __restrict__
   __shared__ double s[256];
   const int inst = first_inst + blockIdx.x;
   const InstDev& D = insts[inst];
-  for (int j = 0; j < 14; ++j) {
+  for (int j = 0; j < kDrag + 2; ++j) {
     double v = 0.0;
-    for (int q = D.slot_begin + threadIdx.x; q < D.slot_end; q += blockDim.x) {
-      const double p = partials[(size_t)q * kPartial + j];
-      v = (j == kResid) ? fmax(v, p) : v + p;
-    }
+    if (j < kDrag)
+      for (int q = D.slot_begin + threadIdx.x; q < D.slot_end; q += blockDim.x) {
+        const double p = partials[(size_t)q * kPartial + j];
+        v = (j == kResid) ? fmax(v, p) : v + p;
+      }
+    // wall record layout: drag x, drag y, in x3, out x3
+    const int r = (j >= kDrag) ? j - kDrag : (j >= kWallIn && j < kResid) ? 2 + (j - kWallIn) : -1;
+    if (r >= 0)
+      for (int q = threadIdx.x; q < D.wall_cap; q += blockDim.x) v += D.wall_rec[(size_t)q * kWallRec + r];
     s[threadIdx.x] = v;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {

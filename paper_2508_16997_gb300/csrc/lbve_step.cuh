@@ -464,42 +464,33 @@ struct MinBlocks {
   static constexpr int value = sizeof(R) == 4 ? LBVE_FP32_MIN_BLOCKS : (kThreads <= 256 ? 2 : 1);
 };
 
-// Ask L2 for everything this thread's node of tile T will load (its 36
-// pulled populations, history and force).  No registers are held: the
-// demand loads of the next tile then hit L2 instead of HBM.
+// One-sided differences along one axis next to the solid mask (same rule as
+// the central and wall-row differences: second order on the fluid side when
+// two fluid nodes lie there, else first order; zero between two solids).
+//   t:        +1 toward +axis, -1 toward -axis (the fluid side)
+//   q0, q1:   (rho, ux, uy) of the node and of its fluid neighbour at +t
+//   has2:     whether the node at +2t is fluid; (r2, u2x, u2y) its values
+//   axis:     0 = x (the cube is rho ux^3), 1 = y (rho uy^3)
 template <typename R>
-__device__ __forceinline__ void prefetch_tile(const InstDev* __restrict__ insts, const TileDev T,
-                                              int parity) {
-  const InstDev& D = insts[T.inst];
-  const int nx = D.nx, ny = D.ny, S = D.stride, TX = D.TX, TY = D.TY;
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int x = T.x0 + tx, y = T.y0 + ty;
-  if (ty >= TY || x >= nx || y >= ny) return;
-  const bool py = D.periodic_y != 0;
-  int rm, rp;
-  neighbour_rows(y, nx, ny, py, rm, rp);
-  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-  const int rc = y * nx, k = rc + x;
-  const int off[9] = {rc + x, rc + xm, rm >= 0 ? rm + x : rc + x, rc + xp, rp >= 0 ? rp + x : rc + x,
-                      rm >= 0 ? rm + xm : rc + x, rm >= 0 ? rm + xp : rc + x,
-                      rp >= 0 ? rp + xp : rc + x, rp >= 0 ? rp + xm : rc + x};
-  const R* src = (const R*)D.pop[parity];
-#pragma unroll
-  for (int l = 0; l < 4; ++l)
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (size_t)(9 * l + i) * S + off[i]));
-  const R* hist = (const R*)D.hist;
-#pragma unroll
-  for (int j = 0; j < 5; ++j) asm volatile("prefetch.global.L2 [%0];" ::"l"(hist + (size_t)j * S + k));
-  if (D.force_field) {
-    const R* force = (const R*)D.force;
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(force + k));
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(force + S + k));
+__device__ __forceinline__ void one_sided(int t, R r0, R ux0, R uy0, R r1, R ux1, R uy1,
+                                          bool has2, R r2, R ux2, R uy2, int axis, R& dux,
+                                          R& duy, R& dcube) {
+  const R v0 = axis == 0 ? ux0 : uy0, v1 = axis == 0 ? ux1 : uy1, v2 = axis == 0 ? ux2 : uy2;
+  const R c0 = r0 * v0 * v0 * v0, c1 = r1 * v1 * v1 * v1, c2 = r2 * v2 * v2 * v2;
+  const R ts = (R)t;
+  if (has2) {
+    const R h = R(0.5) * ts;
+    dux = h * (R(-3) * ux0 + R(4) * ux1 - ux2);
+    duy = h * (R(-3) * uy0 + R(4) * uy1 - uy2);
+    dcube = h * (R(-3) * c0 + R(4) * c1 - c2);
+  } else {
+    dux = ts * (ux1 - ux0);
+    duy = ts * (uy1 - uy0);
+    dcube = ts * (c1 - c0);
   }
 }
 
-template <typename R, int MODE, bool FINAL>
+template <typename R, int MODE, bool FINAL, bool MASKED>
 __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, const TileDev T,
                                              int parity, double* __restrict__ partials, R* s_rho,
                                              R* s_ux, R* s_uy, double (*s_red)[kPartial]) {
@@ -524,7 +515,10 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const bool in_tile = ty < TY;
   const int x = T.x0 + tx, y = T.y0 + ty;
-  const bool active = in_tile && (x < nx) && (y < ny);
+  const bool inside = in_tile && (x < nx) && (y < ny);
+  // solid-mask nodes (masked tiles only) take no part in the update
+  const bool solid = MASKED && inside && D.mask[y * nx + x] != 0;
+  const bool active = inside && !solid;
   const int ri = (ty + hy) * RW + tx + 1;  // this slot in the halo region
   const bool wb = active && !py && y == 0, wt = active && !py && y == ny - 1;
   const int nring = 2 * hy * RW + 2 * TY;
@@ -620,7 +614,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
       }
       cde_moments<R>(g[l], cm[l]);
     }
-  } else if (in_tile) {
+  } else if (in_tile && !inside) {
     // slot outside the domain (ragged tile): it may still be a periodic
     // neighbour of an active node, so fill it with the wrapped node
     const int gx = x % nx, gy = py ? y % ny : y;
@@ -655,11 +649,11 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   if (active) {
     // gradients: grad[g][b] = d_g u_b  (G00 = dx ux, G01 = dx uy, G10 = dy ux, G11 = dy uy)
     const R half = R(0.5);
-    const R G00 = half * (s_ux[ri + 1] - s_ux[ri - 1]);
-    const R G01 = half * (s_uy[ri + 1] - s_uy[ri - 1]);
+    R G00 = half * (s_ux[ri + 1] - s_ux[ri - 1]);
+    R G01 = half * (s_uy[ri + 1] - s_uy[ri - 1]);
     const R cxp = s_rho[ri + 1] * s_ux[ri + 1] * s_ux[ri + 1] * s_ux[ri + 1];
     const R cxm = s_rho[ri - 1] * s_ux[ri - 1] * s_ux[ri - 1] * s_ux[ri - 1];
-    const R dPx = half * (cxp - cxm);
+    R dPx = half * (cxp - cxm);
     R G10, G11, dPy;
     {
       // rows y-2..y+2 of this column (only those a wall row needs are read)
@@ -668,12 +662,65 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
       y_gradients<R>(wb, wt, s_rho[a], s_ux[a], s_uy[a], s_rho[b], s_ux[b], s_uy[b], rho, ux,
                      uy, s_rho[c], s_ux[c], s_uy[c], s_rho[e], s_ux[e], s_uy[e], G10, G11, dPy);
     }
+    if constexpr (MASKED) {
+      // one-sided differences where an axis neighbour is solid; the values
+      // two nodes away come straight from the pulled populations (L2)
+      const uint8_t* __restrict__ M = D.mask;
+      const int xp = x == nx - 1 ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+      const bool sxp = M[y * nx + xp] != 0, sxm = M[y * nx + xm] != 0;
+      if (sxp || sxm) {
+        R gx0 = R(0), gx1 = R(0), gxc = R(0);
+        if (!(sxp && sxm)) {
+          const int t = sxp ? -1 : 1;
+          const int i1 = t > 0 ? ri + 1 : ri - 1;
+          const int x2 = (((x + 2 * t) % nx) + nx) % nx;
+          const bool has2 = M[y * nx + x2] == 0;
+          R r2 = R(1), u2x = R(0), u2y = R(0);
+          if (has2)
+            node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, x2, y, r2, u2x, u2y);
+          one_sided<R>(t, rho, ux, uy, s_rho[i1], s_ux[i1], s_uy[i1], has2, r2, u2x, u2y, 0, gx0,
+                       gx1, gxc);
+        }
+        G00 = gx0;
+        G01 = gx1;
+        dPx = gxc;
+      }
+      if (!wb && !wt) {
+        // rows next to a flat wall carry no mask, so y +- 1 lies in the domain
+        const int yp = (py && y == ny - 1) ? 0 : y + 1, ym = (py && y == 0) ? ny - 1 : y - 1;
+        const bool syp = M[yp * nx + x] != 0, sym = M[ym * nx + x] != 0;
+        if (syp || sym) {
+          R gy0 = R(0), gy1 = R(0), gyc = R(0);
+          if (!(syp && sym)) {
+            const int t = syp ? -1 : 1;
+            const int i1 = t > 0 ? ri + RW : ri - RW;
+            int y2 = y + 2 * t;
+            if (py) y2 = ((y2 % ny) + ny) % ny;
+            const bool has2 = y2 >= 0 && y2 < ny && M[y2 * nx + x] == 0;
+            R r2 = R(1), u2x = R(0), u2y = R(0);
+            if (has2)
+              node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, x, y2, r2, u2x,
+                                  u2y);
+            one_sided<R>(t, rho, ux, uy, s_rho[i1], s_ux[i1], s_uy[i1], has2, r2, u2x, u2y, 1,
+                         gy0, gy1, gyc);
+          }
+          G10 = gy0;
+          G11 = gy1;
+          dPy = gyc;
+        }
+      }
+    }
     if (FINAL) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) part[kWallIn + j] = wall_io[j];
     }
     collide_node<R, MODE, FINAL>(D, k, S, dst, hist, hm, cm, rho, ux, uy, G00, G01, G10, G11,
                                  dPx, dPy, Fx, Fy, So[0], So[1], So[2], uxo, uyo, part);
+  } else if (FINAL && solid) {
+    // a solid node reports zero fields and adds nothing to the totals
+    const int ks = y * nx + x;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) D.fields[(size_t)j * S + ks] = 0.0;
   }
 
   if (FINAL) {
@@ -694,26 +741,19 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   }
 }
 
-template <typename R, int MODE, bool FINAL, bool PERSIST>
+// One CTA per tile.  The plain variant leaves masked tiles to the masked one
+// (which runs over a separate list of just those tiles).
+template <typename R, int MODE, bool FINAL, bool MASKED>
 __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value)
-    step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles, int n_tiles,
+    step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles,
                 int parity, double* __restrict__ partials) {
   __shared__ R s_rho[kRegionMax];
   __shared__ R s_ux[kRegionMax];
   __shared__ R s_uy[kRegionMax];
   __shared__ double s_red[kThreads / 32][kPartial];
-  if constexpr (!PERSIST) {
-    process_tile<R, MODE, FINAL>(insts, tiles[blockIdx.x], parity, partials, s_rho, s_ux, s_uy,
-                                 s_red);
-  } else {
-    // persistent: walk the tile list with a stride of the grid, prefetching
-    // the next tile into L2 before working on the current one
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-      if (t + (int)gridDim.x < n_tiles) prefetch_tile<R>(insts, tiles[t + gridDim.x], parity);
-      process_tile<R, MODE, FINAL>(insts, tiles[t], parity, partials, s_rho, s_ux, s_uy, s_red);
-      __syncthreads();  // the shared halo arrays are reused by the next tile
-    }
-  }
+  const TileDev T = tiles[blockIdx.x];
+  if (!MASKED && T.masked) return;
+  process_tile<R, MODE, FINAL, MASKED>(insts, T, parity, partials, s_rho, s_ux, s_uy, s_red);
 }
 
 }  // namespace lbve

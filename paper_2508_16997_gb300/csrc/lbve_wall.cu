@@ -1,0 +1,190 @@
+// lbve_wall.cu -- wall pass of the solid mask (hand-written CUDA, sm_103a).
+//
+// Runs before every step on the compact list of fluid nodes next to solid
+// nodes (one thread per node).  For each wall link (x_b, i), i.e. x_b - e_i
+// solid, it computes the population that arrives at x_b along e_i and
+// stores it in the solid node's slot i, which is exactly where the step
+// kernel's pull of x_b reads it.  So the fused step needs no wall logic for
+// the mask: it pulls completed populations everywhere.
+//   - Hydrodynamic lattice: linear interpolated bounce-back (Bouzidi,
+//     Firdaouss & Lallemand 2001) at wall fraction q; q = 1/2 is half-way
+//     bounce-back.  It stands in for the curved-wall scheme of Sec. 4.3.
+//   - Conformation lattices: CNEBB (Sec. 3.3) with u_b from the completed
+//     hydrodynamic populations; the closing rest population is written to
+//     the node's own rest slot (only this node pulls it).
+//   - Final step: the momentum-exchange force on the solid (eq_F_x) and the
+//     CNEBB wall in/out amounts, float64, one record per wall node.
+// Reads touch only fluid nodes' slots and writes only solid nodes' slots and
+// the node's own rest slots, so the threads never race.
+#include <cuda_runtime.h>
+
+#include "lbve_internal.h"
+#include "lbve_step.cuh"
+
+namespace lbve {
+namespace {
+
+// D2Q9 velocities, opposites and weights (Sec. 3.1); with unrolled loops the
+// index is a constant and these fold away.
+__device__ __forceinline__ constexpr int ex(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int ey(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int opp(int i) {
+  return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i + 1) % 4 + 5);
+}
+__device__ __forceinline__ constexpr double wt(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+constexpr int kWallThreads = 128;
+
+template <typename R, bool FINAL>
+__global__ void __launch_bounds__(kWallThreads)
+    wall_kernel(const InstDev* __restrict__ insts, const WallDev* __restrict__ walls, int n,
+                int parity, double* __restrict__ rec) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const WallDev W = walls[t];
+  if (W.inst < 0) return;
+  const InstDev& D = insts[W.inst];
+  const int nx = D.nx, ny = D.ny, S = D.stride;
+  const bool py = D.periodic_y != 0;
+  R* __restrict__ p = (R*)D.pop[parity];
+  const int k = W.k, x = k % nx, y = k / nx;
+  // node k + s e_i; mask nodes lie at least three rows from a flat wall, so
+  // no neighbour leaves a walled domain
+  int nb_m[9], nb_p[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    int xm = x - ex(i), xp = x + ex(i), ym = y - ey(i), yp = y + ey(i);
+    xm = xm < 0 ? xm + nx : (xm >= nx ? xm - nx : xm);
+    xp = xp < 0 ? xp + nx : (xp >= nx ? xp - nx : xp);
+    if (py) {
+      ym = ym < 0 ? ym + ny : (ym >= ny ? ym - ny : ym);
+      yp = yp < 0 ? yp + ny : (yp >= ny ? yp - ny : yp);
+    }
+    nb_m[i] = ym * nx + xm;
+    nb_p[i] = yp * nx + xp;
+  }
+  const R Fx = D.force_field ? ((const R*)D.force)[k] : coef<R>(D, kCoefFx);
+  const R Fy = D.force_field ? ((const R*)D.force)[S + k] : coef<R>(D, kCoefFy);
+
+  // ---- hydrodynamic lattice: interpolated bounce-back -----------------------
+  R d[9];
+  double fdx = 0.0, fdy = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    if (i != 0 && ((W.umask >> i) & 1)) {
+      const int ib = opp(i);
+      const double q = W.q[i - 1];
+      const R fb = p[(size_t)ib * S + k];  // own post-collision toward the wall
+      R v;
+      if (q < 0.5) {
+        if ((W.fmask >> i) & 1) {
+          const R ff = p[(size_t)ib * S + nb_p[i]];
+          v = (R)(2.0 * q) * fb + (R)(1.0 - 2.0 * q) * ff;
+        } else {
+          v = fb;  // no second fluid node: half-way bounce-back
+        }
+      } else {
+        const R fo = p[(size_t)i * S + k];
+        const double a = 1.0 / (2.0 * q);
+        v = (R)a * fb + (R)(1.0 - a) * fo;
+      }
+      p[(size_t)i * S + nb_m[i]] = v;
+      d[i] = v;
+      if (FINAL) {
+        // eq_F_x: e_ib (f^dagger_ib + f_i) over the links to the wall
+        const double s = 2.0 * wt(i) + (double)fb + (double)v;
+        fdx -= ex(i) * s;
+        fdy -= ey(i) * s;
+      }
+    } else {
+      d[i] = p[(size_t)i * S + nb_m[i]];
+    }
+  }
+  HydroM<R> hm;
+  hydro_moments<R>(d, hm);
+  const R rho = R(1) + hm.drho;
+  const R irho = R(1) / rho;
+  const R ux = (hm.jx + R(0.5) * Fx) * irho;
+  const R uy = (hm.jy + R(0.5) * Fy) * irho;
+
+  // ---- conformation lattices: CNEBB -----------------------------------------
+  double wio[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    R* __restrict__ pl = p + (size_t)(9 + 9 * l) * S;
+    const R delta = (l == 1) ? R(0) : R(1);
+    R g[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    R dphi = R(0);
+    double out = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      if (i != 0 && ((W.umask >> i) & 1)) {
+        const R post = pl[(size_t)opp(i) * S + k];  // sent toward the wall
+        dphi += post;
+        if (FINAL) out += wt(i) * (double)delta + (double)post;
+      } else {
+        g[i] = pl[(size_t)i * S + nb_m[i]];
+        dphi += g[i];
+      }
+    }
+    const R phib = delta + dphi;
+    // g_i = g_ibar + g^eq_i - g^eq_ibar = g_ibar + 6 w_i phi_b (e_i . u_b)
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+      if ((W.umask >> i) & 1)
+        g[i] = g[opp(i)] + (R)(6.0 * wt(i)) * phib * ((R)ex(i) * ux + (R)ey(i) * uy);
+    R rest = R(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) rest += g[i];
+    const R g0_old = g[0];
+    g[0] = dphi - rest;
+    double in = 0.0;
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+      if ((W.umask >> i) & 1) {
+        pl[(size_t)i * S + nb_m[i]] = g[i];
+        if (FINAL) in += wt(i) * (double)delta + (double)g[i];
+      }
+    pl[k] = g[0];
+    if (FINAL) {
+      wio[l] = in + ((double)g[0] - (double)g0_old);
+      wio[3 + l] = out;
+    }
+  }
+  if (FINAL) {
+    double* r = rec + (size_t)t * kWallRec;
+    r[0] = fdx;
+    r[1] = fdy;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) r[2 + j] = wio[j];
+  }
+}
+
+template <typename R>
+int launch_wall_t(const InstDev* d_insts, const WallDev* d_walls, double* d_rec, int n,
+                  int parity, int flags, cudaStream_t st) {
+  if (n <= 0) return 0;
+  const int grid = (n + kWallThreads - 1) / kWallThreads;
+  if (flags & kFinal)
+    wall_kernel<R, true><<<grid, kWallThreads, 0, st>>>(d_insts, d_walls, n, parity, d_rec);
+  else
+    wall_kernel<R, false><<<grid, kWallThreads, 0, st>>>(d_insts, d_walls, n, parity, d_rec);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+int launch_wall(int prec, const InstDev* d_insts, const WallDev* d_walls, double* d_rec, int n,
+                int parity, int flags, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == 0) return launch_wall_t<double>(d_insts, d_walls, d_rec, n, parity, flags, st);
+  return launch_wall_t<float>(d_insts, d_walls, d_rec, n, parity, flags, st);
+}
+
+}  // namespace lbve

@@ -25,13 +25,13 @@ LBVE_ERR_WORKSPACE = -6
 LBVE_ERR_STATE = -7
 LBVE_FP64 = 0
 LBVE_FP32_DEV = 1
-LBVE_NTOTALS = 12
+LBVE_NTOTALS = 14
 
 EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_step",
             "lbve_status", "lbve_fields", "lbve_totals", "lbve_residual", "lbve_time",
             "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc",
             "lbve_adjoint_workspace_bytes", "lbve_adjoint_step", "lbve_state_bytes", "lbve_save",
-            "lbve_load", "lbve_autotune"]
+            "lbve_load", "lbve_autotune", "lbve_set_wall_distances"]
 
 
 class lbve_params(ctypes.Structure):
@@ -40,7 +40,7 @@ class lbve_params(ctypes.Structure):
                 ("Re", ctypes.c_double), ("Sc", ctypes.c_double), ("Ma", ctypes.c_double),
                 ("Lc", ctypes.c_double), ("Lambda_s", ctypes.c_double),
                 ("Lambda_p", ctypes.c_double), ("Fx", ctypes.c_double), ("Fy", ctypes.c_double),
-                ("tile_tx", ctypes.c_int32)]
+                ("tile_tx", ctypes.c_int32), ("max_wall_nodes", ctypes.c_int32)]
 
 
 class LbveError(RuntimeError):
@@ -86,6 +86,9 @@ def load() -> ctypes.CDLL:
         L.lbve_load.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.lbve_autotune.argtypes = [P, ctypes.c_int32, _vp, ctypes.c_size_t, _vp, ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]
+        L.lbve_set_wall_distances.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int32), _dp]
         L.lbve_destroy.argtypes = [_vp]
         L.lbve_destroy.restype = None
         L.lbve_error_string.argtypes = [ctypes.c_int]
@@ -147,6 +150,19 @@ def lbve_set_geometry(h, inst: int, solid_mask=None, body_force=None, init_field
     bf, bf_ptr = _f64(body_force, 2 * n_nodes) if body_force is not None else (None, None)
     ini, ini_ptr = _f64(init_fields, 6 * n_nodes) if init_fields is not None else (None, None)
     _check(load().lbve_set_geometry(h, inst, mask_ptr, bf_ptr, ini_ptr), "lbve_set_geometry")
+
+
+def lbve_set_wall_distances(h, inst: int, node, direction, q) -> None:
+    """Wall fractions q of wall links (node = y nx + x, direction 1..8)."""
+    node = np.ascontiguousarray(node, dtype=np.int32)
+    direction = np.ascontiguousarray(direction, dtype=np.int32)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if not (node.size == direction.size == q.size):
+        raise ValueError("node, direction and q must have the same length")
+    ip = ctypes.POINTER(ctypes.c_int32)
+    _check(load().lbve_set_wall_distances(h, inst, int(node.size), node.ctypes.data_as(ip),
+                                          direction.ctypes.data_as(ip), q.ctypes.data_as(_dp)),
+           "lbve_set_wall_distances")
 
 
 def lbve_step(h, n_steps: int) -> None:
@@ -240,10 +256,14 @@ def lbve_destroy(h) -> None:
 # ---- convenience wrapper ----------------------------------------------------
 
 def params_from(inst, precision: int = LBVE_FP64, tile_tx: int = 0) -> lbve_params:
-    """lbve_params of a :class:`workloads.Instance`."""
+    """lbve_params of a :class:`workloads.Instance` (room for its mask's wall
+    nodes when it has a solid mask)."""
+    walls = 0
+    if getattr(inst, "solid", None) is not None:
+        walls = len({k for k, _, _ in inst.wall_links()})
     return lbve_params(inst.nx, inst.ny, 1 if inst.periodic_y else 0, precision, inst.beta,
                        inst.Wi, inst.Re, inst.Sc, inst.Ma, inst.Lc, inst.Lambda_s, inst.Lambda_p,
-                       inst.Fx, inst.Fy, tile_tx)
+                       inst.Fx, inst.Fy, tile_tx, walls)
 
 
 class Simulation:
@@ -281,7 +301,12 @@ class Simulation:
                              self.stream.cuda_stream)
         for i, inst in enumerate(self.instances):
             ini = None if init_fields is None else init_fields[i]
-            lbve_set_geometry(self.h, i, None, inst.force_field, ini, n_nodes=inst.n_nodes)
+            solid = getattr(inst, "solid", None)
+            lbve_set_geometry(self.h, i, solid, inst.force_field, ini, n_nodes=inst.n_nodes)
+            if solid is not None and getattr(inst, "wall_q", None) is not None:
+                links = inst.wall_links()
+                lbve_set_wall_distances(self.h, i, [k for k, _, _ in links],
+                                        [d for _, d, _ in links], [q for _, _, q in links])
 
     def __del__(self):
         h = getattr(self, "h", None)
