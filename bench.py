@@ -41,6 +41,7 @@ def parse_args():
     ap.add_argument("--instances", type=int, default=N_INSTANCES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=100)
+    ap.add_argument("--cylinder-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -405,6 +406,11 @@ def run_ours(args):
                            "and the reverse sweep"}
         del aws, asim
 
+    # ---- cylinder in a channel (solid mask, curved walls, drag) -----------
+    cyl = None
+    if args.cylinder_steps > 0:
+        cyl = bench_cylinder(args.cylinder_steps, stream)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -435,6 +441,8 @@ def run_ours(args):
     }
     if adj is not None:
         line["adjoint"] = adj
+    if cyl is not None:
+        line["cylinder"] = cyl
     if world == 1 and not args.no_cpu_baseline:
         sample, nodes = cpu_sample(insts, 50000)
         steps_cpu = 200
@@ -446,6 +454,54 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_cylinder(steps: int, stream) -> dict:
+    """The cylinder-in-channel geometry of Sec. 4.3 at R = 64 (30R x 4R,
+    blockage 1/2, curved wall fractions), body-force driven and periodic in
+    x: MLUPS of the masked path in FP32 and FP64, the same grid without the
+    cylinder for the mask's overhead, and the drag coefficient
+    C_d = F_x / (rho U_avg^2 R) with U_avg the mean u_x over column x = 0, at the
+    end of the timed start-up run (not a steady value)."""
+    import torch
+    from paper_2508_16997_gb300 import lbve, workloads as wl
+    inst = wl.cylinder_channel(64, Wi=0.5)
+    empty = wl.channel(inst.ny - 1, nx=inst.nx, beta=inst.beta, Wi=inst.Wi, Re=inst.Re,
+                       Sc=inst.Sc, Ma=inst.Ma)
+    fluid = int((inst.solid == 0).sum())
+    out = {"workload": f"cylinder R=64 in a {inst.nx}x{inst.ny} channel, beta {inst.beta}, "
+                       f"Wi {inst.Wi}, Re {inst.Re}, Ma {inst.Ma}, curved walls "
+                       f"({len(inst.wall_links())} wall links)",
+           "fluid_nodes": fluid, "steps": steps}
+
+    def timed(sim, n):
+        sim.step(20)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    for prec, name, n in ((lbve.LBVE_FP32_DEV, "fp32", steps), (lbve.LBVE_FP64, "fp64",
+                                                                max(1, steps // 10))):
+        sim = lbve.Simulation([inst], precision=prec)
+        ms = timed(sim, n)
+        ref = lbve.Simulation([empty], precision=prec)
+        ms_empty = timed(ref, n)
+        tot = sim.totals(0)
+        f = sim.fields(0)
+        u_avg = float(f[1][:, 0].mean())
+        out[name] = {"MLUPS": fluid / ms / 1e3, "ms_per_step": ms,
+                     "ms_per_step_without_cylinder": ms_empty,
+                     "mask_overhead": ms / ms_empty - 1.0,
+                     "drag_x": float(tot[12]),
+                     "Cd_start_up": float(tot[12]) / (u_avg * u_avg * 64.0) if u_avg > 0 else None,
+                     "time_steps": int(sim.time(0))}
+        del sim, ref
+    return out
 
 
 def main():

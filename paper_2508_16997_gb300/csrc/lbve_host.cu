@@ -242,6 +242,10 @@ struct lbve_handle {
   // CUDA graph of kGraphSteps non-final steps starting at parity 0, captured
   // on a private stream on first use and replayed on the caller's stream
   cudaStream_t cap_stream = nullptr;
+  // masked tiles run on a forked stream beside the plain ones (disjoint
+  // nodes, shared read-only source), joined before the step ends
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
 };
@@ -251,23 +255,37 @@ namespace {
 constexpr int kGraphSteps = 32;  // even, so a replay leaves the parity unchanged
 
 // Launch one time step of every tile list on stream st with the given parity.
+// With masks the step forks: the side stream runs the wall pass (which
+// completes the populations that wall nodes pull from solid nodes) and then
+// the masked tiles, while the plain tiles, which never read what the wall
+// pass writes, run on the caller's stream; the two join before the step ends.
 int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
-  // wall pass first: it completes the populations the step pulls from solid nodes
-  for (int l = 0; l < kLists; ++l)
-    if (h->nmasked_inst[l] > 0 &&
-        launch_wall(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_walls[l], h->d_wrec[l],
-                    h->plan.wall_cap[l], parity, flags, st))
-      return cuda_fail(cudaGetLastError(), "wall pass launch");
+  const bool fork = h->nmasked_inst[0] + h->nmasked_inst[1] > 0;
+  if (fork) {
+    cudaError_t e = cudaEventRecord(h->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "fork of the masked-tile stream");
+    for (int l = 0; l < kLists; ++l)
+      if (h->nmasked_inst[l] > 0 &&
+          launch_wall(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_walls[l],
+                      h->d_wrec[l], h->plan.wall_cap[l], parity, flags, h->side_stream))
+        return cuda_fail(cudaGetLastError(), "wall pass launch");
+  }
   for (int l = 0; l < kLists; ++l) {
     const int prec = l == 0 ? LBVE_FP64 : LBVE_FP32_DEV;
+    if (h->nmasked[l] > 0 &&
+        launch_step(prec, h->d_insts, h->d_mtiles[l], h->nmasked[l], parity, kModeStep, flags,
+                    h->d_partials, h->side_stream, 1))
+      return cuda_fail(cudaGetLastError(), "masked step kernel launch");
     if (h->plan.ntiles[l] > 0 &&
         launch_step(prec, h->d_insts, h->d_tiles[l], h->plan.ntiles[l], parity, kModeStep, flags,
                     h->d_partials, st))
       return cuda_fail(cudaGetLastError(), "step kernel launch");
-    if (h->nmasked[l] > 0 &&
-        launch_step(prec, h->d_insts, h->d_mtiles[l], h->nmasked[l], parity, kModeStep, flags,
-                    h->d_partials, st, 1))
-      return cuda_fail(cudaGetLastError(), "masked step kernel launch");
+  }
+  if (fork) {
+    cudaError_t e = cudaEventRecord(h->ev_join, h->side_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_join, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "join of the masked-tile stream");
   }
   return LBVE_OK;
 }
@@ -370,6 +388,12 @@ int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
     if (nsolid == 0) m.clear();  // an empty mask is no mask
   }
   if (m.empty() && !had) return LBVE_OK;  // no mask before or after: nothing to change
+  if (!m.empty() && !h->side_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "masked-tile stream creation");
+  }
   auto solid_at = [&](int x, int y) -> bool {
     if (m.empty()) return false;
     x = ((x % nx) + nx) % nx;
@@ -417,17 +441,22 @@ int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
         walls.push_back(W);
       }
   }
-  // flag the tiles holding a solid node or a node with a solid axis neighbour
+  // Flag every tile whose halo region (all TX x TY slots -- a ragged tile
+  // fills the slots past the edge with the wrapped nodes -- one column left
+  // and right, hy rows above and below), grown by one node, holds a solid
+  // node: then no plain tile pulls from a slot the wall pass writes (solid
+  // nodes' slots, wall nodes' rest slots), so plain tiles need not wait for
+  // the wall pass.
   std::vector<TileDev>& T = h->tiles_h[l];
   std::vector<TileDev> mt;
   for (int j = q.tile_begin; j < q.tile_begin + q.ntiles; ++j) {
     TileDev& t = T[j];
     t.masked = 0;
-    for (int y = t.y0; y < std::min(t.y0 + q.TY, ny) && !t.masked && !m.empty(); ++y)
-      for (int x = t.x0; x < std::min(t.x0 + q.TX, nx) && !t.masked; ++x)
-        if (solid_at(x, y) || solid_at(x + 1, y) || solid_at(x - 1, y) || solid_at(x, y + 1) ||
-            solid_at(x, y - 1))
-          t.masked = 1;
+    const int xa = t.x0 - 2, xb = t.x0 + q.TX + 1;
+    const int ya = t.y0 - q.hy - 1, yb = t.y0 + q.TY + q.hy;
+    for (int y = ya; y <= yb && !t.masked && !m.empty(); ++y)
+      for (int x = xa; x <= xb && !t.masked; ++x)
+        if (solid_at(x, y)) t.masked = 1;
     if (t.masked) mt.push_back(t);
   }
   h->mtiles_of[i] = std::move(mt);
@@ -952,6 +981,10 @@ void lbve_destroy(lbve_handle* h) {
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) cudaStreamSynchronize(h->side_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 

@@ -72,38 +72,53 @@ __global__ void __launch_bounds__(kWallThreads)
   const R Fx = D.force_field ? ((const R*)D.force)[k] : coef<R>(D, kCoefFx);
   const R Fy = D.force_field ? ((const R*)D.force)[S + k] : coef<R>(D, kCoefFy);
 
-  // ---- hydrodynamic lattice: interpolated bounce-back -----------------------
-  R d[9];
-  double fdx = 0.0, fdy = 0.0;
+  // ---- every operand first: the loads issue together, before any store ----
+  const R* __restrict__ ps = p;
+  R d[9], a2[9];  // hydro: pulled population, or (wall link) own post toward the wall
+                  // and the second interpolation operand
+  R g[3][9];      // conformation: pulled population, or (wall link) own post
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
+    a2[i] = R(0);
     if (i != 0 && ((W.umask >> i) & 1)) {
       const int ib = opp(i);
-      const double q = W.q[i - 1];
-      const R fb = p[(size_t)ib * S + k];  // own post-collision toward the wall
-      R v;
-      if (q < 0.5) {
-        if ((W.fmask >> i) & 1) {
-          const R ff = p[(size_t)ib * S + nb_p[i]];
-          v = (R)(2.0 * q) * fb + (R)(1.0 - 2.0 * q) * ff;
-        } else {
-          v = fb;  // no second fluid node: half-way bounce-back
-        }
-      } else {
-        const R fo = p[(size_t)i * S + k];
-        const double a = 1.0 / (2.0 * q);
-        v = (R)a * fb + (R)(1.0 - a) * fo;
-      }
-      p[(size_t)i * S + nb_m[i]] = v;
-      d[i] = v;
-      if (FINAL) {
-        // eq_F_x: e_ib (f^dagger_ib + f_i) over the links to the wall
-        const double s = 2.0 * wt(i) + (double)fb + (double)v;
-        fdx -= ex(i) * s;
-        fdy -= ey(i) * s;
-      }
+      d[i] = ps[(size_t)ib * S + k];
+      if (W.q[i - 1] < 0.5)
+        a2[i] = ((W.fmask >> i) & 1) ? ps[(size_t)ib * S + nb_p[i]] : d[i];
+      else
+        a2[i] = ps[(size_t)i * S + k];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) g[l][i] = ps[(size_t)(9 + 9 * l + ib) * S + k];
     } else {
-      d[i] = p[(size_t)i * S + nb_m[i]];
+      d[i] = ps[(size_t)i * S + nb_m[i]];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) g[l][i] = ps[(size_t)(9 + 9 * l + i) * S + nb_m[i]];
+    }
+  }
+
+  // ---- hydrodynamic lattice: interpolated bounce-back -----------------------
+  double fdx = 0.0, fdy = 0.0;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if (!((W.umask >> i) & 1)) continue;
+    const double q = W.q[i - 1];
+    const R fb = d[i];  // own post-collision toward the wall
+    R v;
+    if (q < 0.5) {
+      // second operand: the next fluid node's post toward the wall (half-way
+      // bounce-back, a2 = fb, where there is none)
+      v = (R)(2.0 * q) * fb + (R)(1.0 - 2.0 * q) * a2[i];
+    } else {
+      const double a = 1.0 / (2.0 * q);
+      v = (R)a * fb + (R)(1.0 - a) * a2[i];
+    }
+    p[(size_t)i * S + nb_m[i]] = v;
+    d[i] = v;
+    if (FINAL) {
+      // eq_F_x: e_ib (f^dagger_ib + f_i) over the links to the wall
+      const double sum = 2.0 * wt(i) + (double)fb + (double)v;
+      fdx -= ex(i) * sum;
+      fdy -= ey(i) * sum;
     }
   }
   HydroM<R> hm;
@@ -119,41 +134,36 @@ __global__ void __launch_bounds__(kWallThreads)
   for (int l = 0; l < 3; ++l) {
     R* __restrict__ pl = p + (size_t)(9 + 9 * l) * S;
     const R delta = (l == 1) ? R(0) : R(1);
-    R g[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    // phi_b = known pulled populations + own posts toward the wall
     R dphi = R(0);
     double out = 0.0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      if (i != 0 && ((W.umask >> i) & 1)) {
-        const R post = pl[(size_t)opp(i) * S + k];  // sent toward the wall
-        dphi += post;
-        if (FINAL) out += wt(i) * (double)delta + (double)post;
-      } else {
-        g[i] = pl[(size_t)i * S + nb_m[i]];
-        dphi += g[i];
-      }
+      dphi += g[l][i];
+      if (FINAL && i != 0 && ((W.umask >> i) & 1)) out += wt(i) * (double)delta + (double)g[l][i];
     }
     const R phib = delta + dphi;
-    // g_i = g_ibar + g^eq_i - g^eq_ibar = g_ibar + 6 w_i phi_b (e_i . u_b)
+    // g_i = g_ibar + g^eq_i - g^eq_ibar = g_ibar + 6 w_i phi_b (e_i . u_b); the
+    // opposite of a wall link is never one
 #pragma unroll
     for (int i = 1; i < 9; ++i)
       if ((W.umask >> i) & 1)
-        g[i] = g[opp(i)] + (R)(6.0 * wt(i)) * phib * ((R)ex(i) * ux + (R)ey(i) * uy);
+        g[l][i] = g[l][opp(i)] + (R)(6.0 * wt(i)) * phib * ((R)ex(i) * ux + (R)ey(i) * uy);
     R rest = R(0);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) rest += g[i];
-    const R g0_old = g[0];
-    g[0] = dphi - rest;
+    for (int i = 1; i < 9; ++i) rest += g[l][i];
+    const R g0_old = g[l][0];
+    const R g0 = dphi - rest;
     double in = 0.0;
 #pragma unroll
     for (int i = 1; i < 9; ++i)
       if ((W.umask >> i) & 1) {
-        pl[(size_t)i * S + nb_m[i]] = g[i];
-        if (FINAL) in += wt(i) * (double)delta + (double)g[i];
+        pl[(size_t)i * S + nb_m[i]] = g[l][i];
+        if (FINAL) in += wt(i) * (double)delta + (double)g[l][i];
       }
-    pl[k] = g[0];
+    pl[k] = g0;
     if (FINAL) {
-      wio[l] = in + ((double)g[0] - (double)g0_old);
+      wio[l] = in + ((double)g0 - (double)g0_old);
       wio[3 + l] = out;
     }
   }
