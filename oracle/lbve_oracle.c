@@ -42,12 +42,27 @@
  *      bounce-back) and the momentum-exchange force on the solid (eq_F_x)
  *   8. CNEBB completion of each CDE lattice (Sec. 3.3) on the flat walls and
  *      at the solid-mask boundary nodes
+ *  8b. open channels (inlet column x = 0, outlet column x = nx-1; Sec. 4.3):
+ *      every population of all four lattices at the two columns by
+ *      non-equilibrium extrapolation from the neighbouring column x_f, after
+ *      7-8 completed it: inlet f = f^eq(rho_f, u_in) + f(x_f) - f^eq(rho_f,
+ *      u_f), g = g^eq(A_in, u_in) + g(x_f) - g^eq(phi_f, u_f); outlet f =
+ *      f^eq(1, u_f) + f(x_f) - f^eq(rho_f, u_f) (pressure rho_0 = 1,
+ *      zero-gradient velocity) and g = g(x_f) (zero gradient).  Reading:
+ *      the paper names NEBB for the hydro inlet/outlet and NEQE for the
+ *      conformation lattices without formulas; NEBB's per-row knowns do not
+ *      exist at the corner nodes, so both lattices use the extrapolation, and
+ *      the outlet fixes the pressure (a velocity inlet with an outlet that
+ *      also extrapolates the density leaves the pressure level free)
  *   9. history <- S(t), u(t)
  *
  * Domain: nx x ny nodes, row-major [y][x], periodic in x.  In y either
  * periodic, or wet-node walls on rows y = 0 and y = ny-1 (solid beyond).
  * Optionally a solid mask (orc_set_mask): solid nodes take no part in the
  * update and report zero fields; gradients next to them are one-sided.
+ * Optionally open in x (orc_params.open_x): an inlet column x = 0 with the
+ * profile of orc_set_inlet and a zero-gradient outlet column x = nx-1;
+ * gradients along x are one-sided on those columns.
  *
  * Parity status: every function here is pinned by tests under tests/
  * (closed forms, invariants, special cases); see the per-function comments.
@@ -101,7 +116,7 @@ static void build_tables(void) {
 typedef struct {
   int32_t nx, ny;
   int32_t periodic_y; /* 0: wet-node walls on rows 0 and ny-1          */
-  int32_t reserved;
+  int32_t open_x;     /* 1: inlet column x = 0, outlet x = nx-1 (step 8b) */
   double beta, Wi, Re, Sc, Ma; /* Sec. 2.4-2.5                          */
   double Lc;                   /* characteristic length, lattice units  */
   double Lambda_s, Lambda_p;   /* magic parameters (Secs. 3.1, 3.2)      */
@@ -382,6 +397,7 @@ typedef struct {
   uint8_t* solid; /* [n] 1 = solid node, or NULL (no mask)                 */
   double* qlink;  /* [Q][n] wall distance fraction of link (x, i), i unknown */
   double drag[2]; /* momentum-exchange force on the solid mask, last step   */
+  double* inlet;  /* [5][ny] u_x, u_y, A_xx, A_xy, A_yy of the inlet (open_x) */
 } orc_sim;
 
 static inline int wrap(int a, int n) { return ((a % n) + n) % n; }
@@ -435,16 +451,21 @@ static void compute_moments(orc_sim* s) {
  * at fluid node (x,y) (reading of the paper, which does not state how these
  * gradients are discretised):
  *   - central, (q(+1) - q(-1))/2, in the interior and across periodic wraps;
- *   - one-sided (-3 q0 + 4 q1 - q2)/2 on a wall row, toward the interior;
+ *   - one-sided (-3 q0 + 4 q1 - q2)/2 on a wall row (and along x on the
+ *     inlet and outlet columns), toward the interior;
  *   - next to a solid-mask node on one side: the one-sided second-order
  *     difference toward the fluid side when two fluid nodes lie there, else
  *     the first-order difference with the one fluid neighbour;
  *   - zero when both neighbours along the axis are solid. */
 static double fd(const orc_sim* s, const double* q, int x, int y, int dir) {
-  const int ny = s->ny, dx = dir == 0, dy = dir == 1;
+  const int nx = s->nx, ny = s->ny, dx = dir == 0, dy = dir == 1;
   if (dir == 1 && !s->p.periodic_y && (y == 0 || y == ny - 1)) {
     const int t = y == 0 ? 1 : -1; /* toward the interior */
     return 0.5 * t * (-3.0 * at(s, q, x, y) + 4.0 * at(s, q, x, y + t) - at(s, q, x, y + 2 * t));
+  }
+  if (dir == 0 && s->p.open_x && (x == 0 || x == nx - 1)) {
+    const int t = x == 0 ? 1 : -1; /* toward the interior */
+    return 0.5 * t * (-3.0 * at(s, q, x, y) + 4.0 * at(s, q, x + t, y) - at(s, q, x + 2 * t, y));
   }
   const int sp = is_solid(s, x + dx, y + dy), sm = is_solid(s, x - dx, y - dy);
   if (!sp && !sm) return 0.5 * (at(s, q, x + dx, y + dy) - at(s, q, x - dx, y - dy));
@@ -506,7 +527,7 @@ static void free_sim(orc_sim* s) {
   if (!s) return;
   free(s->f); free(s->g); free(s->fpost); free(s->gpost); free(s->Sold);
   free(s->uold); free(s->F); free(s->mom); free(s->grad); free(s->S);
-  free(s->solid); free(s->qlink);
+  free(s->solid); free(s->qlink); free(s->inlet);
   free(s);
 }
 
@@ -518,6 +539,7 @@ static void free_sim(orc_sim* s) {
 orc_sim* orc_create(const orc_params* p, const double* force, const double* init) {
   build_tables();
   if (p->nx < 1 || p->ny < 1 || (!p->periodic_y && p->ny < 3)) return NULL;
+  if (p->open_x != 0 && (p->open_x != 1 || p->nx < 5)) return NULL;
   orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
   s->p = *p;
   orc_derive(p, &s->c);
@@ -535,11 +557,13 @@ orc_sim* orc_create(const orc_params* p, const double* force, const double* init
   s->mom = (double*)calloc((size_t)6 * n, sizeof(double));
   s->grad = (double*)calloc((size_t)6 * n, sizeof(double));
   s->S = (double*)calloc((size_t)NC * n, sizeof(double));
+  s->inlet = (double*)calloc((size_t)5 * p->ny, sizeof(double));
   if (!s->f || !s->g || !s->fpost || !s->gpost || !s->Sold || !s->uold || !s->F || !s->mom ||
-      !s->grad || !s->S) {
+      !s->grad || !s->S || !s->inlet) {
     free_sim(s);
     return NULL;
   }
+  for (int y = 0; y < p->ny; ++y) s->inlet[2 * p->ny + y] = s->inlet[4 * p->ny + y] = 1.0;
   for (int k = 0; k < n; ++k) {
     s->F[k] = force ? force[k] : p->Fx;
     s->F[n + k] = force ? force[n + k] : p->Fy;
@@ -607,7 +631,9 @@ void orc_step(orc_sim* s, int64_t n_steps) {
           int yd = y + EY[i];
           if (s->p.periodic_y) yd = wrap(yd, ny);
           else if (yd < 0 || yd >= ny) continue; /* leaves toward the wall */
-          const int kd = yd * nx + wrap(x + EX[i], nx);
+          const int xd = x + EX[i];
+          if (s->p.open_x && (xd < 0 || xd >= nx)) continue; /* leaves the open channel */
+          const int kd = yd * nx + wrap(xd, nx);
           if (s->solid && s->solid[kd]) continue; /* leaves toward the mask */
           s->f[i * n + kd] = s->fpost[i * n + k];
           for (int c = 0; c < NC; ++c) s->g[(c * Q + i) * n + kd] = s->gpost[(c * Q + i) * n + k];
@@ -623,7 +649,9 @@ void orc_step(orc_sim* s, int64_t n_steps) {
           const int ys = y - EY[i]; /* source row of direction i */
           known[i] = (ys >= 0 && ys < ny);
         }
-        for (int x = 0; x < nx; ++x) {
+        /* the open columns' corner nodes are completed by 8b instead */
+        const int xa = s->p.open_x ? 1 : 0, xb = s->p.open_x ? nx - 1 : nx;
+        for (int x = xa; x < xb; ++x) {
           const int k = y * nx + x;
           const double Fx = s->F[k], Fy = s->F[n + k];
           double fk[Q];
@@ -697,8 +725,55 @@ void orc_step(orc_sim* s, int64_t n_steps) {
           }
         }
     }
+    if (s->p.open_x) {
+      /* 8b: inlet and outlet columns from their completed neighbours */
+      for (int side = 0; side < 2; ++side) {
+        const int xb = side == 0 ? 0 : nx - 1, xf = side == 0 ? 1 : nx - 2;
+        for (int y = 0; y < ny; ++y) {
+          const int kb = y * nx + xb, kf = y * nx + xf;
+          double ff[Q], rho_f, ux_f, uy_f;
+          for (int i = 0; i < Q; ++i) ff[i] = s->f[i * n + kf];
+          orc_hydro_moments(ff, s->F[kf], s->F[n + kf], &rho_f, &ux_f, &uy_f);
+          double eqb[Q], eqf[Q];
+          if (side == 1) {
+            /* outlet: reference pressure rho_0 = 1, zero-gradient velocity;
+             * the conformation lattices copy the neighbour (zero gradient) */
+            orc_feq(1.0, ux_f, uy_f, eqb);
+            orc_feq(rho_f, ux_f, uy_f, eqf);
+            for (int i = 0; i < Q; ++i) s->f[i * n + kb] = eqb[i] + (ff[i] - eqf[i]);
+            for (int j = 0; j < NC * Q; ++j) s->g[j * n + kb] = s->g[j * n + kf];
+            continue;
+          }
+          /* inlet: prescribed velocity and conformation, density extrapolated */
+          const double ubx = s->inlet[y], uby = s->inlet[ny + y];
+          orc_feq(rho_f, ubx, uby, eqb);
+          orc_feq(rho_f, ux_f, uy_f, eqf);
+          for (int i = 0; i < Q; ++i) s->f[i * n + kb] = eqb[i] + (ff[i] - eqf[i]);
+          for (int c = 0; c < NC; ++c) {
+            double gf[Q], phi_f = 0.0;
+            for (int i = 0; i < Q; ++i) {
+              gf[i] = s->g[(c * Q + i) * n + kf];
+              phi_f += gf[i];
+            }
+            const double phib = s->inlet[(2 + c) * ny + y];
+            orc_geq(phib, ubx, uby, eqb);
+            orc_geq(phi_f, ux_f, uy_f, eqf);
+            for (int i = 0; i < Q; ++i) s->g[(c * Q + i) * n + kb] = eqb[i] + (gf[i] - eqf[i]);
+          }
+        }
+      }
+    }
     s->t += 1;
   }
+}
+
+/* Inlet profile of an open channel: in [5][ny] = u_x, u_y, A_xx, A_xy,
+ * A_yy at the inlet column (the zero velocity and A = I until set).
+ * Returns 0, or -1 if the domain is not open in x. */
+int orc_set_inlet(orc_sim* s, const double* in) {
+  if (!s->p.open_x) return -1;
+  memcpy(s->inlet, in, sizeof(double) * 5 * (size_t)s->ny);
+  return 0;
 }
 
 /* Install a solid mask before the first step.  solid: [ny][nx], nonzero =
@@ -708,7 +783,8 @@ void orc_step(orc_sim* s, int64_t n_steps) {
  * everywhere, the staircase wall).  The moments, gradients, source and
  * history of the initial state are recomputed with the mask.
  * Returns 0, or -1 if the simulation already stepped, -2 if a walled domain
- * has solid nodes on rows 0..2 or ny-3..ny-1, -3 if a fluid node has solid
+ * has solid nodes on rows 0..2 or ny-3..ny-1 (or an open channel on columns
+ * 0..2 or nx-3..nx-1), -3 if a fluid node has solid
  * neighbours on both ends of one lattice line, -4 for q outside (0, 1]. */
 int orc_set_mask(orc_sim* s, const uint8_t* solid, const double* q) {
   const int n = s->n, nx = s->nx, ny = s->ny;
@@ -731,6 +807,10 @@ int orc_set_mask(orc_sim* s, const uint8_t* solid, const double* q) {
     for (int x = 0; x < nx && !rc; ++x)
       for (int r = 0; r < 3 && !rc; ++r)
         if (m[r * nx + x] || m[(ny - 1 - r) * nx + x]) rc = -2;
+  if (s->p.open_x)
+    for (int y = 0; y < ny && !rc; ++y)
+      for (int r = 0; r < 3 && !rc; ++r)
+        if (m[y * nx + r] || m[y * nx + nx - 1 - r]) rc = -2;
   for (int y = 0; y < ny && !rc; ++y)
     for (int x = 0; x < nx && !rc; ++x) {
       const int k = y * nx + x;

@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
 
 class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
-                ("periodic_y", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("periodic_y", ctypes.c_int32), ("open_x", ctypes.c_int32),
                 ("beta", ctypes.c_double), ("Wi", ctypes.c_double), ("Re", ctypes.c_double),
                 ("Sc", ctypes.c_double), ("Ma", ctypes.c_double), ("Lc", ctypes.c_double),
                 ("Lambda_s", ctypes.c_double), ("Lambda_p", ctypes.c_double),
@@ -70,6 +70,8 @@ def lib():
         L.orc_get_state.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.orc_set_state.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.orc_get_coeffs.argtypes = [ctypes.c_void_p, ctypes.POINTER(Coeffs)]
+        L.orc_set_inlet.restype = ctypes.c_int
+        L.orc_set_inlet.argtypes = [ctypes.c_void_p, _dp]
         L.orc_set_mask.restype = ctypes.c_int
         L.orc_set_mask.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8), _dp]
         L.orc_time.restype = ctypes.c_int64
@@ -94,10 +96,10 @@ def _ptr(a: np.ndarray):
 
 
 def make_params(nx, ny, periodic_y=True, beta=0.5, Wi=1.0, Re=1.0, Sc=1e5, Ma=0.1, Lc=None,
-                Lambda_s=0.25, Lambda_p=1e-6, Fx=0.0, Fy=0.0) -> Params:
+                Lambda_s=0.25, Lambda_p=1e-6, Fx=0.0, Fy=0.0, open_x=False) -> Params:
     if Lc is None:
         Lc = float(ny - 1) if not periodic_y else float(nx) / (2 * np.pi)
-    return Params(nx, ny, 1 if periodic_y else 0, 0, beta, Wi, Re, Sc, Ma, Lc, Lambda_s,
+    return Params(nx, ny, 1 if periodic_y else 0, 1 if open_x else 0, beta, Wi, Re, Sc, Ma, Lc, Lambda_s,
                   Lambda_p, Fx, Fy)
 
 
@@ -150,6 +152,12 @@ class Sim:
         out = np.empty(14)
         lib().orc_totals(self._h, _ptr(out))
         return out
+
+    def set_inlet(self, inlet: np.ndarray) -> None:
+        """Inlet profile [5][ny] = u_x, u_y, A_xx, A_xy, A_yy (open channels)."""
+        a = np.ascontiguousarray(inlet, np.float64).reshape(5, self.ny)
+        if lib().orc_set_inlet(self._h, _ptr(a)) != 0:
+            raise ValueError("the domain is not open in x")
 
     def set_mask(self, solid: np.ndarray, q: np.ndarray | None = None) -> None:
         """Solid mask [ny][nx] (nonzero = solid) and optional link fractions

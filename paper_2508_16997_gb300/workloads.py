@@ -58,6 +58,8 @@ class Instance:
     seed: int = 0
     solid: np.ndarray | None = field(default=None, repr=False)   # (ny, nx) uint8, 1 = solid
     wall_q: np.ndarray | None = field(default=None, repr=False)  # (9, ny, nx) link fractions
+    open_x: bool = False     # inlet column x = 0, outlet column x = nx - 1
+    inlet: np.ndarray | None = field(default=None, repr=False)   # (5, ny) ux, uy, Axx, Axy, Ayy
 
     @property
     def n_nodes(self) -> int:
@@ -65,7 +67,7 @@ class Instance:
 
     def scalars(self) -> dict:
         d = asdict(self)
-        for k in ("force_field", "solid", "wall_q"):
+        for k in ("force_field", "solid", "wall_q", "inlet"):
             d.pop(k)
         return d
 
@@ -207,15 +209,33 @@ def _circle_links(solid: np.ndarray, cx: float, cy: float, R: float, periodic_y:
     return q
 
 
+def poiseuille_inlet(H: int, Umax: float, lam: float) -> np.ndarray:
+    """Fully developed Oldroyd-B channel profile on rows y = 0..H (walls at 0
+    and H): u_x = 4 Umax y (H - y) / H^2, u_y = 0, A_xy = lam du/dy,
+    A_xx = 1 + 2 (lam du/dy)^2, A_yy = 1 (Sec. 4.2 closed form, used as the
+    inlet profile of Sec. 4.3).  Returns (5, H + 1)."""
+    y = np.arange(H + 1, dtype=float)
+    u = 4.0 * Umax * y * (H - y) / H ** 2
+    du = 4.0 * Umax * (H - 2.0 * y) / H ** 2
+    out = np.zeros((5, H + 1))
+    out[0] = u
+    out[2] = 1.0 + 2.0 * (lam * du) ** 2
+    out[3] = lam * du
+    out[4] = 1.0
+    return out
+
+
 def cylinder_channel(R: int, L: int | None = None, H: int | None = None, beta=0.59, Wi=0.5,
                      Re=1.0, Sc=1e6, Ma=0.01, Lambda_s=0.25, Lambda_p=2.5e-7,
-                     curved: bool = True, seed: int = 0) -> Instance:
-    """Cylinder of radius R in a channel periodic in x (Sec. 4.3 geometry):
-    L x (H + 1) nodes, wet-node walls on rows 0 and H, cylinder centred at
-    (L/2, H/2), solid where (x - cx)^2 + (y - cy)^2 <= R^2, L_c = R,
-    uniform force F_x = 8 nu_0 U_max / H^2 with U_max = 1.5 U_c (the empty
-    channel's profile of the paper's inlet).  curved: exact link fractions of
-    the circle, else staircase (q = 1/2)."""
+                     curved: bool = True, open_x: bool = False, seed: int = 0) -> Instance:
+    """Cylinder of radius R in a channel (Sec. 4.3 geometry): L x (H + 1)
+    nodes, wet-node walls on rows 0 and H, cylinder centred at (L/2, H/2),
+    solid where (x - cx)^2 + (y - cy)^2 <= R^2, L_c = R, U_max = 1.5 U_c.
+    open_x: the paper's set-up -- inlet column x = 0 with the fully
+    developed profile (poiseuille_inlet, lambda = Wi R / U_c), zero-gradient
+    outlet x = L - 1, no body force.  Otherwise periodic in x and driven by
+    the uniform force F_x = 8 nu_0 U_max / H^2 of that profile.  curved:
+    exact link fractions of the circle, else staircase (q = 1/2)."""
     L = 30 * R if L is None else L
     H = 4 * R if H is None else H
     ny = H + 1
@@ -224,11 +244,15 @@ def cylinder_channel(R: int, L: int | None = None, H: int | None = None, beta=0.
     solid = (((X - cx) ** 2 + (Y - cy) ** 2) <= R * R).astype(np.uint8)
     Lc = float(R)
     nu0 = total_viscosity(Ma, Lc, Re)
-    Fx = 8.0 * nu0 * 1.5 * velocity_scale(Ma) / float(H) ** 2
+    Uc = velocity_scale(Ma)
+    Fx = 0.0 if open_x else 8.0 * nu0 * 1.5 * Uc / float(H) ** 2
     inst = Instance(L, ny, False, beta, Wi, Re, Sc, Ma, Lc, Lambda_s, Lambda_p, Fx, 0.0,
                     "cylinder", None, seed)
     inst.solid = solid
     inst.wall_q = _circle_links(solid, cx, cy, R, False) if curved else None
+    if open_x:
+        inst.open_x = True
+        inst.inlet = poiseuille_inlet(H, 1.5 * Uc, Wi * Lc / Uc)
     return inst
 
 

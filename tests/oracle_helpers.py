@@ -9,8 +9,12 @@ def oracle_params(inst, **override):
     d = dict(beta=inst.beta, Wi=inst.Wi, Re=inst.Re, Sc=inst.Sc, Ma=inst.Ma, Lc=inst.Lc,
              Lambda_s=inst.Lambda_s, Lambda_p=inst.Lambda_p, Fx=inst.Fx, Fy=inst.Fy)
     d.update(override)
-    return o.make_params(inst.nx, inst.ny, inst.periodic_y, **d)
+    return o.make_params(inst.nx, inst.ny, inst.periodic_y, open_x=getattr(inst, "open_x", False),
+                         **d)
 
 
 def oracle_sim(inst, init=None, **override):
-    return o.Sim(oracle_params(inst, **override), force=inst.force_field, init=init)
+    s = o.Sim(oracle_params(inst, **override), force=inst.force_field, init=init)
+    if getattr(inst, "open_x", False) and getattr(inst, "inlet", None) is not None:
+        s.set_inlet(inst.inlet)
+    return s

@@ -603,3 +603,155 @@ def test_mask_gradients_exact_on_linear_fields():
     np.testing.assert_allclose(S[0][check], 2 * b, rtol=0, atol=1e-15 + 2 * abs(b) / lam)
     np.testing.assert_allclose(S[2][check], -2 * b, rtol=0, atol=1e-15 + 2 * abs(b) / lam)
     assert np.all(S[:, solid == 1] == 0.0)
+
+
+# --------------------------------------------------------------------------
+# Open channel: inlet and outlet columns (Sec. 4.3 set-up)
+# --------------------------------------------------------------------------
+
+def _open_channel(H, nx, inlet, **kw):
+    inst = wl.channel(H, nx=nx, **kw)
+    inst.open_x = True
+    inst.inlet = inlet
+    return inst
+
+
+def test_open_columns_carry_inlet_profile_and_outlet_copy():
+    """Non-equilibrium extrapolation moves only the equilibrium part, so after
+    every step the inlet column has its neighbour's density and exactly the
+    prescribed u and A (rho u = sum e f^eq(rho_f, u_in) - F/2 and the
+    non-equilibrium parts carry no mass or momentum), and the zero-gradient
+    outlet column has density 1, its neighbour's velocity and its neighbour's
+    conformation -- from any state."""
+    H, nx = 12, 10
+    inst = wl.channel(H, nx=nx, Wi=2.0, Sc=1e3)
+    Uc = wl.velocity_scale(inst.Ma)
+    prof = wl.poiseuille_inlet(H, 1.3 * Uc, 40.0)
+    prof[1] = 0.2 * prof[0] * np.linspace(-1, 1, H + 1)  # a transverse inlet velocity too
+    inst = _open_channel(H, nx, prof, Wi=2.0, Sc=1e3)
+    s = oracle_sim(inst, init=wl.random_fields(nx, H + 1, seed=41))
+    for _ in range(6):
+        s.step(1)
+        F = s.fields()
+        np.testing.assert_allclose(F[0][:, 0], F[0][:, 1], rtol=1e-15, atol=0)
+        np.testing.assert_allclose(F[1][:, 0], prof[0], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(F[2][:, 0], prof[1], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(F[3:6][:, :, 0], prof[2:5], rtol=1e-14, atol=1e-14)
+        np.testing.assert_allclose(F[0][:, -1], 1.0, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(F[1:3][:, :, -1], F[1:3][:, :, -2], rtol=0, atol=1e-15)
+        np.testing.assert_array_equal(F[3:6][:, :, -1], F[3:6][:, :, -2])
+
+
+def test_open_channel_keeps_the_fully_developed_state():
+    """A channel run periodic in x to machine-precision steady state is a
+    fixed point of the open channel whose inlet carries that state's
+    profile: started from the same populations, the open channel stays on
+    it (the extrapolation, the corner nodes and the one-sided x gradients
+    at the open columns add nothing)."""
+    H = 8
+    per = oracle_sim(wl.channel(H, nx=4, Wi=1.0))
+    per.step(60000)  # the slowest mode decays over ~1100 steps: steady to 1e-16
+    F = per.fields()
+    col = F[:, :, 0]
+    prof = np.stack([col[1], col[2], col[3], col[4], col[5]])
+    nx = 11
+    inst = _open_channel(H, nx, prof, Wi=1.0)
+    init = np.repeat(col[:, :, None], nx, axis=2)
+    o = oracle_sim(inst, init=init)
+    f, g = per.state()
+    o.set_state(np.repeat(f[:, :, :1], nx, axis=2), np.repeat(g[:, :, :, :1], nx, axis=3))
+    o.step(300)
+    G = o.fields()
+    ref = np.repeat(col[:, :, None], nx, axis=2)
+    # the outlet holds rho = 1 while the periodic state's density is
+    # 1 - 1.3e-12; relative to each field's size (A_xx ~ 33 at the walls)
+    scale = np.maximum(np.abs(ref).reshape(6, -1).max(axis=1), 0.05)[:, None, None]
+    assert np.abs((G - ref) / scale).max() < 1e-11, np.abs((G - ref) / scale).max()
+
+
+def test_open_channel_pressure_driven_develops_poiseuille():
+    """Without a body force the inlet alone drives the flow.  A Newtonian
+    (beta = 1), nearly incompressible (Re 10, Ma 0.05: density varies by
+    ~0.4 %) open channel fed with a parabolic profile keeps the mass flux
+    uniform along x and the parabola's shape downstream, with the density
+    falling along x to the outlet's rho = 1 (a pressure gradient)."""
+    H, nx, Ma = 10, 24, 0.05
+    Uc = wl.velocity_scale(Ma)
+    prof = wl.poiseuille_inlet(H, Uc, 0.0)
+    inst = _open_channel(H, nx, prof, beta=1.0, Wi=1.0, Re=10.0, Ma=Ma)
+    inst.Fx = 0.0
+    s = oracle_sim(inst)
+    s.step(6000)
+    F = s.fields()
+    flux = (F[0] * F[1]).sum(axis=0)[1:-1]
+    assert np.ptp(flux) < 1e-3 * flux.mean()
+    mid = F[1][:, nx // 2]
+    assert np.abs(mid / mid.max() - prof[0] / prof[0].max()).max() < 1e-3
+    assert abs(mid.max() / prof[0].max() - 1.0) < 5e-3
+    centre = F[0][H // 2, :]
+    assert np.all(np.diff(centre[1:]) < 0) and abs(centre[-1] - 1.0) < 1e-15
+
+
+def test_open_columns_gradients_exact_on_linear_fields():
+    """Along x the open columns use one-sided second-order differences, exact
+    on a linear field: an open channel (no periodic seam) with A = I and the
+    divergence-free u = (a y' + b x', c x' - b y') has S_xy = a + c,
+    S_xx = 2b, S_yy = -2b at every node, the two open columns included."""
+    H, nx = 11, 9
+    a, b, c = 1.5e-3, -6e-4, 9e-4
+    prof = np.zeros((5, H + 1))
+    prof[2] = prof[4] = 1.0
+    inst = _open_channel(H, nx, prof, Wi=1e6)
+    Y, X = np.mgrid[0:H + 1, 0:nx].astype(float)
+    init = np.zeros((6, H + 1, nx))
+    init[0] = 1.0
+    init[1] = a * (Y - 5.0) + b * (X - 4.0)
+    init[2] = c * (X - 4.0) - b * (Y - 5.0)
+    init[3] = init[5] = 1.0
+    S = oracle_sim(inst, init=init).source()
+    np.testing.assert_allclose(S[1], a + c, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(S[0], 2 * b, rtol=0, atol=1e-15 + 1e-9 * abs(b))
+    np.testing.assert_allclose(S[2], -2 * b, rtol=0, atol=1e-15 + 1e-9 * abs(b))
+
+
+def _hermite_moments(p):
+    """Zeroth, first and second Hermite moments over the 9 directions of
+    populations p[9, ...]."""
+    m0 = p.sum(axis=0)
+    m1 = np.einsum("ia,i...->a...", H1, p)
+    m2 = np.einsum("iab,i...->ab...", H2, p)
+    return m0, m1, m2
+
+
+def test_open_inlet_extrapolates_the_non_equilibrium_moments():
+    """Non-equilibrium extrapolation: at the inlet column every lattice's
+    first and second Hermite moments differ from the neighbour column's by
+    exactly the change of the equilibrium moments (rho_f u_in instead of
+    rho_f u_f; phi_in u_in, phi_in u_in u_in instead of phi_f u_f, phi_f u_f
+    u_f), so the non-equilibrium (diffusive and viscous) fluxes carry over."""
+    H, nx = 9, 8
+    inst = wl.channel(H, nx=nx, Wi=2.0, Sc=1e3)
+    Uc = wl.velocity_scale(inst.Ma)
+    prof = wl.poiseuille_inlet(H, 1.2 * Uc, 25.0)
+    prof[1] = 0.3 * prof[0]
+    inst = _open_channel(H, nx, prof, Wi=2.0, Sc=1e3)
+    s = oracle_sim(inst, init=wl.random_fields(nx, H + 1, seed=43))
+    s.step(3)
+    f, g = s.state()
+    F = s.fields()
+    rho_f, u_f = F[0][:, 1], F[1:3][:, :, 1]
+    u_in = prof[0:2]
+    m0b, m1b, m2b = _hermite_moments(f[:, :, 0])
+    m0f, m1f, m2f = _hermite_moments(f[:, :, 1])
+    np.testing.assert_allclose(m1b - m1f, rho_f * (u_in - u_f), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(m2b - m2f, rho_f * (np.einsum("ay,by->aby", u_in, u_in)
+                                                   - np.einsum("ay,by->aby", u_f, u_f)),
+                               rtol=0, atol=1e-15)
+    for c in range(3):
+        phi_in, phi_f = prof[2 + c], F[3 + c][:, 1]
+        m0b, m1b, m2b = _hermite_moments(g[c][:, :, 0])
+        m0f, m1f, m2f = _hermite_moments(g[c][:, :, 1])
+        np.testing.assert_allclose(m1b - m1f, phi_in * u_in - phi_f * u_f, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(m2b - m2f, phi_in * np.einsum("ay,by->aby", u_in, u_in)
+                                   - phi_f * np.einsum("ay,by->aby", u_f, u_f),
+                                   rtol=0, atol=1e-14)
