@@ -98,6 +98,18 @@ typedef struct {
                          along any lattice direction) lbve_set_geometry may
                          install; 0 = no mask.  Costs nx*ny bytes plus 144
                          bytes per wall node of workspace.                 */
+  int32_t open_x;     /* 0: periodic in x.  1: open channel (Sec. 4.3 set-up):
+                         inlet column x = 0 with the profile of
+                         lbve_set_inlet() (u = 0, A = I until set), outlet
+                         column x = nx - 1 at density 1; nx >= 5.  Every
+                         population of the two columns follows from the
+                         neighbouring column by non-equilibrium
+                         extrapolation: inlet f = f^eq(rho_f, u_in) + f_f -
+                         f^eq(rho_f, u_f), g = g^eq(A_in, u_in) + g_f -
+                         g^eq(phi_f, u_f); outlet f = f^eq(1, u_f) + f_f -
+                         f^eq(rho_f, u_f), g = g_f (zero gradient).  The
+                         columns' wall-row corners take the same rule;
+                         gradients along x are one-sided there.            */
 } lbve_params;
 
 typedef struct lbve_handle lbve_handle;
@@ -152,7 +164,8 @@ int lbve_create(const lbve_params* p, int32_t n_instances, void* d_workspace, si
  *                gradients next to solid nodes are one-sided.
  *                LBVE_ERR_GEOMETRY if the instance has max_wall_nodes = 0
  *                or fewer than the mask's wall nodes, if a walled domain
- *                has solid nodes on rows 0-2 or ny-3..ny-1, if a fluid node
+ *                has solid nodes on rows 0-2 or ny-3..ny-1 (an open channel
+ *                on columns 0-2 or nx-3..nx-1), if a fluid node
  *                has solid nodes on both ends of one lattice line, or if no
  *                fluid node is left.
  *   body_force : host float64 [2][ny][nx], or NULL for the uniform (Fx, Fy).
@@ -164,6 +177,14 @@ int lbve_create(const lbve_params* p, int32_t n_instances, void* d_workspace, si
  * Errors: LBVE_ERR_ARG, LBVE_ERR_GEOMETRY, LBVE_ERR_CUDA. */
 int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
                       const double* body_force, const double* init_fields);
+
+/* Inlet profile of an open channel (open_x = 1): host float64 [5][ny] =
+ * u_x, u_y, A_xx, A_xy, A_yy on the inlet column, rows 0..ny-1 (e.g. the
+ * fully developed Oldroyd-B channel profile of Sec. 4.3).  Takes effect from
+ * the next step; synchronises the stream.
+ * Errors: LBVE_ERR_ARG (null, not finite), LBVE_ERR_GEOMETRY (not open),
+ * LBVE_ERR_CUDA. */
+int lbve_set_inlet(lbve_handle* h, int32_t inst, const double* inlet);
 
 /* Wall fractions of curved walls (Sec. 4.3): for each of the n_links links
  * (node[j] = y nx + x of a fluid node, dir[j] in 1..8 with x - e_dir a solid
@@ -246,7 +267,7 @@ int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps, 
  * (the reverse of each stage of the coupled step of Secs. 3.1-3.3: collisions,
  * source, finite-difference gradients, Zou-He and CNEBB completions, pull
  * streaming) with sqrt(n_steps) checkpointing and recomputation.
- * Instances with a solid mask are refused (LBVE_ERR_GEOMETRY).
+ * Instances with a solid mask or open in x are refused (LBVE_ERR_GEOMETRY).
  * The trajectory is the one that lbve_set_geometry(h, inst, NULL, <current
  * force of inst>, init_fields) followed by lbve_step(n_steps) produces; the
  * forward states are recomputed in the adjoint workspace (the instance's own

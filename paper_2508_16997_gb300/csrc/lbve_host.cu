@@ -83,6 +83,10 @@ int validate(const lbve_params& p, int i) {
                 i);
   if (!std::isfinite(p.Fx) || !std::isfinite(p.Fy))
     return fail(LBVE_ERR_ARG, "instance %d: body force must be finite", i);
+  if (p.open_x != 0 && p.open_x != 1)
+    return fail(LBVE_ERR_ARG, "instance %d: open_x must be 0 or 1", i);
+  if (p.open_x && p.nx < 5)
+    return fail(LBVE_ERR_ARG, "instance %d: an open channel needs nx >= 5", i);
   if (p.max_wall_nodes < 0 || int64_t(p.max_wall_nodes) > int64_t(p.nx) * p.ny)
     return fail(LBVE_ERR_ARG, "instance %d: max_wall_nodes must be in [0, nx*ny]", i);
   if (p.tile_tx != 0 && (p.tile_tx < 1 || p.tile_tx > kTileTXMax || p.tile_tx > p.nx))
@@ -99,7 +103,8 @@ int validate(const lbve_params& p, int i) {
 constexpr int kLists = 2;
 
 struct InstPlan {
-  size_t off_pop[2], off_hist, off_force, off_fields, off_mask;
+  size_t off_pop[2], off_hist, off_force, off_fields, off_mask, off_inlet, off_colbuf;
+  int col_begin;             // first open-column task of this instance in its list
   int wall_begin, wall_cap;  // wall-node records of this instance in its list
   int stride, TX, TY, hy, ntx, nty;
   int list;                  // tile list of this instance
@@ -112,8 +117,9 @@ struct Plan {
   size_t off_insts, off_tiles[kLists], off_partials, off_totals, off_flags, total;
   int ntiles[kLists], nslots;
   int cap_tiles[kLists];  // tile-table capacity: the most tiles any tile width gives
-  size_t off_mtiles[kLists], off_walls[kLists], off_wrec[kLists];
+  size_t off_mtiles[kLists], off_walls[kLists], off_wrec[kLists], off_cols[kLists];
   int wall_cap[kLists];   // wall-node records per list
+  int ncols[kLists];      // open-column tasks per list
 };
 
 int default_tile_tx(const lbve_params& p) { return p.nx >= kTileTX ? kTileTX : p.nx; }
@@ -141,7 +147,7 @@ Plan make_plan(const lbve_params* p, int n) {
   Plan pl;
   pl.inst.resize(n);
   size_t off = 0;
-  for (int l = 0; l < kLists; ++l) pl.ntiles[l] = pl.cap_tiles[l] = pl.wall_cap[l] = 0;
+  for (int l = 0; l < kLists; ++l) pl.ntiles[l] = pl.cap_tiles[l] = pl.wall_cap[l] = pl.ncols[l] = 0;
   for (int i = 0; i < n; ++i) {
     InstPlan& q = pl.inst[i];
     const size_t es = p[i].precision == LBVE_FP64 ? 8 : 4;
@@ -160,11 +166,19 @@ Plan make_plan(const lbve_params* p, int n) {
     off = align_up(off + 6 * size_t(q.stride) * 8, kAlign);
     q.off_mask = off;
     if (p[i].max_wall_nodes > 0) off = align_up(off + size_t(q.stride), kAlign);
+    q.off_inlet = q.off_colbuf = off;
+    if (p[i].open_x) {
+      off = align_up(off + sizeof(double) * 5 * p[i].ny, kAlign);
+      q.off_colbuf = off;
+      off = align_up(off + 36 * 2 * size_t(p[i].ny) * es, kAlign);
+    }
     tile_shape(p[i], q.TX, q.TY, q.hy);
     q.list = p[i].precision == LBVE_FP64 ? 0 : 1;
     q.wall_begin = pl.wall_cap[q.list];
     q.wall_cap = p[i].max_wall_nodes;
     pl.wall_cap[q.list] += q.wall_cap;
+    q.col_begin = pl.ncols[q.list];
+    if (p[i].open_x) pl.ncols[q.list] += 2 * p[i].ny;
     q.ntx = (p[i].nx + q.TX - 1) / q.TX;
     q.nty = (p[i].ny + q.TY - 1) / q.TY;
     q.tile_begin = pl.ntiles[q.list];
@@ -195,6 +209,8 @@ Plan make_plan(const lbve_params* p, int n) {
     off = align_up(off + sizeof(WallDev) * std::max(pl.wall_cap[l], 1), kAlign);
     pl.off_wrec[l] = off;
     off = align_up(off + sizeof(double) * kWallRec * std::max(pl.wall_cap[l], 1), kAlign);
+    pl.off_cols[l] = off;
+    off = align_up(off + sizeof(ColTask) * std::max(pl.ncols[l], 1), kAlign);
   }
   pl.off_partials = off;
   off = align_up(off + sizeof(double) * kPartial * std::max(pl.cap_tiles[0] + pl.cap_tiles[1], 1),
@@ -239,6 +255,9 @@ struct lbve_handle {
   std::vector<std::vector<int32_t>> wall_index; // node -> record, per masked instance
   std::vector<uint64_t> geom_hash;              // mask + wall fractions, 0 = no mask
   std::vector<std::vector<uint8_t>> mask_h;     // host copy of each mask
+  ColTask* d_cols[kLists] = {nullptr, nullptr};  // open-column tasks per list
+  int nopen_inst[kLists] = {0, 0};              // open channels per list
+  std::vector<std::vector<double>> inlet_h;     // inlet profile of each open channel
   // CUDA graph of kGraphSteps non-final steps starting at parity 0, captured
   // on a private stream on first use and replayed on the caller's stream
   cudaStream_t cap_stream = nullptr;
@@ -260,16 +279,23 @@ constexpr int kGraphSteps = 32;  // even, so a replay leaves the parity unchange
 // the masked tiles, while the plain tiles, which never read what the wall
 // pass writes, run on the caller's stream; the two join before the step ends.
 int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
-  const bool fork = h->nmasked_inst[0] + h->nmasked_inst[1] > 0;
+  const bool fork =
+      h->nmasked_inst[0] + h->nmasked_inst[1] + h->nopen_inst[0] + h->nopen_inst[1] > 0;
   if (fork) {
     cudaError_t e = cudaEventRecord(h->ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
     if (e != cudaSuccess) return cuda_fail(e, "fork of the masked-tile stream");
-    for (int l = 0; l < kLists; ++l)
+    for (int l = 0; l < kLists; ++l) {
+      const int prec = l == 0 ? LBVE_FP64 : LBVE_FP32_DEV;
       if (h->nmasked_inst[l] > 0 &&
-          launch_wall(l == 0 ? LBVE_FP64 : LBVE_FP32_DEV, h->d_insts, h->d_walls[l],
-                      h->d_wrec[l], h->plan.wall_cap[l], parity, flags, h->side_stream))
+          launch_wall(prec, h->d_insts, h->d_walls[l], h->d_wrec[l], h->plan.wall_cap[l], parity,
+                      flags, h->side_stream))
         return cuda_fail(cudaGetLastError(), "wall pass launch");
+      if (h->nopen_inst[l] > 0 &&
+          launch_column(prec, h->d_insts, h->d_cols[l], h->plan.ncols[l], parity,
+                        h->side_stream))
+        return cuda_fail(cudaGetLastError(), "column pass launch");
+    }
   }
   for (int l = 0; l < kLists; ++l) {
     const int prec = l == 0 ? LBVE_FP64 : LBVE_FP32_DEV;
@@ -366,6 +392,86 @@ cudaError_t upload_walls(lbve_handle* h, int i) {
   return e;
 }
 
+// Hash of instance i's geometry: mask, wall links and, for an open channel,
+// the inlet profile.
+void update_geometry_hash(lbve_handle* h, int i) {
+  uint64_t x = geometry_hash(h->mask_h[i], h->walls_of[i]);
+  if (h->p[i].open_x) {
+    const std::vector<double>& in = h->inlet_h[i];
+    const unsigned char* c = (const unsigned char*)in.data();
+    if (x == 0) x = 1469598103934665603ull;
+    for (size_t b = 0; b < in.size() * sizeof(double); ++b) {
+      x ^= c[b];
+      x *= 1099511628211ull;
+    }
+    x |= 1;
+  }
+  h->geom_hash[i] = x;
+}
+
+// Flag the tiles of instance i that the masked kernel must run: every tile
+// whose halo region (all TX x TY slots -- a ragged tile fills the slots past
+// the edge with the wrapped nodes -- one column left and right, hy rows above
+// and below), grown by one node, holds a solid node or a node of an open
+// column.  Then no plain tile reads a slot the wall pass writes (solid nodes'
+// slots, wall nodes' rest slots) or an open column's node, so plain tiles
+// need not wait for the wall and column passes.  Rebuilds the list's
+// masked-tile table and uploads both tables.
+int flag_tiles(lbve_handle* h, int i) {
+  const lbve_params& p = h->p[i];
+  const InstPlan& q = h->plan.inst[i];
+  const int nx = p.nx, ny = p.ny, l = q.list;
+  const bool py = p.periodic_y != 0;
+  const std::vector<uint8_t>& m = h->mask_h[i];
+  auto flagged = [&](int x, int y) -> bool {
+    const int xw = ((x % nx) + nx) % nx;
+    if (py) y = ((y % ny) + ny) % ny;
+    else if (y < 0 || y >= ny) return false;
+    if (p.open_x && (xw == 0 || xw == nx - 1)) return true;
+    return !m.empty() && m[size_t(y) * nx + xw] != 0;
+  };
+  std::vector<TileDev>& T = h->tiles_h[l];
+  std::vector<TileDev> mt;
+  const bool any = !m.empty() || p.open_x;
+  for (int j = q.tile_begin; j < q.tile_begin + q.ntiles; ++j) {
+    TileDev& t = T[j];
+    t.masked = 0;
+    const int xa = t.x0 - 2, xb = t.x0 + q.TX + 1;
+    const int ya = t.y0 - q.hy - 1, yb = t.y0 + q.TY + q.hy;
+    for (int y = ya; y <= yb && !t.masked && any; ++y)
+      for (int x = xa; x <= xb && !t.masked; ++x)
+        if (flagged(x, y)) t.masked = 1;
+    if (t.masked) mt.push_back(t);
+  }
+  h->mtiles_of[i] = std::move(mt);
+  std::vector<TileDev> table;
+  for (int j = 0; j < h->n; ++j)
+    if (h->plan.inst[j].list == l) {
+      h->mbegin[j] = (int)table.size();
+      table.insert(table.end(), h->mtiles_of[j].begin(), h->mtiles_of[j].end());
+    }
+  cudaError_t e = cudaMemcpyAsync(h->d_tiles[l] + q.tile_begin, T.data() + q.tile_begin,
+                                  sizeof(TileDev) * q.ntiles, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && !table.empty())
+    e = cudaMemcpyAsync(h->d_mtiles[l], table.data(), sizeof(TileDev) * table.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // table is pageable and local
+  if (e != cudaSuccess) return cuda_fail(e, "tile table upload");
+  h->nmasked[l] = (int)table.size();
+  drop_graph(h);
+  return LBVE_OK;
+}
+
+// Create the forked stream and its events (masks and open channels use them).
+int ensure_side_stream(lbve_handle* h) {
+  if (h->side_stream) return LBVE_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e, "side stream creation");
+  return LBVE_OK;
+}
+
 // Install (mask != null) or remove the solid mask of instance i: validate
 // it, build the wall-node records (wall fraction 1/2), flag the tiles the
 // masked kernel must run, rebuild the list's masked-tile table, upload.
@@ -388,11 +494,9 @@ int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
     if (nsolid == 0) m.clear();  // an empty mask is no mask
   }
   if (m.empty() && !had) return LBVE_OK;  // no mask before or after: nothing to change
-  if (!m.empty() && !h->side_stream) {
-    cudaError_t e = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_fail(e, "masked-tile stream creation");
+  if (!m.empty()) {
+    const int rc = ensure_side_stream(h);
+    if (rc) return rc;
   }
   auto solid_at = [&](int x, int y) -> bool {
     if (m.empty()) return false;
@@ -410,6 +514,13 @@ int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
           if (m[size_t(r) * nx + x] || m[size_t(ny - 1 - r) * nx + x])
             return fail(LBVE_ERR_GEOMETRY,
                         "instance %d: rows 0-2 and ny-3..ny-1 of a walled domain must be fluid", i);
+    if (p.open_x)
+      for (int y = 0; y < ny; ++y)
+        for (int r = 0; r < 3; ++r)
+          if (m[size_t(y) * nx + r] || m[size_t(y) * nx + nx - 1 - r])
+            return fail(LBVE_ERR_GEOMETRY,
+                        "instance %d: columns 0-2 and nx-3..nx-1 of an open channel must be fluid",
+                        i);
     index.assign(nn, -1);
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
@@ -441,49 +552,18 @@ int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
         walls.push_back(W);
       }
   }
-  // Flag every tile whose halo region (all TX x TY slots -- a ragged tile
-  // fills the slots past the edge with the wrapped nodes -- one column left
-  // and right, hy rows above and below), grown by one node, holds a solid
-  // node: then no plain tile pulls from a slot the wall pass writes (solid
-  // nodes' slots, wall nodes' rest slots), so plain tiles need not wait for
-  // the wall pass.
-  std::vector<TileDev>& T = h->tiles_h[l];
-  std::vector<TileDev> mt;
-  for (int j = q.tile_begin; j < q.tile_begin + q.ntiles; ++j) {
-    TileDev& t = T[j];
-    t.masked = 0;
-    const int xa = t.x0 - 2, xb = t.x0 + q.TX + 1;
-    const int ya = t.y0 - q.hy - 1, yb = t.y0 + q.TY + q.hy;
-    for (int y = ya; y <= yb && !t.masked && !m.empty(); ++y)
-      for (int x = xa; x <= xb && !t.masked; ++x)
-        if (solid_at(x, y)) t.masked = 1;
-    if (t.masked) mt.push_back(t);
-  }
-  h->mtiles_of[i] = std::move(mt);
-  std::vector<TileDev> table;
-  for (int j = 0; j < h->n; ++j)
-    if (h->plan.inst[j].list == l) {
-      h->mbegin[j] = (int)table.size();
-      table.insert(table.end(), h->mtiles_of[j].begin(), h->mtiles_of[j].end());
-    }
   h->walls_of[i] = std::move(walls);
   h->wall_index[i] = std::move(index);
-  cudaError_t e = cudaMemcpyAsync(h->d_tiles[l] + q.tile_begin, T.data() + q.tile_begin,
-                                  sizeof(TileDev) * q.ntiles, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess && !table.empty())
-    e = cudaMemcpyAsync(h->d_mtiles[l], table.data(), sizeof(TileDev) * table.size(),
-                        cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess && !m.empty())
+  cudaError_t e = cudaSuccess;
+  if (!m.empty())
     e = cudaMemcpyAsync(h->ws + q.off_mask, m.data(), nn, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = upload_walls(h, i);  // synchronises: the local tables may go
+  if (e == cudaSuccess) e = upload_walls(h, i);  // synchronises: m is pageable and local
   if (e != cudaSuccess) return cuda_fail(e, "mask upload");
   D.mask = m.empty() ? nullptr : (const uint8_t*)(h->ws + q.off_mask);
-  h->nmasked[l] = (int)table.size();
   h->nmasked_inst[l] += (D.mask ? 1 : 0) - (had ? 1 : 0);
-  h->geom_hash[i] = geometry_hash(m, h->walls_of[i]);
   h->mask_h[i] = std::move(m);
-  drop_graph(h);
-  return LBVE_OK;
+  update_geometry_hash(h, i);
+  return flag_tiles(h, i);
 }
 
 }  // namespace
@@ -556,6 +636,8 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
   h->wall_index.assign(n, {});
   h->geom_hash.assign(n, 0);
   h->mask_h.assign(n, {});
+  h->inlet_h.assign(n, {});
+  for (int l = 0; l < kLists; ++l) h->d_cols[l] = (ColTask*)(h->ws + pl.off_cols[l]);
   h->d_partials = (double*)(h->ws + pl.off_partials);
   h->d_totals = (double*)(h->ws + pl.off_totals);
   h->d_flags = (int32_t*)(h->ws + pl.off_flags);
@@ -589,6 +671,9 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     D.mask = nullptr;
     D.wall_rec = (double*)(h->ws + pl.off_wrec[q.list]) + size_t(q.wall_begin) * kWallRec;
     D.wall_cap = q.wall_cap;
+    D.open_x = p[i].open_x;
+    D.colbuf = p[i].open_x ? (void*)(h->ws + q.off_colbuf) : nullptr;
+    D.inlet = p[i].open_x ? (const double*)(h->ws + q.off_inlet) : nullptr;
     D.inv_Uc = 1.0 / c.Uc;
     D.cd[kCoefFx] = p[i].Fx;
     D.cd[kCoefFy] = p[i].Fy;
@@ -648,6 +733,41 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     return cuda_fail(e, "lbve_create upload");
   }
   for (int l = 0; l < kLists; ++l) h->tiles_h[l] = std::move(tiles[l]);
+  // open channels: column tasks, the default inlet (u = 0, A = I), tile flags
+  std::vector<ColTask> cols[kLists];
+  for (int l = 0; l < kLists; ++l) cols[l].resize(pl.ncols[l]);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    if (!p[i].open_x) continue;
+    const InstPlan& q = pl.inst[i];
+    for (int side = 0; side < 2; ++side)
+      for (int y = 0; y < p[i].ny; ++y)
+        cols[q.list][q.col_begin + side * p[i].ny + y] = ColTask{i, y, side, 0};
+    std::vector<double>& in = h->inlet_h[i];
+    in.assign(5 * size_t(p[i].ny), 0.0);
+    for (int y = 0; y < p[i].ny; ++y) in[2 * p[i].ny + y] = in[4 * p[i].ny + y] = 1.0;
+    e = cudaMemcpyAsync(h->ws + q.off_inlet, in.data(), sizeof(double) * in.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+    h->nopen_inst[q.list] += 1;
+  }
+  for (int l = 0; l < kLists && e == cudaSuccess; ++l)
+    if (!cols[l].empty())
+      e = cudaMemcpyAsync(h->d_cols[l], cols[l].data(), sizeof(ColTask) * cols[l].size(),
+                          cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "open-channel tables upload");
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!p[i].open_x) continue;
+    update_geometry_hash(h, i);
+    int rc2 = ensure_side_stream(h);
+    if (rc2 == LBVE_OK) rc2 = flag_tiles(h, i);
+    if (rc2) {
+      lbve_destroy(h);
+      return rc2;
+    }
+  }
   *out = h;
   return LBVE_OK;
 }
@@ -950,6 +1070,23 @@ int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes) {
   return LBVE_OK;
 }
 
+int lbve_set_inlet(lbve_handle* h, int32_t inst, const double* inlet) {
+  if (!h || inst < 0 || inst >= h->n || !inlet) return fail(LBVE_ERR_ARG, "bad handle, instance or pointer");
+  const lbve_params& p = h->p[inst];
+  if (!p.open_x) return fail(LBVE_ERR_GEOMETRY, "instance %d is not an open channel", inst);
+  const size_t cnt = 5 * size_t(p.ny);
+  for (size_t k = 0; k < cnt; ++k)
+    if (!std::isfinite(inlet[k])) return fail(LBVE_ERR_ARG, "inlet profile not finite");
+  std::vector<double>& in = h->inlet_h[inst];
+  in.assign(inlet, inlet + cnt);
+  cudaError_t e = cudaMemcpyAsync(h->ws + h->plan.inst[inst].off_inlet, in.data(),
+                                  sizeof(double) * cnt, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "inlet upload");
+  update_geometry_hash(h, inst);
+  return LBVE_OK;
+}
+
 int lbve_set_wall_distances(lbve_handle* h, int32_t inst, int32_t n_links, const int32_t* node,
                             const int32_t* dir, const double* q) {
   if (!h || inst < 0 || inst >= h->n || n_links < 0 || (n_links > 0 && (!node || !dir || !q)))
@@ -971,7 +1108,7 @@ int lbve_set_wall_distances(lbve_handle* h, int32_t inst, int32_t n_links, const
   for (int32_t j = 0; j < n_links; ++j) W[idx[node[j]]].q[dir[j] - 1] = q[j];
   const cudaError_t e = upload_walls(h, inst);
   if (e != cudaSuccess) return cuda_fail(e, "wall upload");
-  h->geom_hash[inst] = geometry_hash(h->mask_h[inst], W);
+  update_geometry_hash(h, inst);
   return LBVE_OK;
 }
 
@@ -1176,8 +1313,9 @@ extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* ini
   if (!h || inst < 0 || inst >= h->n || !d_dL_dfields || !d_dL_dforce || n_steps < 1)
     return fail(LBVE_ERR_ARG, "bad handle, instance, pointer or step count");
   if (!h->ready[inst]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", inst);
-  if (h->insts[inst].mask)
-    return fail(LBVE_ERR_GEOMETRY, "the adjoint does not cover solid masks (instance %d)", inst);
+  if (h->insts[inst].mask || h->p[inst].open_x)
+    return fail(LBVE_ERR_GEOMETRY,
+                "the adjoint covers neither solid masks nor open channels (instance %d)", inst);
   const lbve_params& p = h->p[inst];
   const InstPlan& q = h->plan.inst[inst];
   const AdjPlan a = make_adj_plan(p, q, n_steps);

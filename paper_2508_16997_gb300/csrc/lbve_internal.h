@@ -62,6 +62,10 @@ struct InstDev {
   int32_t prec, wall_cap;        // wall_cap: wall-node records of this instance
   const uint8_t* mask;           // [stride] 1 = solid node, or null (no mask)
   double* wall_rec;              // [wall_cap][kWallRec] final-step wall sums
+  int32_t open_x, pad2;          // open_x: inlet column x = 0, outlet x = nx - 1
+  void* colbuf;                  // [36][2 ny] completed populations of the two open
+                                 // columns (inlet rows, then outlet rows), deviations
+  const double* inlet;           // [5][ny] u_x, u_y, A_xx, A_xy, A_yy at the inlet
   double inv_Uc;
   // Collision coefficients, in float64 and rounded once to float32, so that
   // neither kernel converts precision per node.
@@ -87,6 +91,11 @@ struct WallDev {
 };
 constexpr int kWallRec = 8;  // drag x, drag y, wall in x3, wall out x3
 
+// One node of an open column: {instance, row, side (0 inlet, 1 outlet)}.
+struct ColTask {
+  int32_t inst, y, side, pad;
+};
+
 // Launchers implemented in lbve_kernels.cu (templated over float/double).
 enum : int { kModeStep = 0, kModeInit = 1 };
 
@@ -99,6 +108,10 @@ int launch_step(int prec, const InstDev* d_insts, const TileDev* d_tiles, int n_
 // kWallRec record per wall node to d_rec (lbve_wall.cu).
 int launch_wall(int prec, const InstDev* d_insts, const WallDev* d_walls, double* d_rec,
                 int n_walls, int parity, int flags, void* stream);
+// Column pass before a step: the completed populations of the open columns'
+// nodes (n_tasks of them) into each instance's colbuf (lbve_wall.cu).
+int launch_column(int prec, const InstDev* d_insts, const ColTask* d_tasks, int n_tasks,
+                  int parity, void* stream);
 // Adjoint pass modes: a normal step, the final fields (the loss), the initial collision.
 enum : int { kAdjStep = 0, kAdjFields = 1, kAdjInit = 2 };
 

@@ -490,6 +490,43 @@ __device__ __forceinline__ void one_sided(int t, R r0, R ux0, R uy0, R r1, R ux1
   }
 }
 
+// Open channels: nodes of the inlet (x = 0) and outlet (x = nx - 1) columns
+// take their completed populations from the column pass's colbuf during a
+// step (the pull would miss the populations entering from outside).
+__device__ __forceinline__ bool open_column(const InstDev& D, int gx) {
+  return D.open_x && (gx == 0 || gx == D.nx - 1);
+}
+template <typename R>
+__device__ __forceinline__ const R* colbuf_node(const InstDev& D, int gx, int gy) {
+  return (const R*)D.colbuf + (gx == 0 ? 0 : D.ny) + gy;  // plane stride 2 ny
+}
+
+// rho, u of region node (gx, gy) for the masked variant: open-column nodes
+// from colbuf during a step, every other node as node_rho_u.
+template <typename R, int MODE>
+__device__ __forceinline__ void region_rho_u(const InstDev& D, const void* src,
+                                             const R* __restrict__ force, bool ffield, R Fx0,
+                                             R Fy0, int S, int nx, int ny, bool py, int gx,
+                                             int gy, R& rho, R& ux, R& uy) {
+  if (MODE == kModeStep && open_column(D, gx)) {
+    const R* cb = colbuf_node<R>(D, gx, gy);
+    const int ld = 2 * ny;
+    R d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = cb[(size_t)i * ld];
+    const int k = gy * nx + gx;
+    const R Fx = ffield ? force[k] : Fx0, Fy = ffield ? force[S + k] : Fy0;
+    HydroM<R> m;
+    hydro_moments<R>(d, m);
+    rho = R(1) + m.drho;
+    const R irho = R(1) / rho;
+    ux = (m.jx + R(0.5) * Fx) * irho;
+    uy = (m.jy + R(0.5) * Fy) * irho;
+    return;
+  }
+  node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, rho, ux, uy);
+}
+
 template <typename R, int MODE, bool FINAL, bool MASKED>
 __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, const TileDev T,
                                              int parity, double* __restrict__ partials, R* s_rho,
@@ -517,10 +554,13 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   const int x = T.x0 + tx, y = T.y0 + ty;
   const bool inside = in_tile && (x < nx) && (y < ny);
   // solid-mask nodes (masked tiles only) take no part in the update
-  const bool solid = MASKED && inside && D.mask[y * nx + x] != 0;
+  const bool solid = MASKED && inside && D.mask && D.mask[y * nx + x] != 0;
   const bool active = inside && !solid;
   const int ri = (ty + hy) * RW + tx + 1;  // this slot in the halo region
   const bool wb = active && !py && y == 0, wt = active && !py && y == ny - 1;
+  // an open column's node arrives completed (colbuf): no wall completion there
+  const bool ocol = MASKED && MODE == kModeStep && active && open_column(D, x);
+  const bool wcomp = (wb || wt) && !ocol;
   const int nring = 2 * hy * RW + 2 * TY;
 
   // (1) first halo-ring node of this thread: issue its pull
@@ -531,10 +571,16 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     ring_slot(threadIdx.x, RW, TY, hy, lx, ly);
     if (region_node(lx, ly, T.x0, T.y0, hy, nx, ny, py, rgx, rgy)) {
       ring_r = ly * RW + lx;
-      int rm, rp;
-      neighbour_rows(rgy, nx, ny, py, rm, rp);
-      const int xm = rgx == 0 ? nx - 1 : rgx - 1, xp = rgx == nx - 1 ? 0 : rgx + 1;
-      PopSource<R, MODE>::hydro(src, S, nx, rgy * nx + rgx, rgy * nx, rm, rp, rgx, xm, xp, dr);
+      if (MASKED && MODE == kModeStep && open_column(D, rgx)) {
+        const R* cb = colbuf_node<R>(D, rgx, rgy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dr[i] = cb[(size_t)i * 2 * ny];
+      } else {
+        int rm, rp;
+        neighbour_rows(rgy, nx, ny, py, rm, rp);
+        const int xm = rgx == 0 ? nx - 1 : rgx - 1, xp = rgx == nx - 1 ? 0 : rgx + 1;
+        PopSource<R, MODE>::hydro(src, S, nx, rgy * nx + rgx, rgy * nx, rm, rp, rgx, xm, xp, dr);
+      }
     }
   }
 
@@ -548,20 +594,32 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     neighbour_rows(y, nx, ny, py, rm, rp);
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const int rc = y * nx;
-    PopSource<R, MODE>::hydro(src, S, nx, k, rc, rm, rp, x, xm, xp, d);
+    if (ocol) {
+      const R* cb = colbuf_node<R>(D, x, y);
+      const int ld = 2 * ny;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) d[i] = cb[(size_t)i * ld];
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[l][i] = cb[(size_t)(9 + 9 * l + i) * ld];
+    } else {
+      PopSource<R, MODE>::hydro(src, S, nx, k, rc, rm, rp, x, xm, xp, d);
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        PopSource<R, MODE>::cde(src, l, S, nx, k, rc, rm, rp, x, xm, xp, g[l]);
+    }
     if (ffield) {
       Fx = force[k];
       Fy = force[S + k];
     }
-#pragma unroll
-    for (int l = 0; l < 3; ++l) PopSource<R, MODE>::cde(src, l, S, nx, k, rc, rm, rp, x, xm, xp, g[l]);
     if (MODE == kModeStep) {
       So[0] = hist[k];
       So[1] = hist[S + k];
       So[2] = hist[2 * S + k];
       uxo = hist[3 * S + k];
       uyo = hist[4 * S + k];
-      if (wb || wt) {
+      if (wcomp) {
         // bottom wall: H = {4, 7, 8}; top wall: H = {2, 5, 6}
         const int h0 = wb ? 4 : 2, h1 = wb ? 7 : 5, h2 = wb ? 8 : 6;
 #pragma unroll
@@ -580,7 +638,9 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     const int rk = rgy * nx + rgx;
     const R rFx = ffield ? force[rk] : Fx0;
     const R rFy = ffield ? force[S + rk] : Fy0;
-    if (MODE == kModeStep && !py && (rgy == 0 || rgy == ny - 1)) zou_he<R>(dr, rFx, rFy, rgy == 0);
+    if (MODE == kModeStep && !py && (rgy == 0 || rgy == ny - 1) &&
+        !(MASKED && open_column(D, rgx)))
+      zou_he<R>(dr, rFx, rFy, rgy == 0);
     HydroM<R> m;
     hydro_moments<R>(dr, m);
     const R rho = R(1) + m.drho;
@@ -596,7 +656,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   R rho = R(1), ux = R(0), uy = R(0);
   double wall_io[6] = {0, 0, 0, 0, 0, 0};
   if (active) {
-    if (MODE == kModeStep && (wb || wt)) zou_he<R>(d, Fx, Fy, wb);
+    if (MODE == kModeStep && wcomp) zou_he<R>(d, Fx, Fy, wb);
     hydro_moments<R>(d, hm);
     rho = R(1) + hm.drho;
     const R irho_own = R(1) / rho;
@@ -607,7 +667,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     s_uy[ri] = uy;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      if (MODE == kModeStep && (wb || wt)) {
+      if (MODE == kModeStep && wcomp) {
         const R delta = (l == 1) ? R(0) : R(1);
         cnebb<R>(g[l], post[l][0], post[l][1], post[l][2], delta, ux, uy, wb, wall_io[l],
                  wall_io[3 + l]);
@@ -620,7 +680,10 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     const int gx = x % nx, gy = py ? y % ny : y;
     if (gy < ny) {
       R r, vx, vy;
-      node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
+      if constexpr (MASKED)
+        region_rho_u<R, MODE>(D, src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
+      else
+        node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
       s_rho[ri] = r;
       s_ux[ri] = vx;
       s_uy[ri] = vy;
@@ -633,7 +696,10 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     ring_slot(q, RW, TY, hy, lx, ly);
     if (!region_node(lx, ly, T.x0, T.y0, hy, nx, ny, py, gx, gy)) continue;
     R r, vx, vy;
-    node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
+    if constexpr (MASKED)
+      region_rho_u<R, MODE>(D, src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
+    else
+      node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
     const int rr = ly * RW + lx;
     s_rho[rr] = r;
     s_ux[rr] = vx;
@@ -665,19 +731,23 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     if constexpr (MASKED) {
       // one-sided differences where an axis neighbour is solid; the values
       // two nodes away come straight from the pulled populations (L2)
+      // a side is blocked by a solid node or, in an open channel, by the
+      // end of the domain beyond the inlet / outlet column
       const uint8_t* __restrict__ M = D.mask;
       const int xp = x == nx - 1 ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
-      const bool sxp = M[y * nx + xp] != 0, sxm = M[y * nx + xm] != 0;
+      const bool sxp = (D.open_x && x == nx - 1) || (M && M[y * nx + xp] != 0);
+      const bool sxm = (D.open_x && x == 0) || (M && M[y * nx + xm] != 0);
       if (sxp || sxm) {
         R gx0 = R(0), gx1 = R(0), gxc = R(0);
         if (!(sxp && sxm)) {
           const int t = sxp ? -1 : 1;
           const int i1 = t > 0 ? ri + 1 : ri - 1;
           const int x2 = (((x + 2 * t) % nx) + nx) % nx;
-          const bool has2 = M[y * nx + x2] == 0;
+          const bool has2 = !(M && M[y * nx + x2] != 0);
           R r2 = R(1), u2x = R(0), u2y = R(0);
           if (has2)
-            node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, x2, y, r2, u2x, u2y);
+            region_rho_u<R, MODE>(D, src, force, ffield, Fx0, Fy0, S, nx, ny, py, x2, y, r2,
+                                  u2x, u2y);
           one_sided<R>(t, rho, ux, uy, s_rho[i1], s_ux[i1], s_uy[i1], has2, r2, u2x, u2y, 0, gx0,
                        gx1, gxc);
         }
@@ -685,7 +755,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
         G01 = gx1;
         dPx = gxc;
       }
-      if (!wb && !wt) {
+      if (!wb && !wt && M) {
         // rows next to a flat wall carry no mask, so y +- 1 lies in the domain
         const int yp = (py && y == ny - 1) ? 0 : y + 1, ym = (py && y == 0) ? ny - 1 : y - 1;
         const bool syp = M[yp * nx + x] != 0, sym = M[ym * nx + x] != 0;
@@ -699,8 +769,8 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
             const bool has2 = y2 >= 0 && y2 < ny && M[y2 * nx + x] == 0;
             R r2 = R(1), u2x = R(0), u2y = R(0);
             if (has2)
-              node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, x, y2, r2, u2x,
-                                  u2y);
+              region_rho_u<R, MODE>(D, src, force, ffield, Fx0, Fy0, S, nx, ny, py, x, y2, r2,
+                                    u2x, u2y);
             one_sided<R>(t, rho, ux, uy, s_rho[i1], s_ux[i1], s_uy[i1], has2, r2, u2x, u2y, 1,
                          gy0, gy1, gyc);
           }

@@ -1,4 +1,5 @@
-// lbve_wall.cu -- wall pass of the solid mask (hand-written CUDA, sm_103a).
+// lbve_wall.cu -- wall pass of the solid mask and column pass of open
+// channels (hand-written CUDA, sm_103a).
 //
 // Runs before every step on the compact list of fluid nodes next to solid
 // nodes (one thread per node).  For each wall link (x_b, i), i.e. x_b - e_i
@@ -176,6 +177,95 @@ __global__ void __launch_bounds__(kWallThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Column pass of an open channel (Sec. 4.3 inlet/outlet), one thread per node
+// of the two open columns.  The node's neighbour x_f (column 1 or nx - 2) is
+// pulled and, on a wall row, completed (Zou-He, CNEBB) exactly as the step
+// does; then every population of the open-column node follows by
+// non-equilibrium extrapolation:
+//   inlet:  f = f^eq(rho_f, u_in) - f^eq(rho_f, u_f) + f(x_f),
+//           g = g^eq(A_in, u_in) - g^eq(phi_f, u_f) + g(x_f);
+//   outlet: f = f^eq(1, u_f) - f^eq(rho_f, u_f) + f(x_f), g = g(x_f).
+// The equilibrium differences are Hermite reconstructions of coefficient
+// differences.  The result goes to the instance's colbuf, which the masked
+// step reads in place of pulling these nodes; src is only read.
+template <typename R>
+__global__ void __launch_bounds__(kWallThreads)
+    column_kernel(const InstDev* __restrict__ insts, const ColTask* __restrict__ tasks, int n,
+                  int parity) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const ColTask T = tasks[t];
+  if (T.inst < 0) return;
+  const InstDev& D = insts[T.inst];
+  const int nx = D.nx, ny = D.ny, S = D.stride, y = T.y, side = T.side;
+  const bool py = D.periodic_y != 0;
+  const R* __restrict__ src = (const R*)D.pop[parity];
+  const int xf = side == 0 ? 1 : nx - 2;
+  const int rc = y * nx, k = rc + xf;
+  int rm, rp;
+  neighbour_rows(y, nx, ny, py, rm, rp);
+  const bool wb = !py && y == 0, wt = !py && y == ny - 1;
+  const R Fx = D.force_field ? ((const R*)D.force)[k] : coef<R>(D, kCoefFx);
+  const R Fy = D.force_field ? ((const R*)D.force)[S + k] : coef<R>(D, kCoefFy);
+  R d[9], g[3][9];
+  pull9<R>(src, S, rc, rm, rp, xf, xf - 1, xf + 1, d);
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+    pull9<R>(src + (size_t)(9 + 9 * l) * S, S, rc, rm, rp, xf, xf - 1, xf + 1, g[l]);
+  if (wb || wt) zou_he<R>(d, Fx, Fy, wb);
+  HydroM<R> hm;
+  hydro_moments<R>(d, hm);
+  const R rho = R(1) + hm.drho;
+  const R irho = R(1) / rho;
+  const R ux = (hm.jx + R(0.5) * Fx) * irho, uy = (hm.jy + R(0.5) * Fy) * irho;
+  if (wb || wt) {
+    // bottom wall: H = {4, 7, 8}; top wall: H = {2, 5, 6}
+    const int h0 = wb ? 4 : 2, h1 = wb ? 7 : 5, h2 = wb ? 8 : 6;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const R* own = src + (size_t)(9 + 9 * l) * S + k;
+      double win, wout;
+      cnebb<R>(g[l], own[h0 * S], own[h1 * S], own[h2 * S], (l == 1) ? R(0) : R(1), ux, uy, wb,
+               win, wout);
+    }
+  }
+  R* __restrict__ cb = (R*)D.colbuf;
+  const int c = side * ny + y, ld = 2 * ny;
+  R e[9];
+  if (side == 0) {
+    const double* in = D.inlet;
+    const R bx = (R)in[y], by = (R)in[ny + y];
+    reconstruct<R>(R(0), rho * (bx - ux), rho * (by - uy), rho * (bx * bx - ux * ux),
+                   rho * (by * by - uy * uy), rho * (bx * by - ux * uy),
+                   rho * (bx * bx * by - ux * ux * uy), rho * (bx * by * by - ux * uy * uy), e);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) cb[(size_t)i * ld + c] = d[i] + e[i];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      CdeM<R> m;
+      cde_moments<R>(g[l], m);
+      const R phif = ((l == 1) ? R(0) : R(1)) + m.dphi;
+      const R phib = (R)in[(2 + l) * ny + y];
+      reconstruct<R>(phib - phif, phib * bx - phif * ux, phib * by - phif * uy,
+                     phib * bx * bx - phif * ux * ux, phib * by * by - phif * uy * uy,
+                     phib * bx * by - phif * ux * uy, R(0), R(0), e);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) cb[(size_t)(9 + 9 * l + i) * ld + c] = g[l][i] + e[i];
+    }
+  } else {
+    const R dr = R(1) - rho;  // density rho_0 = 1 at the outlet
+    reconstruct<R>(dr, dr * ux, dr * uy, dr * ux * ux, dr * uy * uy, dr * ux * uy,
+                   dr * ux * ux * uy, dr * ux * uy * uy, e);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) cb[(size_t)i * ld + c] = d[i] + e[i];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) cb[(size_t)(9 + 9 * l + i) * ld + c] = g[l][i];
+  }
+}
+
 template <typename R>
 int launch_wall_t(const InstDev* d_insts, const WallDev* d_walls, double* d_rec, int n,
                   int parity, int flags, cudaStream_t st) {
@@ -189,6 +279,18 @@ int launch_wall_t(const InstDev* d_insts, const WallDev* d_walls, double* d_rec,
 }
 
 }  // namespace
+
+int launch_column(int prec, const InstDev* d_insts, const ColTask* d_tasks, int n, int parity,
+                  void* stream) {
+  if (n <= 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int grid = (n + kWallThreads - 1) / kWallThreads;
+  if (prec == 0)
+    column_kernel<double><<<grid, kWallThreads, 0, st>>>(d_insts, d_tasks, n, parity);
+  else
+    column_kernel<float><<<grid, kWallThreads, 0, st>>>(d_insts, d_tasks, n, parity);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int launch_wall(int prec, const InstDev* d_insts, const WallDev* d_walls, double* d_rec, int n,
                 int parity, int flags, void* stream) {

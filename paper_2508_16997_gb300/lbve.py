@@ -31,7 +31,7 @@ EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_st
             "lbve_status", "lbve_fields", "lbve_totals", "lbve_residual", "lbve_time",
             "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc",
             "lbve_adjoint_workspace_bytes", "lbve_adjoint_step", "lbve_state_bytes", "lbve_save",
-            "lbve_load", "lbve_autotune", "lbve_set_wall_distances"]
+            "lbve_load", "lbve_autotune", "lbve_set_wall_distances", "lbve_set_inlet"]
 
 
 class lbve_params(ctypes.Structure):
@@ -40,7 +40,8 @@ class lbve_params(ctypes.Structure):
                 ("Re", ctypes.c_double), ("Sc", ctypes.c_double), ("Ma", ctypes.c_double),
                 ("Lc", ctypes.c_double), ("Lambda_s", ctypes.c_double),
                 ("Lambda_p", ctypes.c_double), ("Fx", ctypes.c_double), ("Fy", ctypes.c_double),
-                ("tile_tx", ctypes.c_int32), ("max_wall_nodes", ctypes.c_int32)]
+                ("tile_tx", ctypes.c_int32), ("max_wall_nodes", ctypes.c_int32),
+                ("open_x", ctypes.c_int32)]
 
 
 class LbveError(RuntimeError):
@@ -86,6 +87,7 @@ def load() -> ctypes.CDLL:
         L.lbve_load.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.lbve_autotune.argtypes = [P, ctypes.c_int32, _vp, ctypes.c_size_t, _vp, ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]
+        L.lbve_set_inlet.argtypes = [_vp, ctypes.c_int32, _dp]
         L.lbve_set_wall_distances.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32), _dp]
@@ -150,6 +152,12 @@ def lbve_set_geometry(h, inst: int, solid_mask=None, body_force=None, init_field
     bf, bf_ptr = _f64(body_force, 2 * n_nodes) if body_force is not None else (None, None)
     ini, ini_ptr = _f64(init_fields, 6 * n_nodes) if init_fields is not None else (None, None)
     _check(load().lbve_set_geometry(h, inst, mask_ptr, bf_ptr, ini_ptr), "lbve_set_geometry")
+
+
+def lbve_set_inlet(h, inst: int, inlet) -> None:
+    """Inlet profile [5][ny] = u_x, u_y, A_xx, A_xy, A_yy of an open channel."""
+    a = np.ascontiguousarray(inlet, dtype=np.float64)
+    _check(load().lbve_set_inlet(h, inst, a.ctypes.data_as(_dp)), "lbve_set_inlet")
 
 
 def lbve_set_wall_distances(h, inst: int, node, direction, q) -> None:
@@ -263,7 +271,8 @@ def params_from(inst, precision: int = LBVE_FP64, tile_tx: int = 0) -> lbve_para
         walls = len({k for k, _, _ in inst.wall_links()})
     return lbve_params(inst.nx, inst.ny, 1 if inst.periodic_y else 0, precision, inst.beta,
                        inst.Wi, inst.Re, inst.Sc, inst.Ma, inst.Lc, inst.Lambda_s, inst.Lambda_p,
-                       inst.Fx, inst.Fy, tile_tx, walls)
+                       inst.Fx, inst.Fy, tile_tx, walls,
+                       1 if getattr(inst, "open_x", False) else 0)
 
 
 class Simulation:
@@ -303,6 +312,8 @@ class Simulation:
             ini = None if init_fields is None else init_fields[i]
             solid = getattr(inst, "solid", None)
             lbve_set_geometry(self.h, i, solid, inst.force_field, ini, n_nodes=inst.n_nodes)
+            if getattr(inst, "open_x", False) and getattr(inst, "inlet", None) is not None:
+                lbve_set_inlet(self.h, i, inst.inlet)
             if solid is not None and getattr(inst, "wall_q", None) is not None:
                 links = inst.wall_links()
                 lbve_set_wall_distances(self.h, i, [k for k, _, _ in links],

@@ -108,3 +108,20 @@ def test_autotune_rejects_bad_arguments_on_the_host(L):
     with pytest.raises(L.LbveError) as e:
         L.lbve_autotune(p, 0, n, 0)
     assert e.value.code == L.LBVE_ERR_WORKSPACE
+
+
+def test_open_channel_validation(L):
+    """open_x must be 0 or 1, and an open channel needs nx >= 5."""
+    from paper_2508_16997_gb300 import workloads as wl
+    p = L.params_from(wl.channel(8, nx=6))
+    p.open_x = 1
+    L.lbve_workspace_bytes([p])
+    p.open_x = 2
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_workspace_bytes([p])
+    assert e.value.code == L.LBVE_ERR_ARG
+    p = L.params_from(wl.channel(8, nx=4))
+    p.open_x = 1
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_workspace_bytes([p])
+    assert e.value.code == L.LBVE_ERR_ARG
