@@ -121,6 +121,11 @@ typedef struct {
   double Lc;                   /* characteristic length, lattice units  */
   double Lambda_s, Lambda_p;   /* magic parameters (Secs. 3.1, 3.2)      */
   double Fx, Fy;               /* uniform body force if no field given  */
+  int32_t model;  /* constitutive function F(A) of eq_Constitutive / eq_kramer:
+                     0 Oldroyd-B (eqb4), 1 FENE-P, 2 FENE-CR               */
+  int32_t gtilde; /* G~_i: 0 incompressible form eq_p_G_1, 1 eq_p_G (with the
+                     density gradient)                                      */
+  double L2;      /* FENE extensibility L^2 (> 2), models 1 and 2           */
 } orc_params;
 
 /* Derived lattice coefficients (Sec. 2.4 and the relaxation-time relations
@@ -305,6 +310,53 @@ void orc_cde_collide(const double* g, double rho, double ux, double uy, double F
   }
 }
 
+/* Constitutive function F(A) (eq_Constitutive, eq_kramer; Sec. 2 lists the
+ * models the formalism takes).  The two FENE models fit the paper's single-F
+ * form exactly (the same F relaxes A and gives the stress):
+ *   model 0, Oldroyd-B (eqb4): F = A - I
+ *   model 1, FENE-P:  F = A / (1 - tr A / L2) - I / (1 - 2 / L2)
+ *                     (the 2-D form: F(I) = 0)
+ *   model 2, FENE-CR: F = (A - I) L2 / (L2 - tr A)
+ * A and F are {xx, xy, yy}. */
+void orc_model_F(const double* A, int model, double L2, double* F) {
+  const double tr = A[0] + A[2];
+  if (model == 1) {
+    const double f = 1.0 / (1.0 - tr / L2), a = 1.0 / (1.0 - 2.0 / L2);
+    F[0] = f * A[0] - a;
+    F[1] = f * A[1];
+    F[2] = f * A[2] - a;
+  } else if (model == 2) {
+    const double f = L2 / (L2 - tr);
+    F[0] = f * (A[0] - 1.0);
+    F[1] = f * A[1];
+    F[2] = f * (A[2] - 1.0);
+  } else {
+    F[0] = A[0] - 1.0;
+    F[1] = A[1];
+    F[2] = A[2] - 1.0;
+  }
+}
+
+/* Constitutive source of eq_Constitutive (Sec. 3.2, Phi_ab) for a model:
+ *   S_ab = -F_ab(A)/lambda + A_ag d_g u_b + A_gb d_g u_a + A_ab d_g u_g
+ * grad[g][b] = d_g u_b.  A and S are {xx, xy, yy}. */
+void orc_source_model(const double* A, const double* grad, double lambda, int model, double L2,
+                      double* S) {
+  const double A2[2][2] = {{A[0], A[1]}, {A[1], A[2]}};
+  const double (*G)[2] = (const double (*)[2])grad;
+  const int ab[3][2] = {{0, 0}, {0, 1}, {1, 1}};
+  const double div = G[0][0] + G[1][1];
+  double F[3];
+  orc_model_F(A, model, L2, F);
+  for (int c = 0; c < NC; ++c) {
+    const int a = ab[c][0], b = ab[c][1];
+    double s = -F[c] / lambda;
+    for (int g = 0; g < 2; ++g) s += A2[a][g] * G[g][b] + A2[g][b] * G[g][a];
+    s += A2[a][b] * div;
+    S[c] = s;
+  }
+}
+
 /* Oldroyd-B constitutive source (Sec. 3.2, expression for Phi_ab):
  *   S_ab = -(A_ab - d_ab)/lambda + A_ag d_g u_b + A_gb d_g u_a + A_ab d_g u_g
  * grad[g][b] = d_g u_b.  A and S are {xx, xy, yy}. */
@@ -390,7 +442,8 @@ typedef struct {
   double* uold;  /* [2][n]      u(t-1)                                     */
   double* F;     /* [2][n]      body force                                 */
   double* mom;   /* [6][n]      rho, ux, uy, phi_xx, phi_xy, phi_yy at t   */
-  double* grad;  /* [6][n]      dxux, dxuy, dyux, dyuy, dx(rho ux^3), dy(rho uy^3) */
+  double* grad;  /* [8][n]      dxux, dxuy, dyux, dyuy, dx(rho ux^3), dy(rho uy^3),
+                                dx rho, dy rho (eq_p_G) */
   double* S;     /* [NC][n]                                                */
   int64_t t;
   double wall_in[NC], wall_out[NC];
@@ -493,7 +546,7 @@ static void compute_gradients_and_source(orc_sim* s) {
     for (int x = 0; x < nx; ++x) {
       const int k = y * nx + x;
       if (s->solid && s->solid[k]) {
-        for (int j = 0; j < 6; ++j) s->grad[j * n + k] = 0.0;
+        for (int j = 0; j < 8; ++j) s->grad[j * n + k] = 0.0;
         for (int c = 0; c < NC; ++c) s->S[c * n + k] = 0.0;
         continue;
       }
@@ -503,11 +556,13 @@ static void compute_gradients_and_source(orc_sim* s) {
       s->grad[3 * n + k] = fd(s, uy, x, y, 1);
       s->grad[4 * n + k] = fd(s, cube_x, x, y, 0);
       s->grad[5 * n + k] = fd(s, cube_y, x, y, 1);
+      s->grad[6 * n + k] = fd(s, s->mom, x, y, 0); /* density gradient (eq_p_G) */
+      s->grad[7 * n + k] = fd(s, s->mom, x, y, 1);
       /* grad[g][b] = d_g u_b */
       const double G[2][2] = {{s->grad[k], s->grad[n + k]}, {s->grad[2 * n + k], s->grad[3 * n + k]}};
       const double A[3] = {s->mom[3 * n + k], s->mom[4 * n + k], s->mom[5 * n + k]};
       double S[3];
-      orc_source(A, &G[0][0], s->c.lambda, S);
+      orc_source_model(A, &G[0][0], s->c.lambda, s->p.model, s->p.L2, S);
       for (int c = 0; c < NC; ++c) s->S[c * n + k] = S[c];
     }
   free(cube_x);
@@ -540,6 +595,8 @@ orc_sim* orc_create(const orc_params* p, const double* force, const double* init
   build_tables();
   if (p->nx < 1 || p->ny < 1 || (!p->periodic_y && p->ny < 3)) return NULL;
   if (p->open_x != 0 && (p->open_x != 1 || p->nx < 5)) return NULL;
+  if (p->model < 0 || p->model > 2 || (p->model != 0 && !(p->L2 > 2.0))) return NULL;
+  if (p->gtilde != 0 && p->gtilde != 1) return NULL;
   orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
   s->p = *p;
   orc_derive(p, &s->c);
@@ -555,7 +612,7 @@ orc_sim* orc_create(const orc_params* p, const double* force, const double* init
   s->uold = (double*)calloc((size_t)2 * n, sizeof(double));
   s->F = (double*)calloc((size_t)2 * n, sizeof(double));
   s->mom = (double*)calloc((size_t)6 * n, sizeof(double));
-  s->grad = (double*)calloc((size_t)6 * n, sizeof(double));
+  s->grad = (double*)calloc((size_t)8 * n, sizeof(double));
   s->S = (double*)calloc((size_t)NC * n, sizeof(double));
   s->inlet = (double*)calloc((size_t)5 * p->ny, sizeof(double));
   if (!s->f || !s->g || !s->fpost || !s->gpost || !s->Sold || !s->uold || !s->F || !s->mom ||
@@ -603,9 +660,10 @@ void orc_step(orc_sim* s, int64_t n_steps) {
       const double rho = s->mom[k], ux = s->mom[n + k], uy = s->mom[2 * n + k];
       const double Fx = s->F[k], Fy = s->F[n + k];
       const double A[3] = {s->mom[3 * n + k], s->mom[4 * n + k], s->mom[5 * n + k]};
-      const double tau[3] = {s->c.mup / s->c.lambda * (A[0] - 1.0),
-                             s->c.mup / s->c.lambda * A[1],
-                             s->c.mup / s->c.lambda * (A[2] - 1.0)}; /* eq_kramer, eqb4 */
+      double Fm[3];
+      orc_model_F(A, s->p.model, s->p.L2, Fm);
+      const double tau[3] = {s->c.mup / s->c.lambda * Fm[0], s->c.mup / s->c.lambda * Fm[1],
+                             s->c.mup / s->c.lambda * Fm[2]}; /* eq_kramer */
       const double dPhi[2] = {s->grad[4 * n + k], s->grad[5 * n + k]};
       double fk[Q], out[Q];
       for (int i = 0; i < Q; ++i) fk[i] = s->f[i * n + k];
@@ -614,7 +672,10 @@ void orc_step(orc_sim* s, int64_t n_steps) {
       for (int c = 0; c < NC; ++c) {
         double gk[Q];
         for (int i = 0; i < Q; ++i) gk[i] = s->g[(c * Q + i) * n + k];
-        orc_cde_collide(gk, rho, ux, uy, Fx, Fy, s->S[c * n + k], s->Sold[c * n + k],
+        /* G~_i sees F (eq_p_G_1) or F - c_s^2 grad rho (eq_p_G) */
+        const double Gx = s->p.gtilde ? Fx - CS2 * s->grad[6 * n + k] : Fx;
+        const double Gy = s->p.gtilde ? Fy - CS2 * s->grad[7 * n + k] : Fy;
+        orc_cde_collide(gk, rho, ux, uy, Gx, Gy, s->S[c * n + k], s->Sold[c * n + k],
                         s->uold[k], s->uold[n + k], s->c.tau_p1, s->c.tau_p2, out);
         for (int i = 0; i < Q; ++i) s->gpost[(c * Q + i) * n + k] = out[i];
       }

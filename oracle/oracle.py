@@ -43,7 +43,8 @@ class Params(ctypes.Structure):
                 ("beta", ctypes.c_double), ("Wi", ctypes.c_double), ("Re", ctypes.c_double),
                 ("Sc", ctypes.c_double), ("Ma", ctypes.c_double), ("Lc", ctypes.c_double),
                 ("Lambda_s", ctypes.c_double), ("Lambda_p", ctypes.c_double),
-                ("Fx", ctypes.c_double), ("Fy", ctypes.c_double)]
+                ("Fx", ctypes.c_double), ("Fy", ctypes.c_double),
+                ("model", ctypes.c_int32), ("gtilde", ctypes.c_int32), ("L2", ctypes.c_double)]
 
 
 class Coeffs(ctypes.Structure):
@@ -84,6 +85,9 @@ def lib():
                                         ctypes.c_double, ctypes.c_double, _dp]
         L.orc_cde_collide.argtypes = ([_dp] + [ctypes.c_double] * 11 + [_dp])
         L.orc_source.argtypes = [_dp, _dp, ctypes.c_double, _dp]
+        L.orc_source_model.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                       _dp]
+        L.orc_model_F.argtypes = [_dp, ctypes.c_int, ctypes.c_double, _dp]
         L.orc_zou_he.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
         L.orc_cnebb.argtypes = [_dp, _dp, _ip, ctypes.c_double, ctypes.c_double, _dp, _dp]
         _lib = L
@@ -96,11 +100,12 @@ def _ptr(a: np.ndarray):
 
 
 def make_params(nx, ny, periodic_y=True, beta=0.5, Wi=1.0, Re=1.0, Sc=1e5, Ma=0.1, Lc=None,
-                Lambda_s=0.25, Lambda_p=1e-6, Fx=0.0, Fy=0.0, open_x=False) -> Params:
+                Lambda_s=0.25, Lambda_p=1e-6, Fx=0.0, Fy=0.0, open_x=False, model=0, gtilde=0,
+                L2=0.0) -> Params:
     if Lc is None:
         Lc = float(ny - 1) if not periodic_y else float(nx) / (2 * np.pi)
     return Params(nx, ny, 1 if periodic_y else 0, 1 if open_x else 0, beta, Wi, Re, Sc, Ma, Lc, Lambda_s,
-                  Lambda_p, Fx, Fy)
+                  Lambda_p, Fx, Fy, model, gtilde, L2)
 
 
 def derive(p: Params) -> dict:
@@ -231,11 +236,22 @@ def cde_collide(g, rho, ux, uy, Fx, Fy, S, S_old, uxo, uyo, tau_p1, tau_p2) -> n
     return out
 
 
-def source(A, grad, lam) -> np.ndarray:
+def source(A, grad, lam, model=0, L2=0.0) -> np.ndarray:
     A = np.ascontiguousarray(A, np.float64)
     grad = np.ascontiguousarray(grad, np.float64)
     out = np.empty(3)
-    lib().orc_source(_ptr(A), _ptr(grad), lam, _ptr(out))
+    if model == 0:
+        lib().orc_source(_ptr(A), _ptr(grad), lam, _ptr(out))
+    else:
+        lib().orc_source_model(_ptr(A), _ptr(grad), lam, int(model), float(L2), _ptr(out))
+    return out
+
+
+def model_F(A, model, L2) -> np.ndarray:
+    """Constitutive function F(A) of model 0 (Oldroyd-B), 1 (FENE-P), 2 (FENE-CR)."""
+    A = np.ascontiguousarray(A, np.float64)
+    out = np.empty(3)
+    lib().orc_model_F(_ptr(A), int(model), float(L2), _ptr(out))
     return out
 
 

@@ -59,6 +59,9 @@ class Instance:
     solid: np.ndarray | None = field(default=None, repr=False)   # (ny, nx) uint8, 1 = solid
     wall_q: np.ndarray | None = field(default=None, repr=False)  # (9, ny, nx) link fractions
     open_x: bool = False     # inlet column x = 0, outlet column x = nx - 1
+    model: int = 0           # 0 Oldroyd-B, 1 FENE-P, 2 FENE-CR
+    L2: float = 0.0          # FENE extensibility L^2 (models 1, 2)
+    gtilde: int = 0          # G~_i: 0 eq_p_G_1, 1 eq_p_G (density gradient)
     inlet: np.ndarray | None = field(default=None, repr=False)   # (5, ny) ux, uy, Axx, Axy, Ayy
 
     @property

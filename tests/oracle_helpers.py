@@ -7,7 +7,9 @@ from oracle import oracle as o
 
 def oracle_params(inst, **override):
     d = dict(beta=inst.beta, Wi=inst.Wi, Re=inst.Re, Sc=inst.Sc, Ma=inst.Ma, Lc=inst.Lc,
-             Lambda_s=inst.Lambda_s, Lambda_p=inst.Lambda_p, Fx=inst.Fx, Fy=inst.Fy)
+             Lambda_s=inst.Lambda_s, Lambda_p=inst.Lambda_p, Fx=inst.Fx, Fy=inst.Fy,
+             model=getattr(inst, "model", 0), gtilde=getattr(inst, "gtilde", 0),
+             L2=getattr(inst, "L2", 0.0))
     d.update(override)
     return o.make_params(inst.nx, inst.ny, inst.periodic_y, open_x=getattr(inst, "open_x", False),
                          **d)

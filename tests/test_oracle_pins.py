@@ -755,3 +755,130 @@ def test_open_inlet_extrapolates_the_non_equilibrium_moments():
         np.testing.assert_allclose(m2b - m2f, phi_in * np.einsum("ay,by->aby", u_in, u_in)
                                    - phi_f * np.einsum("ay,by->aby", u_f, u_f),
                                    rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Constitutive models beyond Oldroyd-B (Sec. 2: F(A) in eq_Constitutive and
+# eq_kramer) and the density-gradient form of G~_i (eq_p_G)
+# --------------------------------------------------------------------------
+
+def _shear_grad(gd):
+    g = np.zeros((2, 2))
+    g[1, 0] = gd  # d_y u_x
+    return g
+
+
+@pytest.mark.parametrize("L2", [5.0, 20.0, 300.0])
+@pytest.mark.parametrize("Wi_gd", [0.1, 1.0, 7.0])
+def test_fene_steady_simple_shear_closed_forms(oracle_mod, L2, Wi_gd):
+    """Steady homogeneous shear (d_y u_x = gd): the upper-convected terms give
+    F_xx = 2 lam gd A_xy, F_xy = lam gd A_yy, F_yy = 0.  FENE-P
+    (F = f A - a I, f = 1/(1 - tr A/L2), a = 1/(1 - 2/L2)): A_yy = a z,
+    A_xy = lam gd a z^2, A_xx = a z + 2 (lam gd)^2 a z^3 with z = 1/f the root
+    in (0, 1) of 2 a (lam gd)^2 z^3 + (2a + L2) z - L2 = 0.  FENE-CR
+    (F = f (A - I), f = L2/(L2 - tr A)): A_yy = 1, A_xy = lam gd / f,
+    A_xx = 1 + 2 (lam gd / f)^2, f the positive root of
+    (L2 - 2) f^2 - L2 f - 2 (lam gd)^2 = 0.  The oracle's source vanishes
+    there."""
+    lam = 50.0
+    gd = Wi_gd / lam
+    a = 1.0 / (1.0 - 2.0 / L2)
+    roots = np.roots([2 * a * Wi_gd ** 2, 0.0, 2 * a + L2, -L2])
+    z = [r.real for r in roots if abs(r.imag) < 1e-12 and 0 < r.real < 1][0]
+    A = np.array([a * z + 2 * Wi_gd ** 2 * a * z ** 3, Wi_gd * a * z ** 2, a * z])
+    S = oracle_mod.source(A, _shear_grad(gd), lam, model=1, L2=L2)
+    np.testing.assert_allclose(S, 0.0, atol=1e-13 * np.abs(A).max() / lam)
+    f = (L2 + math.sqrt(L2 ** 2 + 8 * (L2 - 2) * Wi_gd ** 2)) / (2 * (L2 - 2))
+    A = np.array([1 + 2 * (Wi_gd / f) ** 2, Wi_gd / f, 1.0])
+    S = oracle_mod.source(A, _shear_grad(gd), lam, model=2, L2=L2)
+    np.testing.assert_allclose(S, 0.0, atol=1e-13 * np.abs(A).max() / lam)
+    # and the Oldroyd-B limit L2 -> infinity of both
+    for model in (1, 2):
+        A = np.array([1 + 2 * Wi_gd ** 2, Wi_gd, 1.0])
+        S = oracle_mod.source(A, _shear_grad(gd), lam, model=model, L2=1e15)
+        np.testing.assert_allclose(S, 0.0, atol=1e-12 * A.max() / lam)
+
+
+@pytest.mark.parametrize("L2", [10.0, 100.0])
+def test_fene_steady_planar_extension(oracle_mod, L2):
+    """Steady planar extension (u = ed (x, -y)): F_xx = 2 lam ed A_xx,
+    F_yy = -2 lam ed A_yy, A_xy = 0.  FENE-CR: A_xx = f/(f - 2 lam ed),
+    A_yy = f/(f + 2 lam ed) with f = L2/(L2 - tr A); FENE-P: A_xx = a/(f - 2
+    lam ed), A_yy = a/(f + 2 lam ed) with 1/f = 1 - tr A/L2 -- each a scalar
+    root in f (scipy brentq).  The oracle's source vanishes there."""
+    from scipy.optimize import brentq
+    lam, Wi_e = 40.0, 0.3
+    ed = Wi_e / lam
+    g = np.zeros((2, 2))
+    g[0, 0], g[1, 1] = ed, -ed
+    a = 1.0 / (1.0 - 2.0 / L2)
+    # FENE-P
+    fP = brentq(lambda f: 1.0 / f - 1.0 + (a / (f - 2 * Wi_e) + a / (f + 2 * Wi_e)) / L2,
+                2 * Wi_e + 1e-9, 1e6)
+    A = np.array([a / (fP - 2 * Wi_e), 0.0, a / (fP + 2 * Wi_e)])
+    np.testing.assert_allclose(oracle_mod.source(A, g, lam, model=1, L2=L2), 0.0,
+                               atol=1e-13 * A.max() / lam)
+    # FENE-CR
+    fC = brentq(lambda f: f * (L2 - f / (f - 2 * Wi_e) - f / (f + 2 * Wi_e)) - L2,
+                2 * Wi_e + 1e-6, 1e6)
+    A = np.array([fC / (fC - 2 * Wi_e), 0.0, fC / (fC + 2 * Wi_e)])
+    np.testing.assert_allclose(oracle_mod.source(A, g, lam, model=2, L2=L2), 0.0,
+                               atol=1e-13 * A.max() / lam)
+
+
+def test_fene_cr_channel_keeps_the_newtonian_profile():
+    """FENE-CR has a constant shear viscosity (tau_xy = mu_p f A_xy / lam =
+    mu_p du/dy at steady state), so its steady channel flow has the same
+    parabola as Oldroyd-B, while A_xy = lam du/dy / f and A_xx = 1 + 2
+    A_xy^2 with the local f of the shear closed form.  Checks the stress
+    (Kramers) path of the model: a stress of lam^-1 (A - I) would thin the
+    flow."""
+    H, L2 = 16, 12.0
+    base = wl.channel(H, nx=4, Wi=2.0)
+    fene = wl.channel(H, nx=4, Wi=2.0)
+    fene.model, fene.L2 = 2, L2
+    o1, o2 = oracle_sim(base), oracle_sim(fene)
+    o1.step(30000)
+    o2.step(30000)
+    F1, F2 = o1.fields(), o2.fields()
+    Uc = wl.velocity_scale(fene.Ma)
+    assert np.abs(F2[1] - F1[1]).max() < 2e-4 * Uc, np.abs(F2[1] - F1[1]).max() / Uc
+    lam = o2.coeffs()["lambda"]
+    y = np.arange(H + 1)
+    gd = 4.0 * Uc * (H - 2.0 * y) / H ** 2     # du/dy of the parabola (eq_ux_ana)
+    Wg = lam * gd
+    f = (L2 + np.sqrt(L2 ** 2 + 8 * (L2 - 2) * Wg ** 2)) / (2 * (L2 - 2))
+    np.testing.assert_allclose(F2[4][:, 0], Wg / f, rtol=0, atol=5e-3 * np.abs(Wg / f).max())
+    np.testing.assert_allclose(F2[3][:, 0], 1 + 2 * (Wg / f) ** 2, rtol=0,
+                               atol=5e-3 * (2 * (Wg / f) ** 2).max())
+    assert np.abs(F2[4] - F1[4]).max() > 0.05 * np.abs(F1[4]).max()  # the model matters for A
+
+
+def test_gtilde_density_gradient_form_hydrostatic_balance():
+    """eq_p_G replaces F by F - c_s^2 grad rho in G~_i.  In hydrostatic
+    balance (gravity F_y in a walled channel: u -> 0 and c_s^2 d_y rho = F_y,
+    rho linear with span |F_y| H / c_s^2) that force vanishes, so the polymer
+    sees no spurious flux and A stays I to round-off; eq_p_G_1 leaves a
+    permanent A - I of order 1e-5 there.  At uniform density the two forms
+    are bit-identical for a step."""
+    def run(mode, steps):
+        inst = wl.channel(16, nx=4, Wi=1.0, Sc=1e3)
+        inst.Fx, inst.Fy, inst.gtilde = 0.0, -2e-4, mode
+        s = oracle_sim(inst)
+        s.step(steps)
+        return s.fields()
+    F1, F0 = run(1, 20000), run(0, 20000)
+    dev = lambda F: max(np.abs(F[3] - 1).max(), np.abs(F[4]).max(), np.abs(F[5] - 1).max())
+    assert np.abs(F1[1:3]).max() < 1e-14
+    np.testing.assert_allclose(F1[0].max() - F1[0].min(), 2e-4 * 16 / CS2, rtol=1e-9)
+    assert dev(F1) < 1e-12
+    assert dev(F0) > 1e-5
+    N = 12
+    init = wl.random_fields(N, N, seed=62, drho=0.0)
+    a = oracle_sim(wl.frm(N, Wi=1.0, Re=1.0, Ma=0.05), init=init)
+    inst = wl.frm(N, Wi=1.0, Re=1.0, Ma=0.05)
+    inst.gtilde = 1
+    b = oracle_sim(inst, init=init)
+    a.step(1)
+    b.step(1)
+    np.testing.assert_array_equal(a.state()[1], b.state()[1])
