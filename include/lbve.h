@@ -110,6 +110,15 @@ typedef struct {
                          f^eq(rho_f, u_f), g = g_f (zero gradient).  The
                          columns' wall-row corners take the same rule;
                          gradients along x are one-sided there.            */
+  int32_t model;      /* constitutive function F(A) of the conformation
+                         equation and the Kramers stress (Sec. 2; eqb4 is
+                         model 0): 0 Oldroyd-B F = A - I; 1 FENE-P
+                         F = A/(1 - tr A/L2) - I/(1 - 2/L2); 2 FENE-CR
+                         F = (A - I) L2/(L2 - tr A).                        */
+  int32_t gtilde;     /* auxiliary term G~_i: 0 incompressible form eq_p_G_1,
+                         1 the density-gradient form eq_p_G (F - c_s^2
+                         grad rho, gradients as for u).                     */
+  double L2;          /* FENE extensibility L^2 (> 2) for models 1 and 2.   */
 } lbve_params;
 
 typedef struct lbve_handle lbve_handle;
@@ -267,7 +276,8 @@ int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps, 
  * (the reverse of each stage of the coupled step of Secs. 3.1-3.3: collisions,
  * source, finite-difference gradients, Zou-He and CNEBB completions, pull
  * streaming) with sqrt(n_steps) checkpointing and recomputation.
- * Instances with a solid mask or open in x are refused (LBVE_ERR_GEOMETRY).
+ * Instances with a solid mask or open in x are refused (LBVE_ERR_GEOMETRY), and
+ * so are models other than Oldroyd-B and the eq_p_G form (LBVE_ERR_ARG).
  * The trajectory is the one that lbve_set_geometry(h, inst, NULL, <current
  * force of inst>, init_fields) followed by lbve_step(n_steps) produces; the
  * forward states are recomputed in the adjoint workspace (the instance's own

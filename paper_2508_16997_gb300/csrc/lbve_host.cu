@@ -83,6 +83,13 @@ int validate(const lbve_params& p, int i) {
                 i);
   if (!std::isfinite(p.Fx) || !std::isfinite(p.Fy))
     return fail(LBVE_ERR_ARG, "instance %d: body force must be finite", i);
+  if (p.model < 0 || p.model > 2)
+    return fail(LBVE_ERR_ARG, "instance %d: model must be 0 (Oldroyd-B), 1 (FENE-P) or 2 (FENE-CR)",
+                i);
+  if (p.model != 0 && !(std::isfinite(p.L2) && p.L2 > 2.0))
+    return fail(LBVE_ERR_ARG, "instance %d: a FENE model needs L2 > 2", i);
+  if (p.gtilde != 0 && p.gtilde != 1)
+    return fail(LBVE_ERR_ARG, "instance %d: gtilde must be 0 or 1", i);
   if (p.open_x != 0 && p.open_x != 1)
     return fail(LBVE_ERR_ARG, "instance %d: open_x must be 0 or 1", i);
   if (p.open_x && p.nx < 5)
@@ -279,8 +286,7 @@ constexpr int kGraphSteps = 32;  // even, so a replay leaves the parity unchange
 // the masked tiles, while the plain tiles, which never read what the wall
 // pass writes, run on the caller's stream; the two join before the step ends.
 int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
-  const bool fork =
-      h->nmasked_inst[0] + h->nmasked_inst[1] + h->nopen_inst[0] + h->nopen_inst[1] > 0;
+  const bool fork = h->nmasked[0] + h->nmasked[1] > 0;  // any tile of the general variant
   if (fork) {
     cudaError_t e = cudaEventRecord(h->ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
@@ -430,12 +436,15 @@ int flag_tiles(lbve_handle* h, int i) {
     if (p.open_x && (xw == 0 || xw == nx - 1)) return true;
     return !m.empty() && m[size_t(y) * nx + xw] != 0;
   };
+  // a model other than Oldroyd-B or the eq_p_G form of G~ runs every tile of
+  // the instance in the general variant, keeping the plain one specialised
+  const bool general = p.model != 0 || p.gtilde != 0;
   std::vector<TileDev>& T = h->tiles_h[l];
   std::vector<TileDev> mt;
-  const bool any = !m.empty() || p.open_x;
+  const bool any = !m.empty() || p.open_x || general;
   for (int j = q.tile_begin; j < q.tile_begin + q.ntiles; ++j) {
     TileDev& t = T[j];
-    t.masked = 0;
+    t.masked = general ? 1 : 0;
     const int xa = t.x0 - 2, xb = t.x0 + q.TX + 1;
     const int ya = t.y0 - q.hy - 1, yb = t.y0 + q.TY + q.hy;
     for (int y = ya; y <= yb && !t.masked && any; ++y)
@@ -686,6 +695,10 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     D.cd[kCoefHp1] = (c.tau_p1 - 0.5) / c.tau_p1;
     D.cd[kCoefInvLam] = 1.0 / c.lambda;
     D.cd[kCoefMupLam] = c.mup / c.lambda;
+    D.cd[kCoefInvL2] = p[i].model != 0 ? 1.0 / p[i].L2 : 0.0;
+    D.cd[kCoefAfene] = p[i].model == 1 ? 1.0 / (1.0 - 2.0 / p[i].L2) : 1.0;
+    D.model = p[i].model;
+    D.gtilde = p[i].gtilde;
     for (int j = 0; j < kNumCoef; ++j) D.cf[j] = (float)D.cd[j];
     int k = q.tile_begin;
     for (int ty = 0; ty < q.nty; ++ty)
@@ -759,8 +772,8 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     return cuda_fail(e, "open-channel tables upload");
   }
   for (int i = 0; i < n; ++i) {
-    if (!p[i].open_x) continue;
-    update_geometry_hash(h, i);
+    if (!p[i].open_x && p[i].model == 0 && p[i].gtilde == 0) continue;
+    if (p[i].open_x) update_geometry_hash(h, i);
     int rc2 = ensure_side_stream(h);
     if (rc2 == LBVE_OK) rc2 = flag_tiles(h, i);
     if (rc2) {
@@ -1316,6 +1329,9 @@ extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* ini
   if (h->insts[inst].mask || h->p[inst].open_x)
     return fail(LBVE_ERR_GEOMETRY,
                 "the adjoint covers neither solid masks nor open channels (instance %d)", inst);
+  if (h->p[inst].model != 0 || h->p[inst].gtilde != 0)
+    return fail(LBVE_ERR_ARG, "the adjoint covers Oldroyd-B with eq_p_G_1 only (instance %d)",
+                inst);
   const lbve_params& p = h->p[inst];
   const InstPlan& q = h->plan.inst[inst];
   const AdjPlan a = make_adj_plan(p, q, n_steps);

@@ -45,6 +45,8 @@ enum : int {
   kCoefHp1,     // 1 - 1/(2 tau_p1)
   kCoefInvLam,  // 1/lambda
   kCoefMupLam,  // mu_p/lambda
+  kCoefInvL2,   // 1/L^2 of the FENE models (0 for Oldroyd-B)
+  kCoefAfene,   // a = 1/(1 - 2/L^2) of FENE-P
   kNumCoef
 };
 
@@ -63,6 +65,8 @@ struct InstDev {
   const uint8_t* mask;           // [stride] 1 = solid node, or null (no mask)
   double* wall_rec;              // [wall_cap][kWallRec] final-step wall sums
   int32_t open_x, pad2;          // open_x: inlet column x = 0, outlet x = nx - 1
+  int32_t model, gtilde;         // constitutive model (0 Oldroyd-B, 1 FENE-P, 2 FENE-CR);
+                                 // G~ form (0 eq_p_G_1, 1 eq_p_G)
   void* colbuf;                  // [36][2 ny] completed populations of the two open
                                  // columns (inlet rows, then outlet rows), deviations
   const double* inlet;           // [5][ny] u_x, u_y, A_xx, A_xy, A_yy at the inlet

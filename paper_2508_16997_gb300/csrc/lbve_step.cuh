@@ -314,21 +314,33 @@ __device__ __forceinline__ bool region_node(int lx, int ly, int x0, int y0, int 
 //   So, uo  source and velocity of the previous step (ignored at init)
 // Writes the 36 post-collision populations and the 5 history values of node k;
 // on the final step also the float64 fields and this node's partial sums.
-template <typename R, int MODE, bool FINAL>
+template <typename R, int MODE, bool FINAL, bool MASKED>
 __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* __restrict__ dst,
                                              R* __restrict__ hist, const HydroM<R>& hm,
                                              const CdeM<R>* cm, R rho, R ux, R uy, R G00, R G01,
-                                             R G10, R G11, R dPx, R dPy, R Fx, R Fy, R So0,
-                                             R So1, R So2, R uxo, R uyo, double* part) {
-  // conformation tensor, polymer stress (eq_kramer with eqb4), source Phi_ab
+                                             R G10, R G11, R dPx, R dPy, R dRx, R dRy, R Fx,
+                                             R Fy, R So0, R So1, R So2, R uxo, R uyo,
+                                             double* part) {
+  // conformation tensor, constitutive function F(A) (Sec. 2: eqb4 for
+  // Oldroyd-B, FENE-P, FENE-CR) in deviation form F = f (A - I) + (f - a) I,
+  // polymer stress (eq_kramer), source Phi_ab
   const R Axx = R(1) + cm[0].dphi, Axy = cm[1].dphi, Ayy = R(1) + cm[2].dphi;
   const R mpl = coef<R>(D, kCoefMupLam), il = coef<R>(D, kCoefInvLam);
-  const R txx = mpl * cm[0].dphi, txy = mpl * cm[1].dphi, tyy = mpl * cm[2].dphi;
+  R Fxx = cm[0].dphi, Fxy = cm[1].dphi, Fyy = cm[2].dphi;
+  if (MASKED && D.model != 0) {  // other models run in the general variant only
+    const R tr = Axx + Ayy;
+    const R f = R(1) / (R(1) - tr * coef<R>(D, kCoefInvL2));
+    const R a = D.model == 2 ? f : coef<R>(D, kCoefAfene);
+    Fxx = f * cm[0].dphi + (f - a);
+    Fxy = f * cm[1].dphi;
+    Fyy = f * cm[2].dphi + (f - a);
+  }
+  const R txx = mpl * Fxx, txy = mpl * Fxy, tyy = mpl * Fyy;
   const R div = G00 + G11;
   R Sc[3], So[3] = {So0, So1, So2};
-  Sc[0] = -cm[0].dphi * il + R(2) * (Axx * G00 + Axy * G10) + Axx * div;
-  Sc[1] = -cm[1].dphi * il + (Axx * G01 + Axy * G11) + (Axy * G00 + Ayy * G10) + Axy * div;
-  Sc[2] = -cm[2].dphi * il + R(2) * (Axy * G01 + Ayy * G11) + Ayy * div;
+  Sc[0] = -Fxx * il + R(2) * (Axx * G00 + Axy * G10) + Axx * div;
+  Sc[1] = -Fxy * il + (Axx * G01 + Axy * G11) + (Axy * G00 + Ayy * G10) + Axy * div;
+  Sc[2] = -Fyy * il + R(2) * (Axy * G01 + Ayy * G11) + Ayy * div;
   if (MODE != kModeStep) {
     // first step: the backward difference of the CDE source is zero
     So[0] = Sc[0];
@@ -368,6 +380,9 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
     const R ep = coef<R>(D, kCoefEp1), c2 = coef<R>(D, kCoefCp2), h1 = coef<R>(D, kCoefHp1);
     const R irho = R(1) / rho;
     const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    // the force G~_i sees: F (eq_p_G_1) or F - c_s^2 grad rho (eq_p_G)
+    const bool gt = MASKED && D.gtilde;
+    const R Gx = gt ? Fx - cs2 * dRx : Fx, Gy = gt ? Fy - cs2 * dRy : Fy;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       const R phi = (l == 1 ? R(0) : R(1)) + cm[l].dphi;
@@ -381,9 +396,9 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
       const R pr = phi * irho;
       // (1 - 1/tau_p1) B = -B + ep B, kept split so float32 keeps the tiny
       // difference tau_p1 - 1/2 accurately
-      const R cx = (phi * ux - Bx) + ep * Bx + h1 * (pr * Fx + ux * sl) +
+      const R cx = (phi * ux - Bx) + ep * Bx + h1 * (pr * Gx + ux * sl) +
                    R(0.5) * h1 * (ux * sl - uxo * so);
-      const R cy = (phi * uy - By) + ep * By + h1 * (pr * Fy + uy * sl) +
+      const R cy = (phi * uy - By) + ep * By + h1 * (pr * Gy + uy * sl) +
                    R(0.5) * h1 * (uy * sl - uyo * so);
       const R cxx = phi * uxx + c2 * Bxx;
       const R cyy = phi * uyy + c2 * Byy;
@@ -456,6 +471,15 @@ __device__ __forceinline__ void y_gradients(bool wb, bool wt, R rm2, R uxm2, R u
   }
 }
 
+// The same y difference of the density (for the eq_p_G form of G~).
+template <typename R>
+__device__ __forceinline__ R y_drho(bool wb, bool wt, R rm2, R rm1, R r0, R rp1, R rp2) {
+  const R half = R(0.5);
+  if (wb) return half * (R(-3) * r0 + R(4) * rp1 - rp2);
+  if (wt) return half * (R(3) * r0 - R(4) * rm1 + rm2);
+  return half * (rp1 - rm1);
+}
+
 // Resident CTAs per SM the register budget is sized for: the float32 step
 // is HBM-bound and wants more loads in flight; the float64 step is bound by
 // the FP64 pipe.
@@ -474,7 +498,7 @@ struct MinBlocks {
 template <typename R>
 __device__ __forceinline__ void one_sided(int t, R r0, R ux0, R uy0, R r1, R ux1, R uy1,
                                           bool has2, R r2, R ux2, R uy2, int axis, R& dux,
-                                          R& duy, R& dcube) {
+                                          R& duy, R& dcube, R& drho) {
   const R v0 = axis == 0 ? ux0 : uy0, v1 = axis == 0 ? ux1 : uy1, v2 = axis == 0 ? ux2 : uy2;
   const R c0 = r0 * v0 * v0 * v0, c1 = r1 * v1 * v1 * v1, c2 = r2 * v2 * v2 * v2;
   const R ts = (R)t;
@@ -483,10 +507,12 @@ __device__ __forceinline__ void one_sided(int t, R r0, R ux0, R uy0, R r1, R ux1
     dux = h * (R(-3) * ux0 + R(4) * ux1 - ux2);
     duy = h * (R(-3) * uy0 + R(4) * uy1 - uy2);
     dcube = h * (R(-3) * c0 + R(4) * c1 - c2);
+    drho = h * (R(-3) * r0 + R(4) * r1 - r2);
   } else {
     dux = ts * (ux1 - ux0);
     duy = ts * (uy1 - uy0);
     dcube = ts * (c1 - c0);
+    drho = ts * (r1 - r0);
   }
 }
 
@@ -721,12 +747,15 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     const R cxm = s_rho[ri - 1] * s_ux[ri - 1] * s_ux[ri - 1] * s_ux[ri - 1];
     R dPx = half * (cxp - cxm);
     R G10, G11, dPy;
+    // density gradient, only for the eq_p_G form of G~
+    R dRx = (MASKED && D.gtilde) ? half * (s_rho[ri + 1] - s_rho[ri - 1]) : R(0), dRy = R(0);
     {
       // rows y-2..y+2 of this column (only those a wall row needs are read)
       const int a = wb ? ri : (wt ? ri - 2 * RW : ri), b = wb ? ri : (wt ? ri - RW : ri - RW);
       const int c = wb ? ri + RW : (wt ? ri : ri + RW), e = wb ? ri + 2 * RW : ri;
       y_gradients<R>(wb, wt, s_rho[a], s_ux[a], s_uy[a], s_rho[b], s_ux[b], s_uy[b], rho, ux,
                      uy, s_rho[c], s_ux[c], s_uy[c], s_rho[e], s_ux[e], s_uy[e], G10, G11, dPy);
+      if (MASKED && D.gtilde) dRy = y_drho<R>(wb, wt, s_rho[a], s_rho[b], rho, s_rho[c], s_rho[e]);
     }
     if constexpr (MASKED) {
       // one-sided differences where an axis neighbour is solid; the values
@@ -738,7 +767,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
       const bool sxp = (D.open_x && x == nx - 1) || (M && M[y * nx + xp] != 0);
       const bool sxm = (D.open_x && x == 0) || (M && M[y * nx + xm] != 0);
       if (sxp || sxm) {
-        R gx0 = R(0), gx1 = R(0), gxc = R(0);
+        R gx0 = R(0), gx1 = R(0), gxc = R(0), gxr = R(0);
         if (!(sxp && sxm)) {
           const int t = sxp ? -1 : 1;
           const int i1 = t > 0 ? ri + 1 : ri - 1;
@@ -749,18 +778,19 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
             region_rho_u<R, MODE>(D, src, force, ffield, Fx0, Fy0, S, nx, ny, py, x2, y, r2,
                                   u2x, u2y);
           one_sided<R>(t, rho, ux, uy, s_rho[i1], s_ux[i1], s_uy[i1], has2, r2, u2x, u2y, 0, gx0,
-                       gx1, gxc);
+                       gx1, gxc, gxr);
         }
         G00 = gx0;
         G01 = gx1;
         dPx = gxc;
+        dRx = gxr;
       }
       if (!wb && !wt && M) {
         // rows next to a flat wall carry no mask, so y +- 1 lies in the domain
         const int yp = (py && y == ny - 1) ? 0 : y + 1, ym = (py && y == 0) ? ny - 1 : y - 1;
         const bool syp = M[yp * nx + x] != 0, sym = M[ym * nx + x] != 0;
         if (syp || sym) {
-          R gy0 = R(0), gy1 = R(0), gyc = R(0);
+          R gy0 = R(0), gy1 = R(0), gyc = R(0), gyr = R(0);
           if (!(syp && sym)) {
             const int t = syp ? -1 : 1;
             const int i1 = t > 0 ? ri + RW : ri - RW;
@@ -772,11 +802,12 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
               region_rho_u<R, MODE>(D, src, force, ffield, Fx0, Fy0, S, nx, ny, py, x, y2, r2,
                                     u2x, u2y);
             one_sided<R>(t, rho, ux, uy, s_rho[i1], s_ux[i1], s_uy[i1], has2, r2, u2x, u2y, 1,
-                         gy0, gy1, gyc);
+                         gy0, gy1, gyc, gyr);
           }
           G10 = gy0;
           G11 = gy1;
           dPy = gyc;
+          dRy = gyr;
         }
       }
     }
@@ -784,8 +815,9 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
 #pragma unroll
       for (int j = 0; j < 6; ++j) part[kWallIn + j] = wall_io[j];
     }
-    collide_node<R, MODE, FINAL>(D, k, S, dst, hist, hm, cm, rho, ux, uy, G00, G01, G10, G11,
-                                 dPx, dPy, Fx, Fy, So[0], So[1], So[2], uxo, uyo, part);
+    collide_node<R, MODE, FINAL, MASKED>(D, k, S, dst, hist, hm, cm, rho, ux, uy, G00, G01, G10,
+                                         G11,
+                                 dPx, dPy, dRx, dRy, Fx, Fy, So[0], So[1], So[2], uxo, uyo, part);
   } else if (FINAL && solid) {
     // a solid node reports zero fields and adds nothing to the totals
     const int ks = y * nx + x;

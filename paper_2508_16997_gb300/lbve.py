@@ -41,7 +41,8 @@ class lbve_params(ctypes.Structure):
                 ("Lc", ctypes.c_double), ("Lambda_s", ctypes.c_double),
                 ("Lambda_p", ctypes.c_double), ("Fx", ctypes.c_double), ("Fy", ctypes.c_double),
                 ("tile_tx", ctypes.c_int32), ("max_wall_nodes", ctypes.c_int32),
-                ("open_x", ctypes.c_int32)]
+                ("open_x", ctypes.c_int32), ("model", ctypes.c_int32), ("gtilde", ctypes.c_int32),
+                ("L2", ctypes.c_double)]
 
 
 class LbveError(RuntimeError):
@@ -272,7 +273,8 @@ def params_from(inst, precision: int = LBVE_FP64, tile_tx: int = 0) -> lbve_para
     return lbve_params(inst.nx, inst.ny, 1 if inst.periodic_y else 0, precision, inst.beta,
                        inst.Wi, inst.Re, inst.Sc, inst.Ma, inst.Lc, inst.Lambda_s, inst.Lambda_p,
                        inst.Fx, inst.Fy, tile_tx, walls,
-                       1 if getattr(inst, "open_x", False) else 0)
+                       1 if getattr(inst, "open_x", False) else 0, getattr(inst, "model", 0),
+                       getattr(inst, "gtilde", 0), getattr(inst, "L2", 0.0))
 
 
 class Simulation:

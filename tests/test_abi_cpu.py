@@ -125,3 +125,18 @@ def test_open_channel_validation(L):
     with pytest.raises(L.LbveError) as e:
         L.lbve_workspace_bytes([p])
     assert e.value.code == L.LBVE_ERR_ARG
+
+
+def test_model_validation(L):
+    """model in {0, 1, 2}, L2 > 2 for the FENE models, gtilde in {0, 1}."""
+    from paper_2508_16997_gb300 import workloads as wl
+    for model, L2, gt, ok in ((1, 10.0, 0, True), (2, 2.5, 1, True), (3, 10.0, 0, False),
+                              (1, 2.0, 0, False), (2, float("nan"), 0, False), (0, 0.0, 2, False)):
+        p = L.params_from(wl.frm(16))
+        p.model, p.L2, p.gtilde = model, L2, gt
+        if ok:
+            L.lbve_workspace_bytes([p])
+        else:
+            with pytest.raises(L.LbveError) as e:
+                L.lbve_workspace_bytes([p])
+            assert e.value.code == L.LBVE_ERR_ARG
