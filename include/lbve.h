@@ -276,8 +276,9 @@ int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps, 
  * (the reverse of each stage of the coupled step of Secs. 3.1-3.3: collisions,
  * source, finite-difference gradients, Zou-He and CNEBB completions, pull
  * streaming) with sqrt(n_steps) checkpointing and recomputation.
- * Instances with a solid mask or open in x are refused (LBVE_ERR_GEOMETRY), and
- * so are models other than Oldroyd-B and the eq_p_G form (LBVE_ERR_ARG).
+ * Instances open in x are refused (LBVE_ERR_GEOMETRY), and so are models
+ * other than Oldroyd-B and the eq_p_G form (LBVE_ERR_ARG); a solid mask is
+ * covered (see lbve_adjoint_step_ex).
  * The trajectory is the one that lbve_set_geometry(h, inst, NULL, <current
  * force of inst>, init_fields) followed by lbve_step(n_steps) produces; the
  * forward states are recomputed in the adjoint workspace (the instance's own
@@ -296,6 +297,27 @@ int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps, 
 int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* init_fields,
                       const double* d_dL_dfields, int64_t n_steps, void* d_ws, size_t bytes,
                       double* d_dL_dforce);
+
+/* The adjoint with the solid mask's losses and parameters: as
+ * lbve_adjoint_step(), with
+ *   d_dL_dfields : as there, or NULL for no field term;
+ *   dL_ddrag     : host float64 [2], dL/d(F_x, F_y) of the force on the solid
+ *                  over the last step (lbve_totals() out[12..13], eq_F_x), or
+ *                  NULL; needs a solid mask;
+ *   d_dL_dq      : device float64 [8][ny][nx] or NULL; written with dL/dq of
+ *                  each wall link's fraction q (plane i-1 at node k for the
+ *                  link (k, i) of lbve_set_wall_distances; zero elsewhere) --
+ *                  the gradient with respect to the wall geometry; needs a
+ *                  solid mask.
+ * At least one of d_dL_dfields and dL_ddrag must be given.  The forward
+ * states are recomputed with the wall pass; the reverse passes differentiate
+ * the interpolated bounce-back, CNEBB at the mask and the one-sided
+ * gradients next to solid nodes.
+ * Errors: as lbve_adjoint_step(); LBVE_ERR_GEOMETRY for drag or q gradients
+ * without a mask. */
+int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* init_fields,
+                         const double* d_dL_dfields, const double* dL_ddrag, int64_t n_steps,
+                         void* d_ws, size_t bytes, double* d_dL_dforce, double* d_dL_dq);
 
 /* Float64 sums of a macroscopic field array, computed WITHOUT ALLOCATING any
  * device memory.  The paper has no counterpart: this serves callers that

@@ -21,6 +21,13 @@ static AdjArgs<R> cast_args(const AdjArgsRaw& a) {
   A.lam_mh = (R*)a.lam_mh;
   A.lam_cur = (R*)a.lam_cur;
   A.dF = a.dF;
+  A.mask = a.mask;
+  A.widx = a.widx;
+  A.walls = a.walls;
+  A.dq = a.dq;
+  A.drag_w[0] = a.drag_w[0];
+  A.drag_w[1] = a.drag_w[1];
+  A.final_pass = a.final_pass;
   return A;
 }
 

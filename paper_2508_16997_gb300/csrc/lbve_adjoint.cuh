@@ -45,7 +45,94 @@ struct AdjArgs {
   R* lam_mh;          // [8][S]  direct lambda of the raw hydro moments
   R* lam_cur;         // [41][S] lambda_t
   double* dF;         // [2][n]  accumulated dL/dF
+  const uint8_t* mask;     // [S] solid nodes, or null (no mask)
+  const int32_t* widx;     // [S] wall record of a fluid node next to the mask, -1 if none
+  const WallDev* walls;    // the records (instance index 0)
+  double* dq;              // [8][n] accumulated dL/dq of the wall fractions, or null
+  double drag_w[2];        // dL/d(force on the solid) of the final step (final pass)
+  int final_pass;          // 1 in the pass that carries the loss
 };
+
+// D2Q9 velocities, opposites and weights for the mask code below.
+__device__ __forceinline__ constexpr int aex(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int aey(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int aopp(int i) {
+  return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i + 1) % 4 + 5);
+}
+__device__ __forceinline__ constexpr double awt(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// Node index of (x, y) with the periodic wraps; -1 outside a walled domain.
+__device__ __forceinline__ int adj_node(const InstDev& D, int x, int y) {
+  x = ((x % D.nx) + D.nx) % D.nx;
+  if (D.periodic_y) y = ((y % D.ny) + D.ny) % D.ny;
+  else if (y < 0 || y >= D.ny) return -1;
+  return y * D.nx + x;
+}
+__device__ __forceinline__ bool adj_solid(const uint8_t* M, int k) { return M && k >= 0 && M[k]; }
+__device__ __forceinline__ bool adj_fluid(const uint8_t* M, int k) { return k >= 0 && !(M && M[k]); }
+
+// Coefficients c[j + 2], j = -2..2, of the second-order difference along one
+// axis at fluid node (x, y): D q = sum_j c[j + 2] q(x + j e).  The same rule
+// as the forward step: central inside and across periodic wraps, one-sided on
+// wall rows (y), next to a solid node one-sided second order when two fluid
+// nodes lie on the fluid side, else first order, zero between two solids.
+__device__ __forceinline__ void diff_coefs(const InstDev& D, const uint8_t* M, int x, int y,
+                                           int axis, double c[5]) {
+  for (int j = 0; j < 5; ++j) c[j] = 0.0;
+  const int dx = axis == 0, dy = axis == 1;
+  if (axis == 1 && !D.periodic_y && (y == 0 || y == D.ny - 1)) {
+    if (y == 0) {
+      c[2] = -1.5; c[3] = 2.0; c[4] = -0.5;
+    } else {
+      c[2] = 1.5; c[1] = -2.0; c[0] = 0.5;
+    }
+    return;
+  }
+  const bool sp = adj_solid(M, adj_node(D, x + dx, y + dy));
+  const bool sm = adj_solid(M, adj_node(D, x - dx, y - dy));
+  if (!sp && !sm) {
+    c[1] = -0.5; c[3] = 0.5;
+  } else if (sp && sm) {
+    return;
+  } else if (sp) {
+    if (adj_fluid(M, adj_node(D, x - 2 * dx, y - 2 * dy))) {
+      c[2] = 1.5; c[1] = -2.0; c[0] = 0.5;
+    } else {
+      c[2] = 1.0; c[1] = -1.0;
+    }
+  } else {
+    if (adj_fluid(M, adj_node(D, x + 2 * dx, y + 2 * dy))) {
+      c[2] = -1.5; c[3] = 2.0; c[4] = -0.5;
+    } else {
+      c[2] = -1.0; c[3] = 1.0;
+    }
+  }
+}
+
+// Completed wall-link populations of a fluid node next to the mask:
+// interpolated bounce-back at wall fraction q from the raw state X.
+template <typename R>
+__device__ __forceinline__ R bouzidi(const InstDev& D, const R* X, const WallDev& W, int k, int x,
+                                     int y, int i) {
+  const int S = D.stride, ib = aopp(i);
+  const double q = W.q[i - 1];
+  const R fb = X[(size_t)ib * S + k];
+  if (q < 0.5) {
+    if ((W.fmask >> i) & 1) {
+      const int kf = adj_node(D, x + aex(i), y + aey(i));
+      return (R)(2.0 * q) * fb + (R)(1.0 - 2.0 * q) * X[(size_t)ib * S + kf];
+    }
+    return fb;
+  }
+  const double a = 1.0 / (2.0 * q);
+  return (R)a * fb + (R)(1.0 - a) * X[(size_t)i * S + k];
+}
 
 // Forward recompute at one node: completed hydro populations (deviations),
 // force, raw moments and rho, u.  kAdjInit takes the equilibria of the
@@ -67,6 +154,13 @@ __device__ __forceinline__ void adj_hydro_node(const InstDev& D, const AdjArgs<R
   } else {
     pull9<R>(A.X, S, y * nx, rm, rp, x, xm, xp, d);
     if (!py && (y == 0 || y == ny - 1)) zou_he<R>(d, Fx, Fy, y == 0);
+    if (A.widx && A.widx[k] >= 0) {
+      // the wall pass: interpolated bounce-back of the wall links
+      const WallDev& W = A.walls[A.widx[k]];
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        if ((W.umask >> i) & 1) d[i] = bouzidi<R>(D, A.X, W, k, x, y, i);
+    }
   }
   hydro_moments<R>(d, hm);
   rho = R(1) + hm.drho;
@@ -82,6 +176,11 @@ __global__ void adj_moments(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int x = k % D.nx, y = k / D.nx, S = D.stride;
+  if (A.mask && A.mask[k]) {  // solid: never read with a nonzero coefficient
+    A.M[k] = R(1);
+    A.M[S + k] = A.M[2 * S + k] = R(0);
+    return;
+  }
   R d[9], Fx, Fy, rho, ux, uy;
   HydroM<R> hm;
   adj_hydro_node<R, MODE>(D, A, x, y, d, Fx, Fy, hm, rho, ux, uy);
@@ -196,6 +295,59 @@ __device__ __forceinline__ void cnebb_T(const R d[9], R pa, R pb, R pc, R delta,
   lpost[2] += ldphi;
 }
 
+// CNEBB at a fluid node next to the mask (Sec. 3.3), unknown set U = umask,
+// as the wall pass does it: pm[i] (i in U) is the node's own post-collision
+// slot opposite i.
+template <typename R>
+__device__ __forceinline__ void cnebb_mask(R g[9], const R pm[9], R delta, R ubx, R uby,
+                                           int umask) {
+  R dphi = R(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dphi += (i != 0 && ((umask >> i) & 1)) ? pm[i] : g[i];
+  const R phib = delta + dphi;
+#pragma unroll
+  for (int i = 1; i < 9; ++i)
+    if ((umask >> i) & 1)
+      g[i] = g[aopp(i)] + (R)(6.0 * awt(i)) * phib * ((R)aex(i) * ubx + (R)aey(i) * uby);
+  R rest = R(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) rest += g[i];
+  g[0] = dphi - rest;
+}
+
+// Reverse of cnebb_mask(): from lambda of the completed populations lg,
+// add to lambda of the pulled known populations (ld), of the own posts
+// (lpm, i in U) and of u_b.  gp: the pulled populations before completion.
+template <typename R>
+__device__ __forceinline__ void cnebb_mask_T(const R gp[9], const R pm[9], R delta, R ubx, R uby,
+                                             int umask, const R lg[9], R ld[9], R lpm[9],
+                                             R& lubx, R& luby) {
+  R dphi = R(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dphi += (i != 0 && ((umask >> i) & 1)) ? pm[i] : gp[i];
+  const R phib = delta + dphi;
+  R ldphi = lg[0], lphib = R(0);  // g0 = dphi - sum_{i != 0} g_i
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const R lt = lg[i] - lg[0];
+    if ((umask >> i) & 1) {
+      const R a = (R)(6.0 * awt(i));
+      ld[aopp(i)] += lt;
+      lphib += a * ((R)aex(i) * ubx + (R)aey(i) * uby) * lt;
+      lubx += a * phib * (R)aex(i) * lt;
+      luby += a * phib * (R)aey(i) * lt;
+    } else {
+      ld[i] += lt;
+    }
+  }
+  ldphi += lphib;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    if (i != 0 && ((umask >> i) & 1)) lpm[i] += ldphi;
+    else ld[i] += ldphi;
+  }
+}
+
 // Pass 1: local reverse of the collision, source, history and CNEBB.
 template <typename R, int MODE>
 __global__ void adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
@@ -207,6 +359,24 @@ __global__ void adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   const bool py = D.periodic_y != 0;
   const bool wb = !py && y == 0, wt = !py && y == ny - 1;
   const bool walls = (MODE != kAdjInit) && (wb || wt);
+  if (A.mask && A.mask[k]) {
+    // a solid node takes no part: every lambda it would carry is zero
+#pragma unroll
+    for (int q = 9; q < 36; ++q) A.lam_pulled[(size_t)q * S + k] = R(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) A.lam_G[(size_t)j * S + k] = R(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) A.lam_dir[(size_t)j * S + k] = R(0);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) A.lam_mh[(size_t)j * S + k] = R(0);
+    if (MODE != kAdjInit) {
+#pragma unroll
+      for (int j = 0; j < 5; ++j) A.lam_cur[(size_t)(36 + j) * S + k] = R(0);
+    }
+    return;
+  }
+  const int wrec = (MODE != kAdjInit && A.widx) ? A.widx[k] : -1;  // wall record (mask)
+  const int umask = wrec >= 0 ? A.walls[wrec].umask : 0;
 
   // ---- forward recompute ----
   R d[9], Fx, Fy, rho, ux, uy;
@@ -215,7 +385,7 @@ __global__ void adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   int rm, rp;
   neighbour_rows(y, nx, ny, py, rm, rp);
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-  R g[3][9], gp[3][9], post[3][3];
+  R g[3][9], gp[3][9], post[3][3], pm[3][9];
   CdeM<R> cm[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
@@ -235,6 +405,15 @@ __global__ void adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
       double wi, wo;
       cnebb<R>(g[l], post[l][0], post[l][1], post[l][2], (l == 1) ? R(0) : R(1), ux, uy, wb, wi,
                wo);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) pm[l][i] = R(0);
+    if (umask) {
+      const R* own = A.X + (size_t)(9 + 9 * l) * S + k;
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        if ((umask >> i) & 1) pm[l][i] = own[(size_t)aopp(i) * S];
+      cnebb_mask<R>(g[l], pm[l], (l == 1) ? R(0) : R(1), ux, uy, umask);
     }
     cde_moments<R>(g[l], cm[l]);
   }
@@ -264,18 +443,29 @@ __global__ void adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
     const R* Mr = A.M;
     const R* Mx = A.M + S;
     const R* My = A.M + 2 * S;
-    const int kxm = y * nx + xm, kxp = y * nx + xp;
-    const R half = R(0.5);
-    const R G00 = half * (Mx[kxp] - Mx[kxm]);
-    const R G01 = half * (My[kxp] - My[kxm]);
-    const R dPx = half * (Mr[kxp] * Mx[kxp] * Mx[kxp] * Mx[kxp] -
-                          Mr[kxm] * Mx[kxm] * Mx[kxm] * Mx[kxm]);
-    R G10, G11, dPy;
+    // the step's difference rules (central, wall rows, next to solids)
+    R G00 = R(0), G01 = R(0), dPx = R(0), G10 = R(0), G11 = R(0), dPy = R(0);
     {
-      auto at = [&](int yy) { return ((yy % ny) + ny) % ny * nx + x; };
-      const int km2 = at(y - 2), km1 = at(y - 1), kp1 = at(y + 1), kp2 = at(y + 2);
-      y_gradients<R>(wb, wt, Mr[km2], Mx[km2], My[km2], Mr[km1], Mx[km1], My[km1], rho, ux, uy,
-                     Mr[kp1], Mx[kp1], My[kp1], Mr[kp2], Mx[kp2], My[kp2], G10, G11, dPy);
+      double cx[5], cy[5];
+      diff_coefs(D, A.mask, x, y, 0, cx);
+      diff_coefs(D, A.mask, x, y, 1, cy);
+#pragma unroll
+      for (int j = -2; j <= 2; ++j) {
+        if (cx[j + 2] != 0.0) {
+          const int kj = adj_node(D, x + j, y);
+          const R c = (R)cx[j + 2];
+          G00 += c * Mx[kj];
+          G01 += c * My[kj];
+          dPx += c * (Mr[kj] * Mx[kj] * Mx[kj] * Mx[kj]);
+        }
+        if (cy[j + 2] != 0.0) {
+          const int kj = adj_node(D, x, y + j);
+          const R c = (R)cy[j + 2];
+          G10 += c * Mx[kj];
+          G11 += c * My[kj];
+          dPy += c * (Mr[kj] * My[kj] * My[kj] * My[kj]);
+        }
+      }
     }
     const R Axx = R(1) + cm[0].dphi, Axy = cm[1].dphi, Ayy = R(1) + cm[2].dphi;
     const R mpl = coef<R>(D, kCoefMupLam), il = coef<R>(D, kCoefInvLam);
@@ -436,7 +626,17 @@ __global__ void adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
       moments_T<R>(lcm[l][0], lcm[l][1], lcm[l][2], lcm[l][3], lcm[l][4], lcm[l][5], R(0), R(0),
                    lg);
       R ld[9];
-      if (walls) {
+      if (umask) {
+        R lpm[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ld[i] = lpm[i] = R(0);
+        cnebb_mask_T<R>(gp[l], pm[l], (l == 1) ? R(0) : R(1), ux, uy, umask, lg, ld, lpm, lux,
+                        luy);
+        // unknown slots carry lambda of the own posts toward the wall
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          if ((umask >> i) & 1) ld[i] = lpm[i];
+      } else if (walls) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) ld[i] = R(0);
         R lpost[3] = {R(0), R(0), R(0)};
@@ -476,21 +676,6 @@ __global__ void adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   A.dF[n + k] += (double)lFy;
 }
 
-// Coefficient with which q(row yq) enters the y-derivative at row y of a
-// column (central inside, one-sided on wall rows).
-__device__ __forceinline__ double ycoef(int y, int yq, int ny, bool py) {
-  if (py) {
-    const int up = (y + 1) % ny, dn = (y - 1 + ny) % ny;
-    double c = 0.0;
-    if (yq == up) c += 0.5;
-    if (yq == dn) c -= 0.5;
-    return c;
-  }
-  if (y == 0) return yq == 0 ? -1.5 : (yq == 1 ? 2.0 : (yq == 2 ? -0.5 : 0.0));
-  if (y == ny - 1) return yq == y ? 1.5 : (yq == y - 1 ? -2.0 : (yq == y - 2 ? 0.5 : 0.0));
-  return yq == y + 1 ? 0.5 : (yq == y - 1 ? -0.5 : 0.0);
-}
-
 // Pass 2: gather the transposed gradient stencils, reverse u = (j + F/2)/rho
 // and the hydro moments, reverse Zou-He; writes lambda of the hydro pulls and
 // accumulates dL/dF.
@@ -502,41 +687,41 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   if (k >= n) return;
   const int x = k % nx, y = k / nx;
   const bool py = D.periodic_y != 0;
-  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  if (A.mask && A.mask[k]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) A.lam_pulled[(size_t)i * S + k] = R(0);
+    return;
+  }
   const R rho = A.M[k], ux = A.M[S + k], uy = A.M[2 * S + k];
   R lrho = A.lam_dir[k], lux = A.lam_dir[S + k], luy = A.lam_dir[2 * S + k];
-  // x stencils of the nodes left and right of this one: d/dx q(x) = (q(x+1) - q(x-1))/2
+  // transposed difference stencils: every fluid node kk within two nodes
+  // along an axis whose difference reads this node with coefficient c
   {
-    const int kl = y * nx + xm, kr = y * nx + xp;
-    // this node is the right neighbour of kl (+1/2) and the left neighbour of kr (-1/2)
-    R lc = R(0);
-    lux += R(0.5) * (A.lam_G[kl] - A.lam_G[kr]);
-    luy += R(0.5) * (A.lam_G[S + kl] - A.lam_G[S + kr]);
-    lc += R(0.5) * (A.lam_G[4 * S + kl] - A.lam_G[4 * S + kr]);
-    // c = rho ux^3
-    lrho += ux * ux * ux * lc;
-    lux += R(3) * rho * ux * ux * lc;
-  }
-  // y stencils of the nodes of this column that read this row
-  {
-    R lcy = R(0);
-    for (int dy = -2; dy <= 2; ++dy) {
-      int yy = y + dy;
-      if (py) {
-        yy = ((yy % ny) + ny) % ny;
-      } else if (yy < 0 || yy >= ny) {
-        continue;
+    R lcx = R(0), lcy = R(0);
+#pragma unroll
+    for (int axis = 0; axis < 2; ++axis)
+#pragma unroll
+      for (int j = -2; j <= 2; ++j) {
+        const int xk = x - (axis == 0 ? j : 0), yk = y - (axis == 1 ? j : 0);
+        const int kk = adj_node(D, xk, yk);
+        if (kk < 0 || (A.mask && A.mask[kk])) continue;
+        double c[5];
+        diff_coefs(D, A.mask, ((xk % nx) + nx) % nx, kk / nx, axis, c);
+        const R cj = (R)c[j + 2];
+        if (cj == R(0)) continue;
+        if (axis == 0) {
+          lux += cj * A.lam_G[kk];
+          luy += cj * A.lam_G[S + kk];
+          lcx += cj * A.lam_G[4 * S + kk];
+        } else {
+          lux += cj * A.lam_G[2 * S + kk];
+          luy += cj * A.lam_G[3 * S + kk];
+          lcy += cj * A.lam_G[5 * S + kk];
+        }
       }
-      if (py && dy != -1 && dy != 1) continue;  // periodic: central only
-      const double c = ycoef(yy, y, ny, py);
-      if (c == 0.0) continue;
-      const int kk = yy * nx + x;
-      lux += (R)c * A.lam_G[2 * S + kk];
-      luy += (R)c * A.lam_G[3 * S + kk];
-      lcy += (R)c * A.lam_G[5 * S + kk];
-    }
-    // cy = rho uy^3
-    lrho += uy * uy * uy * lcy;
+    // cx = rho ux^3, cy = rho uy^3
+    lrho += ux * ux * ux * lcx + uy * uy * uy * lcy;
+    lux += R(3) * rho * ux * ux * lcx;
     luy += R(3) * rho * uy * uy * lcy;
   }
   // u = (j + F/2) / rho, rho = 1 + drho
@@ -572,6 +757,14 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
       lFy += R(0.25) * (ld[7] + ld[8]);
       ld[4] = ld[7] = ld[8] = R(0);
     }
+    if (A.final_pass && A.widx && A.widx[k] >= 0) {
+      // the loss's share of the final step's force on the solid: e_ib (f^dagger_ib +
+      // f_i) over the wall links (eq_F_x); here the f_i part (the completed links)
+      const int um = A.walls[A.widx[k]].umask;
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        if ((um >> i) & 1) ld[i] -= (R)(A.drag_w[0] * aex(i) + A.drag_w[1] * aey(i));
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) A.lam_pulled[(size_t)i * S + k] = ld[i];
   }
@@ -579,38 +772,84 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   A.dF[n + k] += (double)lFy;
 }
 
-// Pass 3: reverse pull.  lambda_t(y, i) = lambda_pulled(y + e_i, i); at a wall
-// node the CDE slots that point at the wall take the lambda CNEBB stored in
-// the opposite (unknown) slot, and the hydro ones get nothing.
+// Pass 3: reverse pull.  lambda_t(y, i) = lambda_pulled(y + e_i, i).  A
+// population that leaves toward a flat wall or a solid node is not pulled by
+// anyone; instead:
+//   conformation lattices: CNEBB's lambda of the own post, kept in the
+//     opposite (unknown) slot of y;
+//   hydrodynamic lattice at a mask wall: the interpolated bounce-back
+//     weights -- 2q, 1 or 1/(2q) on the own opposite post -- plus, on the
+//     final pass, the loss's share of the force on the solid.
+// The interpolation's other operands add 1 - 1/(2q) (the own post in the
+// same direction, q >= 1/2) and 1 - 2q (the next node's post, q < 1/2), and
+// each wall link adds lambda of its completed population times dv/dq to
+// dL/dq.
 template <typename R>
 __global__ void adj_pull(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   const InstDev& D = *Dp;
-  const int nx = D.nx, ny = D.ny, S = D.stride, n = nx * ny;
+  const int nx = D.nx, S = D.stride, n = nx * D.ny;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int x = k % nx, y = k / nx;
-  const bool py = D.periodic_y != 0;
-  const int EXd[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-  const int EYd[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  const int OPPd[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  if (A.mask && A.mask[k]) {
+#pragma unroll
+    for (int q = 0; q < 36; ++q) A.lam_cur[(size_t)q * S + k] = R(0);
+    return;
+  }
+  const int wrec = A.widx ? A.widx[k] : -1;
+  const WallDev* W = wrec >= 0 ? &A.walls[wrec] : nullptr;
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      int xd = x + EXd[i];
-      xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
-      int yd = y + EYd[i];
+      const int kd = adj_node(D, x + aex(i), y + aey(i));
+      const R* lp = A.lam_pulled + (size_t)(9 * l) * S;
       R v = R(0);
-      if (py) {
-        yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
-        v = A.lam_pulled[(size_t)(9 * l + i) * S + yd * nx + xd];
-      } else if (yd >= 0 && yd < ny) {
-        v = A.lam_pulled[(size_t)(9 * l + i) * S + yd * nx + xd];
+      if (kd >= 0 && !(A.mask && A.mask[kd])) {
+        v = lp[(size_t)i * S + kd];
       } else if (l > 0) {
-        // direction i leaves the domain at this wall node: CNEBB's own slot
-        v = A.lam_pulled[(size_t)(9 * l + OPPd[i]) * S + k];
+        v = lp[(size_t)aopp(i) * S + k];  // CNEBB's own slot
+      } else if (kd >= 0 && W) {
+        // into the mask: the wall link aopp(i) of this node
+        const int j = aopp(i);
+        const double q = W->q[j - 1];
+        const double c = q < 0.5 ? (((W->fmask >> j) & 1) ? 2.0 * q : 1.0) : 1.0 / (2.0 * q);
+        v = (R)c * lp[(size_t)j * S + k];
+        if (A.final_pass) v += (R)(A.drag_w[0] * aex(i) + A.drag_w[1] * aey(i));
+      }
+      if (l == 0) {
+        // the "same direction" operand of this node's own link i (q >= 1/2)
+        if (W && i != 0 && ((W->umask >> i) & 1) && W->q[i - 1] >= 0.5)
+          v += (R)(1.0 - 1.0 / (2.0 * W->q[i - 1])) * lp[(size_t)i * S + k];
+        // the "next node" operand of the link aopp(i) of node k + e_i (q < 1/2)
+        if (i != 0 && kd >= 0 && A.widx && !(A.mask && A.mask[kd]) && A.widx[kd] >= 0) {
+          const WallDev& Wb = A.walls[A.widx[kd]];
+          const int j = aopp(i);
+          if (((Wb.umask >> j) & 1) && ((Wb.fmask >> j) & 1) && Wb.q[j - 1] < 0.5)
+            v += (R)(1.0 - 2.0 * Wb.q[j - 1]) * lp[(size_t)j * S + kd];
+        }
       }
       A.lam_cur[(size_t)(9 * l + i) * S + k] = v;
+    }
+  }
+  if (W && A.dq) {
+    // dL/dq of this node's wall links: lambda of the completed population
+    // times its derivative in q (the raw state X of this step)
+#pragma unroll
+    for (int j = 1; j < 9; ++j) {
+      if (!((W->umask >> j) & 1)) continue;
+      const double q = W->q[j - 1];
+      const double fb = (double)A.X[(size_t)aopp(j) * S + k];
+      double dv = 0.0;
+      if (q < 0.5) {
+        if ((W->fmask >> j) & 1) {
+          const int kf = adj_node(D, x + aex(j), y + aey(j));
+          dv = 2.0 * (fb - (double)A.X[(size_t)aopp(j) * S + kf]);
+        }
+      } else {
+        dv = ((double)A.X[(size_t)j * S + k] - fb) / (2.0 * q * q);
+      }
+      A.dq[(size_t)(j - 1) * n + k] += (double)A.lam_pulled[(size_t)j * S + k] * dv;
     }
   }
 }

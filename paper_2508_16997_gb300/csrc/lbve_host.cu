@@ -1274,11 +1274,18 @@ struct AdjPlan {
   int64_t T, s, nck;             // steps, checkpoint interval, checkpoints
   size_t state_bytes;            // one stored state: 41 planes
   size_t off_desc, off_tiles, off_partials, off_fields, off_stage, off_ck, off_seg, off_lam[2],
-      off_pulled, off_G, off_dir, off_mh, off_M, total;
+      off_pulled, off_G, off_dir, off_mh, off_M, off_zero, total;
+  // solid masks: the raw-state scratch the wall pass completes, the wall
+  // records and final-step records, each node's record, the masked tiles
+  int nwall, nmtiles;
+  size_t off_scratch, off_walls, off_wrec, off_widx, off_mtiles;
 };
 
-AdjPlan make_adj_plan(const lbve_params& p, const InstPlan& q, int64_t T) {
+AdjPlan make_adj_plan(const lbve_params& p, const InstPlan& q, int64_t T, int nwall = 0,
+                      int nmtiles = 0) {
   AdjPlan a;
+  a.nwall = nwall;
+  a.nmtiles = nmtiles;
   a.T = T;
   a.s = 1;
   while (a.s * a.s < T) ++a.s;
@@ -1306,6 +1313,15 @@ AdjPlan make_adj_plan(const lbve_params& p, const InstPlan& q, int64_t T) {
   a.off_dir = take(3 * plane);
   a.off_mh = take(8 * plane);
   a.off_M = take(3 * plane);
+  a.off_zero = take(sizeof(double) * 6 * q.stride);
+  a.off_scratch = a.off_walls = a.off_wrec = a.off_widx = a.off_mtiles = off;
+  if (nwall > 0) {
+    a.off_scratch = take(36 * plane);
+    a.off_walls = take(sizeof(WallDev) * nwall);
+    a.off_wrec = take(sizeof(double) * kWallRec * nwall);
+    a.off_widx = take(sizeof(int32_t) * q.stride);
+    a.off_mtiles = take(sizeof(TileDev) * std::max(nmtiles, 1));
+  }
   a.total = off;
   return a;
 }
@@ -1316,25 +1332,36 @@ extern "C" int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_
                                             size_t* bytes) {
   if (!h || !bytes || inst < 0 || inst >= h->n || n_steps < 1)
     return fail(LBVE_ERR_ARG, "bad handle, instance, step count or output pointer");
-  *bytes = make_adj_plan(h->p[inst], h->plan.inst[inst], n_steps).total;
+  *bytes = make_adj_plan(h->p[inst], h->plan.inst[inst], n_steps, (int)h->walls_of[inst].size(),
+                         (int)h->mtiles_of[inst].size())
+               .total;
   return LBVE_OK;
 }
 
-extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* init_fields,
-                                 const double* d_dL_dfields, int64_t n_steps, void* d_ws,
-                                 size_t bytes, double* d_dL_dforce) {
-  if (!h || inst < 0 || inst >= h->n || !d_dL_dfields || !d_dL_dforce || n_steps < 1)
+extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* init_fields,
+                                    const double* d_dL_dfields, const double* dL_ddrag,
+                                    int64_t n_steps, void* d_ws, size_t bytes,
+                                    double* d_dL_dforce, double* d_dL_dq) {
+  if (!h || inst < 0 || inst >= h->n || !d_dL_dforce || n_steps < 1)
     return fail(LBVE_ERR_ARG, "bad handle, instance, pointer or step count");
+  if (!d_dL_dfields && !dL_ddrag) return fail(LBVE_ERR_ARG, "no loss: dL/dfields and dL/ddrag are null");
   if (!h->ready[inst]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", inst);
-  if (h->insts[inst].mask || h->p[inst].open_x)
-    return fail(LBVE_ERR_GEOMETRY,
-                "the adjoint covers neither solid masks nor open channels (instance %d)", inst);
+  if (h->p[inst].open_x)
+    return fail(LBVE_ERR_GEOMETRY, "the adjoint does not cover open channels (instance %d)", inst);
   if (h->p[inst].model != 0 || h->p[inst].gtilde != 0)
     return fail(LBVE_ERR_ARG, "the adjoint covers Oldroyd-B with eq_p_G_1 only (instance %d)",
                 inst);
+  const bool masked = h->insts[inst].mask != nullptr;
+  if (!masked && (dL_ddrag || d_dL_dq))
+    return fail(LBVE_ERR_GEOMETRY, "drag and wall-fraction gradients need a solid mask");
+  if (dL_ddrag && !(std::isfinite(dL_ddrag[0]) && std::isfinite(dL_ddrag[1])))
+    return fail(LBVE_ERR_ARG, "dL/ddrag not finite");
   const lbve_params& p = h->p[inst];
   const InstPlan& q = h->plan.inst[inst];
-  const AdjPlan a = make_adj_plan(p, q, n_steps);
+  const std::vector<WallDev>& walls_h = h->walls_of[inst];
+  const std::vector<TileDev>& mtiles_h = h->mtiles_of[inst];
+  const AdjPlan a = make_adj_plan(p, q, n_steps, masked ? (int)walls_h.size() : 0,
+                                  masked ? (int)mtiles_h.size() : 0);
   if (!d_ws || bytes < a.total)
     return fail(LBVE_ERR_WORKSPACE, "adjoint workspace of %zu bytes given, %zu needed", bytes,
                 a.total);
@@ -1354,14 +1381,53 @@ extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* ini
   D.slot_begin = 0;
   D.slot_end = q.ntiles;
   std::vector<TileDev> tiles(q.ntiles);
+  std::vector<TileDev> mtiles;
   for (int ty = 0, k = 0; ty < q.nty; ++ty)
-    for (int tx = 0; tx < q.ntx; ++tx, ++k) tiles[k] = TileDev{0, tx * q.TX, ty * q.TY, k};
+    for (int tx = 0; tx < q.ntx; ++tx, ++k) {
+      // the handle's masked flags of this instance's tiles (same order)
+      const int mk = masked ? h->tiles_h[q.list][q.tile_begin + k].masked : 0;
+      tiles[k] = TileDev{0, tx * q.TX, ty * q.TY, k, mk};
+      if (mk) mtiles.push_back(tiles[k]);
+    }
   InstDev* d_desc = (InstDev*)(ws + a.off_desc);
   TileDev* d_tiles = (TileDev*)(ws + a.off_tiles);
   double* d_partials = (double*)(ws + a.off_partials);
   e = cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TileDev) * q.ntiles, cudaMemcpyHostToDevice,
                       st);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint tile upload");
+  // solid mask: the instance's wall records as instance 0, each node's record
+  TileDev* d_mtiles = (TileDev*)(ws + a.off_mtiles);
+  WallDev* d_walls = (WallDev*)(ws + a.off_walls);
+  int32_t* d_widx = (int32_t*)(ws + a.off_widx);
+  char* scratch = ws + a.off_scratch;
+  std::vector<WallDev> wcopy;
+  std::vector<int32_t> widx;
+  if (masked) {
+    wcopy = walls_h;
+    widx.assign(q.stride, -1);
+    for (size_t r = 0; r < wcopy.size(); ++r) {
+      wcopy[r].inst = 0;
+      widx[wcopy[r].k] = (int32_t)r;
+    }
+    if (!wcopy.empty())
+      e = cudaMemcpyAsync(d_walls, wcopy.data(), sizeof(WallDev) * wcopy.size(),
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_widx, widx.data(), sizeof(int32_t) * widx.size(),
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !mtiles.empty())
+      e = cudaMemcpyAsync(d_mtiles, mtiles.data(), sizeof(TileDev) * mtiles.size(),
+                          cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint mask tables");
+  }
+  const int nmt = (int)mtiles.size();
+  auto launch_tiles = [&](int mode, int flags) -> bool {
+    if (launch_step(prec, d_desc, d_tiles, q.ntiles, 0, mode, flags, d_partials, st)) return false;
+    if (nmt > 0 &&
+        launch_step(prec, d_desc, d_mtiles, nmt, 0, mode, flags, d_partials, st, 1))
+      return false;
+    return true;
+  };
   auto set_desc = [&](void* pop0, void* pop1, void* hist) -> cudaError_t {
     D.pop[0] = pop0;
     D.pop[1] = pop1;
@@ -1389,23 +1455,33 @@ extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* ini
   if (e != cudaSuccess) return cuda_fail(e, "adjoint initial-field upload");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "adjoint set-up");
 
-  // one forward step from state `from` into state `to` (history copied, then updated in place)
+  // one forward step from state `from` into state `to` (history copied, then
+  // updated in place).  With a mask the wall pass completes a scratch copy of
+  // `from`, so stored states stay raw (the reverse passes redo the completion).
   auto fwd = [&](char* from, char* to) -> int {
     cudaError_t ee = cudaMemcpyAsync(hist_of(to), hist_of(from), 5 * plane,
                                      cudaMemcpyDeviceToDevice, st);
     if (ee != cudaSuccess) return cuda_fail(ee, "adjoint history copy");
-    if ((ee = set_desc(state(from), state(to), hist_of(to))) != cudaSuccess)
+    char* src = state(from);
+    if (masked) {
+      ee = cudaMemcpyAsync(scratch, state(from), 36 * plane, cudaMemcpyDeviceToDevice, st);
+      if (ee != cudaSuccess) return cuda_fail(ee, "adjoint scratch copy");
+      src = scratch;
+    }
+    if ((ee = set_desc(src, state(to), hist_of(to))) != cudaSuccess)
       return cuda_fail(ee, "adjoint descriptor");
-    if (launch_step(prec, d_desc, d_tiles, q.ntiles, 0, kModeStep, 0, d_partials, st))
-      return cuda_fail(cudaGetLastError(), "adjoint forward step");
+    if (masked && !wcopy.empty() &&
+        launch_wall(prec, d_desc, d_walls, (double*)(ws + a.off_wrec), (int)wcopy.size(), 0, 0,
+                    st))
+      return cuda_fail(cudaGetLastError(), "adjoint wall pass");
+    if (!launch_tiles(kModeStep, 0)) return cuda_fail(cudaGetLastError(), "adjoint forward step");
     return LBVE_OK;
   };
 
   // ---- forward sweep: X_0 from the initial fields, checkpoints every s steps ----
   if ((e = set_desc(stage, state(ck), hist_of(ck))) != cudaSuccess)
     return cuda_fail(e, "adjoint descriptor");
-  if (launch_step(prec, d_desc, d_tiles, q.ntiles, 0, kModeInit, kFinal, d_partials, st))
-    return cuda_fail(cudaGetLastError(), "adjoint init step");
+  if (!launch_tiles(kModeInit, kFinal)) return cuda_fail(cudaGetLastError(), "adjoint init step");
   for (int64_t j = 1; j < a.nck; ++j) {
     // X_{j s} from X_{(j-1) s}: s steps through two rolling buffers of the segment area
     char* cur = ck + (j - 1) * a.state_bytes;
@@ -1430,6 +1506,27 @@ extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* ini
   A.dF = d_dL_dforce;
   if ((e = cudaMemsetAsync(d_dL_dforce, 0, sizeof(double) * 2 * nn, st)) != cudaSuccess)
     return cuda_fail(e, "gradient reset");
+  if (masked) {
+    A.mask = h->insts[inst].mask;
+    A.widx = d_widx;
+    A.walls = d_walls;
+  }
+  if (d_dL_dq) {
+    A.dq = d_dL_dq;
+    if ((e = cudaMemsetAsync(d_dL_dq, 0, sizeof(double) * 8 * nn, st)) != cudaSuccess)
+      return cuda_fail(e, "gradient reset");
+  }
+  if (dL_ddrag) {
+    A.drag_w[0] = dL_ddrag[0];
+    A.drag_w[1] = dL_ddrag[1];
+  }
+  // without a field loss the final pass reads zeros
+  const double* fields_seed = d_dL_dfields;
+  if (!fields_seed) {
+    fields_seed = (const double*)(ws + a.off_zero);
+    if ((e = cudaMemsetAsync(ws + a.off_zero, 0, sizeof(double) * 6 * S, st)) != cudaSuccess)
+      return cuda_fail(e, "adjoint seed");
+  }
   char* lam[2] = {ws + a.off_lam[0], ws + a.off_lam[1]};
   int li = 0;  // lam[li] holds lambda of the most recent (later) state
   const int n_nodes = (int)nn;
@@ -1458,12 +1555,14 @@ extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* ini
       if (first) {
         mode = kAdjFields;
         A.lam_next = nullptr;
-        A.lam_fields = d_dL_dfields;
+        A.lam_fields = fields_seed;
+        A.final_pass = 1;
         first = false;
       } else {
         mode = kAdjStep;
         A.lam_next = lam[li];
         A.lam_fields = nullptr;
+        A.final_pass = 0;
       }
       int rc = pass(mode, 0);
       if (!rc) rc = pass(mode, 1);
@@ -1480,10 +1579,19 @@ extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* ini
   A.lam_next = lam[li];
   A.lam_fields = nullptr;
   A.lam_cur = lam[li ^ 1];
+  A.final_pass = 0;
   int rc = pass(kAdjInit, 0);
   if (!rc) rc = pass(kAdjInit, 1);
   if (!rc) rc = pass(kAdjInit, 2);
   if (rc) return rc;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "lbve_adjoint_step");
   return LBVE_OK;
+}
+
+extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* init_fields,
+                                 const double* d_dL_dfields, int64_t n_steps, void* d_ws,
+                                 size_t bytes, double* d_dL_dforce) {
+  if (!d_dL_dfields) return fail(LBVE_ERR_ARG, "d_dL_dfields is null");
+  return lbve_adjoint_step_ex(h, inst, init_fields, d_dL_dfields, nullptr, n_steps, d_ws, bytes,
+                              d_dL_dforce, nullptr);
 }

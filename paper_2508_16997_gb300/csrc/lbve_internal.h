@@ -133,6 +133,15 @@ struct AdjArgsRaw {
   void* lam_mh;
   void* lam_cur;
   double* dF;
+  // solid masks (null without one): the mask, each node's wall record (-1 if
+  // none), the records (instance index 0), dL/dq [8][n] (or null), and the
+  // weights of the final step's force on the solid in the loss
+  const uint8_t* mask;
+  const int32_t* widx;
+  const WallDev* walls;
+  double* dq;
+  double drag_w[2];
+  int final_pass;
 };
 // pass: 0 moments, 1 local reverse, 2 gather, 3 reverse pull; mode: kAdjStep,
 // kAdjFields, kAdjInit (lbve_adjoint.cuh).

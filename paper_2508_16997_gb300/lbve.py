@@ -31,7 +31,8 @@ EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_st
             "lbve_status", "lbve_fields", "lbve_totals", "lbve_residual", "lbve_time",
             "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc",
             "lbve_adjoint_workspace_bytes", "lbve_adjoint_step", "lbve_state_bytes", "lbve_save",
-            "lbve_load", "lbve_autotune", "lbve_set_wall_distances", "lbve_set_inlet"]
+            "lbve_load", "lbve_autotune", "lbve_set_wall_distances", "lbve_set_inlet",
+            "lbve_adjoint_step_ex"]
 
 
 class lbve_params(ctypes.Structure):
@@ -83,6 +84,8 @@ def load() -> ctypes.CDLL:
                                                     ctypes.POINTER(ctypes.c_size_t)]
         L.lbve_adjoint_step.argtypes = [_vp, ctypes.c_int32, _dp, _vp, ctypes.c_int64, _vp,
                                         ctypes.c_size_t, _vp]
+        L.lbve_adjoint_step_ex.argtypes = [_vp, ctypes.c_int32, _dp, _vp, _dp, ctypes.c_int64,
+                                           _vp, ctypes.c_size_t, _vp, _vp]
         L.lbve_state_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
         L.lbve_save.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.lbve_load.argtypes = [_vp, _vp, ctypes.c_size_t]
@@ -227,6 +230,18 @@ def lbve_adjoint_step(h, inst: int, init_fields, d_dL_dfields: int, n_steps: int
     ini, ini_ptr = _f64(init_fields, 6 * n_nodes) if init_fields is not None else (None, None)
     _check(load().lbve_adjoint_step(h, inst, ini_ptr, _vp(d_dL_dfields), int(n_steps), _vp(d_ws),
                                     nbytes, _vp(d_dL_dforce)), "lbve_adjoint_step")
+
+
+def lbve_adjoint_step_ex(h, inst: int, init_fields, d_dL_dfields: int | None, dL_ddrag,
+                         n_steps: int, d_ws: int, nbytes: int, d_dL_dforce: int,
+                         d_dL_dq: int | None, n_nodes: int) -> None:
+    """Adjoint with an optional field loss (device pointer or None), drag loss
+    weights (2 floats or None) and an optional dL/dq output [8][ny][nx]."""
+    ini, ini_ptr = _f64(init_fields, 6 * n_nodes) if init_fields is not None else (None, None)
+    dr, dr_ptr = _f64(dL_ddrag, 2) if dL_ddrag is not None else (None, None)
+    _check(load().lbve_adjoint_step_ex(h, inst, ini_ptr, _vp(d_dL_dfields or 0), dr_ptr,
+                                       int(n_steps), _vp(d_ws), nbytes, _vp(d_dL_dforce),
+                                       _vp(d_dL_dq or 0)), "lbve_adjoint_step_ex")
 
 
 def lbve_state_bytes(h) -> int:
