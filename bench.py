@@ -502,6 +502,8 @@ def bench_cylinder(steps: int, stream) -> dict:
                      "mask_overhead": ms / ms_empty - 1.0,
                      "drag_x": float(tot[12]),
                      "Cd_start_up": float(tot[12]) / (Uc * Uc * 64.0),
+                     "note": "from rest: the drag stays 0 until the inlet's pressure wave "
+                             "reaches the cylinder (~960/c_s = 1660 steps)",
                      "time_steps": int(sim.time(0)),
                      "finite": bool((sim.status() == 0).all())}
         del sim, ref
