@@ -699,6 +699,7 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     D.cd[kCoefAfene] = p[i].model == 1 ? 1.0 / (1.0 - 2.0 / p[i].L2) : 1.0;
     D.model = p[i].model;
     D.gtilde = p[i].gtilde;
+    D.t32 = q.TX == kTileTX && (!p[i].periodic_y || p[i].ny >= kThreads / kTileTX + 2);
     for (int j = 0; j < kNumCoef; ++j) D.cf[j] = (float)D.cd[j];
     int k = q.tile_begin;
     for (int ty = 0; ty < q.nty; ++ty)

@@ -64,7 +64,9 @@ struct InstDev {
   int32_t prec, wall_cap;        // wall_cap: wall-node records of this instance
   const uint8_t* mask;           // [stride] 1 = solid node, or null (no mask)
   double* wall_rec;              // [wall_cap][kWallRec] final-step wall sums
-  int32_t open_x, pad2;          // open_x: inlet column x = 0, outlet x = nx - 1
+  int32_t open_x;                // inlet column x = 0, outlet x = nx - 1
+  int32_t t32;                   // tiles are kTileTX wide and rows wrap at most once
+                                 // inside a tile's halo region (plain tiles specialise)
   int32_t model, gtilde;         // constitutive model (0 Oldroyd-B, 1 FENE-P, 2 FENE-CR);
                                  // G~ form (0 eq_p_G_1, 1 eq_p_G)
   void* colbuf;                  // [36][2 ny] completed populations of the two open

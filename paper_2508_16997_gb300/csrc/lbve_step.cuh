@@ -307,6 +307,26 @@ __device__ __forceinline__ bool region_node(int lx, int ly, int x0, int y0, int 
   return gy >= 0 && gy < ny;
 }
 
+// v wrapped into [0, n) when it lies less than one period outside it.
+__device__ __forceinline__ int wrap_once(int v, int n) {
+  return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+// region_node for a kTileTX-wide tile of an instance with D.t32 set: its
+// halo columns x0-1 .. x0+kTileTX and (periodic) rows y0-2 .. y0+TY+1 lie
+// less than one period outside the domain (nx >= kTileTX; ny >= TY + 2 when
+// periodic), so one conditional wrap replaces the modulo.
+__device__ __forceinline__ bool region_node_once(int lx, int ly, int x0, int y0, int hy, int nx,
+                                                 int ny, bool py, int& gx, int& gy) {
+  gx = wrap_once(x0 - 1 + lx, nx);
+  gy = y0 - hy + ly;
+  if (py) {
+    gy = wrap_once(gy, ny);
+    return true;
+  }
+  return gy >= 0 && gy < ny;
+}
+
 // Source, both collisions, stores and final-step bookkeeping of one node
 // whose populations are already reduced to (wall-completed) moments:
 //   hm      raw hydro moments, cm[3] raw conformation moments
@@ -575,7 +595,18 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   // before any of them is used, so the tile's whole HBM traffic is in flight
   // together.  Own hydro and conformation populations are then reduced to
   // moments (walls completed first); rho and u go to shared memory.
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  // Thread and halo-slot indices.  For plain kTileTX-wide tiles (D.t32) the
+  // divisions by the width and the wraps use compile-time constants; the
+  // arithmetic after this prologue is one code path for every width.
+  const bool t32 = !MASKED && D.t32;
+  int tx, ty;
+  if (t32) {
+    tx = threadIdx.x % kTileTX;
+    ty = threadIdx.x / kTileTX;
+  } else {
+    tx = threadIdx.x % TX;
+    ty = threadIdx.x / TX;
+  }
   const bool in_tile = ty < TY;
   const int x = T.x0 + tx, y = T.y0 + ty;
   const bool inside = in_tile && (x < nx) && (y < ny);
@@ -594,8 +625,15 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   R dr[9];
   if (threadIdx.x < nring) {
     int lx, ly;
-    ring_slot(threadIdx.x, RW, TY, hy, lx, ly);
-    if (region_node(lx, ly, T.x0, T.y0, hy, nx, ny, py, rgx, rgy)) {
+    bool in_domain;
+    if (t32) {
+      ring_slot(threadIdx.x, kTileTX + 2, kThreads / kTileTX, hy, lx, ly);
+      in_domain = region_node_once(lx, ly, T.x0, T.y0, hy, nx, ny, py, rgx, rgy);
+    } else {
+      ring_slot(threadIdx.x, RW, TY, hy, lx, ly);
+      in_domain = region_node(lx, ly, T.x0, T.y0, hy, nx, ny, py, rgx, rgy);
+    }
+    if (in_domain) {
       ring_r = ly * RW + lx;
       if (MASKED && MODE == kModeStep && open_column(D, rgx)) {
         const R* cb = colbuf_node<R>(D, rgx, rgy);
@@ -703,7 +741,8 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   } else if (in_tile && !inside) {
     // slot outside the domain (ragged tile): it may still be a periodic
     // neighbour of an active node, so fill it with the wrapped node
-    const int gx = x % nx, gy = py ? y % ny : y;
+    const int gx = t32 ? wrap_once(x, nx) : x % nx;
+    const int gy = py ? (t32 ? wrap_once(y, ny) : y % ny) : y;
     if (gy < ny) {
       R r, vx, vy;
       if constexpr (MASKED)
