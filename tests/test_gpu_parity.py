@@ -49,13 +49,13 @@ def assert_fp64_parity(gpu, ref, tol=FP64_TOL, what=""):
     assert np.abs(gpu[0] - ref[0]).max() <= 1e-13, (what, err)
 
 
-def test_frm64_fp64_1000_steps(lbve):
+def test_frm64_fp64_2000_steps(lbve):
     """Four-roll mill 64^2, beta 0.5, Wi 5, Re 0.01, Sc 1e5, Ma 1e-3, FP64:
-    the small configuration, 1000 steps."""
+    the small configuration as specified, 2000 steps."""
     inst = wl.frm(64)
-    sim, (o,) = run_pair(lbve, [inst], 1000)
+    sim, (o,) = run_pair(lbve, [inst], 2000)
     assert_fp64_parity(sim.fields(0), o.fields(), what="frm64")
-    assert sim.time(0) == 1000
+    assert sim.time(0) == 2000
 
 
 def test_channel_fp64_walls(lbve):
