@@ -67,10 +67,25 @@ __device__ __forceinline__ constexpr double awt(int i) {
   return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
-// Node index of (x, y) with the periodic wraps; -1 outside a walled domain.
+// v wrapped into [0, n) when it lies at most two nodes outside (every caller
+// offsets an in-domain coordinate by -2..2): at most two corrections, even
+// for n = 1.
+__device__ __forceinline__ int adj_wrap(int v, int n) {
+  if (v < 0) {
+    v += n;
+    if (v < 0) v += n;
+  } else if (v >= n) {
+    v -= n;
+    if (v >= n) v -= n;
+  }
+  return v;
+}
+
+// Node index of (x, y), x and y at most two nodes outside the domain, with
+// the periodic wraps; -1 outside a walled domain.
 __device__ __forceinline__ int adj_node(const InstDev& D, int x, int y) {
-  x = ((x % D.nx) + D.nx) % D.nx;
-  if (D.periodic_y) y = ((y % D.ny) + D.ny) % D.ny;
+  x = adj_wrap(x, D.nx);
+  if (D.periodic_y) y = adj_wrap(y, D.ny);
   else if (y < 0 || y >= D.ny) return -1;
   return y * D.nx + x;
 }
@@ -349,8 +364,11 @@ __device__ __forceinline__ void cnebb_mask_T(const R gp[9], const R pm[9], R del
 }
 
 // Pass 1: local reverse of the collision, source, history and CNEBB.
+// float32: a budget of 128 registers (two CTAs per SM) trades a few spills
+// for twice the warps in flight; float64 keeps its full register file.
 template <typename R, int MODE>
-__global__ void adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
+    adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   const InstDev& D = *Dp;
   const int nx = D.nx, ny = D.ny, S = D.stride, n = nx * ny;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -706,7 +724,7 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
         const int kk = adj_node(D, xk, yk);
         if (kk < 0 || (A.mask && A.mask[kk])) continue;
         double c[5];
-        diff_coefs(D, A.mask, ((xk % nx) + nx) % nx, kk / nx, axis, c);
+        diff_coefs(D, A.mask, adj_wrap(xk, nx), kk / nx, axis, c);
         const R cj = (R)c[j + 2];
         if (cj == R(0)) continue;
         if (axis == 0) {
