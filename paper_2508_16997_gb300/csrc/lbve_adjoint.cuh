@@ -463,7 +463,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     const R* My = A.M + 2 * S;
     // the step's difference rules (central, wall rows, next to solids)
     R G00 = R(0), G01 = R(0), dPx = R(0), G10 = R(0), G11 = R(0), dPy = R(0);
-    {
+    if (!A.mask && !wb && !wt) {
+      // central differences along both axes: the general rule's result, term
+      // by term in the same order, without looking the rule up
+      const int kxm = y * nx + adj_wrap(x - 1, nx), kxp = y * nx + adj_wrap(x + 1, nx);
+      const int kym = adj_node(D, x, y - 1), kyp = adj_node(D, x, y + 1);
+      const R cm_ = R(-0.5), cp_ = R(0.5);
+      G00 += cm_ * Mx[kxm];
+      G01 += cm_ * My[kxm];
+      dPx += cm_ * (Mr[kxm] * Mx[kxm] * Mx[kxm] * Mx[kxm]);
+      G10 += cm_ * Mx[kym];
+      G11 += cm_ * My[kym];
+      dPy += cm_ * (Mr[kym] * My[kym] * My[kym] * My[kym]);
+      G00 += cp_ * Mx[kxp];
+      G01 += cp_ * My[kxp];
+      dPx += cp_ * (Mr[kxp] * Mx[kxp] * Mx[kxp] * Mx[kxp]);
+      G10 += cp_ * Mx[kyp];
+      G11 += cp_ * My[kyp];
+      dPy += cp_ * (Mr[kyp] * My[kyp] * My[kyp] * My[kyp]);
+    } else {
       double cx[5], cy[5];
       diff_coefs(D, A.mask, x, y, 0, cx);
       diff_coefs(D, A.mask, x, y, 1, cy);
@@ -716,6 +734,25 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   // along an axis whose difference reads this node with coefficient c
   {
     R lcx = R(0), lcy = R(0);
+    if (!A.mask && (py || (y >= 3 && y <= ny - 4))) {
+      // every stencil reaching this node is central (no mask, no wall row
+      // within two rows): the general loop's terms in the same order
+      const int kxp = y * nx + adj_wrap(x + 1, nx), kxm = y * nx + adj_wrap(x - 1, nx);
+      const int kyp = adj_node(D, x, y + 1), kym = adj_node(D, x, y - 1);
+      const R cm_ = R(-0.5), cp_ = R(0.5);
+      lux += cm_ * A.lam_G[kxp];
+      luy += cm_ * A.lam_G[S + kxp];
+      lcx += cm_ * A.lam_G[4 * S + kxp];
+      lux += cp_ * A.lam_G[kxm];
+      luy += cp_ * A.lam_G[S + kxm];
+      lcx += cp_ * A.lam_G[4 * S + kxm];
+      lux += cm_ * A.lam_G[2 * S + kyp];
+      luy += cm_ * A.lam_G[3 * S + kyp];
+      lcy += cm_ * A.lam_G[5 * S + kyp];
+      lux += cp_ * A.lam_G[2 * S + kym];
+      luy += cp_ * A.lam_G[3 * S + kym];
+      lcy += cp_ * A.lam_G[5 * S + kym];
+    } else {
 #pragma unroll
     for (int axis = 0; axis < 2; ++axis)
 #pragma unroll
@@ -737,6 +774,7 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
           lcy += cj * A.lam_G[5 * S + kk];
         }
       }
+    }
     // cx = rho ux^3, cy = rho uy^3
     lrho += ux * ux * ux * lcx + uy * uy * uy * lcy;
     lux += R(3) * rho * ux * ux * lcx;
@@ -816,6 +854,10 @@ __global__ void adj_pull(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   }
   const int wrec = A.widx ? A.widx[k] : -1;
   const WallDev* W = wrec >= 0 ? &A.walls[wrec] : nullptr;
+  // every value is gathered before the first store: lam_cur and lam_pulled
+  // are distinct buffers, but the compiler cannot know it, and interleaved
+  // stores would hold each load back behind the previous one
+  R vals[36];
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
 #pragma unroll
@@ -847,9 +889,11 @@ __global__ void adj_pull(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
             v += (R)(1.0 - 2.0 * Wb.q[j - 1]) * lp[(size_t)j * S + kd];
         }
       }
-      A.lam_cur[(size_t)(9 * l + i) * S + k] = v;
+      vals[9 * l + i] = v;
     }
   }
+#pragma unroll
+  for (int q = 0; q < 36; ++q) A.lam_cur[(size_t)q * S + k] = vals[q];
   if (W && A.dq) {
     // dL/dq of this node's wall links: lambda of the completed population
     // times its derivative in q (the raw state X of this step)
