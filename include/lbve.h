@@ -271,6 +271,19 @@ int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes);
  * recomputed segment of stored states, plus the adjoint fields).  Host only. */
 int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps, size_t* bytes);
 
+/* Bytes of adjoint workspace for a checkpoint interval of `interval` steps
+ * (1 <= interval <= n_steps): ceil(n_steps/interval) stored states plus a
+ * recomputed segment of `interval` states.  The paper has no counterpart:
+ * it trades memory for recomputation.  lbve_adjoint_step() takes the
+ * shortest interval whose workspace fits the bytes it is given, so a caller
+ * with memory to spare passes more: interval 1 stores every forward state and
+ * recomputes none (about n_steps x 41 planes of the storage precision).  The
+ * gradient does not depend on the interval (every state is recomputed by the
+ * same step from the same predecessor).  Host only.
+ * Errors: LBVE_ERR_ARG. */
+int lbve_adjoint_workspace_bytes_interval(lbve_handle* h, int32_t inst, int64_t n_steps,
+                                          int64_t interval, size_t* bytes);
+
 /* Gradient of a loss L on the fields at time n_steps with respect to the
  * per-node body force of instance inst, by a discrete adjoint of every step
  * (the reverse of each stage of the coupled step of Secs. 3.1-3.3: collisions,
@@ -288,7 +301,9 @@ int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps, 
  *   d_dL_dfields : device float64 [6][ny][nx], dL/d(rho, ux, uy, Axx, Axy, Ayy)
  *                  at time n_steps
  *   d_ws, bytes  : device workspace >= lbve_adjoint_workspace_bytes(), 256-byte
- *                  aligned, owned by the caller
+ *                  aligned, owned by the caller; the shortest checkpoint
+ *                  interval (down to 1) whose workspace fits `bytes` is used
+ *                  (lbve_adjoint_workspace_bytes_interval)
  *   d_dL_dforce  : device float64 [2][ny][nx], overwritten with dL/dF (the
  *                  derivative with respect to a per-node force, also when the
  *                  instance uses a uniform force)

@@ -1282,14 +1282,22 @@ struct AdjPlan {
   size_t off_scratch, off_walls, off_wrec, off_widx, off_mtiles;
 };
 
+// The square-root checkpoint interval: ceil(sqrt(T)).
+int64_t sqrt_interval(int64_t T) {
+  int64_t s = 1;
+  while (s * s < T) ++s;
+  return s;
+}
+
+// Workspace plan of the adjoint for T steps with checkpoints every `interval`
+// steps (0: the square-root interval).
 AdjPlan make_adj_plan(const lbve_params& p, const InstPlan& q, int64_t T, int nwall = 0,
-                      int nmtiles = 0) {
+                      int nmtiles = 0, int64_t interval = 0) {
   AdjPlan a;
   a.nwall = nwall;
   a.nmtiles = nmtiles;
   a.T = T;
-  a.s = 1;
-  while (a.s * a.s < T) ++a.s;
+  a.s = interval > 0 ? interval : sqrt_interval(T);
   a.nck = (T + a.s - 1) / a.s;
   const size_t es = p.precision == LBVE_FP64 ? 8 : 4;
   const size_t plane = size_t(q.stride) * es;
@@ -1339,6 +1347,18 @@ extern "C" int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_
   return LBVE_OK;
 }
 
+extern "C" int lbve_adjoint_workspace_bytes_interval(lbve_handle* h, int32_t inst,
+                                                     int64_t n_steps, int64_t interval,
+                                                     size_t* bytes) {
+  if (!h || !bytes || inst < 0 || inst >= h->n || n_steps < 1 || interval < 1 ||
+      interval > n_steps)
+    return fail(LBVE_ERR_ARG, "bad handle, instance, step count, interval or output pointer");
+  *bytes = make_adj_plan(h->p[inst], h->plan.inst[inst], n_steps, (int)h->walls_of[inst].size(),
+                         (int)h->mtiles_of[inst].size(), interval)
+               .total;
+  return LBVE_OK;
+}
+
 extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* init_fields,
                                     const double* d_dL_dfields, const double* dL_ddrag,
                                     int64_t n_steps, void* d_ws, size_t bytes,
@@ -1361,8 +1381,18 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
   const InstPlan& q = h->plan.inst[inst];
   const std::vector<WallDev>& walls_h = h->walls_of[inst];
   const std::vector<TileDev>& mtiles_h = h->mtiles_of[inst];
-  const AdjPlan a = make_adj_plan(p, q, n_steps, masked ? (int)walls_h.size() : 0,
-                                  masked ? (int)mtiles_h.size() : 0);
+  // the shortest checkpoint interval whose plan fits the workspace given
+  // (the square-root interval needs the least)
+  const int nw = masked ? (int)walls_h.size() : 0, nm = masked ? (int)mtiles_h.size() : 0;
+  const int64_t s_max = sqrt_interval(n_steps);
+  AdjPlan a = make_adj_plan(p, q, n_steps, nw, nm, s_max);
+  for (int64_t s = 1; s < s_max; ++s) {
+    const AdjPlan b = make_adj_plan(p, q, n_steps, nw, nm, s);
+    if (b.total <= bytes) {
+      a = b;
+      break;
+    }
+  }
   if (!d_ws || bytes < a.total)
     return fail(LBVE_ERR_WORKSPACE, "adjoint workspace of %zu bytes given, %zu needed", bytes,
                 a.total);
@@ -1539,15 +1569,19 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
   bool first = true;  // the last state carries the loss
   for (int64_t j = a.nck - 1; j >= 0; --j) {
     const int64_t m0 = j * a.s, m1 = std::min<int64_t>((j + 1) * a.s, a.T);  // states m0..m1-1
-    // recompute the segment's states into seg[0 .. m1-m0-1]
-    e = cudaMemcpyAsync(seg, ck + j * a.state_bytes, a.state_bytes, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "adjoint checkpoint copy");
+    // recompute the segment's states into seg[0 .. m1-m0-1] (with interval 1
+    // every state is a checkpoint and is read in place)
+    if (a.s > 1) {
+      e = cudaMemcpyAsync(seg, ck + j * a.state_bytes, a.state_bytes, cudaMemcpyDeviceToDevice,
+                          st);
+      if (e != cudaSuccess) return cuda_fail(e, "adjoint checkpoint copy");
+    }
     for (int64_t m = m0 + 1; m < m1; ++m) {
       const int rc = fwd(seg + (m - 1 - m0) * a.state_bytes, seg + (m - m0) * a.state_bytes);
       if (rc) return rc;
     }
     for (int64_t m = m1 - 1; m >= m0; --m) {
-      char* X = seg + (m - m0) * a.state_bytes;
+      char* X = a.s > 1 ? seg + (m - m0) * a.state_bytes : ck + j * a.state_bytes;
       if ((e = set_desc(state(X), state(X), hist_of(X))) != cudaSuccess)
         return cuda_fail(e, "adjoint descriptor");
       A.X = X;

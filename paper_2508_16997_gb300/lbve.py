@@ -32,7 +32,7 @@ EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_st
             "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc",
             "lbve_adjoint_workspace_bytes", "lbve_adjoint_step", "lbve_state_bytes", "lbve_save",
             "lbve_load", "lbve_autotune", "lbve_set_wall_distances", "lbve_set_inlet",
-            "lbve_adjoint_step_ex"]
+            "lbve_adjoint_step_ex", "lbve_adjoint_workspace_bytes_interval"]
 
 
 class lbve_params(ctypes.Structure):
@@ -82,6 +82,9 @@ def load() -> ctypes.CDLL:
         L.lbve_field_totals_noalloc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
         L.lbve_adjoint_workspace_bytes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64,
                                                     ctypes.POINTER(ctypes.c_size_t)]
+        L.lbve_adjoint_workspace_bytes_interval.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64,
+                                                            ctypes.c_int64,
+                                                            ctypes.POINTER(ctypes.c_size_t)]
         L.lbve_adjoint_step.argtypes = [_vp, ctypes.c_int32, _dp, _vp, ctypes.c_int64, _vp,
                                         ctypes.c_size_t, _vp]
         L.lbve_adjoint_step_ex.argtypes = [_vp, ctypes.c_int32, _dp, _vp, _dp, ctypes.c_int64,
@@ -222,6 +225,14 @@ def lbve_adjoint_workspace_bytes(h, inst: int, n_steps: int) -> int:
     out = ctypes.c_size_t()
     _check(load().lbve_adjoint_workspace_bytes(h, inst, int(n_steps), ctypes.byref(out)),
            "lbve_adjoint_workspace_bytes")
+    return out.value
+
+
+def lbve_adjoint_workspace_bytes_interval(h, inst: int, n_steps: int, interval: int) -> int:
+    out = ctypes.c_size_t()
+    _check(load().lbve_adjoint_workspace_bytes_interval(h, inst, int(n_steps), int(interval),
+                                                        ctypes.byref(out)),
+           "lbve_adjoint_workspace_bytes_interval")
     return out.value
 
 
