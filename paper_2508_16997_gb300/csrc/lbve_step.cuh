@@ -31,7 +31,7 @@
 #include "lbve_internal.h"
 
 #ifndef LBVE_FP32_MIN_BLOCKS
-#define LBVE_FP32_MIN_BLOCKS 3
+#define LBVE_FP32_MIN_BLOCKS 7
 #endif
 
 namespace lbve {
@@ -505,7 +505,8 @@ __device__ __forceinline__ R y_drho(bool wb, bool wt, R rm2, R rm1, R r0, R rp1,
 // the FP64 pipe.
 template <typename R>
 struct MinBlocks {
-  static constexpr int value = sizeof(R) == 4 ? LBVE_FP32_MIN_BLOCKS : (kThreads <= 256 ? 2 : 1);
+  static constexpr int value =
+      sizeof(R) == 4 ? LBVE_FP32_MIN_BLOCKS : (kThreads <= 256 ? 512 / kThreads : 1);
 };
 
 // One-sided differences along one axis next to the solid mask (same rule as

@@ -85,11 +85,11 @@ def test_tile_width_validation_and_layout(L):
     from paper_2508_16997_gb300 import workloads as wl
     base = [L.params_from(wl.frm(130)), L.params_from(wl.channel(33, nx=20), L.LBVE_FP32_DEV)]
     n0 = L.lbve_workspace_bytes(base)
-    for tx in (1, 3, 8, 16, 20, 64, 128):
+    for tx in (1, 3, 8, 16, 20, 48):
         p = [L.params_from(wl.frm(130), tile_tx=tx),
              L.params_from(wl.channel(33, nx=20), L.LBVE_FP32_DEV, tile_tx=min(tx, 20))]
         assert L.lbve_workspace_bytes(p) == n0
-    for bad_tx in (-1, 129, 131):
+    for bad_tx in (-1, 49, 131):
         with pytest.raises(L.LbveError) as e:
             L.lbve_workspace_bytes([L.params_from(wl.frm(256), tile_tx=bad_tx)])
         assert e.value.code == L.LBVE_ERR_ARG
