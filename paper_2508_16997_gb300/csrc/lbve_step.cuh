@@ -72,13 +72,18 @@ __device__ __forceinline__ void cde_moments(const R d[9], CdeM<R>& m) {
 // Rebuild the nine (deviation) populations from Hermite coefficients:
 //   d_i = w_i [ b0' + 3 e.b + 4.5 (H_xx bxx + 2 H_xy bxy + H_yy byy)
 //               + 13.5 (H_xxy bxxy + H_xyy bxyy) ]
-// with b0' the zeroth coefficient minus the rest value.
+// with b0' the zeroth coefficient minus the rest value.  The rest population
+// is taken as b0' minus the other eight, which equals its formula in exact
+// arithmetic and keeps sum_i d_i = b0' up to unbiased rounding.  Evaluated
+// from the formula, the rounded weights would scale the zeroth moment by
+// sum_i fl(w_i) = 1 + 7.5e-9 (float32) at every collision; that bias
+// accumulates over a conformation lattice's relaxation time (lambda steps)
+// into an error proportional to Wi.
 template <typename R>
 __device__ __forceinline__ void reconstruct(R b0p, R bx, R by, R bxx, R byy, R bxy, R bxxy,
                                             R bxyy, R out[9]) {
-  const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+  const R w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
   const R s = bxx + byy;
-  out[0] = w0 * (b0p - R(1.5) * s);
   const R b13 = b0p + R(3.0) * bxx - R(1.5) * byy;
   const R o13 = R(3.0) * bx - R(4.5) * bxyy;
   out[1] = w1 * (b13 + o13);
@@ -95,6 +100,7 @@ __device__ __forceinline__ void reconstruct(R b0p, R bx, R by, R bxx, R byy, R b
   out[7] = w5 * ((bd + xy9) - o57);
   out[6] = w5 * ((bd - xy9) + o68);
   out[8] = w5 * ((bd - xy9) - o68);
+  out[0] = b0p - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
 }
 
 // Pull the nine populations of one lattice arriving at (x, y): d_i(x) =
