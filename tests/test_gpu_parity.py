@@ -138,13 +138,13 @@ def test_fp32_dev_frm(lbve):
 
 @pytest.mark.parametrize("Wi", [1.0, 10.0, 100.0])
 def test_fp32_dev_channel(lbve, Wi):
-    """FP32 deviation storage on the Oldroyd-B channel (H = 32) for Wi <= 100.
-
-    The stated 1e-5 bound holds after 1000 steps.  Beyond that the float32
-    rounding of the conformation lattices accumulates a drift of about
-    6e-9 per step in C (measured against the FP64 path for H = 64, Wi = 1 to
-    1e4, 500 to 32000 steps), so after 4000 steps the test asserts the
-    drift bound 1e-8 per step instead; long runs that need 1e-5 keep FP64."""
+    """FP32 deviation storage on the Oldroyd-B channel (H = 32) for Wi <= 100:
+    within the stated 1e-5 of the FP64 oracle after 1000 and after 8000
+    steps.  The second check guards the closure of the rest population in
+    the reconstruction: evaluated from its rounded weights instead, the
+    float32 zeroth moment of each conformation lattice grew by 7.5e-9 per
+    step, and C left 1e-5 after a few thousand steps at Wi >= 10 (measured
+    against the FP64 path for H = 64)."""
     inst = wl.channel(32, nx=4, Wi=Wi)
     sim = lbve.Simulation([inst], precision=1)
     o = oracle_sim(inst)
@@ -152,10 +152,10 @@ def test_fp32_dev_channel(lbve, Wi):
     o.step(1000)
     err = parity_errors(sim.fields(0), o.fields())
     assert err["u"] <= FP32_TOL and err["C"] <= FP32_TOL, err
-    sim.step(3000)
-    o.step(3000)
+    sim.step(7000)
+    o.step(7000)
     err = parity_errors(sim.fields(0), o.fields())
-    assert err["u"] <= 4000 * 1e-8 and err["C"] <= 4000 * 1e-8, err
+    assert err["u"] <= FP32_TOL and err["C"] <= FP32_TOL, err
 
 
 def test_status_flags_nonfinite(lbve):
