@@ -72,18 +72,20 @@ __device__ __forceinline__ void cde_moments(const R d[9], CdeM<R>& m) {
 // Rebuild the nine (deviation) populations from Hermite coefficients:
 //   d_i = w_i [ b0' + 3 e.b + 4.5 (H_xx bxx + 2 H_xy bxy + H_yy byy)
 //               + 13.5 (H_xxy bxxy + H_xyy bxyy) ]
-// with b0' the zeroth coefficient minus the rest value.  The rest population
-// is taken as b0' minus the other eight, which equals its formula in exact
-// arithmetic and keeps sum_i d_i = b0' up to unbiased rounding.  Evaluated
-// from the formula, the rounded weights would scale the zeroth moment by
-// sum_i fl(w_i) = 1 + 7.5e-9 (float32) at every collision; that bias
+// with b0' the zeroth coefficient minus the rest value.  In float32 the rest
+// population is taken as b0' minus the other eight, which equals its formula
+// in exact arithmetic and keeps sum_i d_i = b0' up to unbiased rounding.
+// Evaluated from the formula, the rounded weights would scale the zeroth
+// moment by sum_i fl(w_i) = 1 + 7.5e-9 at every collision; that bias
 // accumulates over a conformation lattice's relaxation time (lambda steps)
-// into an error proportional to Wi.
+// into an error proportional to Wi.  In float64 the same bias is ~1e-17 and
+// the formula is kept (the float64 step is bound by the FP64 pipe).
 template <typename R>
 __device__ __forceinline__ void reconstruct(R b0p, R bx, R by, R bxx, R byy, R bxy, R bxxy,
                                             R bxyy, R out[9]) {
-  const R w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+  const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
   const R s = bxx + byy;
+  if constexpr (sizeof(R) == 8) out[0] = w0 * (b0p - R(1.5) * s);
   const R b13 = b0p + R(3.0) * bxx - R(1.5) * byy;
   const R o13 = R(3.0) * bx - R(4.5) * bxyy;
   out[1] = w1 * (b13 + o13);
@@ -100,7 +102,8 @@ __device__ __forceinline__ void reconstruct(R b0p, R bx, R by, R bxx, R byy, R b
   out[7] = w5 * ((bd + xy9) - o57);
   out[6] = w5 * ((bd - xy9) + o68);
   out[8] = w5 * ((bd - xy9) - o68);
-  out[0] = b0p - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
+  if constexpr (sizeof(R) == 4)
+    out[0] = b0p - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
 }
 
 // Pull the nine populations of one lattice arriving at (x, y): d_i(x) =
@@ -509,10 +512,16 @@ __device__ __forceinline__ R y_drho(bool wb, bool wt, R rm2, R rm1, R r0, R rp1,
 // Resident CTAs per SM the register budget is sized for: the float32 step
 // is HBM-bound and wants more loads in flight; the float64 step is bound by
 // the FP64 pipe.
-template <typename R>
+// Masked tiles carry the mask's one-sided differences: a budget of 5 CTAs
+// per SM lets them keep their registers without spills.
+#ifndef LBVE_FP32_MASKED_MIN_BLOCKS
+#define LBVE_FP32_MASKED_MIN_BLOCKS 5
+#endif
+template <typename R, bool MASKED>
 struct MinBlocks {
   static constexpr int value =
-      sizeof(R) == 4 ? LBVE_FP32_MIN_BLOCKS : (kThreads <= 256 ? 512 / kThreads : 1);
+      sizeof(R) == 4 ? (MASKED ? LBVE_FP32_MASKED_MIN_BLOCKS : LBVE_FP32_MIN_BLOCKS)
+                     : (kThreads <= 256 ? 512 / kThreads : 1);
 };
 
 // One-sided differences along one axis next to the solid mask (same rule as
@@ -892,7 +901,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
 // One CTA per tile.  The plain variant leaves masked tiles to the masked one
 // (which runs over a separate list of just those tiles).
 template <typename R, int MODE, bool FINAL, bool MASKED>
-__global__ void __launch_bounds__(kThreads, MinBlocks<R>::value)
+__global__ void __launch_bounds__(kThreads, MinBlocks<R, MASKED>::value)
     step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles,
                 int parity, double* __restrict__ partials) {
   __shared__ R s_rho[kRegionMax];
