@@ -140,3 +140,28 @@ def test_model_validation(L):
             with pytest.raises(L.LbveError) as e:
                 L.lbve_workspace_bytes([p])
             assert e.value.code == L.LBVE_ERR_ARG
+
+
+def test_empty_degenerate_and_maximum_sizes(L):
+    """An empty batch and a zero-width grid are rejected; the largest grid
+    (2^25 nodes, which keeps 36 planes of indices in int32) is sized without
+    overflow, and one node more is rejected."""
+    from paper_2508_16997_gb300 import workloads as wl
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_workspace_bytes([])
+    assert e.value.code == L.LBVE_ERR_ARG
+    bad = L.params_from(wl.frm(8))
+    bad.nx = 0
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_workspace_bytes([bad])
+    assert e.value.code == L.LBVE_ERR_ARG
+    big = L.params_from(wl.frm(8))
+    big.nx, big.ny = 8192, 4096  # 2^25 nodes
+    n64 = L.lbve_workspace_bytes([big])
+    assert n64 > 2 * 36 * (1 << 25) * 8  # the two population buffers, float64
+    big.precision = L.LBVE_FP32_DEV
+    assert 2 * 36 * (1 << 25) * 4 < L.lbve_workspace_bytes([big]) < n64
+    big.ny = 4097
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_workspace_bytes([big])
+    assert e.value.code == L.LBVE_ERR_ARG

@@ -123,3 +123,41 @@ def test_full_mix_invariants(full_mix):
         mass = sim.totals(i)[0]
         n = inst.nx * inst.ny
         assert abs(mass - n) <= 1e-12 * n, (i, mass, n)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_maximum_grid_patches(lbve, precision):
+    """The largest grid a handle takes, 8192 x 4096 = 2^25 nodes (36 planes of
+    indices just inside int32), periodic, with a random per-node force: after
+    10 steps, 9 x 9 patches at the start, the middle and the very end of the
+    arrays match the oracle on their periodic windows (half-width 30 >=
+    2 T + 1 + 4 + 1).  Float64 to 1e-12, float32 to 1e-5.  The force
+    amplitude 1e-3 keeps u near 1e-3: the oracle stores full populations
+    (about 0.1), whose round-off leaves about 1e-16 absolute in u, so with a
+    1e-5 force (u near 1e-5) the two sides differed by 1e-11 relative on any
+    grid size, 256 x 128 included."""
+    nx, ny, T, h = 8192, 4096, 10, 30
+    inst = wl.Instance(nx, ny, True, 0.5, 2.0, 1.0, 1e4, 0.1, ny / (2 * np.pi), 0.25, 1e-6,
+                       kind="custom")
+    inst.force_field = wl.random_force(nx, ny, seed=77, amp=1e-3)
+    sim = lbve.Simulation([inst], precision=precision)
+    sim.step(T)
+    assert not sim.status().any()
+    got_all = sim.fields(0)
+    tol = 1e-12 if precision == 0 else FP32_TOL
+    for cx, cy in ((2, 1), (nx // 2 + 17, ny // 2 - 5), (nx - 3, ny - 2)):
+        xs = np.arange(cx - h, cx + h + 1) % nx
+        ys = np.arange(cy - h, cy + h + 1) % ny
+        F = inst.force_field[:, ys][:, :, xs]
+        w = wl.Instance(2 * h + 1, 2 * h + 1, True, inst.beta, inst.Wi, inst.Re, inst.Sc, inst.Ma,
+                        inst.Lc, inst.Lambda_s, inst.Lambda_p, 0.0, 0.0, "window",
+                        np.ascontiguousarray(F))
+        o = oracle_sim(w)
+        o.step(T)
+        ref = o.fields()[:, h - PATCH:h + PATCH + 1, h - PATCH:h + PATCH + 1]
+        pxs = np.arange(cx - PATCH, cx + PATCH + 1) % nx
+        pys = np.arange(cy - PATCH, cy + PATCH + 1) % ny
+        got = got_all[:, pys][:, :, pxs]
+        eu, eC = rel_l2(got[1:3], ref[1:3]), rel_l2(got[3:6], ref[3:6])
+        assert eu <= tol and eC <= tol, (precision, cx, cy, eu, eC)
+    del sim
