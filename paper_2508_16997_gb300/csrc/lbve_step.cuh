@@ -286,15 +286,18 @@ __device__ __forceinline__ float coef<float>(const InstDev& D, int i) {
 }
 
 // Position of halo-ring slot q in the (TX+2) x (TY+2hy) region: hy rows
-// above, hy rows below, one column left and one right of the tile.
+// above and hy rows below the tile (its TX columns), one column left and one
+// right of it.  The region's four corner blocks are never computed: every
+// difference stencil runs along a single axis, so no node reads them.
 __device__ __forceinline__ void ring_slot(int q, int RW, int TY, int hy, int& lx, int& ly) {
-  if (q < hy * RW) {
-    ly = q / RW;
-    lx = q % RW;
-  } else if ((q -= hy * RW) < hy * RW) {
-    ly = hy + TY + q / RW;
-    lx = q % RW;
-  } else if ((q -= hy * RW) < TY) {
+  const int TX = RW - 2;
+  if (q < hy * TX) {
+    ly = q / TX;
+    lx = 1 + q % TX;
+  } else if ((q -= hy * TX) < hy * TX) {
+    ly = hy + TY + q / TX;
+    lx = 1 + q % TX;
+  } else if ((q -= hy * TX) < TY) {
     lx = 0;
     ly = hy + q;
   } else {
@@ -634,7 +637,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   // an open column's node arrives completed (colbuf): no wall completion there
   const bool ocol = MASKED && MODE == kModeStep && active && open_column(D, x);
   const bool wcomp = (wb || wt) && !ocol;
-  const int nring = 2 * hy * RW + 2 * TY;
+  const int nring = 2 * hy * TX + 2 * TY;  // the halo ring without its corners
 
   // (1) first halo-ring node of this thread: issue its pull
   int ring_r = -1, rgx = 0, rgy = 0;
