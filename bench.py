@@ -231,6 +231,36 @@ def time_oracle(sample, steps: int):
     return time.perf_counter() - t0
 
 
+def _oracle_worker(job):
+    """Pool worker: step a share of the sample's instances on the oracle and
+    return the seconds spent stepping (set-up excluded)."""
+    insts, steps = job
+    from oracle import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle_helpers import oracle_sim
+    oracle.build()
+    sims = [oracle_sim(inst) for inst in insts]
+    t0 = time.perf_counter()
+    for s in sims:
+        s.step(steps)
+    return time.perf_counter() - t0
+
+
+def time_oracle_all_cores(sample, steps: int):
+    """The same oracle runs spread over every host core: the independent
+    instances are dealt round-robin (largest first) to one process per core,
+    started with spawn (this process already holds a CUDA context).  Returns
+    (seconds of the slowest worker, workers)."""
+    import multiprocessing as mp
+    workers = max(1, min(os.cpu_count() or 1, len(sample)))
+    shares = [[] for _ in range(workers)]
+    for j, inst in enumerate(sorted(sample, key=lambda i: -i.n_nodes)):
+        shares[j % workers].append(inst)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        secs = pool.map(_oracle_worker, [(sh, steps) for sh in shares])
+    return max(secs), workers
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -486,6 +516,15 @@ def run_ours(args):
             "value": nodes * steps_cpu / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"FP64 oracle, {len(sample)} smallest instances of the mix "
                       f"({nodes} nodes) x {steps_cpu} steps, single thread"}
+        # the same sample on every host core (independent instances, one
+        # process per core): a larger sample so that each core has work
+        sample_all, nodes_all = cpu_sample(insts, 50000 * (os.cpu_count() or 1))
+        dt_all, workers = time_oracle_all_cores(sample_all, steps_cpu)
+        line["cpu_baseline_all_cores"] = {
+            "value": nodes_all * steps_cpu / dt_all / 1e6, "unit": UNIT, "cores": workers,
+            "kind": "oracle",
+            "sample": f"FP64 oracle, {len(sample_all)} smallest instances of the mix "
+                      f"({nodes_all} nodes) x {steps_cpu} steps, one process per core"}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
