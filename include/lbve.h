@@ -87,7 +87,8 @@ typedef struct {
   double Lambda_p;    /* conformation magic parameter (Sec. 3.2), > 0       */
   double Fx, Fy;      /* uniform body force, used when no force field given */
   int32_t tile_tx;    /* tile width in nodes along x for the step kernel:
-                         0 = library default (min(32, nx)), else 1..48 and
+                         0 = library default (min(32, nx)), else 1..48
+                         (float32; 1..128 for float64) and
                          <= nx (e.g. a width lbve_autotune() returned).  A
                          pure performance setting: each node's update does
                          not depend on the tiling; only the summation order
@@ -129,7 +130,8 @@ int lbve_workspace_bytes(const lbve_params* p, int32_t n_instances, size_t* byte
 
 /* Tile-width autotuner (the paper has no counterpart: the step kernel's
  * tiling is an implementation choice).  Times the batch p[0..n-1] with
- * candidate tile widths -- the widths 8, 16, 32 that fit nx,
+ * candidate tile widths -- the widths 8, 16, 32 (float32; up to 128 for
+ * float64) that fit nx,
  * or nx itself when nx < 8 -- and writes the fastest width of each instance
  * to tile_tx_out[0..n-1] (never 0).  Instances with the same candidates,
  * precision and wall layout share one width; one pass of coordinate descent

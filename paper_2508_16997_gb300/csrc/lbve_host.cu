@@ -96,9 +96,10 @@ int validate(const lbve_params& p, int i) {
     return fail(LBVE_ERR_ARG, "instance %d: an open channel needs nx >= 5", i);
   if (p.max_wall_nodes < 0 || int64_t(p.max_wall_nodes) > int64_t(p.nx) * p.ny)
     return fail(LBVE_ERR_ARG, "instance %d: max_wall_nodes must be in [0, nx*ny]", i);
-  if (p.tile_tx != 0 && (p.tile_tx < 1 || p.tile_tx > kTileTXMax || p.tile_tx > p.nx))
+  if (p.tile_tx != 0 &&
+      (p.tile_tx < 1 || p.tile_tx > tile_tx_max(p.precision) || p.tile_tx > p.nx))
     return fail(LBVE_ERR_ARG, "instance %d: tile_tx must be 0 or in [1, min(%d, nx)]", i,
-                kTileTXMax);
+                tile_tx_max(p.precision));
   const Coeffs c = derive(p);
   if (!(c.tau_s1 > 0.5) || !(c.tau_p1 > 0.5) || !std::isfinite(c.tau_s2) ||
       !std::isfinite(c.tau_p2) || !finite_pos(c.lambda))
@@ -133,12 +134,12 @@ int default_tile_tx(const lbve_params& p) { return p.nx >= kTileTX ? kTileTX : p
 
 void tile_shape(const lbve_params& p, int& TX, int& TY, int& hy) {
   TX = p.tile_tx > 0 ? p.tile_tx : default_tile_tx(p);
-  TY = kThreads / TX;
+  TY = threads_of(p.precision) / TX;
   hy = p.periodic_y ? 1 : 2;
 }
 
 int64_t tiles_for(const lbve_params& p, int TX) {
-  const int TY = kThreads / TX;
+  const int TY = threads_of(p.precision) / TX;
   return int64_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
 }
 
@@ -146,7 +147,8 @@ int64_t tiles_for(const lbve_params& p, int TX) {
 // sized by it, so the same workspace serves every tile width.
 int64_t max_tiles(const lbve_params& p) {
   int64_t m = 0;
-  for (int TX = 1; TX <= std::min(kTileTXMax, p.nx); ++TX) m = std::max(m, tiles_for(p, TX));
+  for (int TX = 1; TX <= std::min(tile_tx_max(p.precision), p.nx); ++TX)
+    m = std::max(m, tiles_for(p, TX));
   return m;
 }
 
@@ -699,7 +701,8 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     D.cd[kCoefAfene] = p[i].model == 1 ? 1.0 / (1.0 - 2.0 / p[i].L2) : 1.0;
     D.model = p[i].model;
     D.gtilde = p[i].gtilde;
-    D.t32 = q.TX == kTileTX && (!p[i].periodic_y || p[i].ny >= kThreads / kTileTX + 2);
+    D.t32 = q.TX == kTileTX &&
+            (!p[i].periodic_y || p[i].ny >= threads_of(p[i].precision) / kTileTX + 2);
     for (int j = 0; j < kNumCoef; ++j) D.cf[j] = (float)D.cd[j];
     int k = q.tile_begin;
     for (int ty = 0; ty < q.nty; ++ty)
@@ -1156,7 +1159,7 @@ constexpr int kAutotuneRepeats = 2;  // the fastest of these timings counts
 std::vector<int> width_candidates(const lbve_params& p) {
   std::vector<int> c;
   if (p.nx < 8) c.push_back(p.nx);
-  for (int t = 8; t <= kTileTXMax; t *= 2)
+  for (int t = 8; t <= tile_tx_max(p.precision); t *= 2)
     if (t <= p.nx) c.push_back(t);
   return c;
 }

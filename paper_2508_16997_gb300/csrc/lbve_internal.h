@@ -5,22 +5,34 @@
 
 namespace lbve {
 
-// 96 threads (32 x 3 tiles) measured fastest on GB300 among 64..256 for the
-// float32 step: seven such CTAs per SM give 21 warps in seven independent
-// load / barrier / compute phases.
+// Threads per CTA of the step kernel, per storage precision.  Float32: 96
+// (32 x 3 tiles) measured fastest on GB300 among 64..256; seven such CTAs per
+// SM give 21 warps in seven independent load / barrier / compute phases.
+// Float64 (bound by the FP64 pipe): 256 (32 x 8 tiles), two per SM.
 #ifndef LBVE_THREADS
 #define LBVE_THREADS 96
+#endif
+#ifndef LBVE_THREADS_FP64
+#define LBVE_THREADS_FP64 256
 #endif
 #ifndef LBVE_TILE_TX
 #define LBVE_TILE_TX 32
 #endif
-constexpr int kThreads = LBVE_THREADS;  // threads per CTA of the step kernel
+constexpr int kThreads = LBVE_THREADS;          // float32 step kernel
+constexpr int kThreads64 = LBVE_THREADS_FP64;   // float64 step kernel
 constexpr int kTileTX = LBVE_TILE_TX;   // default tile width (nodes along x) for nx >= kTileTX
-constexpr int kTileTXMax = kThreads / 2;  // widest tile a caller may ask for
-// Halo region of a tile: (TX+2)(TY+2*hy) <= (TX+2)(kThreads/TX+4)
-// = kThreads + 4 TX + 2 kThreads/TX + 8, which is convex in TX and equals
-// 3 (kThreads + 4) at both ends of 1 <= TX <= kTileTXMax (TY = kThreads/TX, hy <= 2).
-constexpr int kRegionMax = 3 * (kThreads + 4);
+// threads per CTA and widest tile a caller may ask for, by precision
+// (0 = float64, 1 = float32, as LBVE_FP64 / LBVE_FP32_DEV)
+__host__ __device__ constexpr int threads_of(int prec) { return prec == 0 ? kThreads64 : kThreads; }
+__host__ __device__ constexpr int tile_tx_max(int prec) { return threads_of(prec) / 2; }
+template <typename R>
+struct StepThreads {
+  static constexpr int value = sizeof(R) == 8 ? kThreads64 : kThreads;
+};
+// Halo region of a tile: (TX+2)(TY+2*hy) <= (TX+2)(T/TX+4) = T + 4 TX + 2 T/TX
+// + 8 for T threads, which is convex in TX and equals 3 (T + 4) at both ends
+// of 1 <= TX <= T/2 (TY = T/TX, hy <= 2).
+__host__ __device__ constexpr int region_max(int threads) { return 3 * (threads + 4); }
 constexpr int kPartial = 16;      // doubles per tile partial record
 constexpr int kTotals = 16;       // doubles per instance totals record
 

@@ -10,7 +10,7 @@ namespace lbve {
 template <typename R, int MODE, bool FINAL, bool MASKED>
 static void launch_step_k(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
                           double* d_partials, cudaStream_t st) {
-  step_kernel<R, MODE, FINAL, MASKED><<<n_tiles, kThreads, 0, st>>>(d_insts, d_tiles, parity,
+  step_kernel<R, MODE, FINAL, MASKED><<<n_tiles, StepThreads<R>::value, 0, st>>>(d_insts, d_tiles, parity,
                                                                     d_partials);
 }
 

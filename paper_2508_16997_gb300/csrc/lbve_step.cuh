@@ -524,7 +524,7 @@ template <typename R, bool MASKED>
 struct MinBlocks {
   static constexpr int value =
       sizeof(R) == 4 ? (MASKED ? LBVE_FP32_MASKED_MIN_BLOCKS : LBVE_FP32_MIN_BLOCKS)
-                     : (kThreads <= 256 ? 512 / kThreads : 1);
+                     : (kThreads64 <= 256 ? 512 / kThreads64 : 1);
 };
 
 // One-sided differences along one axis next to the solid mask (same rule as
@@ -646,7 +646,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     int lx, ly;
     bool in_domain;
     if (t32) {
-      ring_slot(threadIdx.x, kTileTX + 2, kThreads / kTileTX, hy, lx, ly);
+      ring_slot(threadIdx.x, kTileTX + 2, StepThreads<R>::value / kTileTX, hy, lx, ly);
       in_domain = region_node_once(lx, ly, T.x0, T.y0, hy, nx, ny, py, rgx, rgy);
     } else {
       ring_slot(threadIdx.x, RW, TY, hy, lx, ly);
@@ -894,7 +894,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     if (threadIdx.x < 14) {
       const int j = threadIdx.x;
       double v = s_red[0][j];
-      for (int w = 1; w < kThreads / 32; ++w)
+      for (int w = 1; w < StepThreads<R>::value / 32; ++w)
         v = (j == kResid) ? fmax(v, s_red[w][j]) : v + s_red[w][j];
       partials[(size_t)T.slot * kPartial + j] = v;
     }
@@ -904,13 +904,14 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
 // One CTA per tile.  The plain variant leaves masked tiles to the masked one
 // (which runs over a separate list of just those tiles).
 template <typename R, int MODE, bool FINAL, bool MASKED>
-__global__ void __launch_bounds__(kThreads, MinBlocks<R, MASKED>::value)
+__global__ void __launch_bounds__(StepThreads<R>::value, MinBlocks<R, MASKED>::value)
     step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles,
                 int parity, double* __restrict__ partials) {
-  __shared__ R s_rho[kRegionMax];
-  __shared__ R s_ux[kRegionMax];
-  __shared__ R s_uy[kRegionMax];
-  __shared__ double s_red[kThreads / 32][kPartial];
+  constexpr int kRegion = region_max(StepThreads<R>::value);
+  __shared__ R s_rho[kRegion];
+  __shared__ R s_ux[kRegion];
+  __shared__ R s_uy[kRegion];
+  __shared__ double s_red[StepThreads<R>::value / 32][kPartial];
   const TileDev T = tiles[blockIdx.x];
   if (!MASKED && T.masked) return;
   process_tile<R, MODE, FINAL, MASKED>(insts, T, parity, partials, s_rho, s_ux, s_uy, s_red);

@@ -89,10 +89,14 @@ def test_tile_width_validation_and_layout(L):
         p = [L.params_from(wl.frm(130), tile_tx=tx),
              L.params_from(wl.channel(33, nx=20), L.LBVE_FP32_DEV, tile_tx=min(tx, 20))]
         assert L.lbve_workspace_bytes(p) == n0
-    for bad_tx in (-1, 49, 131):
+    for bad_tx in (-1, 129, 131):  # float64 tiles take up to 128
         with pytest.raises(L.LbveError) as e:
             L.lbve_workspace_bytes([L.params_from(wl.frm(256), tile_tx=bad_tx)])
         assert e.value.code == L.LBVE_ERR_ARG
+    L.lbve_workspace_bytes([L.params_from(wl.frm(256), tile_tx=128)])
+    with pytest.raises(L.LbveError) as e:  # float32 tiles take up to 48
+        L.lbve_workspace_bytes([L.params_from(wl.frm(256), L.LBVE_FP32_DEV, tile_tx=49)])
+    assert e.value.code == L.LBVE_ERR_ARG
     with pytest.raises(L.LbveError) as e:  # wider than the grid
         L.lbve_workspace_bytes([L.params_from(wl.channel(33, nx=4), tile_tx=8)])
     assert e.value.code == L.LBVE_ERR_ARG
