@@ -159,22 +159,51 @@ def kernel_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    capture, or None when the kernel sources changed since the capture."""
+def profile_values(name):
+    """Key/value lines of a committed profile summary, or None when the
+    kernel sources changed since the capture it records."""
     try:
         vals = {}
-        with open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             for line in f:
                 if line.startswith("#") or not line.strip():
                     continue
                 k, v = line.split(None, 1)
                 vals[k] = v.strip()
-        if vals.get("sources_sha256") != kernel_sources_sha256():
-            return None
-        return float(vals["dram_bytes_per_launch"])
-    except (OSError, KeyError, ValueError):
+    except (OSError, ValueError):
         return None
+    if vals.get("sources_sha256") != kernel_sources_sha256():
+        return None
+    return vals
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    capture, or None when the kernel sources changed since the capture."""
+    vals = profile_values("roofline_traffic.txt")
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (TypeError, KeyError, ValueError):
+        return None
+
+
+def measured_flops(mlups):
+    """Floating-point work of the float32 step kernel: flops per lattice
+    update counted by ncu (fadd + fmul + 2 ffma per node), the throughput
+    they make at `mlups`, and the fraction of the FP32 (non-tensor) peak
+    derived from 152 SMs x 128 lanes x 2 flops x 2.07 GHz.  None when the
+    kernel changed since the count."""
+    vals = profile_values("step_kernel_fp32_flop_count.txt")
+    try:
+        per_lu, peak = float(vals["flop_per_lu"]), float(vals["fp32_peak_tflops"])
+    except (TypeError, KeyError, ValueError):
+        return None
+    achieved = per_lu * mlups * 1e6 / 1e12
+    return {"per_lu": per_lu, "achieved": achieved, "unit": "TFLOP/s", "peak": peak,
+            "peak_kind": "derived from unit counts and the maximum SM clock",
+            "frac": achieved / peak,
+            "source": "ncu thread-instruction counters of step_kernel<float> on four-roll "
+                      "mills 512^2 x 8"}
 
 
 def dist_setup(args):
@@ -496,6 +525,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h / K,
                 "region": "lbve_set_geometry (pinned host force + initial fields) for every "
                           "instance, lbve_step(K), lbve_fields to pinned host"},
+        "flops": measured_flops(value),
         "gpu_launches": K + 1,
         "clocks": clocks,
         "fp64_plain": {"value": value64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64,
