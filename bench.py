@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--cylinder-steps", type=int, default=2000)
+    ap.add_argument("--frm64-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -193,7 +194,7 @@ def measured_flops(mlups):
     they make at `mlups`, and the fraction of the FP32 (non-tensor) peak
     derived from 152 SMs x 128 lanes x 2 flops x 2.07 GHz.  None when the
     kernel changed since the count."""
-    vals = profile_values("step_kernel_fp32_flop_count.txt")
+    vals = profile_values("step_kernel_flop_count.txt")
     try:
         per_lu, peak = float(vals["flop_per_lu"]), float(vals["fp32_peak_tflops"])
     except (TypeError, KeyError, ValueError):
@@ -203,6 +204,26 @@ def measured_flops(mlups):
             "peak_kind": "derived from unit counts and the maximum SM clock",
             "frac": achieved / peak,
             "source": "ncu thread-instruction counters of step_kernel<float> on four-roll "
+                      "mills 512^2 x 8"}
+
+
+def measured_fp64_pipe(mlups):
+    """The float64 step kernel against its FP64 pipe: FP64 instructions per
+    lattice update counted by ncu (dadd + dmul + dfma per node), the
+    instruction rate they make at `mlups`, and the fraction of the pipe's
+    peak derived from 152 SMs x 2 FP64 instructions per clock x 2.07 GHz.
+    None when the kernel changed since the count."""
+    vals = profile_values("step_kernel_flop_count.txt")
+    try:
+        per_lu = float(vals["fp64_inst_per_lu"])
+        peak = float(vals["fp64_peak_ginst"])
+    except (TypeError, KeyError, ValueError):
+        return None
+    achieved = per_lu * mlups * 1e6 / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP64 inst/s",
+            "frac": achieved / peak, "inst_per_lu": per_lu,
+            "peak_kind": "derived from unit counts and the maximum SM clock",
+            "source": "ncu thread-instruction counters of step_kernel<double> on four-roll "
                       "mills 512^2 x 8"}
 
 
@@ -505,6 +526,11 @@ def run_ours(args):
     if args.cylinder_steps > 0:
         cyl = bench_cylinder(args.cylinder_steps, stream)
 
+    # ---- the small four-roll mill as specified (64^2, FP64, from rest) ------
+    c1, c1_fields = None, None
+    if args.frm64_steps > 0:
+        c1, c1_fields = bench_frm64(args.frm64_steps, stream)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -529,7 +555,8 @@ def run_ours(args):
         "gpu_launches": K + 1,
         "clocks": clocks,
         "fp64_plain": {"value": value64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64,
-                       "speedup_fp32_over_fp64": value / value64},
+                       "speedup_fp32_over_fp64": value / value64,
+                       "roofline": measured_fp64_pipe(value64)},
         "fp32_vs_fp64_rel_l2": {"max_all": err_all, "max_Wi_le_100": err_le100,
                                 "steps": W + K64, "target_Wi_le_100": 1e-5},
         "nonfinite_instances": int((flags != 0).sum()),
@@ -538,6 +565,8 @@ def run_ours(args):
         line["adjoint"] = adj
     if cyl is not None:
         line["cylinder"] = cyl
+    if c1 is not None:
+        line["frm64"] = c1
     if world == 1 and not args.no_cpu_baseline:
         sample, nodes = cpu_sample(insts, 50000)
         steps_cpu = 200
@@ -555,9 +584,56 @@ def run_ours(args):
             "kind": "oracle",
             "sample": f"FP64 oracle, {len(sample_all)} smallest instances of the mix "
                       f"({nodes_all} nodes) x {steps_cpu} steps, one process per core"}
+        if c1 is not None:
+            # the same run on the oracle: its time, and the GPU's fields against it
+            from oracle import oracle
+            sys.path.insert(0, os.path.join(ROOT, "tests"))
+            from oracle_helpers import oracle_sim
+            from paper_2508_16997_gb300 import workloads as wl
+            oracle.build()
+            osim = oracle_sim(wl.frm(64))
+            t0 = time.perf_counter()
+            osim.step(args.frm64_steps)
+            dt_o = time.perf_counter() - t0
+            ref = osim.fields()
+
+            def rel(a, r):
+                return float(np.linalg.norm(a - r) / np.linalg.norm(r))
+            c1["oracle"] = {"value": 64 * 64 * args.frm64_steps / dt_o / 1e6, "unit": UNIT,
+                            "cores": 1, "seconds": dt_o,
+                            "gpu_vs_oracle_rel_l2": {"u": rel(c1_fields[1:3], ref[1:3]),
+                                                     "A": rel(c1_fields[3:6], ref[3:6]),
+                                                     "target": 1e-12}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_frm64(steps: int, stream):
+    """The four-roll mill 64^2 as specified (beta 0.5, Wi 5, Re 0.01, Sc 1e5,
+    Ma 1e-3, FP64), `steps` steps from rest: returns the timing of the run
+    and its fields after `steps` steps.  The first run from rest gives the
+    fields and warms the handle up (graph capture); the timed run continues
+    the same handle for another `steps` steps of identical cost.  A grid this
+    small is bound by launch latency, not by HBM."""
+    import torch
+    from paper_2508_16997_gb300 import lbve, workloads as wl
+    sim = lbve.Simulation([wl.frm(64)], precision=lbve.LBVE_FP64)
+    sim.step(steps)
+    fields = sim.fields(0)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out = {"workload": "four-roll mill 64^2, beta 0.5, Wi 5, Re 0.01, Sc 1e5, Ma 1e-3, FP64, "
+                       f"{steps} steps from rest", "value": 64 * 64 * steps / (ms / 1e3) / 1e6,
+           "unit": UNIT, "ms": ms, "us_per_step": ms * 1e3 / steps,
+           "finite": not bool(sim.status()[0])}
+    return out, fields
 
 
 def bench_cylinder(steps: int, stream) -> dict:
