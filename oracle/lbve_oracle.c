@@ -259,7 +259,9 @@ void orc_hydro_collide(const double* f, double Fx, double Fy, const double* tau,
   }
 }
 
-/* CDE source term F~_i (eq_p_F) for source S and velocity u. */
+/* CDE source term F~_i (eq_p_F) for source S and velocity u.  Its e.u S
+ * part cancels the U S share of the flux error (tau_p1 - 1/2) d_t(phi u);
+ * pinned by test_source_velocity_term_removes_the_relaxation_drift. */
 static void cde_source(double S, double ux, double uy, double tau_p1, double* Ft) {
   const double u[2] = {ux, uy};
   for (int i = 0; i < Q; ++i) {
@@ -274,7 +276,9 @@ static void cde_source(double S, double ux, double uy, double tau_p1, double* Ft
  *   auxiliary term G~_i (eq_p_G_1), source F~_i(t) (eq_p_F) and
  *   (dt^2/2) d_t F~_i with the backward difference of Sec. 3.2, dt = 1.
  * u, rho, F are the hydrodynamic velocity, density and body force at t;
- * S, S_old are the source at t and t-1; uold the velocity at t-1. */
+ * S, S_old are the source at t and t-1; uold the velocity at t-1.
+ * G~_i cancels the phi a share of the flux error (tau_p1 - 1/2) d_t(phi u);
+ * pinned by test_gtilde_removes_the_acceleration_drift. */
 void orc_cde_collide(const double* g, double rho, double ux, double uy, double Fx,
                      double Fy, double S, double S_old, double uxo, double uyo,
                      double tau_p1, double tau_p2, double* out) {

@@ -419,6 +419,67 @@ def test_cde_fourier_mode():
     assert np.abs(F[1] - U).max() < 1e-15  # uniform flow is untouched
 
 
+def _mode_displacement(Sc, N, T, Fx, u0, Wi, eps=0.1, ny=4):
+    """Passive polymer (beta = 1) on an N x ny periodic strip with uniform
+    velocity u0 and uniform body force Fx; A_xx = 1 + eps cos(k x) at t = 0.
+    Returns (displacement X of the A_xx mode after T steps, from the phase of
+    its Fourier coefficient, tau_p1)."""
+    from oracle import oracle as o
+    p = oracle_params(wl.frm(N, beta=1.0, Wi=Wi, Re=1.0, Ma=0.1, Sc=Sc, Lambda_p=0.25))
+    p.ny = ny
+    p.Fx, p.Fy = Fx, 0.0
+    k = 2 * np.pi / N
+    init = np.zeros((6, ny, N))
+    init[0], init[1], init[5] = 1.0, u0, 1.0
+    init[3] = 1 + eps * np.cos(k * np.arange(N))[None, :]
+    s = o.Sim(p, init=init)
+    s.step(T)
+    m = (s.fields()[3] - 1).mean(axis=0)
+    z = (m * np.exp(-1j * k * np.arange(N))).sum()
+    return -np.angle(z) / k, s.coeffs()["tau_p1"]
+
+
+def test_gtilde_removes_the_acceleration_drift():
+    """eq_p_G_1: in a uniformly accelerating flow, d_t(phi u) = phi a, and the
+    CDE's second-order flux error -(tau_p1 - 1/2) d_t(phi u) would advect a
+    conformation mode with u - (tau_p1 - 1/2) a.  G~_i removes it, so the
+    mode moves with the flow only: u(t) = u(0) + a t with u(0) = u0 + a/2
+    (eq_ev_f0), and u0 = -aT/2 makes X = int_0^T u dt = aT/2, the same for
+    every tau_p1.  The antisymmetric history also cancels the lattice's
+    advection dispersion, which is proportional to u.
+
+    Calibration (N = 512, a = 1e-4, T = 200, tau_p1 = 0.6 and 1.5): relative
+    deviation from aT/2 -2.4e-5 and 7.4e-5 (-9.6e-5 and 3.0e-4 at N = 256:
+    the k^2 of lattice dispersion).  In copies of the oracle, G~ dropped
+    gives -0.20 / -1.99, its factor (1 - 1/tau) in place of (1 - 1/(2 tau))
+    -1.00 / -1.00, its sign flipped -0.40 / -3.98.  Tolerance 1e-3."""
+    N, a, T = 512, 1e-4, 200
+    taus = []
+    for Sc in (141.6, 14.16):
+        X, tau = _mode_displacement(Sc, N, T, Fx=a, u0=-a * T / 2, Wi=1e9)
+        taus.append(tau)
+        assert abs(X - a * T / 2) < 1e-3 * (a * T / 2), (tau, X)
+    assert taus[0] < 0.61 and taus[1] > 1.49  # two clearly different relaxation times
+
+
+def test_source_velocity_term_removes_the_relaxation_drift():
+    """eq_p_F: with a source S = -(A - I)/lambda in a uniform flow U,
+    d_t(phi u) = U S, and without the (1 - 1/(2 tau_p1)) e.u S / c_s^2 part
+    of F~_i the mode would drift against the flow by (tau_p1 - 1/2) U T /
+    lambda.  With it the mode moves exactly U T, whatever tau_p1 (the decay
+    by 1/lambda shifts no phase).
+
+    Calibration (N = 512, U = 0.02, T = 60, lambda = 70.6 steps, tau_p1 =
+    0.6 and 1.5): relative deviation from U T -4.8e-5 and 3.2e-5.  In copies
+    of the oracle, the velocity part dropped gives 1.4e-3 / 1.4e-2, its factor
+    (1 - 1/tau) in place of (1 - 1/(2 tau)) 7.0e-3 / 7.1e-3.  Tolerance
+    2.5e-4."""
+    N, U, T = 512, 0.02, 60
+    for Sc in (141.6, 14.16):
+        X, tau = _mode_displacement(Sc, N, T, Fx=0.0, u0=U, Wi=0.05)
+        assert abs(X - U * T) < 2.5e-4 * (U * T), (tau, X)
+
+
 # --------------------------------------------------------------------------
 # Solid mask: interpolated bounce-back, CNEBB at mask walls, drag (Sec. 4.3)
 # --------------------------------------------------------------------------
