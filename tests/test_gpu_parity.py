@@ -175,3 +175,48 @@ def test_fields_on_device(lbve):
     sim = lbve.Simulation([inst])
     sim.step(11)
     np.testing.assert_array_equal(sim.fields_device(0).cpu().numpy(), sim.fields(0))
+
+
+def _mode_x(fields, N):
+    """Displacement of the A_xx mode cos(k x), k = 2 pi / N, from the phase of
+    its Fourier coefficient (row average)."""
+    k = 2 * np.pi / N
+    m = (fields[3] - 1).mean(axis=0)
+    return -np.angle((m * np.exp(-1j * k * np.arange(N))).sum()) / k
+
+
+@pytest.mark.parametrize("case", ["accelerating", "relaxing"])
+def test_strip_mode_drift(lbve, case):
+    """The flow-level set-ups that pin G~ (eq_p_G_1) and the e.u S part of F~
+    (eq_p_F) on the oracle, run on the GPU.  Passive polymer (beta = 1) on a
+    512 x 4 periodic strip (a periodic grid lower than a float32 tile plus
+    its halo), A_xx = 1 + 0.1 cos(k x):
+      accelerating: uniform force a = 1e-4, u0 = -aT/2, T = 200, lambda huge;
+        the mode must move aT/2;
+      relaxing: u0 = U = 0.02, no force, lambda = 70.6 steps, T = 60; the
+        mode must move U T.
+    At tau_p1 = 0.6 and 1.5 (Sc chosen for each): FP64 matches the oracle to
+    1e-12 and its own mode displacement meets the oracle pins' tolerances
+    (1e-3 and 2.5e-4 relative); FP32 matches the oracle within 1e-5."""
+    N, ny = 512, 4
+    if case == "accelerating":
+        a, u0, T, Wi, tol, X_exact = 1e-4, -1e-4 * 200 / 2, 200, 1e9, 1e-3, 1e-4 * 200 / 2
+    else:
+        a, u0, T, Wi, tol, X_exact = 0.0, 0.02, 60, 0.05, 2.5e-4, 0.02 * 60
+    insts, inits = [], []
+    for Sc in (141.6, 14.16):
+        insts.append(wl.Instance(N, ny, True, 1.0, Wi, 1.0, Sc, 0.1, N / (2 * np.pi), 0.25, 0.25,
+                                 a, 0.0, "custom"))
+        init = np.zeros((6, ny, N))
+        init[0], init[1], init[5] = 1.0, u0, 1.0
+        init[3] = 1 + 0.1 * np.cos(2 * np.pi * np.arange(N) / N)[None, :]
+        inits.append(init)
+    sim, orcs = run_pair(lbve, insts, T, inits=inits)
+    for i, o in enumerate(orcs):
+        g = sim.fields(i)
+        assert_fp64_parity(g, o.fields(), what=f"{case} {i}")
+        assert abs(_mode_x(g, N) - X_exact) < tol * X_exact, (case, i, _mode_x(g, N))
+    sim32, orcs = run_pair(lbve, insts, T, precision=1, inits=inits)
+    for i, o in enumerate(orcs):
+        err = parity_errors(sim32.fields(i), o.fields())
+        assert err["u"] <= FP32_TOL and err["C"] <= FP32_TOL, (case, i, err)
