@@ -93,7 +93,10 @@ typedef struct {
                          pure performance setting: each node's update does
                          not depend on the tiling; only the summation order
                          of the float64 totals follows the tiles.  The
-                         workspace size does not depend on it.             */
+                         workspace size does not depend on it.  A float64
+                         batch with fewer 256-node tiles than the GPU's 152
+                         SMs runs 64-thread tiles (TX x 64/TX) unless one of
+                         its float64 instances asks for a width above 32.  */
   int32_t max_wall_nodes; /* capacity for a solid mask: the most fluid nodes
                          next to solid nodes (nodes with a solid neighbour
                          along any lattice direction) lbve_set_geometry may

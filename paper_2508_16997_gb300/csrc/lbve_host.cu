@@ -125,6 +125,7 @@ struct Plan {
   size_t off_insts, off_tiles[kLists], off_partials, off_totals, off_flags, total;
   int ntiles[kLists], nslots;
   int cap_tiles[kLists];  // tile-table capacity: the most tiles any tile width gives
+  int threads[kLists];    // CTA size of each list's step launches
   size_t off_mtiles[kLists], off_walls[kLists], off_wrec[kLists], off_cols[kLists];
   int wall_cap[kLists];   // wall-node records per list
   int ncols[kLists];      // open-column tasks per list
@@ -132,24 +133,46 @@ struct Plan {
 
 int default_tile_tx(const lbve_params& p) { return p.nx >= kTileTX ? kTileTX : p.nx; }
 
-void tile_shape(const lbve_params& p, int& TX, int& TY, int& hy) {
+// Tile of TX x (threads / TX) nodes for CTAs of `threads` threads.
+void tile_shape(const lbve_params& p, int threads, int& TX, int& TY, int& hy) {
   TX = p.tile_tx > 0 ? p.tile_tx : default_tile_tx(p);
-  TY = threads_of(p.precision) / TX;
+  TY = threads / TX;
   hy = p.periodic_y ? 1 : 2;
 }
 
-int64_t tiles_for(const lbve_params& p, int TX) {
-  const int TY = threads_of(p.precision) / TX;
+int64_t tiles_for(const lbve_params& p, int TX, int threads) {
+  const int TY = threads / TX;
   return int64_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
 }
 
-// Most tiles any admissible tile width gives for p: the workspace layout is
-// sized by it, so the same workspace serves every tile width.
+// Most tiles any admissible tile width and CTA size give for p: the
+// workspace layout is sized by it, so the same workspace serves every tile
+// width (and the CTA size the widths imply for the batch).
 int64_t max_tiles(const lbve_params& p) {
   int64_t m = 0;
-  for (int TX = 1; TX <= std::min(tile_tx_max(p.precision), p.nx); ++TX)
-    m = std::max(m, tiles_for(p, TX));
+  for (int TX = 1; TX <= std::min(tile_tx_max(p.precision), p.nx); ++TX) {
+    m = std::max(m, tiles_for(p, TX, threads_of(p.precision)));
+    if (p.precision == LBVE_FP64 && TX <= kThreads64Small / 2)
+      m = std::max(m, tiles_for(p, TX, kThreads64Small));
+  }
   return m;
+}
+
+// CTA size of the float64 list.  The FP64 pipe bounds the float64 step, so a
+// batch whose 256-thread tiles would not give every SM one tile leaves SMs
+// idle while the others work through 256 nodes each; 64-thread tiles spread
+// the same nodes over four times as many CTAs.  Chosen from the parameters
+// alone (the workspace plan needs no device): the small size when the
+// 256-thread tiles number fewer than the SMs and no float64 instance asks
+// for a tile wider than a 64-thread CTA takes.
+int fp64_threads(const lbve_params* p, int n) {
+  int64_t big = 0;
+  for (int i = 0; i < n; ++i) {
+    if (p[i].precision != LBVE_FP64) continue;
+    if (p[i].tile_tx > kThreads64Small / 2) return kThreads64;
+    big += tiles_for(p[i], p[i].tile_tx > 0 ? p[i].tile_tx : default_tile_tx(p[i]), kThreads64);
+  }
+  return big > 0 && big < kNumSMs ? kThreads64Small : kThreads64;
 }
 
 Plan make_plan(const lbve_params* p, int n) {
@@ -157,6 +180,8 @@ Plan make_plan(const lbve_params* p, int n) {
   pl.inst.resize(n);
   size_t off = 0;
   for (int l = 0; l < kLists; ++l) pl.ntiles[l] = pl.cap_tiles[l] = pl.wall_cap[l] = pl.ncols[l] = 0;
+  pl.threads[0] = fp64_threads(p, n);
+  pl.threads[1] = kThreads;
   for (int i = 0; i < n; ++i) {
     InstPlan& q = pl.inst[i];
     const size_t es = p[i].precision == LBVE_FP64 ? 8 : 4;
@@ -181,8 +206,8 @@ Plan make_plan(const lbve_params* p, int n) {
       q.off_colbuf = off;
       off = align_up(off + 36 * 2 * size_t(p[i].ny) * es, kAlign);
     }
-    tile_shape(p[i], q.TX, q.TY, q.hy);
     q.list = p[i].precision == LBVE_FP64 ? 0 : 1;
+    tile_shape(p[i], pl.threads[q.list], q.TX, q.TY, q.hy);
     q.wall_begin = pl.wall_cap[q.list];
     q.wall_cap = p[i].max_wall_nodes;
     pl.wall_cap[q.list] += q.wall_cap;
@@ -308,11 +333,13 @@ int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
   for (int l = 0; l < kLists; ++l) {
     const int prec = l == 0 ? LBVE_FP64 : LBVE_FP32_DEV;
     if (h->nmasked[l] > 0 &&
-        launch_step(prec, h->d_insts, h->d_mtiles[l], h->nmasked[l], parity, kModeStep, flags,
+        launch_step(prec, h->plan.threads[l], h->d_insts, h->d_mtiles[l], h->nmasked[l], parity,
+                    kModeStep, flags,
                     h->d_partials, h->side_stream, 1))
       return cuda_fail(cudaGetLastError(), "masked step kernel launch");
     if (h->plan.ntiles[l] > 0 &&
-        launch_step(prec, h->d_insts, h->d_tiles[l], h->plan.ntiles[l], parity, kModeStep, flags,
+        launch_step(prec, h->plan.threads[l], h->d_insts, h->d_tiles[l], h->plan.ntiles[l],
+                    parity, kModeStep, flags,
                     h->d_partials, st))
       return cuda_fail(cudaGetLastError(), "step kernel launch");
   }
@@ -701,8 +728,7 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     D.cd[kCoefAfene] = p[i].model == 1 ? 1.0 / (1.0 - 2.0 / p[i].L2) : 1.0;
     D.model = p[i].model;
     D.gtilde = p[i].gtilde;
-    D.t32 = q.TX == kTileTX &&
-            (!p[i].periodic_y || p[i].ny >= threads_of(p[i].precision) / kTileTX + 2);
+    D.t32 = q.TX == kTileTX && (!p[i].periodic_y || p[i].ny >= q.TY + 2);
     for (int j = 0; j < kNumCoef; ++j) D.cf[j] = (float)D.cd[j];
     int k = q.tile_begin;
     for (int ty = 0; ty < q.nty; ++ty)
@@ -845,11 +871,13 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
   e = cudaMemsetAsync(h->d_flags + inst, 0, sizeof(int32_t), h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "flag reset");
   // collide the equilibrium state of t = 0: reads pop[P^1] (staging), writes pop[P]
-  if (launch_step(p.precision, h->d_insts, h->d_tiles[q.list] + q.tile_begin, q.ntiles, P ^ 1,
+  if (launch_step(p.precision, h->plan.threads[q.list], h->d_insts,
+                  h->d_tiles[q.list] + q.tile_begin, q.ntiles, P ^ 1,
                   kModeInit, kFinal, h->d_partials, h->stream))
     return cuda_fail(cudaGetLastError(), "init kernel launch");
   if (!h->mtiles_of[inst].empty() &&
-      launch_step(p.precision, h->d_insts, h->d_mtiles[q.list] + h->mbegin[inst],
+      launch_step(p.precision, h->plan.threads[q.list], h->d_insts,
+                  h->d_mtiles[q.list] + h->mbegin[inst],
                   (int)h->mtiles_of[inst].size(), P ^ 1, kModeInit, kFinal, h->d_partials,
                   h->stream, 1))
     return cuda_fail(cudaGetLastError(), "masked init kernel launch");
@@ -1456,9 +1484,11 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
   }
   const int nmt = (int)mtiles.size();
   auto launch_tiles = [&](int mode, int flags) -> bool {
-    if (launch_step(prec, d_desc, d_tiles, q.ntiles, 0, mode, flags, d_partials, st)) return false;
+    const int nt = h->plan.threads[q.list];
+    if (launch_step(prec, nt, d_desc, d_tiles, q.ntiles, 0, mode, flags, d_partials, st))
+      return false;
     if (nmt > 0 &&
-        launch_step(prec, d_desc, d_mtiles, nmt, 0, mode, flags, d_partials, st, 1))
+        launch_step(prec, nt, d_desc, d_mtiles, nmt, 0, mode, flags, d_partials, st, 1))
       return false;
     return true;
   };

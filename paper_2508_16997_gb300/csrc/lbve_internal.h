@@ -8,27 +8,32 @@ namespace lbve {
 // Threads per CTA of the step kernel, per storage precision.  Float32: 96
 // (32 x 3 tiles) measured fastest on GB300 among 64..256; seven such CTAs per
 // SM give 21 warps in seven independent load / barrier / compute phases.
-// Float64 (bound by the FP64 pipe): 256 (32 x 8 tiles), two per SM.
+// Float64 (bound by the FP64 pipe): 256 (32 x 8 tiles), two per SM.  A
+// float64 batch too small to give every SM one such tile runs 64-thread CTAs
+// (32 x 2 tiles, eight per SM, the same registers per thread) instead: each
+// SM's FP64 pipe then has a quarter of the nodes to work through.
 #ifndef LBVE_THREADS
 #define LBVE_THREADS 96
 #endif
 #ifndef LBVE_THREADS_FP64
 #define LBVE_THREADS_FP64 256
 #endif
+#ifndef LBVE_THREADS_FP64_SMALL
+#define LBVE_THREADS_FP64_SMALL 64
+#endif
 #ifndef LBVE_TILE_TX
 #define LBVE_TILE_TX 32
 #endif
 constexpr int kThreads = LBVE_THREADS;          // float32 step kernel
 constexpr int kThreads64 = LBVE_THREADS_FP64;   // float64 step kernel
+constexpr int kThreads64Small = LBVE_THREADS_FP64_SMALL;  // float64, small batches
+constexpr int kNumSMs = 152;  // GB300; sizes the small-batch choice only
 constexpr int kTileTX = LBVE_TILE_TX;   // default tile width (nodes along x) for nx >= kTileTX
-// threads per CTA and widest tile a caller may ask for, by precision
-// (0 = float64, 1 = float32, as LBVE_FP64 / LBVE_FP32_DEV)
+// threads per CTA (for float64, the size of all but small batches) and the
+// widest tile a caller may ask for, by precision (0 = float64, 1 = float32,
+// as LBVE_FP64 / LBVE_FP32_DEV)
 __host__ __device__ constexpr int threads_of(int prec) { return prec == 0 ? kThreads64 : kThreads; }
 __host__ __device__ constexpr int tile_tx_max(int prec) { return threads_of(prec) / 2; }
-template <typename R>
-struct StepThreads {
-  static constexpr int value = sizeof(R) == 8 ? kThreads64 : kThreads;
-};
 // Halo region of a tile: (TX+2)(TY+2*hy) <= (TX+2)(T/TX+4) = T + 4 TX + 2 T/TX
 // + 8 for T threads, which is convex in TX and equals 3 (T + 4) at both ends
 // of 1 <= TX <= T/2 (TY = T/TX, hy <= 2).
@@ -120,9 +125,11 @@ struct ColTask {
 // Launchers implemented in lbve_kernels.cu (templated over float/double).
 enum : int { kModeStep = 0, kModeInit = 1 };
 
-// masked = 0 runs the plain kernel (which skips masked tiles), 1 the masked variant.
-int launch_step(int prec, const InstDev* d_insts, const TileDev* d_tiles, int n_tiles,
-                int parity, int mode, int flags, double* d_partials, void* stream,
+// threads: CTA size of the tiles (kThreads for float32; kThreads64 or
+// kThreads64Small for float64).  masked = 0 runs the plain kernel (which
+// skips masked tiles), 1 the masked variant.
+int launch_step(int prec, int threads, const InstDev* d_insts, const TileDev* d_tiles,
+                int n_tiles, int parity, int mode, int flags, double* d_partials, void* stream,
                 int masked = 0);
 // Wall pass before a step: completes the populations of the wall links of
 // n_walls records in the buffer pop[parity]; on the final step it writes one

@@ -7,41 +7,56 @@
 
 namespace lbve {
 
-template <typename R, int MODE, bool FINAL, bool MASKED>
+template <typename R, int MODE, bool FINAL, bool MASKED, int NT>
 static void launch_step_k(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
                           double* d_partials, cudaStream_t st) {
-  step_kernel<R, MODE, FINAL, MASKED><<<n_tiles, StepThreads<R>::value, 0, st>>>(d_insts, d_tiles, parity,
-                                                                    d_partials);
+  step_kernel<R, MODE, FINAL, MASKED, NT><<<n_tiles, NT, 0, st>>>(d_insts, d_tiles, parity,
+                                                                  d_partials);
 }
 
-template <typename R, bool MASKED>
+template <typename R, bool MASKED, int NT>
 static int launch_step_t(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
                          int mode, int flags, double* d_partials, cudaStream_t st) {
   if (n_tiles <= 0) return 0;
   const bool fin = (flags & kFinal) != 0;
   if (mode == kModeStep) {
     if (fin)
-      launch_step_k<R, kModeStep, true, MASKED>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
+      launch_step_k<R, kModeStep, true, MASKED, NT>(d_insts, d_tiles, n_tiles, parity, d_partials,
+                                                    st);
     else
-      launch_step_k<R, kModeStep, false, MASKED>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
+      launch_step_k<R, kModeStep, false, MASKED, NT>(d_insts, d_tiles, n_tiles, parity,
+                                                     d_partials, st);
   } else {
-    launch_step_k<R, kModeInit, true, MASKED>(d_insts, d_tiles, n_tiles, parity, d_partials, st);
+    launch_step_k<R, kModeInit, true, MASKED, NT>(d_insts, d_tiles, n_tiles, parity, d_partials,
+                                                  st);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_step(int prec, const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
-                int mode, int flags, double* d_partials, void* stream, int masked) {
-  cudaStream_t st = (cudaStream_t)stream;
-  if (prec == 0)
-    return masked ? launch_step_t<double, true>(d_insts, d_tiles, n_tiles, parity, mode, flags,
-                                                d_partials, st)
-                  : launch_step_t<double, false>(d_insts, d_tiles, n_tiles, parity, mode, flags,
-                                                 d_partials, st);
-  return masked ? launch_step_t<float, true>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+template <typename R, int NT>
+static int launch_step_m(const InstDev* d_insts, const TileDev* d_tiles, int n_tiles, int parity,
+                         int mode, int flags, double* d_partials, cudaStream_t st, int masked) {
+  return masked ? launch_step_t<R, true, NT>(d_insts, d_tiles, n_tiles, parity, mode, flags,
                                              d_partials, st)
-                : launch_step_t<float, false>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                : launch_step_t<R, false, NT>(d_insts, d_tiles, n_tiles, parity, mode, flags,
                                               d_partials, st);
+}
+
+// Only the CTA sizes the host plans are instantiated; any other is refused.
+int launch_step(int prec, int threads, const InstDev* d_insts, const TileDev* d_tiles,
+                int n_tiles, int parity, int mode, int flags, double* d_partials, void* stream,
+                int masked) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == 0 && threads == kThreads64)
+    return launch_step_m<double, kThreads64>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                                             d_partials, st, masked);
+  if (prec == 0 && threads == kThreads64Small)
+    return launch_step_m<double, kThreads64Small>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                                                  d_partials, st, masked);
+  if (prec == 1 && threads == kThreads)
+    return launch_step_m<float, kThreads>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                                          d_partials, st, masked);
+  return -1;
 }
 
 // One CTA per instance: sum (max for the residual) the partial records of the

@@ -520,11 +520,12 @@ __device__ __forceinline__ R y_drho(bool wb, bool wt, R rm2, R rm1, R r0, R rp1,
 #ifndef LBVE_FP32_MASKED_MIN_BLOCKS
 #define LBVE_FP32_MASKED_MIN_BLOCKS 5
 #endif
-template <typename R, bool MASKED>
+// Float64 CTAs of NT threads: 512 / NT per SM (128 registers per thread).
+template <typename R, bool MASKED, int NT>
 struct MinBlocks {
   static constexpr int value =
       sizeof(R) == 4 ? (MASKED ? LBVE_FP32_MASKED_MIN_BLOCKS : LBVE_FP32_MIN_BLOCKS)
-                     : (kThreads64 <= 256 ? 512 / kThreads64 : 1);
+                     : (NT <= 512 ? 512 / NT : 1);
 };
 
 // One-sided differences along one axis next to the solid mask (same rule as
@@ -592,7 +593,7 @@ __device__ __forceinline__ void region_rho_u(const InstDev& D, const void* src,
   node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, rho, ux, uy);
 }
 
-template <typename R, int MODE, bool FINAL, bool MASKED>
+template <typename R, int MODE, bool FINAL, bool MASKED, int NT>
 __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, const TileDev T,
                                              int parity, double* __restrict__ partials, R* s_rho,
                                              R* s_ux, R* s_uy, double (*s_red)[kPartial]) {
@@ -646,7 +647,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     int lx, ly;
     bool in_domain;
     if (t32) {
-      ring_slot(threadIdx.x, kTileTX + 2, StepThreads<R>::value / kTileTX, hy, lx, ly);
+      ring_slot(threadIdx.x, kTileTX + 2, NT / kTileTX, hy, lx, ly);
       in_domain = region_node_once(lx, ly, T.x0, T.y0, hy, nx, ny, py, rgx, rgy);
     } else {
       ring_slot(threadIdx.x, RW, TY, hy, lx, ly);
@@ -894,27 +895,30 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     if (threadIdx.x < 14) {
       const int j = threadIdx.x;
       double v = s_red[0][j];
-      for (int w = 1; w < StepThreads<R>::value / 32; ++w)
+      for (int w = 1; w < NT / 32; ++w)
         v = (j == kResid) ? fmax(v, s_red[w][j]) : v + s_red[w][j];
       partials[(size_t)T.slot * kPartial + j] = v;
     }
   }
 }
 
-// One CTA per tile.  The plain variant leaves masked tiles to the masked one
-// (which runs over a separate list of just those tiles).
-template <typename R, int MODE, bool FINAL, bool MASKED>
-__global__ void __launch_bounds__(StepThreads<R>::value, MinBlocks<R, MASKED>::value)
+// One CTA of NT threads per tile (NT a multiple of 32, at least 32, with
+// TX * TY <= NT for every tile of the launch).  The plain variant leaves
+// masked tiles to the masked one (which runs over a separate list of just
+// those tiles).
+template <typename R, int MODE, bool FINAL, bool MASKED, int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<R, MASKED, NT>::value)
     step_kernel(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles,
                 int parity, double* __restrict__ partials) {
-  constexpr int kRegion = region_max(StepThreads<R>::value);
+  static_assert(NT % 32 == 0 && NT >= 32, "whole warps; the final-step reduction reads 14 lanes");
+  constexpr int kRegion = region_max(NT);
   __shared__ R s_rho[kRegion];
   __shared__ R s_ux[kRegion];
   __shared__ R s_uy[kRegion];
-  __shared__ double s_red[StepThreads<R>::value / 32][kPartial];
+  __shared__ double s_red[NT / 32][kPartial];
   const TileDev T = tiles[blockIdx.x];
   if (!MASKED && T.masked) return;
-  process_tile<R, MODE, FINAL, MASKED>(insts, T, parity, partials, s_rho, s_ux, s_uy, s_red);
+  process_tile<R, MODE, FINAL, MASKED, NT>(insts, T, parity, partials, s_rho, s_ux, s_uy, s_red);
 }
 
 }  // namespace lbve
