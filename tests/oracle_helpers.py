@@ -20,3 +20,13 @@ def oracle_sim(inst, init=None, **override):
     if getattr(inst, "open_x", False) and getattr(inst, "inlet", None) is not None:
         s.set_inlet(inst.inlet)
     return s
+
+
+def oracle_fields_after(job):
+    """Process-pool worker: the oracle's fields after `steps` steps of `inst`
+    from its default initial state.  job = (inst, steps)."""
+    inst, steps = job
+    o.build()
+    s = oracle_sim(inst)
+    s.step(steps)
+    return s.fields()

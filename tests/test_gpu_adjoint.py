@@ -248,3 +248,71 @@ def test_adjoint_checkpoint_interval_does_not_change_gradient(lbve, precision):
         assert np.abs(grads[0]).max() > 0
         np.testing.assert_array_equal(grads[1], grads[0])
         np.testing.assert_array_equal(grads[2], grads[0])
+
+
+def test_adjoint_workload_fd_gate_32(lbve):
+    """The adjoint workload's finite-difference gate on a 32^2 oracle: the
+    four-roll mill with the small configuration's parameters (beta 0.5,
+    Wi 5, Re 0.01, Sc 1e5, Ma 1e-3), T = 2000 steps from rest (the adjoint
+    workload's horizon; checkpoints every 45 steps), loss
+    L = 1/2 sum |u(T) - u_t|^2 with u_t from the oracle run with the force
+    F + 0.01 F0 xi (xi ~ N(0, 1) per node and component, seed 5).  The FP64
+    adjoint against fourth-order central differences of the oracle with
+    h = 1e-3 F0: the three largest and three random entries of dL/dF to 1e-6
+    of the largest entry, and three random directions to 1e-6 relative.
+    Calibration on the oracle: the directional difference at h = 1e-3 F0
+    and at 1e-2 F0 agree to 5e-10 relative.  The 37 oracle runs (2 s each)
+    go to a spawn pool over the host cores (this process holds a CUDA
+    context)."""
+    import copy
+    import multiprocessing as mp
+    import os
+    import torch
+    from oracle_helpers import oracle_fields_after
+    N, T = 32, 2000
+    inst = wl.frm(N)
+    F = inst.force_field.copy()
+    F0 = float(np.abs(F).max())
+    xi = np.random.default_rng(5).standard_normal(F.shape)
+
+    def with_force(Fp):
+        i = copy.copy(inst)
+        i.force_field = Fp
+        return i
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        ut = pool.map(oracle_fields_after, [(with_force(F + 0.01 * F0 * xi), T)])[0][1:3]
+        sim = lbve.Simulation([inst], precision=0)
+        sim.step(T)
+        g_fields = np.zeros((6, N, N))
+        g_fields[1:3] = sim.fields(0)[1:3] - ut
+        d_g = torch.from_numpy(g_fields).cuda()
+        nbytes = lbve.lbve_adjoint_workspace_bytes(sim.h, 0, T)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        out = torch.empty((2, N, N), dtype=torch.float64, device="cuda")
+        lbve.lbve_adjoint_step(sim.h, 0, None, d_g.data_ptr(), T, ws.data_ptr(), nbytes,
+                               out.data_ptr(), inst.n_nodes)
+        g = out.cpu().numpy()
+        scale = np.abs(g).max()
+        assert scale > 0
+
+        rng = np.random.default_rng(6)
+        dirs = []
+        for flat in list(np.argsort(np.abs(g).ravel())[-3:]) + list(rng.integers(g.size, size=3)):
+            v = np.zeros(g.size)
+            v[flat] = 1.0
+            dirs.append(("entry", v.reshape(g.shape)))
+        for _ in range(3):
+            dirs.append(("direction", rng.standard_normal(g.shape)))
+        h = 1e-3 * F0
+        jobs = [(with_force(F + s * h * v), T) for _, v in dirs for s in (1, -1, 2, -2)]
+        us = [f[1:3] for f in pool.map(oracle_fields_after, jobs)]
+    losses = np.array([0.5 * float(((u - ut) ** 2).sum()) for u in us]).reshape(len(dirs), 4)
+    for (kind, v), (lp1, lm1, lp2, lm2) in zip(dirs, losses):
+        fd = (8 * (lp1 - lm1) - (lp2 - lm2)) / (12 * h)
+        ad = float(np.sum(g * v))
+        if kind == "entry":
+            assert abs(ad - fd) <= 1e-6 * scale, (kind, ad, fd, scale)
+        else:
+            assert abs(ad - fd) <= 1e-6 * abs(fd), (kind, ad, fd)
