@@ -56,7 +56,7 @@ int launch_adjoint(int prec, int mode, int pass, const InstDev* d_desc, const Ad
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == 0) run_mode<double>(mode, pass, d_desc, cast_args<double>(a), blocks, st);
   else run_mode<float>(mode, pass, d_desc, cast_args<float>(a), blocks, st);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 
 }  // namespace lbve

@@ -30,7 +30,7 @@ static int launch_step_t(const InstDev* d_insts, const TileDev* d_tiles, int n_t
     launch_step_k<R, kModeInit, true, MASKED, NT>(d_insts, d_tiles, n_tiles, parity, d_partials,
                                                   st);
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 
 template <typename R, int NT>
@@ -102,7 +102,7 @@ int launch_reduce(const InstDev* d_insts, int first_inst, int n_insts, const dou
   if (n_insts <= 0) return 0;
   reduce_kernel<<<n_insts, 256, 0, (cudaStream_t)stream>>>(d_insts, first_inst, d_partials,
                                                            d_totals, d_flags);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 
 template <typename R>
@@ -124,7 +124,7 @@ int launch_convert_force(int prec, const double* d_src, void* d_dst, int n, int 
   else
     convert_force_kernel<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(d_src, (float*)d_dst, n,
                                                                          stride);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 
 }  // namespace lbve

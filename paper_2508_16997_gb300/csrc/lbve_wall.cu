@@ -275,7 +275,7 @@ int launch_wall_t(const InstDev* d_insts, const WallDev* d_walls, double* d_rec,
     wall_kernel<R, true><<<grid, kWallThreads, 0, st>>>(d_insts, d_walls, n, parity, d_rec);
   else
     wall_kernel<R, false><<<grid, kWallThreads, 0, st>>>(d_insts, d_walls, n, parity, d_rec);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 
 }  // namespace
@@ -289,7 +289,7 @@ int launch_column(int prec, const InstDev* d_insts, const ColTask* d_tasks, int 
     column_kernel<double><<<grid, kWallThreads, 0, st>>>(d_insts, d_tasks, n, parity);
   else
     column_kernel<float><<<grid, kWallThreads, 0, st>>>(d_insts, d_tasks, n, parity);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 
 int launch_wall(int prec, const InstDev* d_insts, const WallDev* d_walls, double* d_rec, int n,
