@@ -178,6 +178,41 @@ def test_cnebb_node(oracle_mod):
         assert abs(win - wout) < 1e-15 and abs(wout - gpost[H].sum()) < 1e-15
 
 
+def test_cnebb_node_every_unknown_set(oracle_mod):
+    """The same statements for every unknown set a mask wall can produce: any
+    choice of none, one or the other end of each of the four lattice lines
+    (1,3), (2,4), (5,7), (6,8) except the empty set, 3^4 - 1 = 80 sets (both
+    ends of one line unknown is excluded by the validity rule R23).  Corner
+    and concave-step nodes are among them; the set rule must close the
+    budget there too."""
+    import itertools
+    rng = _rng(16)
+    opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+    lines = ((1, 3), (2, 4), (5, 7), (6, 8))
+    n_sets = 0
+    for choice in itertools.product((None, 0, 1), repeat=4):
+        unknown = tuple(line[c] for line, c in zip(lines, choice) if c is not None)
+        if not unknown:
+            continue
+        n_sets += 1
+        known = np.array([0 if i in unknown else 1 for i in range(9)])
+        g = W * (1.0 + 0.3 * rng.standard_normal(9))
+        gpost = W * (1.0 + 0.3 * rng.standard_normal(9))
+        ux, uy = 0.02 * rng.standard_normal(2)
+        out, win, wout = oracle_mod.cnebb(g, gpost, known, ux, uy)
+        H = [opp[i] for i in unknown]
+        phi_b = g[known == 1].sum() + gpost[H].sum()
+        assert abs(out.sum() - phi_b) < 1e-15, unknown
+        geq = oracle_mod.geq(phi_b, ux, uy)
+        for i in unknown:
+            assert abs((out[i] - out[opp[i]]) - (geq[i] - geq[opp[i]])) < 1e-15, unknown
+        for i in range(1, 9):
+            if known[i]:
+                assert out[i] == g[i], unknown
+        assert abs(win - wout) < 1e-15 and abs(wout - gpost[H].sum()) < 1e-15, unknown
+    assert n_sets == 80
+
+
 # --------------------------------------------------------------------------
 # Whole-step invariants
 # --------------------------------------------------------------------------
