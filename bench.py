@@ -44,6 +44,7 @@ def parse_args():
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--cylinder-steps", type=int, default=2000)
     ap.add_argument("--frm64-steps", type=int, default=2000)
+    ap.add_argument("--error-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -56,6 +57,13 @@ def rank_seed(rank: int) -> int:
 def workload(rank: int, n: int):
     from paper_2508_16997_gb300 import workloads as wl
     return wl.batch_mix(n=n, base_seed=rank_seed(rank))
+
+
+def workspace_bytes(insts, precision: int = 1) -> int:
+    """Device workspace a rank's batch needs (lbve_workspace_bytes, a host-only
+    call of the library): the plan of its buffers in HBM."""
+    from paper_2508_16997_gb300 import lbve
+    return lbve.lbve_workspace_bytes([lbve.params_from(i, precision) for i in insts])
 
 
 def job_value(job_nodes: int, steps: int, seconds_max: float) -> float:
@@ -106,6 +114,12 @@ class ClockSampler:
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
+
+    def wait_first(self, timeout: float = 3.0):
+        """Wait until the first sample has arrived (or the sampler is absent)."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.02)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -375,27 +389,43 @@ def run_ours(args):
     K, W = args.steps, args.warmup
 
     # ---- headline: FP32-deviation batch, inputs resident in HBM -------------
+    # The clock sampler starts before the warm-up, so that its start-up does
+    # not leave the GPU idle right before the timed steps.  The library times
+    # every launch of the step kernel in the timed region with CUDA events on
+    # the stream it launches on (lbve_profile), next to the whole region.
     sim = lbve.Simulation(insts, precision=lbve.LBVE_FP32_DEV)
-    sim.step(W)
-    torch.cuda.synchronize()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ws_bytes = sim.nbytes
     with ClockSampler(local) as clk:
+        clk.wait_first()
+        sim.step(W)
+        torch.cuda.synchronize()
+        barrier()
+        lbve.lbve_profile(sim.h, K)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
         sim.step(K)
         e1.record(stream)
         torch.cuda.synchronize()
-    barrier()
+        barrier()
     ms = max_over_ranks(e0.elapsed_time(e1))
+    n_timed, k_tot, k_min, k_max = lbve.lbve_profile_read(sim.h, lbve.LBVE_FP32_DEV)
+    lbve.lbve_profile(sim.h, 0)
+    kernel_ms = max_over_ranks(k_tot / max(n_timed, 1))
     flags = sim.status()
     value = job_value(job_nodes, K, ms / 1e3)
     bytes_launch = sum(i.n_nodes * bytes_per_lu(i, 4) for i in insts)
-    achieved = bytes_launch / (ms / 1e3 / K) / 1e9
+    achieved = bytes_launch / (kernel_ms / 1e3) / 1e9
+    achieved_step = bytes_launch / (ms / 1e3 / K) / 1e9
     peak, peak_kind = measured_peaks()
 
     # ---- end to end through the C ABI with host buffers --------------------
+    # One call of the public API per instance uploads its state (pinned host
+    # force field and initial fields) and initialises it, lbve_step(K)
+    # advances the batch, lbve_fields copies every instance's fields back to
+    # pinned host memory.  The upload happens once per K steps: bytes are
+    # stated per call and per step (per call / K).
     pinned_force = [None if i.force_field is None else
                     torch.from_numpy(np.ascontiguousarray(i.force_field)).pin_memory()
                     for i in insts]
@@ -417,19 +447,28 @@ def run_ours(args):
         lbve.lbve_set_geometry(sim.h, j, None,
                                None if pinned_force[j] is None else pinned_force[j].numpy(),
                                pinned_init[j].numpy(), n_nodes=inst.n_nodes)
+    t1 = time.perf_counter()
     sim.step(K)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     for j in range(len(insts)):
         lbve.lbve_fields(sim.h, j, pinned_out[j].data_ptr(), False)
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    t3 = time.perf_counter()
+    e2e_s = max_over_ranks(t3 - t0)
     e2e_value = job_value(job_nodes, K, e2e_s)
 
     # ---- plain FP64 on the same mix, and the FP32 error against it ---------
-    K64 = max(1, K // 10)
+    # FP64 is timed over K64 steps (per-launch kernel time alongside); both
+    # precisions then run to E steps from the same initial state and the
+    # FP32 fields are compared with the FP64 ones, per decade of Wi.
+    K64 = max(1, min(K, 200))
+    E = max(args.error_steps, W + K64)
     sim64 = lbve.Simulation(insts, precision=lbve.LBVE_FP64)
     sim64.step(W)
     torch.cuda.synchronize()
     barrier()
+    lbve.lbve_profile(sim64.h, K64)
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
@@ -437,13 +476,20 @@ def run_ours(args):
     f1.record(stream)
     torch.cuda.synchronize()
     ms64 = max_over_ranks(f0.elapsed_time(f1))
+    n64, k64_tot, _, _ = lbve.lbve_profile_read(sim64.h, lbve.LBVE_FP64)
+    lbve.lbve_profile(sim64.h, 0)
+    kernel_ms64 = max_over_ranks(k64_tot / max(n64, 1))
     value64 = job_value(job_nodes, K64, ms64 / 1e3)
+    sim64.step(E - W - K64)
     for j in range(len(insts)):  # FP32 run from the same initial state, same step count
         lbve.lbve_set_geometry(sim.h, j, None, insts[j].force_field, None,
                                n_nodes=insts[j].n_nodes)
-    sim.step(W + K64)
-    err_all, err_le100 = 0.0, 0.0
+    sim.step(E)
     flags64 = sim64.status()
+    bins = {"1-10": (1.0, 10.0), "10-100": (10.0, 100.0), "100-1e3": (100.0, 1e3),
+            "1e3-1e4": (1e3, 1e4 + 1)}
+    per_bin = {k: {"u": 0.0, "C": 0.0, "instances": 0} for k in bins}
+    err_all, err_le100 = 0.0, 0.0
     for j, inst in enumerate(insts):
         if flags64[j]:
             continue
@@ -455,6 +501,12 @@ def run_ours(args):
         err_all = max(err_all, e)
         if inst.Wi <= 100:
             err_le100 = max(err_le100, e)
+        for k, (lo, hi) in bins.items():
+            if lo <= inst.Wi < hi:
+                b_ = per_bin[k]
+                b_["u"] = max(b_["u"], eu)
+                b_["C"] = max(b_["C"], eC)
+                b_["instances"] += 1
     err_all = max_over_ranks(err_all)
     err_le100 = max_over_ranks(err_le100)
 
@@ -540,25 +592,36 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_desc(insts, total_nodes),
+        "config": dict(workload_desc(insts, total_nodes), workspace_bytes_per_gpu=ws_bytes),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": measured_traffic(),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_launch,
-                     "kernel": "step_kernel<float> (one launch per step; per-step CUDA-event "
-                               "time incl. the end-of-call reduction)"},
+                     "kernel": "step_kernel<float> (one launch per step)",
+                     "kernel_ms": kernel_ms, "kernel_ms_min": k_min, "kernel_ms_max": k_max,
+                     "launches_timed": n_timed,
+                     "timing": "CUDA events around every step-kernel launch of the timed "
+                               "region, on the stream it is launched on (lbve_profile)",
+                     "whole_step": {"ms": ms / K, "achieved": achieved_step,
+                                    "frac": achieved_step / peak,
+                                    "includes": "the last step's float64 field write and the "
+                                                "end-of-call reduction"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
-                "d2h_bytes_per_step": d2h / K,
-                "region": "lbve_set_geometry (pinned host force + initial fields) for every "
-                          "instance, lbve_step(K), lbve_fields to pinned host"},
+                "d2h_bytes_per_step": d2h / K, "h2d_bytes_per_call": h2d,
+                "d2h_bytes_per_call": d2h, "steps_per_call": K,
+                "seconds": {"upload_and_init": t1 - t0, "steps": t2 - t1, "download": t3 - t2},
+                "region": "once per K steps: lbve_set_geometry (pinned host force + initial "
+                          "fields) for every instance, lbve_step(K), lbve_fields of every "
+                          "instance to pinned host"},
         "flops": measured_flops(value),
         "gpu_launches": K + 1,
         "clocks": clocks,
         "fp64_plain": {"value": value64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64,
+                       "kernel_ms": kernel_ms64,
                        "speedup_fp32_over_fp64": value / value64,
                        "roofline": measured_fp64_pipe(value64)},
         "fp32_vs_fp64_rel_l2": {"max_all": err_all, "max_Wi_le_100": err_le100,
-                                "steps": W + K64, "target_Wi_le_100": 1e-5},
+                                "per_Wi": per_bin, "steps": E, "target_Wi_le_100": 1e-5},
         "nonfinite_instances": int((flags != 0).sum()),
     }
     if adj is not None:

@@ -223,6 +223,27 @@ int lbve_set_wall_distances(lbve_handle* h, int32_t inst, int32_t n_links, const
  * LBVE_ERR_CUDA if a launch failed. */
 int lbve_step(lbve_handle* h, int64_t n_steps);
 
+/* Per-launch timing of the step kernel (the paper has no counterpart: a
+ * measurement facility).  Synchronises the stream and arms CUDA events
+ * around each of the next max_launches launches of the plain (unmasked) step
+ * kernel of each precision, recorded on the handle's stream; the earlier
+ * events are released.  While armed, lbve_step launches every step directly
+ * instead of replaying its graph, so that each launch gets its own events.
+ * max_launches = 0 disarms and releases the events.  Launches beyond
+ * max_launches run untimed.
+ * Errors: LBVE_ERR_ARG (max_launches outside [0, 2^20]), LBVE_ERR_STATE (the
+ * stream is capturing), LBVE_ERR_CUDA. */
+int lbve_profile(lbve_handle* h, int32_t max_launches);
+
+/* Read the launches timed since lbve_profile() for the step kernel of one
+ * precision (LBVE_FP64 or LBVE_FP32_DEV): their number, the sum of their
+ * durations and the shortest and longest (ms; ms_min, ms_max may be NULL).
+ * Waits for the last timed launch to finish.  Zero launches when nothing was
+ * armed or no instance has that precision.
+ * Errors: LBVE_ERR_ARG, LBVE_ERR_CUDA. */
+int lbve_profile_read(lbve_handle* h, int32_t precision, int32_t* launches, double* ms_total,
+                      double* ms_min, double* ms_max);
+
 /* Synchronise the stream and copy per-instance status flags into
  * flags[0..n-1] (bit 0: a non-finite field was seen at the end of an
  * lbve_step call).  Returns LBVE_ERR_NONFINITE if any flag is set. */
@@ -353,15 +374,17 @@ int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* init_fields
  * Asynchronous on cuda_stream (a cudaStream_t, NULL for the default stream).
  * Scratch: one file-scope static device array of 16384 partial records
  * (1 MiB) that every GPU loading the library keeps until the process exits;
- * it limits a call to nx * ny <= 16,777,216 nodes (LBVE_ERR_ARG beyond, with
- * a message on stderr).  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call shares the array and
+ * it limits a call to nx * ny <= 16,777,216 nodes (LBVE_ERR_ARG beyond).  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * call the entry point after cudaDeviceReset (the array may then move).  Every call shares the array and
  * leaves its records behind; each call overwrites the records it reads, so
  * nothing needs clearing, but calls that overlap on the GPU (other streams,
  * other threads) race on it and must be serialised by the caller.
  * Errors: LBVE_ERR_ARG (null pointer, bad size, over the limit),
- * LBVE_ERR_CUDA (device query, symbol lookup or launch failed). */
+ * LBVE_ERR_CUDA (device query, symbol lookup or launch failed); every error
+ * leaves its detail in lbve_last_error(). */
 int lbve_field_totals_noalloc(const double* d_fields, int32_t nx, int32_t ny, double* d_out,
                               void* cuda_stream);
 

@@ -20,11 +20,11 @@
 using namespace lbve;
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
-int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
-int fail(int code, const char* fmt, ...) {
+namespace lbve {
+int set_error(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -33,9 +33,13 @@ int fail(int code, const char* fmt, ...) {
   g_last_error = buf;
   return code;
 }
+}  // namespace lbve
+
+namespace {
+
 
 int cuda_fail(cudaError_t e, const char* what) {
-  return fail(LBVE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(LBVE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
 constexpr size_t kAlign = 256;
@@ -66,44 +70,44 @@ Coeffs derive(const lbve_params& p) {
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 int validate(const lbve_params& p, int i) {
-  if (p.nx < 1 || p.ny < 1) return fail(LBVE_ERR_ARG, "instance %d: nx, ny must be >= 1", i);
+  if (p.nx < 1 || p.ny < 1) return set_error(LBVE_ERR_ARG, "instance %d: nx, ny must be >= 1", i);
   if (!p.periodic_y && p.ny < 3)
-    return fail(LBVE_ERR_ARG, "instance %d: a walled channel needs ny >= 3", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: a walled channel needs ny >= 3", i);
   if (int64_t(p.nx) * p.ny > kMaxNodes)
-    return fail(LBVE_ERR_ARG, "instance %d: more than %lld nodes", i, (long long)kMaxNodes);
+    return set_error(LBVE_ERR_ARG, "instance %d: more than %lld nodes", i, (long long)kMaxNodes);
   if (p.precision != LBVE_FP64 && p.precision != LBVE_FP32_DEV)
-    return fail(LBVE_ERR_ARG, "instance %d: unknown precision %d", i, p.precision);
+    return set_error(LBVE_ERR_ARG, "instance %d: unknown precision %d", i, p.precision);
   if (p.periodic_y != 0 && p.periodic_y != 1)
-    return fail(LBVE_ERR_ARG, "instance %d: periodic_y must be 0 or 1", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: periodic_y must be 0 or 1", i);
   if (!(std::isfinite(p.beta) && p.beta > 0.0 && p.beta <= 1.0))
-    return fail(LBVE_ERR_ARG, "instance %d: beta must be in (0, 1]", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: beta must be in (0, 1]", i);
   if (!finite_pos(p.Wi) || !finite_pos(p.Re) || !finite_pos(p.Sc) || !finite_pos(p.Ma) ||
       !finite_pos(p.Lc) || !finite_pos(p.Lambda_s) || !finite_pos(p.Lambda_p))
-    return fail(LBVE_ERR_ARG, "instance %d: Wi, Re, Sc, Ma, Lc, Lambda_s, Lambda_p must be > 0",
+    return set_error(LBVE_ERR_ARG, "instance %d: Wi, Re, Sc, Ma, Lc, Lambda_s, Lambda_p must be > 0",
                 i);
   if (!std::isfinite(p.Fx) || !std::isfinite(p.Fy))
-    return fail(LBVE_ERR_ARG, "instance %d: body force must be finite", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: body force must be finite", i);
   if (p.model < 0 || p.model > 2)
-    return fail(LBVE_ERR_ARG, "instance %d: model must be 0 (Oldroyd-B), 1 (FENE-P) or 2 (FENE-CR)",
+    return set_error(LBVE_ERR_ARG, "instance %d: model must be 0 (Oldroyd-B), 1 (FENE-P) or 2 (FENE-CR)",
                 i);
   if (p.model != 0 && !(std::isfinite(p.L2) && p.L2 > 2.0))
-    return fail(LBVE_ERR_ARG, "instance %d: a FENE model needs L2 > 2", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: a FENE model needs L2 > 2", i);
   if (p.gtilde != 0 && p.gtilde != 1)
-    return fail(LBVE_ERR_ARG, "instance %d: gtilde must be 0 or 1", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: gtilde must be 0 or 1", i);
   if (p.open_x != 0 && p.open_x != 1)
-    return fail(LBVE_ERR_ARG, "instance %d: open_x must be 0 or 1", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: open_x must be 0 or 1", i);
   if (p.open_x && p.nx < 5)
-    return fail(LBVE_ERR_ARG, "instance %d: an open channel needs nx >= 5", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: an open channel needs nx >= 5", i);
   if (p.max_wall_nodes < 0 || int64_t(p.max_wall_nodes) > int64_t(p.nx) * p.ny)
-    return fail(LBVE_ERR_ARG, "instance %d: max_wall_nodes must be in [0, nx*ny]", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: max_wall_nodes must be in [0, nx*ny]", i);
   if (p.tile_tx != 0 &&
       (p.tile_tx < 1 || p.tile_tx > tile_tx_max(p.precision) || p.tile_tx > p.nx))
-    return fail(LBVE_ERR_ARG, "instance %d: tile_tx must be 0 or in [1, min(%d, nx)]", i,
+    return set_error(LBVE_ERR_ARG, "instance %d: tile_tx must be 0 or in [1, min(%d, nx)]", i,
                 tile_tx_max(p.precision));
   const Coeffs c = derive(p);
   if (!(c.tau_s1 > 0.5) || !(c.tau_p1 > 0.5) || !std::isfinite(c.tau_s2) ||
       !std::isfinite(c.tau_p2) || !finite_pos(c.lambda))
-    return fail(LBVE_ERR_ARG, "instance %d: derived relaxation times are degenerate", i);
+    return set_error(LBVE_ERR_ARG, "instance %d: derived relaxation times are degenerate", i);
   return LBVE_OK;
 }
 
@@ -131,11 +135,20 @@ struct Plan {
   int ncols[kLists];      // open-column tasks per list
 };
 
-int default_tile_tx(const lbve_params& p) { return p.nx >= kTileTX ? kTileTX : p.nx; }
+// Default tile width: 32 (one warp along x), or 8 for the one-warp float64
+// CTAs, whose 8 x 4 tiles have a third of the halo ring of 32 x 1 tiles.
+int default_tile_tx(const lbve_params& p, int threads = kThreads) {
+  const int w = threads == kThreads64Tiny ? kTileTXTiny : kTileTX;
+  return p.nx >= w ? w : p.nx;
+}
+
+int tile_width(const lbve_params& p, int threads) {
+  return p.tile_tx > 0 ? p.tile_tx : default_tile_tx(p, threads);
+}
 
 // Tile of TX x (threads / TX) nodes for CTAs of `threads` threads.
 void tile_shape(const lbve_params& p, int threads, int& TX, int& TY, int& hy) {
-  TX = p.tile_tx > 0 ? p.tile_tx : default_tile_tx(p);
+  TX = tile_width(p, threads);
   TY = threads / TX;
   hy = p.periodic_y ? 1 : 2;
 }
@@ -154,6 +167,8 @@ int64_t max_tiles(const lbve_params& p) {
     m = std::max(m, tiles_for(p, TX, threads_of(p.precision)));
     if (p.precision == LBVE_FP64 && TX <= kThreads64Small / 2)
       m = std::max(m, tiles_for(p, TX, kThreads64Small));
+    if (p.precision == LBVE_FP64 && TX <= kThreads64Tiny / 2)
+      m = std::max(m, tiles_for(p, TX, kThreads64Tiny));
   }
   return m;
 }
@@ -161,18 +176,26 @@ int64_t max_tiles(const lbve_params& p) {
 // CTA size of the float64 list.  The FP64 pipe bounds the float64 step, so a
 // batch whose 256-thread tiles would not give every SM one tile leaves SMs
 // idle while the others work through 256 nodes each; 64-thread tiles spread
-// the same nodes over four times as many CTAs.  Chosen from the parameters
-// alone (the workspace plan needs no device): the small size when the
-// 256-thread tiles number fewer than the SMs and no float64 instance asks
-// for a tile wider than a 64-thread CTA takes.
+// the same nodes over four times as many CTAs, and one-warp tiles over eight
+// times as many when even the 64-thread tiles number fewer than the SMs.
+// Chosen from the parameters alone (the workspace plan needs no device): the
+// smallest size whose larger neighbour would leave SMs without a tile, as
+// long as no float64 instance asks for a tile wider than half the CTA.
 int fp64_threads(const lbve_params* p, int n) {
-  int64_t big = 0;
+  int64_t t256 = 0, t64 = 0;
+  int maxtx = 0;
+  bool any = false;
   for (int i = 0; i < n; ++i) {
     if (p[i].precision != LBVE_FP64) continue;
     if (p[i].tile_tx > kThreads64Small / 2) return kThreads64;
-    big += tiles_for(p[i], p[i].tile_tx > 0 ? p[i].tile_tx : default_tile_tx(p[i]), kThreads64);
+    any = true;
+    maxtx = std::max(maxtx, (int)p[i].tile_tx);
+    t256 += tiles_for(p[i], tile_width(p[i], kThreads64), kThreads64);
+    t64 += tiles_for(p[i], tile_width(p[i], kThreads64Small), kThreads64Small);
   }
-  return big > 0 && big < kNumSMs ? kThreads64Small : kThreads64;
+  if (!any || t256 >= kNumSMs) return kThreads64;
+  if (maxtx > kThreads64Tiny / 2 || t64 >= kNumSMs) return kThreads64Small;
+  return kThreads64Tiny;
 }
 
 Plan make_plan(const lbve_params* p, int n) {
@@ -301,6 +324,11 @@ struct lbve_handle {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  // per-launch timing of the plain step kernels (lbve_profile): two events
+  // per launch and tile list, recorded on the caller's stream
+  int prof_cap = 0;
+  int prof_n[kLists] = {0, 0};
+  std::vector<cudaEvent_t> prof_ev[kLists];
 };
 
 namespace {
@@ -337,11 +365,21 @@ int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
                     kModeStep, flags,
                     h->d_partials, h->side_stream, 1))
       return cuda_fail(cudaGetLastError(), "masked step kernel launch");
-    if (h->plan.ntiles[l] > 0 &&
-        launch_step(prec, h->plan.threads[l], h->d_insts, h->d_tiles[l], h->plan.ntiles[l],
+    if (h->plan.ntiles[l] <= 0) continue;
+    const bool timed = h->prof_cap > 0 && st == h->stream && h->prof_n[l] < h->prof_cap;
+    if (timed) {
+      const cudaError_t e = cudaEventRecord(h->prof_ev[l][2 * h->prof_n[l]], st);
+      if (e != cudaSuccess) return cuda_fail(e, "profile event");
+    }
+    if (launch_step(prec, h->plan.threads[l], h->d_insts, h->d_tiles[l], h->plan.ntiles[l],
                     parity, kModeStep, flags,
                     h->d_partials, st))
       return cuda_fail(cudaGetLastError(), "step kernel launch");
+    if (timed) {
+      const cudaError_t e = cudaEventRecord(h->prof_ev[l][2 * h->prof_n[l] + 1], st);
+      if (e != cudaSuccess) return cuda_fail(e, "profile event");
+      ++h->prof_n[l];
+    }
   }
   if (fork) {
     cudaError_t e = cudaEventRecord(h->ev_join, h->side_stream);
@@ -382,6 +420,25 @@ void drop_graph(lbve_handle* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   h->graph_exec = nullptr;
   h->graph = nullptr;
+}
+
+// Whether every value is finite (exponent field not all ones); branch-free,
+// so that the host compiler vectorises it over large arrays.
+bool all_finite(const double* a, size_t n) {
+  uint64_t bad = 0;
+  for (size_t k = 0; k < n; ++k) {
+    uint64_t b;
+    std::memcpy(&b, a + k, sizeof b);
+    bad |= (uint64_t)(((b >> 52) & 0x7ffu) == 0x7ffu);
+  }
+  return bad == 0;
+}
+
+// Whether every value is > 0 (false for NaN), branch-free as all_finite.
+bool all_positive(const double* a, size_t n) {
+  uint64_t bad = 0;
+  for (size_t k = 0; k < n; ++k) bad |= (uint64_t)!(a[k] > 0.0);
+  return bad == 0;
 }
 
 constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -524,11 +581,11 @@ int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
   std::vector<uint8_t> m;
   if (mask) {
     if (p.max_wall_nodes <= 0)
-      return fail(LBVE_ERR_GEOMETRY, "instance %d: max_wall_nodes is 0, so no mask fits", i);
+      return set_error(LBVE_ERR_GEOMETRY, "instance %d: max_wall_nodes is 0, so no mask fits", i);
     m.assign(nn, 0);
     size_t nsolid = 0;
     for (size_t k = 0; k < nn; ++k) nsolid += (m[k] = mask[k] ? 1 : 0);
-    if (nsolid == nn) return fail(LBVE_ERR_GEOMETRY, "instance %d: the mask leaves no fluid", i);
+    if (nsolid == nn) return set_error(LBVE_ERR_GEOMETRY, "instance %d: the mask leaves no fluid", i);
     if (nsolid == 0) m.clear();  // an empty mask is no mask
   }
   if (m.empty() && !had) return LBVE_OK;  // no mask before or after: nothing to change
@@ -550,13 +607,13 @@ int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
       for (int x = 0; x < nx; ++x)
         for (int r = 0; r < 3; ++r)
           if (m[size_t(r) * nx + x] || m[size_t(ny - 1 - r) * nx + x])
-            return fail(LBVE_ERR_GEOMETRY,
+            return set_error(LBVE_ERR_GEOMETRY,
                         "instance %d: rows 0-2 and ny-3..ny-1 of a walled domain must be fluid", i);
     if (p.open_x)
       for (int y = 0; y < ny; ++y)
         for (int r = 0; r < 3; ++r)
           if (m[size_t(y) * nx + r] || m[size_t(y) * nx + nx - 1 - r])
-            return fail(LBVE_ERR_GEOMETRY,
+            return set_error(LBVE_ERR_GEOMETRY,
                         "instance %d: columns 0-2 and nx-3..nx-1 of an open channel must be fluid",
                         i);
     index.assign(nn, -1);
@@ -568,7 +625,7 @@ int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
         for (int d = 1; d < 9; ++d) {
           if (!solid_at(x - kEx[d], y - kEy[d])) continue;
           if (solid_at(x + kEx[d], y + kEy[d]))
-            return fail(LBVE_ERR_GEOMETRY,
+            return set_error(LBVE_ERR_GEOMETRY,
                         "instance %d: fluid node (%d, %d) has solid on both ends of link %d", i,
                         x, y, d);
           umask |= 1 << d;
@@ -577,7 +634,7 @@ int install_mask(lbve_handle* h, int i, const uint8_t* mask) {
         }
         if (!umask) continue;
         if ((int)walls.size() >= p.max_wall_nodes)
-          return fail(LBVE_ERR_GEOMETRY, "instance %d: more wall nodes than max_wall_nodes (%d)",
+          return set_error(LBVE_ERR_GEOMETRY, "instance %d: more wall nodes than max_wall_nodes (%d)",
                       i, p.max_wall_nodes);
         WallDev W;
         std::memset(&W, 0, sizeof(W));
@@ -625,7 +682,7 @@ const char* lbve_error_string(int code) {
 const char* lbve_last_error(void) { return g_last_error.c_str(); }
 
 int lbve_workspace_bytes(const lbve_params* p, int32_t n, size_t* bytes) {
-  if (!p || !bytes || n < 1) return fail(LBVE_ERR_ARG, "null pointer or n_instances < 1");
+  if (!p || !bytes || n < 1) return set_error(LBVE_ERR_ARG, "null pointer or n_instances < 1");
   for (int i = 0; i < n; ++i) {
     const int rc = validate(p[i], i);
     if (rc) return rc;
@@ -636,20 +693,20 @@ int lbve_workspace_bytes(const lbve_params* p, int32_t n, size_t* bytes) {
 
 int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes,
                 void* cuda_stream, lbve_handle** out) {
-  if (!out) return fail(LBVE_ERR_ARG, "out is null");
+  if (!out) return set_error(LBVE_ERR_ARG, "out is null");
   *out = nullptr;
   size_t need = 0;
   int rc = lbve_workspace_bytes(p, n, &need);
   if (rc) return rc;
   if (!d_workspace || bytes < need)
-    return fail(LBVE_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", bytes, need);
+    return set_error(LBVE_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", bytes, need);
   if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)
-    return fail(LBVE_ERR_WORKSPACE, "workspace not %zu-byte aligned", kAlign);
+    return set_error(LBVE_ERR_WORKSPACE, "workspace not %zu-byte aligned", kAlign);
   cudaPointerAttributes attr;
   cudaError_t e = cudaPointerGetAttributes(&attr, d_workspace);
   if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
     cudaGetLastError();
-    return fail(LBVE_ERR_WORKSPACE, "workspace is not device memory");
+    return set_error(LBVE_ERR_WORKSPACE, "workspace is not device memory");
   }
 
   lbve_handle* h = new lbve_handle();
@@ -817,19 +874,17 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
 
 int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
                       const double* body_force, const double* init_fields) {
-  if (!h || inst < 0 || inst >= h->n) return fail(LBVE_ERR_ARG, "bad handle or instance");
+  if (!h || inst < 0 || inst >= h->n) return set_error(LBVE_ERR_ARG, "bad handle or instance");
   {
     // every host-side check before anything changes
     const size_t nn = size_t(h->p[inst].nx) * h->p[inst].ny;
-    if (body_force)
-      for (size_t k = 0; k < 2 * nn; ++k)
-        if (!std::isfinite(body_force[k])) return fail(LBVE_ERR_ARG, "body force not finite");
+    if (body_force && !all_finite(body_force, 2 * nn))
+      return set_error(LBVE_ERR_ARG, "body force not finite");
     if (init_fields) {
-      for (size_t k = 0; k < 6 * nn; ++k)
-        if (!std::isfinite(init_fields[k]))
-          return fail(LBVE_ERR_ARG, "initial fields not finite");
-      for (size_t k = 0; k < nn; ++k)
-        if (!(init_fields[k] > 0.0)) return fail(LBVE_ERR_ARG, "initial density must be > 0");
+      if (!all_finite(init_fields, 6 * nn))
+        return set_error(LBVE_ERR_ARG, "initial fields not finite");
+      if (!all_positive(init_fields, nn))
+        return set_error(LBVE_ERR_ARG, "initial density must be > 0");
     }
     const int rc = install_mask(h, inst, solid_mask);
     if (rc) return rc;
@@ -893,13 +948,14 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
 }
 
 int lbve_step(lbve_handle* h, int64_t n_steps) {
-  if (!h || n_steps < 0) return fail(LBVE_ERR_ARG, "bad handle or negative step count");
+  if (!h || n_steps < 0) return set_error(LBVE_ERR_ARG, "bad handle or negative step count");
   for (int i = 0; i < h->n; ++i)
-    if (!h->ready[i]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", i);
+    if (!h->ready[i]) return set_error(LBVE_ERR_STATE, "instance %d was never initialised", i);
   if (n_steps == 0) return LBVE_OK;
   int64_t left = n_steps - 1;  // non-final steps
-  // non-final steps: whole graphs where possible (they start at parity 0)
-  if (left >= kGraphSteps + (h->parity ? 1 : 0)) {
+  // non-final steps: whole graphs where possible (they start at parity 0);
+  // while lbve_profile times launches, every step is launched directly
+  if (h->prof_cap == 0 && left >= kGraphSteps + (h->parity ? 1 : 0)) {
     if (h->parity) {
       const int rc = launch_one_step(h, 1, 0, h->stream);
       if (rc) return rc;
@@ -930,19 +986,19 @@ int lbve_step(lbve_handle* h, int64_t n_steps) {
 }
 
 int lbve_status(lbve_handle* h, int32_t* flags) {
-  if (!h || !flags) return fail(LBVE_ERR_ARG, "null argument");
+  if (!h || !flags) return set_error(LBVE_ERR_ARG, "null argument");
   cudaError_t e = cudaMemcpyAsync(flags, h->d_flags, sizeof(int32_t) * h->n,
                                   cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbve_status");
   for (int i = 0; i < h->n; ++i)
-    if (flags[i] & 1) return fail(LBVE_ERR_NONFINITE, "instance %d has a non-finite field", i);
+    if (flags[i] & 1) return set_error(LBVE_ERR_NONFINITE, "instance %d has a non-finite field", i);
   return LBVE_OK;
 }
 
 int lbve_fields(lbve_handle* h, int32_t inst, double* out, int32_t on_device) {
-  if (!h || !out || inst < 0 || inst >= h->n) return fail(LBVE_ERR_ARG, "bad argument");
-  if (!h->ready[inst]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", inst);
+  if (!h || !out || inst < 0 || inst >= h->n) return set_error(LBVE_ERR_ARG, "bad argument");
+  if (!h->ready[inst]) return set_error(LBVE_ERR_STATE, "instance %d was never initialised", inst);
   const lbve_params& p = h->p[inst];
   const size_t nn = size_t(p.nx) * p.ny, S = h->plan.inst[inst].stride;
   cudaError_t e = cudaMemcpy2DAsync(out, nn * 8, h->insts[inst].fields, S * 8, nn * 8, 6,
@@ -954,8 +1010,8 @@ int lbve_fields(lbve_handle* h, int32_t inst, double* out, int32_t on_device) {
 }
 
 static int read_totals(lbve_handle* h, int32_t inst, double* rec) {
-  if (!h || inst < 0 || inst >= h->n) return fail(LBVE_ERR_ARG, "bad argument");
-  if (!h->ready[inst]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", inst);
+  if (!h || inst < 0 || inst >= h->n) return set_error(LBVE_ERR_ARG, "bad argument");
+  if (!h->ready[inst]) return set_error(LBVE_ERR_STATE, "instance %d was never initialised", inst);
   cudaError_t e = cudaMemcpyAsync(rec, h->d_totals + (size_t)inst * kTotals,
                                   sizeof(double) * kTotals, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -964,7 +1020,7 @@ static int read_totals(lbve_handle* h, int32_t inst, double* rec) {
 }
 
 int lbve_totals(lbve_handle* h, int32_t inst, double out[LBVE_NTOTALS]) {
-  if (!out) return fail(LBVE_ERR_ARG, "out is null");
+  if (!out) return set_error(LBVE_ERR_ARG, "out is null");
   double rec[kTotals];
   const int rc = read_totals(h, inst, rec);
   if (rc) return rc;
@@ -975,7 +1031,7 @@ int lbve_totals(lbve_handle* h, int32_t inst, double out[LBVE_NTOTALS]) {
 }
 
 int lbve_residual(lbve_handle* h, int32_t inst, double* out) {
-  if (!out) return fail(LBVE_ERR_ARG, "out is null");
+  if (!out) return set_error(LBVE_ERR_ARG, "out is null");
   double rec[kTotals];
   const int rc = read_totals(h, inst, rec);
   if (rc) return rc;
@@ -984,7 +1040,7 @@ int lbve_residual(lbve_handle* h, int32_t inst, double* out) {
 }
 
 int lbve_time(lbve_handle* h, int32_t inst, int64_t* t) {
-  if (!h || !t || inst < 0 || inst >= h->n) return fail(LBVE_ERR_ARG, "bad argument");
+  if (!h || !t || inst < 0 || inst >= h->n) return set_error(LBVE_ERR_ARG, "bad argument");
   *t = h->t[inst];
   return LBVE_OK;
 }
@@ -1009,7 +1065,7 @@ size_t inst_state_bytes(const lbve_params& p) {
 }  // namespace
 
 int lbve_state_bytes(lbve_handle* h, size_t* bytes) {
-  if (!h || !bytes) return fail(LBVE_ERR_ARG, "null argument");
+  if (!h || !bytes) return set_error(LBVE_ERR_ARG, "null argument");
   size_t b = sizeof(StateHeader);
   for (int i = 0; i < h->n; ++i) b += inst_state_bytes(h->p[i]);
   *bytes = b;
@@ -1020,7 +1076,7 @@ int lbve_save(lbve_handle* h, void* host_buf, size_t bytes) {
   size_t need = 0;
   int rc = lbve_state_bytes(h, &need);
   if (rc) return rc;
-  if (!host_buf || bytes < need) return fail(LBVE_ERR_ARG, "state buffer of %zu bytes, %zu needed", bytes, need);
+  if (!host_buf || bytes < need) return set_error(LBVE_ERR_ARG, "state buffer of %zu bytes, %zu needed", bytes, need);
   char* out = (char*)host_buf;
   StateHeader H{kStateMagic, kStateVersion, h->n, 0};
   std::memcpy(out, &H, sizeof(H));
@@ -1060,13 +1116,13 @@ int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes) {
   size_t need = 0;
   int rc = lbve_state_bytes(h, &need);
   if (rc) return rc;
-  if (!host_buf || bytes < need) return fail(LBVE_ERR_ARG, "state buffer of %zu bytes, %zu needed", bytes, need);
+  if (!host_buf || bytes < need) return set_error(LBVE_ERR_ARG, "state buffer of %zu bytes, %zu needed", bytes, need);
   const char* in = (const char*)host_buf;
   StateHeader H;
   std::memcpy(&H, in, sizeof(H));
   in += sizeof(H);
   if (H.magic != kStateMagic || H.version != kStateVersion || H.n != h->n)
-    return fail(LBVE_ERR_ARG, "state was not saved by lbve_save for this instance count");
+    return set_error(LBVE_ERR_ARG, "state was not saved by lbve_save for this instance count");
   // validate every instance header before touching the device
   const char* scan = in;
   for (int i = 0; i < h->n; ++i) {
@@ -1074,9 +1130,9 @@ int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes) {
     std::memcpy(&I, scan, sizeof(I));
     const lbve_params& p = h->p[i];
     if (I.nx != p.nx || I.ny != p.ny || I.precision != p.precision || I.periodic_y != p.periodic_y)
-      return fail(LBVE_ERR_ARG, "saved instance %d does not match this handle's parameters", i);
+      return set_error(LBVE_ERR_ARG, "saved instance %d does not match this handle's parameters", i);
     if (I.geometry != h->geom_hash[i])
-      return fail(LBVE_ERR_GEOMETRY,
+      return set_error(LBVE_ERR_GEOMETRY,
                   "saved instance %d was run on another solid mask (set it before loading)", i);
     scan += inst_state_bytes(p);
   }
@@ -1116,12 +1172,12 @@ int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes) {
 }
 
 int lbve_set_inlet(lbve_handle* h, int32_t inst, const double* inlet) {
-  if (!h || inst < 0 || inst >= h->n || !inlet) return fail(LBVE_ERR_ARG, "bad handle, instance or pointer");
+  if (!h || inst < 0 || inst >= h->n || !inlet) return set_error(LBVE_ERR_ARG, "bad handle, instance or pointer");
   const lbve_params& p = h->p[inst];
-  if (!p.open_x) return fail(LBVE_ERR_GEOMETRY, "instance %d is not an open channel", inst);
+  if (!p.open_x) return set_error(LBVE_ERR_GEOMETRY, "instance %d is not an open channel", inst);
   const size_t cnt = 5 * size_t(p.ny);
   for (size_t k = 0; k < cnt; ++k)
-    if (!std::isfinite(inlet[k])) return fail(LBVE_ERR_ARG, "inlet profile not finite");
+    if (!std::isfinite(inlet[k])) return set_error(LBVE_ERR_ARG, "inlet profile not finite");
   std::vector<double>& in = h->inlet_h[inst];
   in.assign(inlet, inlet + cnt);
   cudaError_t e = cudaMemcpyAsync(h->ws + h->plan.inst[inst].off_inlet, in.data(),
@@ -1135,20 +1191,20 @@ int lbve_set_inlet(lbve_handle* h, int32_t inst, const double* inlet) {
 int lbve_set_wall_distances(lbve_handle* h, int32_t inst, int32_t n_links, const int32_t* node,
                             const int32_t* dir, const double* q) {
   if (!h || inst < 0 || inst >= h->n || n_links < 0 || (n_links > 0 && (!node || !dir || !q)))
-    return fail(LBVE_ERR_ARG, "bad handle, instance, count or pointer");
-  if (!h->insts[inst].mask) return fail(LBVE_ERR_GEOMETRY, "instance %d has no solid mask", inst);
+    return set_error(LBVE_ERR_ARG, "bad handle, instance, count or pointer");
+  if (!h->insts[inst].mask) return set_error(LBVE_ERR_GEOMETRY, "instance %d has no solid mask", inst);
   const lbve_params& p = h->p[inst];
   const int64_t nn = int64_t(p.nx) * p.ny;
   std::vector<WallDev>& W = h->walls_of[inst];
   const std::vector<int32_t>& idx = h->wall_index[inst];
   for (int32_t j = 0; j < n_links; ++j) {
     if (node[j] < 0 || node[j] >= nn || dir[j] < 1 || dir[j] > 8)
-      return fail(LBVE_ERR_ARG, "link %d: node or direction out of range", j);
+      return set_error(LBVE_ERR_ARG, "link %d: node or direction out of range", j);
     const int32_t r = idx[node[j]];
     if (r < 0 || !((W[r].umask >> dir[j]) & 1))
-      return fail(LBVE_ERR_GEOMETRY, "link %d (node %d, direction %d) is not a wall link", j,
+      return set_error(LBVE_ERR_GEOMETRY, "link %d (node %d, direction %d) is not a wall link", j,
                   node[j], dir[j]);
-    if (!(q[j] > 0.0 && q[j] <= 1.0)) return fail(LBVE_ERR_ARG, "link %d: q must be in (0, 1]", j);
+    if (!(q[j] > 0.0 && q[j] <= 1.0)) return set_error(LBVE_ERR_ARG, "link %d: q must be in (0, 1]", j);
   }
   for (int32_t j = 0; j < n_links; ++j) W[idx[node[j]]].q[dir[j] - 1] = q[j];
   const cudaError_t e = upload_walls(h, inst);
@@ -1157,9 +1213,74 @@ int lbve_set_wall_distances(lbve_handle* h, int32_t inst, int32_t n_links, const
   return LBVE_OK;
 }
 
+static void release_profile(lbve_handle* h) {
+  for (int l = 0; l < kLists; ++l) {
+    for (cudaEvent_t e : h->prof_ev[l]) cudaEventDestroy(e);
+    h->prof_ev[l].clear();
+    h->prof_n[l] = 0;
+  }
+  h->prof_cap = 0;
+}
+
+int lbve_profile(lbve_handle* h, int32_t max_launches) {
+  if (!h || max_launches < 0 || max_launches > (1 << 20))
+    return set_error(LBVE_ERR_ARG, "bad handle or max_launches outside [0, 2^20]");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(h->stream, &cs);
+  if (e != cudaSuccess) return cuda_fail(e, "lbve_profile");
+  if (cs != cudaStreamCaptureStatusNone)
+    return set_error(LBVE_ERR_STATE, "lbve_profile: the stream is capturing");
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbve_profile");
+  release_profile(h);
+  if (max_launches == 0) return LBVE_OK;
+  for (int l = 0; l < kLists; ++l) {
+    if (h->plan.ntiles[l] <= 0) continue;
+    h->prof_ev[l].resize(2 * (size_t)max_launches, nullptr);
+    for (auto& ev : h->prof_ev[l]) {
+      e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) {
+        ev = nullptr;
+        release_profile(h);
+        return cuda_fail(e, "lbve_profile: event creation");
+      }
+    }
+  }
+  h->prof_cap = max_launches;
+  return LBVE_OK;
+}
+
+int lbve_profile_read(lbve_handle* h, int32_t precision, int32_t* launches, double* ms_total,
+                      double* ms_min, double* ms_max) {
+  if (!h || !launches || !ms_total || (precision != LBVE_FP64 && precision != LBVE_FP32_DEV))
+    return set_error(LBVE_ERR_ARG, "bad handle, precision or null output");
+  const int l = precision == LBVE_FP64 ? 0 : 1;
+  *launches = 0;
+  *ms_total = 0.0;
+  double lo = 0.0, hi = 0.0;
+  const int n = h->prof_cap > 0 ? h->prof_n[l] : 0;
+  if (n > 0) {
+    cudaError_t e = cudaEventSynchronize(h->prof_ev[l][2 * n - 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "lbve_profile_read");
+    for (int j = 0; j < n; ++j) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, h->prof_ev[l][2 * j], h->prof_ev[l][2 * j + 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "lbve_profile_read");
+      *ms_total += ms;
+      lo = j == 0 ? ms : std::min(lo, (double)ms);
+      hi = j == 0 ? ms : std::max(hi, (double)ms);
+    }
+  }
+  *launches = n;
+  if (ms_min) *ms_min = lo;
+  if (ms_max) *ms_max = hi;
+  return LBVE_OK;
+}
+
 void lbve_destroy(lbve_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  release_profile(h);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1226,23 +1347,28 @@ int time_batch(const std::vector<lbve_params>& q, void* d_ws, size_t bytes, cuda
 
 extern "C" int lbve_autotune(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes,
                              void* cuda_stream, int32_t trial_steps, int32_t* tile_tx_out) {
-  if (!tile_tx_out) return fail(LBVE_ERR_ARG, "tile_tx_out is null");
+  if (!tile_tx_out) return set_error(LBVE_ERR_ARG, "tile_tx_out is null");
   if (trial_steps < 1 || trial_steps > 100000)
-    return fail(LBVE_ERR_ARG, "trial_steps must be in [1, 100000]");
+    return set_error(LBVE_ERR_ARG, "trial_steps must be in [1, 100000]");
   size_t need = 0;
   int rc = lbve_workspace_bytes(p, n, &need);
   if (rc) return rc;
   if (!d_workspace || bytes < need)
-    return fail(LBVE_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", bytes, need);
+    return set_error(LBVE_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", bytes, need);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(st, &cs);
   if (e != cudaSuccess) return cuda_fail(e, "stream query");
   if (cs != cudaStreamCaptureStatusNone)
-    return fail(LBVE_ERR_STATE, "lbve_autotune cannot run while the stream is being captured");
+    return set_error(LBVE_ERR_STATE, "lbve_autotune cannot run while the stream is being captured");
 
   std::vector<lbve_params> q(p, p + n);
-  for (auto& x : q) x.tile_tx = x.tile_tx > 0 ? x.tile_tx : default_tile_tx(x);
+  // the incumbent: every unset width at the default of the CTA size the
+  // batch gets without tuning
+  const int nt64 = fp64_threads(p, n);
+  for (auto& x : q)
+    x.tile_tx = x.tile_tx > 0 ? x.tile_tx
+                              : default_tile_tx(x, x.precision == LBVE_FP64 ? nt64 : kThreads);
   // classes of instances with the same candidates, precision and walls
   std::vector<int> cls(n, -1);
   std::vector<std::vector<int>> cand_of;
@@ -1371,7 +1497,7 @@ AdjPlan make_adj_plan(const lbve_params& p, const InstPlan& q, int64_t T, int nw
 extern "C" int lbve_adjoint_workspace_bytes(lbve_handle* h, int32_t inst, int64_t n_steps,
                                             size_t* bytes) {
   if (!h || !bytes || inst < 0 || inst >= h->n || n_steps < 1)
-    return fail(LBVE_ERR_ARG, "bad handle, instance, step count or output pointer");
+    return set_error(LBVE_ERR_ARG, "bad handle, instance, step count or output pointer");
   *bytes = make_adj_plan(h->p[inst], h->plan.inst[inst], n_steps, (int)h->walls_of[inst].size(),
                          (int)h->mtiles_of[inst].size())
                .total;
@@ -1383,7 +1509,7 @@ extern "C" int lbve_adjoint_workspace_bytes_interval(lbve_handle* h, int32_t ins
                                                      size_t* bytes) {
   if (!h || !bytes || inst < 0 || inst >= h->n || n_steps < 1 || interval < 1 ||
       interval > n_steps)
-    return fail(LBVE_ERR_ARG, "bad handle, instance, step count, interval or output pointer");
+    return set_error(LBVE_ERR_ARG, "bad handle, instance, step count, interval or output pointer");
   *bytes = make_adj_plan(h->p[inst], h->plan.inst[inst], n_steps, (int)h->walls_of[inst].size(),
                          (int)h->mtiles_of[inst].size(), interval)
                .total;
@@ -1395,19 +1521,19 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
                                     int64_t n_steps, void* d_ws, size_t bytes,
                                     double* d_dL_dforce, double* d_dL_dq) {
   if (!h || inst < 0 || inst >= h->n || !d_dL_dforce || n_steps < 1)
-    return fail(LBVE_ERR_ARG, "bad handle, instance, pointer or step count");
-  if (!d_dL_dfields && !dL_ddrag) return fail(LBVE_ERR_ARG, "no loss: dL/dfields and dL/ddrag are null");
-  if (!h->ready[inst]) return fail(LBVE_ERR_STATE, "instance %d was never initialised", inst);
+    return set_error(LBVE_ERR_ARG, "bad handle, instance, pointer or step count");
+  if (!d_dL_dfields && !dL_ddrag) return set_error(LBVE_ERR_ARG, "no loss: dL/dfields and dL/ddrag are null");
+  if (!h->ready[inst]) return set_error(LBVE_ERR_STATE, "instance %d was never initialised", inst);
   if (h->p[inst].open_x)
-    return fail(LBVE_ERR_GEOMETRY, "the adjoint does not cover open channels (instance %d)", inst);
+    return set_error(LBVE_ERR_GEOMETRY, "the adjoint does not cover open channels (instance %d)", inst);
   if (h->p[inst].model != 0 || h->p[inst].gtilde != 0)
-    return fail(LBVE_ERR_ARG, "the adjoint covers Oldroyd-B with eq_p_G_1 only (instance %d)",
+    return set_error(LBVE_ERR_ARG, "the adjoint covers Oldroyd-B with eq_p_G_1 only (instance %d)",
                 inst);
   const bool masked = h->insts[inst].mask != nullptr;
   if (!masked && (dL_ddrag || d_dL_dq))
-    return fail(LBVE_ERR_GEOMETRY, "drag and wall-fraction gradients need a solid mask");
+    return set_error(LBVE_ERR_GEOMETRY, "drag and wall-fraction gradients need a solid mask");
   if (dL_ddrag && !(std::isfinite(dL_ddrag[0]) && std::isfinite(dL_ddrag[1])))
-    return fail(LBVE_ERR_ARG, "dL/ddrag not finite");
+    return set_error(LBVE_ERR_ARG, "dL/ddrag not finite");
   const lbve_params& p = h->p[inst];
   const InstPlan& q = h->plan.inst[inst];
   const std::vector<WallDev>& walls_h = h->walls_of[inst];
@@ -1425,10 +1551,10 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
     }
   }
   if (!d_ws || bytes < a.total)
-    return fail(LBVE_ERR_WORKSPACE, "adjoint workspace of %zu bytes given, %zu needed", bytes,
+    return set_error(LBVE_ERR_WORKSPACE, "adjoint workspace of %zu bytes given, %zu needed", bytes,
                 a.total);
   if (reinterpret_cast<uintptr_t>(d_ws) % kAlign)
-    return fail(LBVE_ERR_WORKSPACE, "adjoint workspace not %zu-byte aligned", kAlign);
+    return set_error(LBVE_ERR_WORKSPACE, "adjoint workspace not %zu-byte aligned", kAlign);
   char* ws = (char*)d_ws;
   cudaStream_t st = h->stream;
   const int prec = p.precision;
@@ -1659,7 +1785,7 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
 extern "C" int lbve_adjoint_step(lbve_handle* h, int32_t inst, const double* init_fields,
                                  const double* d_dL_dfields, int64_t n_steps, void* d_ws,
                                  size_t bytes, double* d_dL_dforce) {
-  if (!d_dL_dfields) return fail(LBVE_ERR_ARG, "d_dL_dfields is null");
+  if (!d_dL_dfields) return set_error(LBVE_ERR_ARG, "d_dL_dfields is null");
   return lbve_adjoint_step_ex(h, inst, init_fields, d_dL_dfields, nullptr, n_steps, d_ws, bytes,
                               d_dL_dforce, nullptr);
 }

@@ -5,6 +5,10 @@
 
 namespace lbve {
 
+// Record a one-line detail of an error for lbve_last_error() on the calling
+// thread and return code (every entry point reports its errors this way).
+int set_error(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+
 // Threads per CTA of the step kernel, per storage precision.  Float32: 96
 // (32 x 3 tiles) measured fastest on GB300 among 64..256; seven such CTAs per
 // SM give 21 warps in seven independent load / barrier / compute phases.
@@ -21,12 +25,20 @@ namespace lbve {
 #ifndef LBVE_THREADS_FP64_SMALL
 #define LBVE_THREADS_FP64_SMALL 64
 #endif
+// Float64 batches too small to give every SM one 64-thread tile run one-warp
+// CTAs (default tiles 8 x 4): one tile per SM spreads the FP64 work of a few
+// thousand nodes over up to all 152 SMs.
+#ifndef LBVE_THREADS_FP64_TINY
+#define LBVE_THREADS_FP64_TINY 32
+#endif
 #ifndef LBVE_TILE_TX
 #define LBVE_TILE_TX 32
 #endif
 constexpr int kThreads = LBVE_THREADS;          // float32 step kernel
 constexpr int kThreads64 = LBVE_THREADS_FP64;   // float64 step kernel
 constexpr int kThreads64Small = LBVE_THREADS_FP64_SMALL;  // float64, small batches
+constexpr int kThreads64Tiny = LBVE_THREADS_FP64_TINY;    // float64, tiny batches
+constexpr int kTileTXTiny = 8;  // default tile width of the one-warp float64 CTAs
 constexpr int kNumSMs = 152;  // GB300; sizes the small-batch choice only
 constexpr int kTileTX = LBVE_TILE_TX;   // default tile width (nodes along x) for nx >= kTileTX
 // threads per CTA (for float64, the size of all but small batches) and the
@@ -125,8 +137,8 @@ struct ColTask {
 // Launchers implemented in lbve_kernels.cu (templated over float/double).
 enum : int { kModeStep = 0, kModeInit = 1 };
 
-// threads: CTA size of the tiles (kThreads for float32; kThreads64 or
-// kThreads64Small for float64).  masked = 0 runs the plain kernel (which
+// threads: CTA size of the tiles (kThreads for float32; kThreads64,
+// kThreads64Small or kThreads64Tiny for float64).  masked = 0 runs the plain kernel (which
 // skips masked tiles), 1 the masked variant.
 int launch_step(int prec, int threads, const InstDev* d_insts, const TileDev* d_tiles,
                 int n_tiles, int parity, int mode, int flags, double* d_partials, void* stream,

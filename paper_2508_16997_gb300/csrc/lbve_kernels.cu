@@ -50,6 +50,9 @@ int launch_step(int prec, int threads, const InstDev* d_insts, const TileDev* d_
   if (prec == 0 && threads == kThreads64)
     return launch_step_m<double, kThreads64>(d_insts, d_tiles, n_tiles, parity, mode, flags,
                                              d_partials, st, masked);
+  if (prec == 0 && threads == kThreads64Tiny)
+    return launch_step_m<double, kThreads64Tiny>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                                                 d_partials, st, masked);
   if (prec == 0 && threads == kThreads64Small)
     return launch_step_m<double, kThreads64Small>(d_insts, d_tiles, n_tiles, parity, mode, flags,
                                                   d_partials, st, masked);

@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "../../include/lbve.h"
+#include "lbve_internal.h"
 
 namespace {
 
@@ -79,7 +80,9 @@ __global__ void __launch_bounds__(kThreadsNA) final_sums(const double* __restric
 
 // Device address of g_partials for each device, looked up once per device
 // with that device current (in host code the symbol itself is only a
-// host-side stand-in, not a device address).
+// host-side stand-in, not a device address).  The cache lives for the
+// process: after cudaDeviceReset the module is loaded again and the array
+// may move, so the entry point must not be used after a reset.
 constexpr int kMaxDevices = 64;
 double* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
@@ -88,31 +91,55 @@ std::mutex g_scratch_mutex;
 
 extern "C" int lbve_field_totals_noalloc(const double* d_fields, int32_t nx, int32_t ny,
                                          double* d_out, void* cuda_stream) {
-  if (!d_fields || !d_out || nx < 1 || ny < 1) return LBVE_ERR_ARG;
+  using lbve::set_error;
+  if (!d_fields || !d_out)
+    return set_error(LBVE_ERR_ARG, "lbve_field_totals_noalloc: null field or output pointer");
+  if (nx < 1 || ny < 1)
+    return set_error(LBVE_ERR_ARG, "lbve_field_totals_noalloc: nx = %d, ny = %d must be >= 1",
+                     (int)nx, (int)ny);
   const long long n = (long long)nx * ny;
-  if (n > (long long)kMaxChunks * kChunk) {
-    fprintf(stderr,
-            "lbve_field_totals_noalloc: %lld nodes exceed the static scratch limit of %d "
-            "nodes (%d chunks of %d)\n",
-            n, kMaxChunks * kChunk, kMaxChunks, kChunk);
-    return LBVE_ERR_ARG;
-  }
+  if (n > (long long)kMaxChunks * kChunk)
+    return set_error(LBVE_ERR_ARG,
+                     "lbve_field_totals_noalloc: %lld nodes exceed the static scratch limit of "
+                     "%d nodes (%d chunks of %d)",
+                     n, kMaxChunks * kChunk, kMaxChunks, kChunk);
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBVE_ERR_CUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess)
+    return set_error(LBVE_ERR_CUDA, "lbve_field_totals_noalloc: cudaGetDevice: %s",
+                     cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_error(LBVE_ERR_CUDA, "lbve_field_totals_noalloc: device %d beyond the %d supported",
+                     dev, kMaxDevices);
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_ptr[dev]) {
       void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
-      if (e != cudaSuccess || !p) return LBVE_ERR_CUDA;
+      e = cudaGetSymbolAddress(&p, g_partials);
+      if (e != cudaSuccess || !p)
+        return set_error(LBVE_ERR_CUDA,
+                         "lbve_field_totals_noalloc: address of the static scratch on device "
+                         "%d: %s",
+                         dev, cudaGetErrorString(e));
       g_scratch_ptr[dev] = (double*)p;
     }
     scratch = g_scratch_ptr[dev];
   }
-  const int n_chunks = (int)((n + kChunk - 1) / kChunk);
+  int n_nodes = (int)n;
+  int n_chunks = (int)((n + kChunk - 1) / kChunk);
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  chunk_sums<<<n_chunks, kThreadsNA, 0, st>>>(d_fields, (int)n, scratch);
-  final_sums<<<1, kThreadsNA, 0, st>>>(scratch, n_chunks, d_out);
-  return cudaGetLastError() == cudaSuccess ? LBVE_OK : LBVE_ERR_CUDA;
+  // cudaLaunchKernel reports the error of this launch itself, so an earlier,
+  // unrelated asynchronous error is neither blamed on it nor cleared
+  void* args1[] = {(void*)&d_fields, (void*)&n_nodes, (void*)&scratch};
+  e = cudaLaunchKernel((const void*)chunk_sums, dim3(n_chunks), dim3(kThreadsNA), args1, 0, st);
+  if (e != cudaSuccess)
+    return set_error(LBVE_ERR_CUDA, "lbve_field_totals_noalloc: chunk pass launch: %s",
+                     cudaGetErrorString(e));
+  void* args2[] = {(void*)&scratch, (void*)&n_chunks, (void*)&d_out};
+  e = cudaLaunchKernel((const void*)final_sums, dim3(1), dim3(kThreadsNA), args2, 0, st);
+  if (e != cudaSuccess)
+    return set_error(LBVE_ERR_CUDA, "lbve_field_totals_noalloc: final pass launch: %s",
+                     cudaGetErrorString(e));
+  return LBVE_OK;
 }

@@ -520,12 +520,14 @@ __device__ __forceinline__ R y_drho(bool wb, bool wt, R rm2, R rm1, R r0, R rp1,
 #ifndef LBVE_FP32_MASKED_MIN_BLOCKS
 #define LBVE_FP32_MASKED_MIN_BLOCKS 5
 #endif
-// Float64 CTAs of NT threads: 512 / NT per SM (128 registers per thread).
+// Float64 CTAs: 256 threads two per SM (128 registers per thread).  The
+// 64- and one-warp CTAs serve batches with fewer tiles than 4 and 2 per SM,
+// so they are budgeted for that many and keep every value in registers.
 template <typename R, bool MASKED, int NT>
 struct MinBlocks {
   static constexpr int value =
       sizeof(R) == 4 ? (MASKED ? LBVE_FP32_MASKED_MIN_BLOCKS : LBVE_FP32_MIN_BLOCKS)
-                     : (NT <= 512 ? 512 / NT : 1);
+                     : (NT <= 32 ? 2 : NT <= 64 ? 4 : (NT <= 512 ? 512 / NT : 1));
 };
 
 // One-sided differences along one axis next to the solid mask (same rule as

@@ -32,7 +32,8 @@ EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_st
             "lbve_destroy", "lbve_error_string", "lbve_last_error", "lbve_field_totals_noalloc",
             "lbve_adjoint_workspace_bytes", "lbve_adjoint_step", "lbve_state_bytes", "lbve_save",
             "lbve_load", "lbve_autotune", "lbve_set_wall_distances", "lbve_set_inlet",
-            "lbve_adjoint_step_ex", "lbve_adjoint_workspace_bytes_interval"]
+            "lbve_adjoint_step_ex", "lbve_adjoint_workspace_bytes_interval", "lbve_profile",
+            "lbve_profile_read"]
 
 
 class lbve_params(ctypes.Structure):
@@ -98,6 +99,9 @@ def load() -> ctypes.CDLL:
         L.lbve_set_wall_distances.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32), _dp]
+        L.lbve_profile.argtypes = [_vp, ctypes.c_int32]
+        L.lbve_profile_read.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _dp,
+                                        _dp, _dp]
         L.lbve_destroy.argtypes = [_vp]
         L.lbve_destroy.restype = None
         L.lbve_error_string.argtypes = [ctypes.c_int]
@@ -182,6 +186,20 @@ def lbve_set_wall_distances(h, inst: int, node, direction, q) -> None:
 
 def lbve_step(h, n_steps: int) -> None:
     _check(load().lbve_step(h, int(n_steps)), "lbve_step")
+
+
+def lbve_profile(h, max_launches: int) -> None:
+    _check(load().lbve_profile(h, int(max_launches)), "lbve_profile")
+
+
+def lbve_profile_read(h, precision: int):
+    """(launches, total ms, shortest ms, longest ms) of the timed step-kernel
+    launches of one precision."""
+    n = ctypes.c_int32()
+    tot, lo, hi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().lbve_profile_read(h, int(precision), ctypes.byref(n), ctypes.byref(tot),
+                                    ctypes.byref(lo), ctypes.byref(hi)), "lbve_profile_read")
+    return n.value, tot.value, lo.value, hi.value
 
 
 def lbve_status(h, n_instances: int) -> np.ndarray:

@@ -43,6 +43,74 @@ def poiseuille_steady(H: int, Wi: float, Uc: float):
     return Uc * u, 1.0 + 2.0 * (Wi * du) ** 2, Wi * du, np.ones_like(ys)
 
 
+def poiseuille_steady_diffusive(H: int, Wi: float, Uc: float, beta: float, kappa: float,
+                                y=None):
+    """Steady Oldroyd-B plane Poiseuille flow WITH the stress diffusion of the
+    conformation equation (eq_Constitutive with kappa > 0, Sec. 2) and
+    zero-flux walls (the conservation CNEBB enforces, Sec. 3.3).
+
+    The kappa = 0 profile of poiseuille_steady() cannot meet a zero-flux wall
+    (its A_xy = lambda u' has a non-zero wall gradient), so a boundary layer
+    of width delta = sqrt(kappa beta lambda) forms.  With x-invariance,
+    A_yy = 1 exactly, and with eta = H/2 - y, F/mu_0 = 8 U_c/H^2 (the
+    channel force of Sec. 4.2), lambda = Wi H/U_c, r = (1-beta)/beta:
+      momentum:  mu_s u' + (mu_p/lambda) a = F eta            (a = A_xy)
+      A_xy:      kappa a'' - a/lambda + u' = 0,   a' = 0 at the walls
+      A_xx - 1:  kappa b'' - b/lambda + 2 a u' = 0, b' = 0 at the walls
+    Eliminating u' gives kappa a'' - a/(beta lambda) = -F eta/mu_s, so
+      a   = lambda (F/mu_0) [eta - delta sinh(eta/delta)/cosh(H/2delta)],
+      u'  = (F/mu_0) [eta + r delta sinh(eta/delta)/cosh(H/2delta)],
+      u   = (F/mu_0) [y (H - y)/2 + r delta^2 (cosh(H/2delta) - cosh(eta/delta))/cosh(H/2delta)],
+    and b solves l^2 b'' - b = -2 lambda^2 (F/mu_0)^2 [eta^2 + (r-1) delta eta s/c - r delta^2 s^2/c^2]
+    (s = sinh(eta/delta), c = cosh(H/2delta), l^2 = kappa lambda) with
+    b'(+-H/2) = 0: a particular solution term by term (eta^2, eta s and
+    cosh(eta/delta), cosh(2 eta/delta), a constant) plus D cosh(eta/l).
+    Needs 0 < beta < 1 and kappa > 0.  As kappa -> 0 it reduces to
+    poiseuille_steady().  Returns (ux, Axx, Axy, Ayy) on rows y (default
+    0..H)."""
+    ys = np.arange(H + 1, dtype=float) if y is None else np.asarray(y, dtype=float)
+    eta = H / 2.0 - ys
+    lam = Wi * H / Uc
+    Fm = 8.0 * Uc / H ** 2
+    r = (1.0 - beta) / beta
+    d = math.sqrt(kappa * beta * lam)
+    l2 = kappa * lam
+    l = math.sqrt(l2)
+    E = H / 2.0
+    # ratios of hyperbolic functions written so that they cannot overflow
+    def sc(x):   # sinh(x/d) / cosh(E/d)
+        return 0.5 * (np.exp((x - E) / d) - np.exp((-x - E) / d)) / (0.5 * (1 + math.exp(-2 * E / d)))
+
+    def cc(x):   # cosh(x/d) / cosh(E/d)
+        return 0.5 * (np.exp((x - E) / d) + np.exp((-x - E) / d)) / (0.5 * (1 + math.exp(-2 * E / d)))
+
+    a = lam * Fm * (eta - d * sc(eta))
+    u = Fm * (ys * (H - ys) / 2.0 + r * d * d * (1.0 - cc(eta)))
+    K = 2.0 * lam ** 2 * Fm ** 2
+    # particular solution of l^2 b'' - b = -K [eta^2 + (r-1) d eta s/c - r d^2 s^2/c^2]
+    # in terms of the bounded ratios sc, cc and cc2(x) = cosh(2x/d)/cosh(E/d)^2
+    P = -K * (r - 1.0) * d * beta / (1.0 - beta)
+    Q = -2.0 * P * d / (1.0 - beta)
+    M = K * r * d * d / (2.0 * (4.0 / beta - 1.0))
+    C0 = K * r * d * d / 2.0
+    denom = (0.5 * (1 + math.exp(-2 * E / d))) ** 2
+
+    def cc2(x):
+        return 0.5 * (np.exp((2 * x - 2 * E) / d) + np.exp((-2 * x - 2 * E) / d)) / denom
+
+    def sc2(x):
+        return 0.5 * (np.exp((2 * x - 2 * E) / d) - np.exp((-2 * x - 2 * E) / d)) / denom
+
+    c2 = 4.0 * math.exp(-2 * E / d) / (1 + math.exp(-2 * E / d)) ** 2  # 1/cosh(E/d)^2
+    bp = K * (eta ** 2 + 2 * l2) + P * eta * sc(eta) + Q * cc(eta) + M * cc2(eta) + C0 * c2
+    dbpE = (2 * K * E + P * (sc(E) + E / d * cc(E)) + Q / d * sc(E) + 2 * M / d * sc2(E))
+    # homogeneous part D cosh(eta/l) with D l^-1 sinh(E/l) = -b_p'(E), written as
+    # D cosh(eta/l) = -l b_p'(E) cosh(eta/l)/sinh(E/l)
+    ratio = (np.exp((eta - E) / l) + np.exp((-eta - E) / l)) / (1 - math.exp(-2 * E / l))
+    b = bp - l * dbpE * ratio
+    return u, 1.0 + b, a, np.ones_like(ys)
+
+
 def waters_king_u(ystar: float, tstar, Wi: float, Re: float, beta: float,
                   n_terms: int = 400):
     """Start-up Oldroyd-B Poiseuille velocity u*(y*, t*) (Sec. 4.2, Waters-King).

@@ -12,6 +12,7 @@ macroscopic fields element by element.  Tolerances:
 import numpy as np
 import pytest
 
+import closed_forms as cf
 from gpu_helpers import parity_errors
 from oracle_helpers import oracle_sim
 from paper_2508_16997_gb300 import workloads as wl
@@ -63,6 +64,34 @@ def test_channel_fp64_walls(lbve):
     inst = wl.channel(16, nx=4, Wi=10.0)
     sim, (o,) = run_pair(lbve, [inst], 1500)
     assert_fp64_parity(sim.fields(0), o.fields(), what="channel")
+
+
+def test_channel_fp64_high_wi(lbve):
+    """The channel workload at the top of the paper's Wi range, H = 64
+    (nx = 4, beta 0.5, Re 1, Sc 1e6): Wi = 1e3 and 1e4 (lambda = 1.1e6 and
+    1.1e7 steps), each from rest and from the steady closed form (eq_ux_ana /
+    eq_Tab_ana, A_xx - 1 up to 3.2e9), four instances in one batch, 1000
+    steps, against the oracle to 1e-12."""
+    H, insts, inits = 64, [], []
+    for Wi in (1e3, 1e4):
+        for start in ("rest", "closed"):
+            inst = wl.channel(H, nx=4, beta=0.5, Wi=Wi)
+            insts.append(inst)
+            if start == "rest":
+                inits.append(None)
+                continue
+            ue, Axx, Axy, Ayy = cf.poiseuille_steady(H, Wi, wl.velocity_scale(inst.Ma))
+            f = np.zeros((6, H + 1, 4))
+            f[0] = 1.0
+            f[1], f[3], f[4], f[5] = ue[:, None], Axx[:, None], Axy[:, None], Ayy[:, None]
+            inits.append(f)
+    sim = lbve.Simulation(insts, precision=lbve.LBVE_FP64, init_fields=inits)
+    sim.step(1000)
+    for i, inst in enumerate(insts):
+        o = oracle_sim(inst, init=inits[i])
+        o.step(1000)
+        assert_fp64_parity(sim.fields(i), o.fields(), what=f"Wi {inst.Wi} start {i % 2}")
+    assert not sim.status().any()
 
 
 @pytest.mark.parametrize("nx,ny,periodic", [(37, 21, True), (45, 19, False), (1, 9, False),

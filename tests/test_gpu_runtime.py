@@ -99,3 +99,46 @@ def test_autotune_picks_admissible_widths(lbve):
     ref.step(40)
     for i in range(len(insts)):
         np.testing.assert_array_equal(s.fields(i), ref.fields(i))
+
+
+def test_fp64_cta_sizes_bit_identical(lbve):
+    """The float64 CTA size follows the batch (one-warp tiles for a 64^2 mill
+    or the five Wi-sweep channels, 64 and 256 threads when a wider tile is
+    asked for): the fields are bit-identical whichever runs them."""
+    for insts in ([wl.frm(64, Wi=2.0, Re=1.0, Ma=0.05)],
+                  [wl.channel(64, nx=4, Wi=w) for w in (1.0, 10.0, 100.0, 1e3, 1e4)]):
+        inits = [wl.random_fields(i.nx, i.ny, seed=5 + k, du=1e-3, dA=0.05)
+                 for k, i in enumerate(insts)]
+        runs = []
+        for tx in (0, 32, 64):
+            widths = [min(tx, i.nx) for i in insts]
+            s = lbve.Simulation(insts, precision=lbve.LBVE_FP64, init_fields=inits, tile_tx=widths)
+            s.step(50)
+            runs.append([s.fields(i) for i in range(len(insts))])
+        for r in runs[1:]:
+            for a, b in zip(r, runs[0]):
+                np.testing.assert_array_equal(a, b)
+
+
+def test_profile_times_every_launch(lbve):
+    """lbve_profile arms per-launch events for the plain step kernel: every
+    launch of the next step calls is timed up to the cap, while armed the
+    steps run as direct launches with fields bit-identical to a graph-replayed
+    run, and disarming releases the events."""
+    insts = _batch()
+    a = lbve.Simulation(insts, precision=1)
+    b = lbve.Simulation(insts, precision=1)
+    lbve.lbve_profile(a.h, 50)
+    a.step(7)
+    n, tot, lo, hi = lbve.lbve_profile_read(a.h, lbve.LBVE_FP32_DEV)
+    assert n == 7 and tot > 0 and 0 < lo <= hi <= tot
+    assert lbve.lbve_profile_read(a.h, lbve.LBVE_FP64)[0] == 0  # no float64 instance
+    a.step(70)  # 43 more timed launches, the rest untimed
+    assert lbve.lbve_profile_read(a.h, lbve.LBVE_FP32_DEV)[0] == 50
+    b.step(77)  # two graph replays of 32 steps
+    for i in range(len(insts)):
+        np.testing.assert_array_equal(a.fields(i), b.fields(i))
+    lbve.lbve_profile(a.h, 0)
+    assert lbve.lbve_profile_read(a.h, lbve.LBVE_FP32_DEV)[0] == 0
+    with pytest.raises(lbve.LbveError):
+        lbve.lbve_profile(a.h, -1)

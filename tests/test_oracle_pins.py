@@ -321,6 +321,184 @@ def test_oldroyd_b_poiseuille_steady():
     assert np.abs(F[1] - F[1][:, :1]).max() < 1e-15
 
 
+def _channel_fields(H, form):
+    """Initial fields [6][H+1][1] of an x-invariant channel from a profile
+    (ux, Axx, Axy, Ayy) on rows 0..H, at unit density."""
+    ue, Axx, Axy, Ayy = form
+    f = np.zeros((6, H + 1, 1))
+    f[0] = 1.0
+    f[1, :, 0], f[3, :, 0], f[4, :, 0], f[5, :, 0] = ue, Axx, Axy, Ayy
+    return f
+
+
+def _gre(num, ana):
+    """Global relative error sum |num - ana| / sum |ana| (the paper's GRE, Sec. 4)."""
+    return float(np.abs(num - ana).sum() / np.abs(ana).sum())
+
+
+def _channel_gres(F, form):
+    ue, Axx, Axy, _ = form
+    return np.array([_gre(F[1][:, 0], ue), _gre(F[3][:, 0] - 1.0, Axx - 1.0),
+                     _gre(F[4][:, 0], Axy)])
+
+
+def _relax(s, Uc, H, tol, max_steps):
+    """Step in chunks of one convective time H/U_c until the residual
+    max |u(t) - u(t - chunk)|/U_c (2eq4 form) is below tol; returns
+    (steps, residual)."""
+    chunk = int(round(H / Uc))
+    prev = s.fields()[1].copy()
+    n, res = 0, np.inf
+    while n < max_steps:
+        s.step(chunk)
+        n += chunk
+        u = s.fields()[1]
+        res = float(np.abs(u - prev).max() / Uc)
+        prev = u.copy()
+        if res < tol:
+            break
+    return n, res
+
+
+def test_diffusive_poiseuille_closed_form_solves_the_model():
+    """The closed form with stress diffusion (closed_forms.poiseuille_steady_
+    diffusive) checked against its own defining equations, independently of
+    the oracle: at 301 interior points, fourth-order finite differences of
+    the profiles satisfy the momentum balance mu_s u' + (mu_p/lambda) A_xy =
+    F (H/2 - y), kappa A_xy'' - A_xy/lambda + u' = 0 and kappa A_xx'' -
+    (A_xx - 1)/lambda + 2 A_xy u' = 0 (each relative to its largest term, to
+    1e-7: the difference error at h = 1e-2); the walls have no slip and zero
+    diffusive flux; and as kappa -> 0 the profile tends to eq_ux_ana /
+    eq_Tab_ana."""
+    for H, Wi, Sc in ((64, 1e4, 1e6), (16, 10.0, 100.0), (32, 1e3, 1e5)):
+        beta = 0.5
+        Uc = wl.velocity_scale(0.1)
+        nu0 = Uc * H  # Re = 1
+        kappa = beta * nu0 / Sc
+        lam = Wi * H / Uc
+        F = 8.0 * nu0 * Uc / H ** 2
+        mus, mup = beta * nu0, (1 - beta) * nu0
+        y = np.linspace(0.5, H - 0.5, 301)
+        h = 1e-2
+
+        def prof(yy):
+            return cf.poiseuille_steady_diffusive(H, Wi, Uc, beta, kappa, yy)
+
+        P = [prof(y + j * h) for j in (-2, -1, 0, 1, 2)]
+
+        def d1(c):
+            return (P[0][c] - 8 * P[1][c] + 8 * P[3][c] - P[4][c]) / (12 * h)
+
+        def d2(c):
+            return (-P[0][c] + 16 * P[1][c] - 30 * P[2][c] + 16 * P[3][c] - P[4][c]) / (12 * h * h)
+
+        u, Axx, Axy, Ayy = P[2]
+        mom = mus * d1(0) + mup / lam * Axy - F * (H / 2 - y)
+        assert np.abs(mom).max() < 1e-7 * F * H / 2
+        ra = kappa * d2(2) - Axy / lam + d1(0)
+        assert np.abs(ra).max() < 1e-7 * np.abs(Axy / lam).max()
+        rb = kappa * d2(1) - (Axx - 1) / lam + 2 * Axy * d1(0)
+        assert np.abs(rb).max() < 1e-7 * np.abs((Axx - 1) / lam).max()
+        assert np.all(Ayy == 1.0)
+        ends = np.array([0.0, float(H)])
+        W = [cf.poiseuille_steady_diffusive(H, Wi, Uc, beta, kappa, ends + j * h)
+             for j in (-2, -1, 1, 2)]
+        for c in (1, 2):  # zero flux of A_xx and A_xy at both walls
+            flux = (W[0][c] - 8 * W[1][c] + 8 * W[2][c] - W[3][c]) / (12 * h)
+            assert np.abs(flux).max() < 1e-7 * np.abs(P[2][c] - (c == 1)).max()
+        assert np.abs(cf.poiseuille_steady_diffusive(H, Wi, Uc, beta, kappa, ends)[0]).max() < 1e-15
+    # kappa -> 0: the boundary layer vanishes
+    H, Wi, Uc = 16, 10.0, wl.velocity_scale(0.1)
+    a = cf.poiseuille_steady_diffusive(H, Wi, Uc, 0.5, 1e-14)
+    b = cf.poiseuille_steady(H, Wi, Uc)
+    for x, z in zip(a, b):
+        assert np.abs(x - z).max() < 1e-5 * np.abs(z).max()
+
+
+def test_oldroyd_b_poiseuille_high_wi_from_the_closed_form():
+    """Large relaxation times (Wi up to 1e4, lambda up to 2.8e6 steps, A_xx - 1
+    up to 3.2e9): the oracle started from the steady closed form (eq_ux_ana /
+    eq_Tab_ana, H = 16, Re = 1, Sc = 1e6, beta = 0.5) keeps it for 10^4 steps
+    to the accuracy it has at Wi = 1.  The GRE of u, A_xx - 1 and A_xy after
+    10^4 steps at every Wi stays within 10x of the Wi = 1 run's (measured
+    ratios: u up to 7x, A_xx 1.5x, A_xy 3x; the start from bare equilibria
+    makes a fast transient of that size).  A_yy stays 1 to 1e-12 of A_xx - 1,
+    and the source Phi_ab the oracle evaluates on the closed-form state is 0
+    to 1e-10 of (A_xx - 1)/lambda, the size of its two cancelling terms: a
+    dropped or misweighted term of Phi_ab gives O(1) there."""
+    H, T = 16, 10000
+    gres = {}
+    for Wi in (1.0, 10.0, 100.0, 1e3, 1e4):
+        inst = wl.channel(H, nx=1, beta=0.5, Wi=Wi)
+        probe = oracle_sim(inst)
+        c = probe.coeffs()
+        form = cf.poiseuille_steady(H, Wi, c["Uc"])
+        s = oracle_sim(inst, init=_channel_fields(H, form))
+        S = s.source()
+        assert np.abs(S).max() < 1e-10 * np.abs(form[1] - 1).max() / c["lambda"], Wi
+        s.step(T)
+        F = s.fields()
+        assert np.all(np.isfinite(F))
+        assert np.abs(F[5] - 1).max() < 1e-12 * np.abs(form[1] - 1).max(), Wi
+        gres[Wi] = _channel_gres(F, form)
+    for Wi, g in gres.items():
+        assert np.all(g <= 10.0 * gres[1.0]), (Wi, g, gres[1.0])
+
+
+@pytest.mark.parametrize("Wi,tol_u,tol_xy,tol_xx", [(10.0, 3e-4, 7e-3, 2.5e-2),
+                                                    (100.0, 1e-3, 2e-2, 5e-2)])
+def test_oldroyd_b_poiseuille_relaxes_at_high_wi(Wi, tol_u, tol_xy, tol_xx):
+    """Oldroyd-B channel from rest (H = 16, beta = 0.5, Re = 1, Sc = 1e6) to
+    steady state (residual below 1e-9, at most 40 lambda) at Wi = 10 and 100,
+    against eq_ux_ana / eq_Tab_ana: u to tol_u U_c, A_xy and A_xx - 1 to
+    tol_xy / tol_xx of their maxima (measured 1.3e-4 / 3.2e-3 / 1.2e-2 at
+    Wi = 10 and 4.9e-4 / 9.3e-3 / 2.3e-2 at Wi = 100, the odd-even row
+    pattern of the barely damped conformation flux mode; a dropped or
+    misweighted term of Phi_ab, T_i or CNEBB gives O(1)).  The boundary
+    layer of the stress diffusion is below a tenth of a node here."""
+    H = 16
+    inst = wl.channel(H, nx=1, beta=0.5, Wi=Wi)
+    s = oracle_sim(inst)
+    c = s.coeffs()
+    n, res = _relax(s, c["Uc"], H, 1e-9, int(40 * c["lambda"]))
+    F = s.fields()
+    ue, Axx, Axy, Ayy = cf.poiseuille_steady(H, Wi, c["Uc"])
+    assert np.abs(F[1][:, 0] - ue).max() < tol_u * c["Uc"]
+    assert np.abs(F[4][:, 0] - Axy).max() < tol_xy * np.abs(Axy).max()
+    assert np.abs(F[3][:, 0] - Axx).max() < tol_xx * np.abs(Axx - 1).max()
+    assert np.abs(F[5][:, 0] - 1).max() < 1e-9
+
+
+def test_stress_diffusion_boundary_layer_converges_first_order():
+    """Where the stress diffusion matters: the steady channel depends on the
+    parameters only through beta and kappa lambda / H^2 (scale A_xy by
+    lambda and A_xx - 1 by lambda^2), so Wi = 10, Sc = 100 has the steady
+    state of Wi = 1e5 at the paper's Sc = 1e6, with a boundary layer
+    delta = sqrt(kappa beta lambda) = 0.158 H at the walls.  The oracle's
+    steady states at H = 16 and 32 (Lambda_p = 1e-3) approach the closed form
+    with diffusion and zero-flux walls at first order in the grid spacing
+    (GRE of u and A_xx - 1 halve: measured ratios 1.83 and 1.98; the wet-node
+    wall places the zero-flux condition to O(dx)), to GRE(u) 1.6e-2 at
+    H = 32, while the kappa = 0 closed form stays 0.17-0.19 away in u.  A
+    kappa wrong by a factor 2 (tau_p1) misses the closed form by 0.12."""
+    out = {}
+    for H in (16, 32):
+        inst = wl.channel(H, nx=1, beta=0.5, Wi=10.0, Sc=100.0, Lambda_p=1e-3)
+        s = oracle_sim(inst)
+        c = s.coeffs()
+        n, res = _relax(s, c["Uc"], H, 1e-10, int(40 * c["lambda"]))
+        assert res < 1e-10
+        F = s.fields()
+        out[H] = (_channel_gres(F, cf.poiseuille_steady_diffusive(H, 10.0, c["Uc"], 0.5,
+                                                                   c["kappa"])),
+                  _channel_gres(F, cf.poiseuille_steady(H, 10.0, c["Uc"])))
+    kd16, k016 = out[16]
+    kd32, k032 = out[32]
+    assert kd32[0] < 2e-2 and kd32[1] < 7e-2 and kd32[2] < 3e-2
+    assert np.all(kd16[:2] / kd32[:2] > 1.6)
+    assert k016[0] > 0.1 and k032[0] > 0.1
+
+
 @pytest.mark.parametrize("beta,Wi", [(0.1, 1.0), (0.5, 1.0), (0.9, 1.0), (0.5, 10.0)])
 def test_waters_king_startup(beta, Wi):
     """Start-up Oldroyd-B Poiseuille flow: centre-line u*(t*) against the
