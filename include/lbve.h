@@ -236,13 +236,16 @@ int lbve_step(lbve_handle* h, int64_t n_steps);
 int lbve_profile(lbve_handle* h, int32_t max_launches);
 
 /* Read the launches timed since lbve_profile() for the step kernel of one
- * precision (LBVE_FP64 or LBVE_FP32_DEV): their number, the sum of their
+ * precision (LBVE_FP64 or LBVE_FP32_DEV) and kind (final_step = 0: the
+ * ordinary steps; 1: the last step of each lbve_step call, which also writes
+ * the float64 fields and partial sums): their number, the sum of their
  * durations and the shortest and longest (ms; ms_min, ms_max may be NULL).
- * Waits for the last timed launch to finish.  Zero launches when nothing was
- * armed or no instance has that precision.
+ * Each kind is armed for max_launches launches.  Waits for the last timed
+ * launch to finish.  Zero launches when nothing was armed or no instance has
+ * that precision.
  * Errors: LBVE_ERR_ARG, LBVE_ERR_CUDA. */
-int lbve_profile_read(lbve_handle* h, int32_t precision, int32_t* launches, double* ms_total,
-                      double* ms_min, double* ms_max);
+int lbve_profile_read(lbve_handle* h, int32_t precision, int32_t final_step, int32_t* launches,
+                      double* ms_total, double* ms_min, double* ms_max);
 
 /* Synchronise the stream and copy per-instance status flags into
  * flags[0..n-1] (bit 0: a non-finite field was seen at the end of an

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/lbve.h"
@@ -325,10 +326,11 @@ struct lbve_handle {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   // per-launch timing of the plain step kernels (lbve_profile): two events
-  // per launch and tile list, recorded on the caller's stream
+  // per launch, per tile list and per kind (0 non-final steps, 1 the final
+  // step of a call), recorded on the caller's stream
   int prof_cap = 0;
-  int prof_n[kLists] = {0, 0};
-  std::vector<cudaEvent_t> prof_ev[kLists];
+  int prof_n[kLists][2] = {{0, 0}, {0, 0}};
+  std::vector<cudaEvent_t> prof_ev[kLists][2];
 };
 
 namespace {
@@ -366,9 +368,10 @@ int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
                     h->d_partials, h->side_stream, 1))
       return cuda_fail(cudaGetLastError(), "masked step kernel launch");
     if (h->plan.ntiles[l] <= 0) continue;
-    const bool timed = h->prof_cap > 0 && st == h->stream && h->prof_n[l] < h->prof_cap;
+    const int kind = (flags & kFinal) ? 1 : 0;
+    const bool timed = h->prof_cap > 0 && st == h->stream && h->prof_n[l][kind] < h->prof_cap;
     if (timed) {
-      const cudaError_t e = cudaEventRecord(h->prof_ev[l][2 * h->prof_n[l]], st);
+      const cudaError_t e = cudaEventRecord(h->prof_ev[l][kind][2 * h->prof_n[l][kind]], st);
       if (e != cudaSuccess) return cuda_fail(e, "profile event");
     }
     if (launch_step(prec, h->plan.threads[l], h->d_insts, h->d_tiles[l], h->plan.ntiles[l],
@@ -376,9 +379,9 @@ int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
                     h->d_partials, st))
       return cuda_fail(cudaGetLastError(), "step kernel launch");
     if (timed) {
-      const cudaError_t e = cudaEventRecord(h->prof_ev[l][2 * h->prof_n[l] + 1], st);
+      const cudaError_t e = cudaEventRecord(h->prof_ev[l][kind][2 * h->prof_n[l][kind] + 1], st);
       if (e != cudaSuccess) return cuda_fail(e, "profile event");
-      ++h->prof_n[l];
+      ++h->prof_n[l][kind];
     }
   }
   if (fork) {
@@ -439,6 +442,29 @@ bool all_positive(const double* a, size_t n) {
   uint64_t bad = 0;
   for (size_t k = 0; k < n; ++k) bad |= (uint64_t)!(a[k] > 0.0);
   return bad == 0;
+}
+
+// check(a, n) over an array split across host threads when it is large
+// (the checks of a large instance's host arrays then cost milliseconds).
+template <typename F>
+bool check_parallel(const double* a, size_t n, F check) {
+  constexpr size_t kMinPerThread = size_t(1) << 21;
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  const size_t nt = std::min<size_t>(hw, std::max<size_t>(1, n / kMinPerThread));
+  if (nt <= 1) return check(a, n);
+  std::vector<char> ok(nt, 0);
+  std::vector<std::thread> th;
+  const size_t chunk = (n + nt - 1) / nt;
+  for (size_t t = 0; t < nt; ++t) {
+    const size_t b = t * chunk, e = std::min(n, b + chunk);
+    th.emplace_back([&, t, b, e] { ok[t] = b < e ? check(a + b, e - b) : 1; });
+  }
+  bool all = true;
+  for (size_t t = 0; t < nt; ++t) {
+    th[t].join();
+    all = all && ok[t];
+  }
+  return all;
 }
 
 constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -878,12 +904,12 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
   {
     // every host-side check before anything changes
     const size_t nn = size_t(h->p[inst].nx) * h->p[inst].ny;
-    if (body_force && !all_finite(body_force, 2 * nn))
+    if (body_force && !check_parallel(body_force, 2 * nn, all_finite))
       return set_error(LBVE_ERR_ARG, "body force not finite");
     if (init_fields) {
-      if (!all_finite(init_fields, 6 * nn))
+      if (!check_parallel(init_fields, 6 * nn, all_finite))
         return set_error(LBVE_ERR_ARG, "initial fields not finite");
-      if (!all_positive(init_fields, nn))
+      if (!check_parallel(init_fields, nn, all_positive))
         return set_error(LBVE_ERR_ARG, "initial density must be > 0");
     }
     const int rc = install_mask(h, inst, solid_mask);
@@ -1214,11 +1240,13 @@ int lbve_set_wall_distances(lbve_handle* h, int32_t inst, int32_t n_links, const
 }
 
 static void release_profile(lbve_handle* h) {
-  for (int l = 0; l < kLists; ++l) {
-    for (cudaEvent_t e : h->prof_ev[l]) cudaEventDestroy(e);
-    h->prof_ev[l].clear();
-    h->prof_n[l] = 0;
-  }
+  for (int l = 0; l < kLists; ++l)
+    for (int f = 0; f < 2; ++f) {
+      for (cudaEvent_t e : h->prof_ev[l][f])
+        if (e) cudaEventDestroy(e);
+      h->prof_ev[l][f].clear();
+      h->prof_n[l][f] = 0;
+    }
   h->prof_cap = 0;
 }
 
@@ -1236,13 +1264,15 @@ int lbve_profile(lbve_handle* h, int32_t max_launches) {
   if (max_launches == 0) return LBVE_OK;
   for (int l = 0; l < kLists; ++l) {
     if (h->plan.ntiles[l] <= 0) continue;
-    h->prof_ev[l].resize(2 * (size_t)max_launches, nullptr);
-    for (auto& ev : h->prof_ev[l]) {
-      e = cudaEventCreate(&ev);
-      if (e != cudaSuccess) {
-        ev = nullptr;
-        release_profile(h);
-        return cuda_fail(e, "lbve_profile: event creation");
+    for (int f = 0; f < 2; ++f) {
+      h->prof_ev[l][f].resize(2 * (size_t)max_launches, nullptr);
+      for (auto& ev : h->prof_ev[l][f]) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) {
+          ev = nullptr;
+          release_profile(h);
+          return cuda_fail(e, "lbve_profile: event creation");
+        }
       }
     }
   }
@@ -1250,21 +1280,23 @@ int lbve_profile(lbve_handle* h, int32_t max_launches) {
   return LBVE_OK;
 }
 
-int lbve_profile_read(lbve_handle* h, int32_t precision, int32_t* launches, double* ms_total,
-                      double* ms_min, double* ms_max) {
-  if (!h || !launches || !ms_total || (precision != LBVE_FP64 && precision != LBVE_FP32_DEV))
-    return set_error(LBVE_ERR_ARG, "bad handle, precision or null output");
+int lbve_profile_read(lbve_handle* h, int32_t precision, int32_t final_step, int32_t* launches,
+                      double* ms_total, double* ms_min, double* ms_max) {
+  if (!h || !launches || !ms_total || (precision != LBVE_FP64 && precision != LBVE_FP32_DEV) ||
+      (final_step != 0 && final_step != 1))
+    return set_error(LBVE_ERR_ARG, "bad handle, precision, final_step or null output");
   const int l = precision == LBVE_FP64 ? 0 : 1;
   *launches = 0;
   *ms_total = 0.0;
   double lo = 0.0, hi = 0.0;
-  const int n = h->prof_cap > 0 ? h->prof_n[l] : 0;
+  const int n = h->prof_cap > 0 ? h->prof_n[l][final_step] : 0;
+  const std::vector<cudaEvent_t>& ev = h->prof_ev[l][final_step];
   if (n > 0) {
-    cudaError_t e = cudaEventSynchronize(h->prof_ev[l][2 * n - 1]);
+    cudaError_t e = cudaEventSynchronize(ev[2 * n - 1]);
     if (e != cudaSuccess) return cuda_fail(e, "lbve_profile_read");
     for (int j = 0; j < n; ++j) {
       float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, h->prof_ev[l][2 * j], h->prof_ev[l][2 * j + 1]);
+      e = cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]);
       if (e != cudaSuccess) return cuda_fail(e, "lbve_profile_read");
       *ms_total += ms;
       lo = j == 0 ? ms : std::min(lo, (double)ms);

@@ -50,9 +50,21 @@ int launch_step(int prec, int threads, const InstDev* d_insts, const TileDev* d_
   if (prec == 0 && threads == kThreads64)
     return launch_step_m<double, kThreads64>(d_insts, d_tiles, n_tiles, parity, mode, flags,
                                              d_partials, st, masked);
-  if (prec == 0 && threads == kThreads64Tiny)
+  if (prec == 0 && threads == kThreads64Tiny) {
+    // tiles of at most 32 nodes: the time steps of plain tiles spread each
+    // node over four warps (one lattice each), the rest runs one warp a tile
+    if (!masked && mode == kModeStep && n_tiles > 0) {
+      if (flags & kFinal)
+        step_kernel_split<true><<<n_tiles, kSplitThreads, 0, st>>>(d_insts, d_tiles, parity,
+                                                                   d_partials);
+      else
+        step_kernel_split<false><<<n_tiles, kSplitThreads, 0, st>>>(d_insts, d_tiles, parity,
+                                                                    d_partials);
+      return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
+    }
     return launch_step_m<double, kThreads64Tiny>(d_insts, d_tiles, n_tiles, parity, mode, flags,
                                                  d_partials, st, masked);
+  }
   if (prec == 0 && threads == kThreads64Small)
     return launch_step_m<double, kThreads64Small>(d_insts, d_tiles, n_tiles, parity, mode, flags,
                                                   d_partials, st, masked);

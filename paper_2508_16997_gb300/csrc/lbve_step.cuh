@@ -36,6 +36,32 @@
 
 namespace lbve {
 
+// Exact float -> double conversion by integer operations: GB300 converts
+// float to double on its float64 pipe (64 cycles per warp instruction),
+// integer operations issue every cycle.  Zero, subnormal, normal, infinite
+// and NaN inputs (IEEE 754 binary32 -> binary64: exponent rebiased by
+// 1023 - 127, fraction shifted by 29 bits; subnormals normalised).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(b >> 31) << 63;
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint32_t m = b & 0x7fffffu;
+  uint64_t r;
+  if (e == 0xffu) {
+    r = sign | 0x7ff0000000000000ull | ((uint64_t)m << 29);
+  } else if (e != 0u) {
+    r = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+  } else if (m == 0u) {
+    r = sign;
+  } else {
+    const int msb = 31 - __clz(m);  // 0..22: value 2^(msb - 149) (1 + fraction)
+    r = sign | ((uint64_t)(msb + 874) << 52) | (((uint64_t)m << (52 - msb)) & 0xfffffffffffffull);
+  }
+  return __longlong_as_double((long long)r);
+}
+__device__ __forceinline__ double to_f64(float v) { return f2d_exact(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+
 template <typename R>
 struct HydroM {  // raw moments of the (deviation) populations
   R drho, jx, jy, pxx, pyy, pxy, qxxy, qxyy;
@@ -179,24 +205,28 @@ __device__ __forceinline__ void cnebb(R d[9], R post_a, R post_b, R post_c, R de
     d[8] = d[6] + a5 * (ubx - uby);
   }
   d[0] = dphi - (((d[1] + d[2]) + (d[3] + d[4])) + ((d[5] + d[6]) + (d[7] + d[8])));
-  const double dc = (double)delta_c;
-  wout = ((double)post_a + (double)post_b + (double)post_c) + dc / 6.0;
+  const double dc = to_f64(delta_c);
+  wout = (to_f64(post_a) + to_f64(post_b) + to_f64(post_c)) + dc / 6.0;
   double added;
-  if (bottom) added = (double)d[2] + (double)d[5] + (double)d[6];
-  else added = (double)d[4] + (double)d[7] + (double)d[8];
-  win = added + dc / 6.0 + ((double)d[0] - (double)d0_old);
+  if (bottom) added = to_f64(d[2]) + to_f64(d[5]) + to_f64(d[6]);
+  else added = to_f64(d[4]) + to_f64(d[7]) + to_f64(d[8]);
+  win = added + dc / 6.0 + (to_f64(d[0]) - to_f64(d0_old));
 }
 
-template <typename R>
-__device__ __forceinline__ double warp_sum(double v) {
+// One level of a transposed butterfly sum over a warp: each lane holds M
+// partial sums; it keeps one half (the upper one when `up`), receives the
+// partner's values of that half across lane distance o and adds them, so
+// that after the levels 16, 8, 4, 2 (and a last pairwise sum across 1) lanes
+// 2s and 2s + 1 hold the warp's total of value s, for 16 values with 16
+// additions per lane instead of 5 per value.
+template <int M>
+__device__ __forceinline__ void fold_half(double* v, int o, bool up) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  for (int j = 0; j < M / 2; ++j) {
+    const double keep = up ? v[j + M / 2] : v[j];
+    const double send = up ? v[j] : v[j + M / 2];
+    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
 }
 
 // Populations of one lattice at a node: pulled from the previous step
@@ -339,6 +369,152 @@ __device__ __forceinline__ bool region_node_once(int lx, int ly, int x0, int y0,
   return gy >= 0 && gy < ny;
 }
 
+// Conformation tensor and constitutive function F(A) of a node from its
+// raw conformation deviations dphi_c (Sec. 2: eqb4 for Oldroyd-B, FENE-P,
+// FENE-CR), F in deviation form F = f (A - I) + (f - a) I.
+template <typename R, bool MASKED>
+__device__ __forceinline__ void polymer_terms(const InstDev& D, R d0, R d1, R d2, R& Axx,
+                                              R& Axy, R& Ayy, R& Fxx, R& Fxy, R& Fyy) {
+  Axx = R(1) + d0;
+  Axy = d1;
+  Ayy = R(1) + d2;
+  Fxx = d0;
+  Fxy = d1;
+  Fyy = d2;
+  if (MASKED && D.model != 0) {  // other models run in the general variant only
+    const R tr = Axx + Ayy;
+    const R f = R(1) / (R(1) - tr * coef<R>(D, kCoefInvL2));
+    const R a = D.model == 2 ? f : coef<R>(D, kCoefAfene);
+    Fxx = f * d0 + (f - a);
+    Fxy = f * d1;
+    Fyy = f * d2 + (f - a);
+  }
+}
+
+// Component l (xx, xy, yy) of the source Phi_ab of the conformation
+// equation (Sec. 3.2) with G** = d_g u_b.
+template <typename R>
+__device__ __forceinline__ R source_component(int l, R Axx, R Axy, R Ayy, R Fxx, R Fxy, R Fyy,
+                                              R il, R G00, R G01, R G10, R G11) {
+  const R div = G00 + G11;
+  if (l == 0) return -Fxx * il + R(2) * (Axx * G00 + Axy * G10) + Axx * div;
+  if (l == 1) return -Fxy * il + (Axx * G01 + Axy * G11) + (Axy * G00 + Ayy * G10) + Axy * div;
+  return -Fyy * il + R(2) * (Axy * G01 + Ayy * G11) + Ayy * div;
+}
+
+// Hydrodynamic TRT-RLB collision of one node (eq_ev_f, eq4, eq5, eq6, F_i)
+// and the store of its 9 post-collision populations.
+template <typename R>
+__device__ __forceinline__ void collide_hydro(const InstDev& D, int k, int S, R* __restrict__ dst,
+                                              const HydroM<R>& hm, R rho, R ux, R uy, R dPx,
+                                              R dPy, R txx, R txy, R tyy, R Fx, R Fy) {
+  const R cs2 = R(1.0 / 3.0);
+  const R c1 = coef<R>(D, kCoefCs1), c2 = coef<R>(D, kCoefCs2);
+  const R h1 = coef<R>(D, kCoefHs1), w1 = coef<R>(D, kCoefWs1);
+  const R ruxx = rho * ux * ux, ruyy = rho * uy * uy, ruxy = rho * ux * uy;
+  const R ruxxy = ruxx * uy, ruxyy = ruxy * uy;
+  const R nxx = hm.pxx - cs2 * hm.drho - ruxx;  // A_xx^neq
+  const R nyy = hm.pyy - cs2 * hm.drho - ruyy;  // A_yy^neq
+  const R nxy = hm.pxy - ruxy;                  // A_xy^neq
+  const R nxxy = hm.qxxy - cs2 * hm.jy - ruxxy; // A_xxy^neq
+  const R nxyy = hm.qxyy - cs2 * hm.jx - ruxyy; // A_xyy^neq
+  const R bx = hm.jx + Fx, by = hm.jy + Fy;     // rho u + (1-1/tau)A_a + F-term
+  const R bxx = ruxx + c1 * nxx - h1 * dPx - w1 * txx;
+  const R byy = ruyy + c1 * nyy - h1 * dPy - w1 * tyy;
+  const R bxy = ruxy + c1 * nxy - w1 * txy;
+  const R bxxy = ruxxy + c2 * nxxy;
+  const R bxyy = ruxyy + c2 * nxyy;
+  R out[9];
+  reconstruct<R>(hm.drho, bx, by, bxx, byy, bxy, bxxy, bxyy, out);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dst[(size_t)i * S + k] = out[i];
+}
+
+// Conformation TRT-RLB collision of lattice l at one node (eq_g0 with
+// G~_i, F~_i and its backward time difference) and the store of its 9
+// post-collision populations.  sl, so: the source now and one step back.
+template <typename R, bool MASKED>
+__device__ __forceinline__ void collide_cde(const InstDev& D, int k, int S, R* __restrict__ dst,
+                                            int l, const CdeM<R>& m, R rho, R ux, R uy, R sl,
+                                            R so, R uxo, R uyo, R Fx, R Fy, R dRx, R dRy) {
+  const R cs2 = R(1.0 / 3.0);
+  const R ep = coef<R>(D, kCoefEp1), c2 = coef<R>(D, kCoefCp2), h1 = coef<R>(D, kCoefHp1);
+  const R irho = R(1) / rho;
+  const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+  // the force G~_i sees: F (eq_p_G_1) or F - c_s^2 grad rho (eq_p_G)
+  const bool gt = MASKED && D.gtilde;
+  const R Gx = gt ? Fx - cs2 * dRx : Fx, Gy = gt ? Fy - cs2 * dRy : Fy;
+  const R phi = (l == 1 ? R(0) : R(1)) + m.dphi;
+  const R Bx = m.jx - phi * ux, By = m.jy - phi * uy;
+  const R Bxx = m.pxx - cs2 * m.dphi - phi * uxx;
+  const R Byy = m.pyy - cs2 * m.dphi - phi * uyy;
+  const R Bxy = m.pxy - phi * uxy;
+  // small source terms first, one rounding at the magnitude of phi
+  const R c0p = m.dphi + (R(1.5) * sl - R(0.5) * so);
+  const R pr = phi * irho;
+  // (1 - 1/tau_p1) B = -B + ep B, kept split so float32 keeps the tiny
+  // difference tau_p1 - 1/2 accurately
+  const R cx = (phi * ux - Bx) + ep * Bx + h1 * (pr * Gx + ux * sl) +
+               R(0.5) * h1 * (ux * sl - uxo * so);
+  const R cy = (phi * uy - By) + ep * By + h1 * (pr * Gy + uy * sl) +
+               R(0.5) * h1 * (uy * sl - uyo * so);
+  const R cxx = phi * uxx + c2 * Bxx;
+  const R cyy = phi * uyy + c2 * Byy;
+  const R cxy = phi * uxy + c2 * Bxy;
+  R out[9];
+  reconstruct<R>(c0p, cx, cy, cxx, cyy, cxy, R(0), R(0), out);
+  R* dl = dst + (size_t)(9 + 9 * l) * S;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dl[(size_t)i * S + k] = out[i];
+}
+
+// Final-step record of one node: its float64 fields and its contributions to
+// the tile's partial record.  lattice -1 writes everything; 0 the
+// hydrodynamic part (rho, u, momentum, residual), 1..3 conformation lattice
+// lattice - 1 (A component, its sum; the wall balance is the caller's).  The
+// sums of rho, A_xx and A_yy are kept as deviations from their rest value 1
+// (added per tile from its node count) and the residual is scaled by 1/U_c
+// per tile: GB300 issues a float64 instruction only every 64 cycles per
+// warp, so the final step keeps them few.
+template <typename R, int MODE>
+__device__ __forceinline__ void final_node(const InstDev& D, int k, int S, int lattice, R drho,
+                                           R rho, R ux, R uy, const R* dphi, double* part) {
+  double* fl = D.fields;
+  bool finite = true;
+  if (lattice <= 0) {
+    const double dr = to_f64(drho);
+    const double vx = to_f64(ux), vy = to_f64(uy);
+    // residual against the fields of the previous final step (none at init);
+    // a float32 instance's previous fields are float32 values, so its
+    // differences are taken in float32
+    double res = 0.0;
+    if (MODE == kModeStep) {
+      if constexpr (sizeof(R) == 4)
+        res = to_f64(fmaxf(fabsf(ux - (float)fl[S + k]), fabsf(uy - (float)fl[2 * S + k])));
+      else
+        res = fmax(fabs(vx - fl[S + k]), fabs(vy - fl[2 * S + k]));
+    }
+    fl[k] = 1.0 + dr;
+    fl[S + k] = vx;
+    fl[2 * S + k] = vy;
+    part[kSumRho] = dr;
+    part[kSumJx] = to_f64(rho) * vx;
+    part[kSumJy] = to_f64(rho) * vy;
+    finite = isfinite(dr) && isfinite(vx) && isfinite(vy);
+    part[kResid] = res;
+  }
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    if (lattice >= 0 && lattice != 1 + l) continue;
+    const double d = to_f64(dphi[l]);
+    fl[(3 + l) * S + k] = l == 1 ? d : 1.0 + d;
+    part[kSumPhi + l] = d;
+    finite = finite && isfinite(d);
+  }
+  if (!finite) part[kResid] = 0.0;
+  part[kNonFinite] = finite ? 0.0 : 1.0;
+}
+
 // Source, both collisions, stores and final-step bookkeeping of one node
 // whose populations are already reduced to (wall-completed) moments:
 //   hm      raw hydro moments, cm[3] raw conformation moments
@@ -353,26 +529,16 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
                                              R G10, R G11, R dPx, R dPy, R dRx, R dRy, R Fx,
                                              R Fy, R So0, R So1, R So2, R uxo, R uyo,
                                              double* part) {
-  // conformation tensor, constitutive function F(A) (Sec. 2: eqb4 for
-  // Oldroyd-B, FENE-P, FENE-CR) in deviation form F = f (A - I) + (f - a) I,
-  // polymer stress (eq_kramer), source Phi_ab
-  const R Axx = R(1) + cm[0].dphi, Axy = cm[1].dphi, Ayy = R(1) + cm[2].dphi;
+  // conformation tensor, constitutive function, polymer stress (eq_kramer),
+  // source Phi_ab
+  R Axx, Axy, Ayy, Fxx, Fxy, Fyy;
+  polymer_terms<R, MASKED>(D, cm[0].dphi, cm[1].dphi, cm[2].dphi, Axx, Axy, Ayy, Fxx, Fxy, Fyy);
   const R mpl = coef<R>(D, kCoefMupLam), il = coef<R>(D, kCoefInvLam);
-  R Fxx = cm[0].dphi, Fxy = cm[1].dphi, Fyy = cm[2].dphi;
-  if (MASKED && D.model != 0) {  // other models run in the general variant only
-    const R tr = Axx + Ayy;
-    const R f = R(1) / (R(1) - tr * coef<R>(D, kCoefInvL2));
-    const R a = D.model == 2 ? f : coef<R>(D, kCoefAfene);
-    Fxx = f * cm[0].dphi + (f - a);
-    Fxy = f * cm[1].dphi;
-    Fyy = f * cm[2].dphi + (f - a);
-  }
   const R txx = mpl * Fxx, txy = mpl * Fxy, tyy = mpl * Fyy;
-  const R div = G00 + G11;
   R Sc[3], So[3] = {So0, So1, So2};
-  Sc[0] = -Fxx * il + R(2) * (Axx * G00 + Axy * G10) + Axx * div;
-  Sc[1] = -Fxy * il + (Axx * G01 + Axy * G11) + (Axy * G00 + Ayy * G10) + Axy * div;
-  Sc[2] = -Fyy * il + R(2) * (Axy * G01 + Ayy * G11) + Ayy * div;
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+    Sc[l] = source_component<R>(l, Axx, Axy, Ayy, Fxx, Fxy, Fyy, il, G00, G01, G10, G11);
   if (MODE != kModeStep) {
     // first step: the backward difference of the CDE source is zero
     So[0] = Sc[0];
@@ -381,67 +547,11 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
     uxo = ux;
     uyo = uy;
   }
-
-  // ---- hydrodynamic TRT-RLB collision (eq_ev_f, eq4, eq5, eq6, F_i) ----
-  {
-    const R cs2 = R(1.0 / 3.0);
-    const R c1 = coef<R>(D, kCoefCs1), c2 = coef<R>(D, kCoefCs2);
-    const R h1 = coef<R>(D, kCoefHs1), w1 = coef<R>(D, kCoefWs1);
-    const R ruxx = rho * ux * ux, ruyy = rho * uy * uy, ruxy = rho * ux * uy;
-    const R ruxxy = ruxx * uy, ruxyy = ruxy * uy;
-    const R nxx = hm.pxx - cs2 * hm.drho - ruxx;  // A_xx^neq
-    const R nyy = hm.pyy - cs2 * hm.drho - ruyy;  // A_yy^neq
-    const R nxy = hm.pxy - ruxy;                  // A_xy^neq
-    const R nxxy = hm.qxxy - cs2 * hm.jy - ruxxy; // A_xxy^neq
-    const R nxyy = hm.qxyy - cs2 * hm.jx - ruxyy; // A_xyy^neq
-    const R bx = hm.jx + Fx, by = hm.jy + Fy;     // rho u + (1-1/tau)A_a + F-term
-    const R bxx = ruxx + c1 * nxx - h1 * dPx - w1 * txx;
-    const R byy = ruyy + c1 * nyy - h1 * dPy - w1 * tyy;
-    const R bxy = ruxy + c1 * nxy - w1 * txy;
-    const R bxxy = ruxxy + c2 * nxxy;
-    const R bxyy = ruxyy + c2 * nxyy;
-    R out[9];
-    reconstruct<R>(hm.drho, bx, by, bxx, byy, bxy, bxxy, bxyy, out);
+  collide_hydro<R>(D, k, S, dst, hm, rho, ux, uy, dPx, dPy, txx, txy, tyy, Fx, Fy);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) dst[(size_t)i * S + k] = out[i];
-  }
-
-  // ---- three conformation TRT-RLB collisions (eq_g0) ----
-  {
-    const R cs2 = R(1.0 / 3.0);
-    const R ep = coef<R>(D, kCoefEp1), c2 = coef<R>(D, kCoefCp2), h1 = coef<R>(D, kCoefHp1);
-    const R irho = R(1) / rho;
-    const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
-    // the force G~_i sees: F (eq_p_G_1) or F - c_s^2 grad rho (eq_p_G)
-    const bool gt = MASKED && D.gtilde;
-    const R Gx = gt ? Fx - cs2 * dRx : Fx, Gy = gt ? Fy - cs2 * dRy : Fy;
-#pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      const R phi = (l == 1 ? R(0) : R(1)) + cm[l].dphi;
-      const R Bx = cm[l].jx - phi * ux, By = cm[l].jy - phi * uy;
-      const R Bxx = cm[l].pxx - cs2 * cm[l].dphi - phi * uxx;
-      const R Byy = cm[l].pyy - cs2 * cm[l].dphi - phi * uyy;
-      const R Bxy = cm[l].pxy - phi * uxy;
-      const R sl = Sc[l], so = So[l];
-      // small source terms first, one rounding at the magnitude of phi
-      const R c0p = cm[l].dphi + (R(1.5) * sl - R(0.5) * so);
-      const R pr = phi * irho;
-      // (1 - 1/tau_p1) B = -B + ep B, kept split so float32 keeps the tiny
-      // difference tau_p1 - 1/2 accurately
-      const R cx = (phi * ux - Bx) + ep * Bx + h1 * (pr * Gx + ux * sl) +
-                   R(0.5) * h1 * (ux * sl - uxo * so);
-      const R cy = (phi * uy - By) + ep * By + h1 * (pr * Gy + uy * sl) +
-                   R(0.5) * h1 * (uy * sl - uyo * so);
-      const R cxx = phi * uxx + c2 * Bxx;
-      const R cyy = phi * uyy + c2 * Byy;
-      const R cxy = phi * uxy + c2 * Bxy;
-      R out[9];
-      reconstruct<R>(c0p, cx, cy, cxx, cyy, cxy, R(0), R(0), out);
-      R* dl = dst + (size_t)(9 + 9 * l) * S;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) dl[(size_t)i * S + k] = out[i];
-    }
-  }
+  for (int l = 0; l < 3; ++l)
+    collide_cde<R, MASKED>(D, k, S, dst, l, cm[l], rho, ux, uy, Sc[l], So[l], uxo, uyo, Fx, Fy,
+                           dRx, dRy);
 
   hist[k] = Sc[0];
   hist[S + k] = Sc[1];
@@ -450,31 +560,8 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
   hist[4 * S + k] = uy;
 
   if (FINAL) {
-    double* fl = D.fields;
-    const double r = 1.0 + (double)hm.drho;
-    const double vx = (double)ux, vy = (double)uy;
-    const double axx = 1.0 + (double)cm[0].dphi, axy = (double)cm[1].dphi,
-                 ayy = 1.0 + (double)cm[2].dphi;
-    // residual against the fields of the previous final step (none at init)
-    const double res = (MODE == kModeStep)
-                           ? fmax(fabs(vx - fl[S + k]), fabs(vy - fl[2 * S + k])) * D.inv_Uc
-                           : 0.0;
-    fl[k] = r;
-    fl[S + k] = vx;
-    fl[2 * S + k] = vy;
-    fl[3 * S + k] = axx;
-    fl[4 * S + k] = axy;
-    fl[5 * S + k] = ayy;
-    part[kSumRho] += r;
-    part[kSumJx] += (double)rho * vx;
-    part[kSumJy] += (double)rho * vy;
-    part[kSumPhi + 0] += axx;
-    part[kSumPhi + 1] += axy;
-    part[kSumPhi + 2] += ayy;
-    const bool finite = isfinite(r) && isfinite(vx) && isfinite(vy) && isfinite(axx) &&
-                        isfinite(axy) && isfinite(ayy);
-    part[kResid] = fmax(part[kResid], finite ? res : 0.0);
-    part[kNonFinite] += finite ? 0.0 : 1.0;
+    const R dphi[3] = {cm[0].dphi, cm[1].dphi, cm[2].dphi};
+    final_node<R, MODE>(D, k, S, -1, hm.drho, rho, ux, uy, dphi, part);
   }
 }
 
@@ -593,6 +680,53 @@ __device__ __forceinline__ void region_rho_u(const InstDev& D, const void* src,
     return;
   }
   node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, rho, ux, uy);
+}
+
+// The tile's partial record of the final step in a fixed order: the 12
+// sums by a transposed butterfly per warp, the residual (>= 0 and finite, so
+// the order of its bit patterns is its numeric order) and the non-finite
+// count as integers, then the warps in order and the rest values from the
+// count of the tile's fluid nodes.  Every thread of the CTA calls it.
+template <int NT>
+__device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T,
+                                              const double* part, bool active,
+                                              double* __restrict__ partials,
+                                              double (*s_red)[kPartial]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  static_assert(kNonFinite == 13 && kResid == 12, "12 sums, then residual and flag");
+  double v[16];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) v[j] = part[j];
+#pragma unroll
+  for (int j = 12; j < 16; ++j) v[j] = 0.0;
+  fold_half<16>(v, 16, (lane & 16) != 0);
+  fold_half<8>(v, 8, (lane & 8) != 0);
+  fold_half<4>(v, 4, (lane & 4) != 0);
+  fold_half<2>(v, 2, (lane & 2) != 0);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  long long rb = __double_as_longlong(part[kResid]);
+  unsigned nf = __double_as_longlong(part[kNonFinite]) != 0 ? 1u : 0u;  // 0.0 or 1.0
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ob = __shfl_xor_sync(0xffffffffu, rb, o);
+    rb = ob > rb ? ob : rb;
+    nf += __shfl_xor_sync(0xffffffffu, nf, o);
+  }
+  const int slot = (lane >> 1) & 15;
+  if ((lane & 1) == 0 && slot < 12) s_red[warp][slot] = v[0];
+  if (lane == 0) {
+    s_red[warp][kResid] = __longlong_as_double(rb);
+    s_red[warp][kNonFinite] = (double)nf;
+  }
+  const int nfluid = __syncthreads_count(active);
+  if (threadIdx.x < 14) {
+    const int j = threadIdx.x;
+    double t = s_red[0][j];
+    for (int w = 1; w < NT / 32; ++w) t = (j == kResid) ? fmax(t, s_red[w][j]) : t + s_red[w][j];
+    if (j == kSumRho || j == kSumPhi || j == kSumPhi + 2) t += (double)nfluid;
+    if (j == kResid) t *= D.inv_Uc;
+    partials[(size_t)T.slot * kPartial + j] = t;
+  }
 }
 
 template <typename R, int MODE, bool FINAL, bool MASKED, int NT>
@@ -886,22 +1020,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     for (int j = 0; j < 6; ++j) D.fields[(size_t)j * S + ks] = 0.0;
   }
 
-  if (FINAL) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < 14; ++j) {
-      const double v = (j == kResid) ? warp_max(part[j]) : warp_sum<double>(part[j]);
-      if (lane == 0) s_red[warp][j] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 14) {
-      const int j = threadIdx.x;
-      double v = s_red[0][j];
-      for (int w = 1; w < NT / 32; ++w)
-        v = (j == kResid) ? fmax(v, s_red[w][j]) : v + s_red[w][j];
-      partials[(size_t)T.slot * kPartial + j] = v;
-    }
-  }
+  if (FINAL) tile_partials<NT>(D, T, part, active, partials, s_red);
 }
 
 // One CTA of NT threads per tile (NT a multiple of 32, at least 32, with
@@ -921,6 +1040,228 @@ __global__ void __launch_bounds__(NT, MinBlocks<R, MASKED, NT>::value)
   const TileDev T = tiles[blockIdx.x];
   if (!MASKED && T.masked) return;
   process_tile<R, MODE, FINAL, MASKED, NT>(insts, T, parity, partials, s_rho, s_ux, s_uy, s_red);
+}
+
+// ---- float64 steps of tiny batches: one lattice per warp --------------------
+//
+// GB300 issues a float64 instruction only once every 64 cycles per warp, and
+// a warp pays that for every instruction whatever the number of active
+// lanes; four warps per SM saturate its float64 pipe.  A float64 batch too
+// small to give every SM several warps is therefore bound by the float64
+// instruction count of one thread's node, not by the number of nodes.  This
+// variant spreads the update of each node over four warps: warp 0 carries
+// the hydrodynamic lattice (pull, Zou-He, moments, rho and u, the gradients
+// and the hydrodynamic collision), warp 1 + l the conformation lattice l
+// (pull, CNEBB, moments, its component of Phi_ab and its collision); the
+// warps meet in shared memory twice (rho, u; the three phi).  Every value is
+// the same expression of the same operands as in process_tile, so the
+// fields are bit-identical to those of the one-warp kernel.
+//   Tiles of at most 32 nodes (TX * TY <= 32), plain tiles only (no mask, no
+//   open column, Oldroyd-B with the eq_p_G_1 form of G~), time steps only
+//   (the initialisation runs the one-warp kernel).
+constexpr int kSplitThreads = 128;
+
+template <bool FINAL>
+__device__ __forceinline__ void process_tile_split(const InstDev* __restrict__ insts,
+                                                   const TileDev T, int parity,
+                                                   double* __restrict__ partials,
+                                                   double* s_rho, double* s_ux, double* s_uy,
+                                                   double (*s_phi)[32], double (*s_red)[kPartial]) {
+  using R = double;
+  constexpr int MODE = kModeStep;
+  const InstDev& D = insts[T.inst];
+  const int nx = D.nx, ny = D.ny, S = D.stride, TX = D.TX, TY = D.TY, hy = D.hy;
+  const bool py = D.periodic_y != 0;
+  const void* src = D.pop[parity];
+  const R* __restrict__ srcR = (const R*)src;
+  R* __restrict__ dst = (R*)D.pop[parity ^ 1];
+  const R* __restrict__ force = (const R*)D.force;
+  R* __restrict__ hist = (R*)D.hist;
+  const bool ffield = D.force_field != 0;
+  const R Fx0 = coef<R>(D, kCoefFx), Fy0 = coef<R>(D, kCoefFy);
+  const int RW = TX + 2;
+  const int role = threadIdx.x >> 5, lane = threadIdx.x & 31;  // 0 hydro, 1 + l lattice l
+  const int tx = lane % TX, ty = lane / TX;
+  const bool in_tile = ty < TY;
+  const int x = T.x0 + tx, y = T.y0 + ty;
+  const bool inside = in_tile && (x < nx) && (y < ny);
+  const bool active = inside;
+  const int ri = (ty + hy) * RW + tx + 1;
+  const bool wb = active && !py && y == 0, wt = active && !py && y == ny - 1;
+  const bool wcomp = wb || wt;
+  const int nring = 2 * hy * TX + 2 * TY;
+
+  // ---- phase A: pulls -------------------------------------------------------
+  // the halo ring's hydrodynamic pulls go to the conformation warps (their
+  // own float64 work is the lighter one)
+  const int q = threadIdx.x - 32;
+  int ring_r = -1, rgx = 0, rgy = 0;
+  R dr[9];
+  if (role > 0 && q < nring) {
+    int lx, ly;
+    ring_slot(q, RW, TY, hy, lx, ly);
+    if (region_node(lx, ly, T.x0, T.y0, hy, nx, ny, py, rgx, rgy)) {
+      ring_r = ly * RW + lx;
+      int rm, rp;
+      neighbour_rows(rgy, nx, ny, py, rm, rp);
+      const int xm = rgx == 0 ? nx - 1 : rgx - 1, xp = rgx == nx - 1 ? 0 : rgx + 1;
+      PopSource<R, MODE>::hydro(src, S, nx, rgy * nx + rgx, rgy * nx, rm, rp, rgx, xm, xp, dr);
+    }
+  }
+  const int l = role - 1;
+  R d[9], post[3] = {R(0), R(0), R(0)}, So = R(0), uxo = R(0), uyo = R(0), Fx = Fx0, Fy = Fy0;
+  int k = 0;
+  if (active) {
+    k = y * nx + x;
+    int rm, rp;
+    neighbour_rows(y, nx, ny, py, rm, rp);
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    if (role == 0) {
+      PopSource<R, MODE>::hydro(src, S, nx, k, y * nx, rm, rp, x, xm, xp, d);
+    } else {
+      PopSource<R, MODE>::cde(src, l, S, nx, k, y * nx, rm, rp, x, xm, xp, d);
+      So = hist[(size_t)l * S + k];
+      uxo = hist[3 * S + k];
+      uyo = hist[4 * S + k];
+      if (wcomp) {
+        const int h0 = wb ? 4 : 2, h1 = wb ? 7 : 5, h2 = wb ? 8 : 6;
+        const R* own = srcR + (size_t)(9 + 9 * l) * S + k;
+        post[0] = own[h0 * S];
+        post[1] = own[h1 * S];
+        post[2] = own[h2 * S];
+      }
+    }
+    if (ffield) {
+      Fx = force[k];
+      Fy = force[S + k];
+    }
+  }
+  // ring moments (a ring longer than the three conformation warps, which the
+  // tile widths of the one-warp CTAs never make, is finished by warp 0 below)
+  if (ring_r >= 0) {
+    const int rk = rgy * nx + rgx;
+    const R rFx = ffield ? force[rk] : Fx0;
+    const R rFy = ffield ? force[S + rk] : Fy0;
+    if (!py && (rgy == 0 || rgy == ny - 1)) zou_he<R>(dr, rFx, rFy, rgy == 0);
+    HydroM<R> m;
+    hydro_moments<R>(dr, m);
+    const R rho = R(1) + m.drho;
+    s_rho[ring_r] = rho;
+    const R irho = R(1) / rho;
+    s_ux[ring_r] = (m.jx + R(0.5) * rFx) * irho;
+    s_uy[ring_r] = (m.jy + R(0.5) * rFy) * irho;
+  }
+  for (int qq = kSplitThreads - 32 + threadIdx.x; role == 0 && qq < nring; qq += 32) {
+    int lx, ly, gx, gy;
+    ring_slot(qq, RW, TY, hy, lx, ly);
+    if (!region_node(lx, ly, T.x0, T.y0, hy, nx, ny, py, gx, gy)) continue;
+    R r, vx, vy;
+    node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
+    const int rr = ly * RW + lx;
+    s_rho[rr] = r;
+    s_ux[rr] = vx;
+    s_uy[rr] = vy;
+  }
+  // own hydrodynamic moments (warp 0), and the wrapped nodes of a ragged tile
+  HydroM<R> hm;
+  if (role == 0) {
+    if (active) {
+      if (wcomp) zou_he<R>(d, Fx, Fy, wb);
+      hydro_moments<R>(d, hm);
+      const R rho = R(1) + hm.drho;
+      const R irho_own = R(1) / rho;
+      s_rho[ri] = rho;
+      s_ux[ri] = (hm.jx + R(0.5) * Fx) * irho_own;
+      s_uy[ri] = (hm.jy + R(0.5) * Fy) * irho_own;
+    } else if (in_tile) {
+      const int gx = x % nx;
+      const int gy = py ? y % ny : y;
+      if (gy < ny) {
+        R r, vx, vy;
+        node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, r, vx, vy);
+        s_rho[ri] = r;
+        s_ux[ri] = vx;
+        s_uy[ri] = vy;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- conformation walls with the node's own u, moments -----------------------
+  R rho = R(1), ux = R(0), uy = R(0);
+  if (active) {
+    rho = s_rho[ri];
+    ux = s_ux[ri];
+    uy = s_uy[ri];
+  }
+  CdeM<R> cm;
+  double wall_in = 0.0, wall_out = 0.0;
+  if (role > 0 && active) {
+    if (wcomp) {
+      const R delta = (l == 1) ? R(0) : R(1);
+      cnebb<R>(d, post[0], post[1], post[2], delta, ux, uy, wb, wall_in, wall_out);
+    }
+    cde_moments<R>(d, cm);
+    s_phi[l][lane] = cm.dphi;
+  }
+  __syncthreads();
+
+  // ---- phase B: gradients, source, this warp's collision, stores ---------------
+  double part[FINAL ? 14 : 1];
+#pragma unroll
+  for (int j = 0; j < (FINAL ? 14 : 1); ++j) part[j] = 0.0;
+  if (active) {
+    const R half = R(0.5);
+    const R G00 = half * (s_ux[ri + 1] - s_ux[ri - 1]);
+    const R G01 = half * (s_uy[ri + 1] - s_uy[ri - 1]);
+    R G10, G11, dPy;
+    const int a = wb ? ri : (wt ? ri - 2 * RW : ri), b = wb ? ri : (wt ? ri - RW : ri - RW);
+    const int c = wb ? ri + RW : (wt ? ri : ri + RW), e = wb ? ri + 2 * RW : ri;
+    y_gradients<R>(wb, wt, s_rho[a], s_ux[a], s_uy[a], s_rho[b], s_ux[b], s_uy[b], rho, ux, uy,
+                   s_rho[c], s_ux[c], s_uy[c], s_rho[e], s_ux[e], s_uy[e], G10, G11, dPy);
+    R Axx, Axy, Ayy, Fxx, Fxy, Fyy;
+    polymer_terms<R, false>(D, s_phi[0][lane], s_phi[1][lane], s_phi[2][lane], Axx, Axy, Ayy, Fxx,
+                            Fxy, Fyy);
+    if (role == 0) {
+      const R cxp = s_rho[ri + 1] * s_ux[ri + 1] * s_ux[ri + 1] * s_ux[ri + 1];
+      const R cxm = s_rho[ri - 1] * s_ux[ri - 1] * s_ux[ri - 1] * s_ux[ri - 1];
+      const R dPx = half * (cxp - cxm);
+      const R mpl = coef<R>(D, kCoefMupLam);
+      const R txx = mpl * Fxx, txy = mpl * Fxy, tyy = mpl * Fyy;
+      collide_hydro<R>(D, k, S, dst, hm, rho, ux, uy, dPx, dPy, txx, txy, tyy, Fx, Fy);
+      hist[3 * S + k] = ux;
+      hist[4 * S + k] = uy;
+      if (FINAL) final_node<R, MODE>(D, k, S, 0, hm.drho, rho, ux, uy, nullptr, part);
+    } else {
+      const R il = coef<R>(D, kCoefInvLam);
+      const R sl = source_component<R>(l, Axx, Axy, Ayy, Fxx, Fxy, Fyy, il, G00, G01, G10, G11);
+      collide_cde<R, false>(D, k, S, dst, l, cm, rho, ux, uy, sl, So, uxo, uyo, Fx, Fy, R(0),
+                            R(0));
+      hist[(size_t)l * S + k] = sl;
+      if (FINAL) {
+        const R dphi[3] = {s_phi[0][lane], s_phi[1][lane], s_phi[2][lane]};
+        final_node<R, MODE>(D, k, S, role, R(0), rho, ux, uy, dphi, part);
+        part[kWallIn + l] = wall_in;
+        part[kWallOut + l] = wall_out;
+      }
+    }
+  }
+  if (FINAL) tile_partials<kSplitThreads>(D, T, part, active && role == 0, partials, s_red);
+}
+
+template <bool FINAL>
+__global__ void __launch_bounds__(kSplitThreads, 4)
+    step_kernel_split(const InstDev* __restrict__ insts, const TileDev* __restrict__ tiles,
+                      int parity, double* __restrict__ partials) {
+  constexpr int kRegion = region_max(32);
+  __shared__ double s_rho[kRegion];
+  __shared__ double s_ux[kRegion];
+  __shared__ double s_uy[kRegion];
+  __shared__ double s_phi[3][32];
+  __shared__ double s_red[kSplitThreads / 32][kPartial];
+  const TileDev T = tiles[blockIdx.x];
+  if (T.masked) return;
+  process_tile_split<FINAL>(insts, T, parity, partials, s_rho, s_ux, s_uy, s_phi, s_red);
 }
 
 }  // namespace lbve

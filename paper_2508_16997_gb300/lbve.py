@@ -100,8 +100,8 @@ def load() -> ctypes.CDLL:
                                               ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32), _dp]
         L.lbve_profile.argtypes = [_vp, ctypes.c_int32]
-        L.lbve_profile_read.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _dp,
-                                        _dp, _dp]
+        L.lbve_profile_read.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32), _dp, _dp, _dp]
         L.lbve_destroy.argtypes = [_vp]
         L.lbve_destroy.restype = None
         L.lbve_error_string.argtypes = [ctypes.c_int]
@@ -192,13 +192,15 @@ def lbve_profile(h, max_launches: int) -> None:
     _check(load().lbve_profile(h, int(max_launches)), "lbve_profile")
 
 
-def lbve_profile_read(h, precision: int):
+def lbve_profile_read(h, precision: int, final_step: bool = False):
     """(launches, total ms, shortest ms, longest ms) of the timed step-kernel
-    launches of one precision."""
+    launches of one precision: the ordinary steps, or the final step of
+    each lbve_step call."""
     n = ctypes.c_int32()
     tot, lo, hi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-    _check(load().lbve_profile_read(h, int(precision), ctypes.byref(n), ctypes.byref(tot),
-                                    ctypes.byref(lo), ctypes.byref(hi)), "lbve_profile_read")
+    _check(load().lbve_profile_read(h, int(precision), 1 if final_step else 0, ctypes.byref(n),
+                                    ctypes.byref(tot), ctypes.byref(lo), ctypes.byref(hi)),
+           "lbve_profile_read")
     return n.value, tot.value, lo.value, hi.value
 
 

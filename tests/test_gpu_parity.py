@@ -66,31 +66,71 @@ def test_channel_fp64_walls(lbve):
     assert_fp64_parity(sim.fields(0), o.fields(), what="channel")
 
 
+def _closed_form_channel(H, Wi, Ma):
+    ue, Axx, Axy, Ayy = cf.poiseuille_steady(H, Wi, wl.velocity_scale(Ma))
+    f = np.zeros((6, H + 1, 4))
+    f[0] = 1.0
+    f[1], f[3], f[4], f[5] = ue[:, None], Axx[:, None], Axy[:, None], Ayy[:, None]
+    return f
+
+
+def _self_sensitivity(inst, init, steps, rng):
+    """The oracle's own round-off sensitivity: the relative L2 change of u and
+    of C after `steps` steps when every population is perturbed by half an
+    ulp (x-invariantly, as the channel is) after the first 10 steps."""
+    ref = oracle_sim(inst, init=init)
+    ref.step(steps)
+    p = oracle_sim(inst, init=init)
+    p.step(10)
+    f, g = p.state()
+    f = f * (1 + 2.0 ** -53 * rng.standard_normal(f.shape[:-1] + (1,)))
+    g = g * (1 + 2.0 ** -53 * rng.standard_normal(g.shape[:-1] + (1,)))
+    p.set_state(f, g)
+    p.step(steps - 10)
+    e = parity_errors(p.fields(), ref.fields())
+    return max(e["u"], e["C"])
+
+
 def test_channel_fp64_high_wi(lbve):
     """The channel workload at the top of the paper's Wi range, H = 64
     (nx = 4, beta 0.5, Re 1, Sc 1e6): Wi = 1e3 and 1e4 (lambda = 1.1e6 and
     1.1e7 steps), each from rest and from the steady closed form (eq_ux_ana /
     eq_Tab_ana, A_xx - 1 up to 3.2e9), four instances in one batch, 1000
-    steps, against the oracle to 1e-12."""
+    steps, against the oracle.
+
+    From rest: 1e-12.  From the closed form the problem is ill-conditioned:
+    the polymer normal stress tau_xx = mu_p/lambda (A_xx - 1) reaches 54
+    (Wi = 1e3) and 540 (Wi = 1e4) lattice units, 160 and 1600 times the
+    pressure, and the hydrodynamic populations that carry it through T_i grow
+    to 30 and 300, so one rounding of the state moves u by 1.5e-13 and
+    1.4e-12 after 1000 steps (measured here on the oracle alone:
+    _self_sensitivity).  Two correct implementations round differently on
+    every step; the differences add up like a random walk (sqrt(1000) = 32
+    roundings' worth), so the bound is 100 x the measured sensitivity, and
+    never below 1e-12.  The density's uniform mode (total mass) is undamped
+    and gathers the rounding of each step: |rho_gpu - rho_oracle| is bounded
+    by steps x 2^-52 x the largest population magnitude of the oracle's
+    state (4e-11 at Wi = 1e4, 1e-13 from rest)."""
     H, insts, inits = 64, [], []
     for Wi in (1e3, 1e4):
         for start in ("rest", "closed"):
             inst = wl.channel(H, nx=4, beta=0.5, Wi=Wi)
             insts.append(inst)
-            if start == "rest":
-                inits.append(None)
-                continue
-            ue, Axx, Axy, Ayy = cf.poiseuille_steady(H, Wi, wl.velocity_scale(inst.Ma))
-            f = np.zeros((6, H + 1, 4))
-            f[0] = 1.0
-            f[1], f[3], f[4], f[5] = ue[:, None], Axx[:, None], Axy[:, None], Ayy[:, None]
-            inits.append(f)
+            inits.append(None if start == "rest" else _closed_form_channel(H, Wi, inst.Ma))
     sim = lbve.Simulation(insts, precision=lbve.LBVE_FP64, init_fields=inits)
     sim.step(1000)
+    rng = np.random.default_rng(3)
     for i, inst in enumerate(insts):
         o = oracle_sim(inst, init=inits[i])
         o.step(1000)
-        assert_fp64_parity(sim.fields(i), o.fields(), what=f"Wi {inst.Wi} start {i % 2}")
+        tol = FP64_TOL
+        if inits[i] is not None:
+            tol = max(FP64_TOL, 100.0 * _self_sensitivity(inst, inits[i], 1000, rng))
+        got, ref = sim.fields(i), o.fields()
+        err = parity_errors(got, ref)
+        assert err["u"] <= tol and err["C"] <= tol, (inst.Wi, i % 2, tol, err)
+        fmax = float(np.abs(o.state()[0]).max())
+        assert np.abs(got[0] - ref[0]).max() <= 1000 * 2.0 ** -52 * max(fmax, 0.5), (inst.Wi, fmax)
     assert not sim.status().any()
 
 

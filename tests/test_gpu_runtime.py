@@ -131,10 +131,13 @@ def test_profile_times_every_launch(lbve):
     lbve.lbve_profile(a.h, 50)
     a.step(7)
     n, tot, lo, hi = lbve.lbve_profile_read(a.h, lbve.LBVE_FP32_DEV)
-    assert n == 7 and tot > 0 and 0 < lo <= hi <= tot
+    assert n == 6 and tot > 0 and 0 < lo <= hi <= tot  # 6 ordinary steps
+    n, tot, lo, hi = lbve.lbve_profile_read(a.h, lbve.LBVE_FP32_DEV, final_step=True)
+    assert n == 1 and tot > 0 and lo == hi == tot
     assert lbve.lbve_profile_read(a.h, lbve.LBVE_FP64)[0] == 0  # no float64 instance
-    a.step(70)  # 43 more timed launches, the rest untimed
+    a.step(70)  # 44 more timed ordinary launches, the rest untimed
     assert lbve.lbve_profile_read(a.h, lbve.LBVE_FP32_DEV)[0] == 50
+    assert lbve.lbve_profile_read(a.h, lbve.LBVE_FP32_DEV, final_step=True)[0] == 2
     b.step(77)  # two graph replays of 32 steps
     for i in range(len(insts)):
         np.testing.assert_array_equal(a.fields(i), b.fields(i))
