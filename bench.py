@@ -494,6 +494,7 @@ def run_ours(args):
     bins = {"1-10": (1.0, 10.0), "10-100": (10.0, 100.0), "100-1e3": (100.0, 1e3),
             "1e3-1e4": (1e3, 1e4 + 1)}
     per_bin = {k: {"u": 0.0, "C": 0.0, "instances": 0} for k in bins}
+    per_kind = {k: {"u": 0.0, "C": 0.0, "instances": 0} for k in ("channel", "frm")}
     err_all, err_le100 = 0.0, 0.0
     for j, inst in enumerate(insts):
         if flags64[j]:
@@ -512,6 +513,11 @@ def run_ours(args):
                 b_["u"] = max(b_["u"], eu)
                 b_["C"] = max(b_["C"], eC)
                 b_["instances"] += 1
+        if inst.kind in per_kind:
+            b_ = per_kind[inst.kind]
+            b_["u"] = max(b_["u"], eu)
+            b_["C"] = max(b_["C"], eC)
+            b_["instances"] += 1
     err_all = max_over_ranks(err_all)
     err_le100 = max_over_ranks(err_le100)
 
@@ -628,7 +634,8 @@ def run_ours(args):
                        "speedup_fp32_over_fp64": value / value64,
                        "roofline": measured_fp64_pipe(value64)},
         "fp32_vs_fp64_rel_l2": {"max_all": err_all, "max_Wi_le_100": err_le100,
-                                "per_Wi": per_bin, "steps": E, "target_Wi_le_100": 1e-5},
+                                "per_Wi": per_bin, "per_kind": per_kind, "steps": E,
+                                "target_Wi_le_100": 1e-5},
         "nonfinite_instances": int((flags != 0).sum()),
     }
     if adj is not None:

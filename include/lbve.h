@@ -188,6 +188,11 @@ int lbve_create(const lbve_params* p, int32_t n_instances, void* d_workspace, si
  * Populations start at the equilibria (eq2, eq_geq) of the initial fields;
  * the history of the CDE source is set so that its time difference is zero
  * on the first step.  Host arrays may be freed when the call returns.
+ * The geometry is checked on the host before anything changes; the values
+ * of body_force and init_fields on the device after their upload: a value
+ * that is not finite or an initial density that is not > 0 returns
+ * LBVE_ERR_ARG and leaves the instance uninitialised (its previous state is
+ * lost; lbve_step returns LBVE_ERR_STATE until the instance is set again).
  * Errors: LBVE_ERR_ARG, LBVE_ERR_GEOMETRY, LBVE_ERR_CUDA. */
 int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
                       const double* body_force, const double* init_fields);
@@ -249,7 +254,9 @@ int lbve_profile_read(lbve_handle* h, int32_t precision, int32_t final_step, int
 
 /* Synchronise the stream and copy per-instance status flags into
  * flags[0..n-1] (bit 0: a non-finite field was seen at the end of an
- * lbve_step call).  Returns LBVE_ERR_NONFINITE if any flag is set. */
+ * lbve_step call; bit 1: the last lbve_set_geometry of the instance
+ * rejected its force or initial fields).  Returns LBVE_ERR_NONFINITE if bit 0
+ * of any flag is set. */
 int lbve_status(lbve_handle* h, int32_t* flags);
 
 /* Macroscopic fields of instance inst at its current time:

@@ -12,7 +12,6 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "../../include/lbve.h"
@@ -423,48 +422,6 @@ void drop_graph(lbve_handle* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   h->graph_exec = nullptr;
   h->graph = nullptr;
-}
-
-// Whether every value is finite (exponent field not all ones); branch-free,
-// so that the host compiler vectorises it over large arrays.
-bool all_finite(const double* a, size_t n) {
-  uint64_t bad = 0;
-  for (size_t k = 0; k < n; ++k) {
-    uint64_t b;
-    std::memcpy(&b, a + k, sizeof b);
-    bad |= (uint64_t)(((b >> 52) & 0x7ffu) == 0x7ffu);
-  }
-  return bad == 0;
-}
-
-// Whether every value is > 0 (false for NaN), branch-free as all_finite.
-bool all_positive(const double* a, size_t n) {
-  uint64_t bad = 0;
-  for (size_t k = 0; k < n; ++k) bad |= (uint64_t)!(a[k] > 0.0);
-  return bad == 0;
-}
-
-// check(a, n) over an array split across host threads when it is large
-// (the checks of a large instance's host arrays then cost milliseconds).
-template <typename F>
-bool check_parallel(const double* a, size_t n, F check) {
-  constexpr size_t kMinPerThread = size_t(1) << 21;
-  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  const size_t nt = std::min<size_t>(hw, std::max<size_t>(1, n / kMinPerThread));
-  if (nt <= 1) return check(a, n);
-  std::vector<char> ok(nt, 0);
-  std::vector<std::thread> th;
-  const size_t chunk = (n + nt - 1) / nt;
-  for (size_t t = 0; t < nt; ++t) {
-    const size_t b = t * chunk, e = std::min(n, b + chunk);
-    th.emplace_back([&, t, b, e] { ok[t] = b < e ? check(a + b, e - b) : 1; });
-  }
-  bool all = true;
-  for (size_t t = 0; t < nt; ++t) {
-    th[t].join();
-    all = all && ok[t];
-  }
-  return all;
 }
 
 constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -902,16 +859,9 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
                       const double* body_force, const double* init_fields) {
   if (!h || inst < 0 || inst >= h->n) return set_error(LBVE_ERR_ARG, "bad handle or instance");
   {
-    // every host-side check before anything changes
-    const size_t nn = size_t(h->p[inst].nx) * h->p[inst].ny;
-    if (body_force && !check_parallel(body_force, 2 * nn, all_finite))
-      return set_error(LBVE_ERR_ARG, "body force not finite");
-    if (init_fields) {
-      if (!check_parallel(init_fields, 6 * nn, all_finite))
-        return set_error(LBVE_ERR_ARG, "initial fields not finite");
-      if (!check_parallel(init_fields, nn, all_positive))
-        return set_error(LBVE_ERR_ARG, "initial density must be > 0");
-    }
+    // the geometry is checked on the host before anything changes; the
+    // values of the force and the initial fields on the device, after the
+    // upload (below)
     const int rc = install_mask(h, inst, solid_mask);
     if (rc) return rc;
   }
@@ -923,12 +873,18 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
   InstDev& D = h->insts[inst];
   cudaError_t e = cudaSuccess;
 
+  // from here on the instance's state is being replaced: it counts as
+  // initialised again only when the call succeeds
+  h->ready[inst] = 0;
+  e = cudaMemsetAsync(h->d_flags + inst, 0, sizeof(int32_t), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "flag reset");
+  double* fstage = nullptr;
   if (body_force) {
-    double* stage = (double*)D.pop[P];  // staging: float64 [2][S]
-    e = cudaMemcpy2DAsync(stage, S * 8, body_force, nn * 8, nn * 8, 2, cudaMemcpyHostToDevice,
+    fstage = (double*)D.pop[P];  // staging: float64 [2][S]
+    e = cudaMemcpy2DAsync(fstage, S * 8, body_force, nn * 8, nn * 8, 2, cudaMemcpyHostToDevice,
                           h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "force upload");
-    if (launch_convert_force(p.precision, stage, D.force, (int)nn, (int)S, h->stream))
+    if (launch_convert_force(p.precision, fstage, D.force, (int)nn, (int)S, h->stream))
       return cuda_fail(cudaGetLastError(), "force conversion launch");
     D.force_field = 1;
   } else {
@@ -940,17 +896,15 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
   if (init_fields) {
     e = cudaMemcpy2DAsync(stage, S * 8, init_fields, nn * 8, nn * 8, 6, cudaMemcpyHostToDevice,
                           h->stream);
-  } else {
-    std::vector<double> def(6 * nn, 0.0);
-    for (size_t k = 0; k < nn; ++k) def[k] = def[3 * nn + k] = def[5 * nn + k] = 1.0;
-    e = cudaMemcpy2DAsync(stage, S * 8, def.data(), nn * 8, nn * 8, 6, cudaMemcpyHostToDevice,
-                          h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "initial field upload");
+  } else if (launch_fill_default_fields(stage, (int)nn, (int)S, h->stream)) {
+    return cuda_fail(cudaGetLastError(), "default field launch");
   }
-  if (e != cudaSuccess) return cuda_fail(e, "initial field upload");
+  if (launch_check_inputs(fstage, init_fields ? stage : nullptr, (int)nn, (int)S,
+                          h->d_flags + inst, kFlagBadInput, h->stream))
+    return cuda_fail(cudaGetLastError(), "input check launch");
   e = cudaMemcpyAsync(h->d_insts + inst, &D, sizeof(InstDev), cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "descriptor upload");
-  e = cudaMemsetAsync(h->d_flags + inst, 0, sizeof(int32_t), h->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "flag reset");
   // collide the equilibrium state of t = 0: reads pop[P^1] (staging), writes pop[P]
   if (launch_step(p.precision, h->plan.threads[q.list], h->d_insts,
                   h->d_tiles[q.list] + q.tile_begin, q.ntiles, P ^ 1,
@@ -965,9 +919,18 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
   if (launch_reduce(h->d_insts, inst, 1, h->d_partials, h->d_totals, h->d_flags, h->stream))
     return cuda_fail(cudaGetLastError(), "reduce launch");
   // the pageable copy of D above is staged before return; make the device
-  // state consistent before the caller reuses its arrays
-  e = cudaStreamSynchronize(h->stream);
+  // state consistent before the caller reuses its arrays, and read the
+  // input check
+  int32_t flag = 0;
+  e = cudaMemcpyAsync(&flag, h->d_flags + inst, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                      h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbve_set_geometry");
+  if (flag & (1 << kFlagBadInput))
+    return set_error(LBVE_ERR_ARG,
+                     "instance %d: a body force or initial field is not finite, or an initial "
+                     "density is not > 0; the instance is left uninitialised",
+                     inst);
   h->t[inst] = 0;
   h->ready[inst] = 1;
   return LBVE_OK;

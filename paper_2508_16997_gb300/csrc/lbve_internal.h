@@ -187,5 +187,12 @@ int launch_reduce(const InstDev* d_insts, int first_inst, int n_insts, const dou
                   double* d_totals, int32_t* d_flags, void* stream);
 int launch_convert_force(int prec, const double* d_src, void* d_dst, int n, int stride,
                          void* stream);
+// Default initial fields (rho = 1, u = 0, A = I) into float64 staging planes.
+int launch_fill_default_fields(double* d_stage, int n, int stride, void* stream);
+// Set bit `bit` of *d_flag if a staged force component or initial field is
+// not finite or an initial density is not in (0, inf) (either may be null).
+int launch_check_inputs(const double* d_force, const double* d_init, int n, int stride,
+                        int32_t* d_flag, int bit, void* stream);
+constexpr int kFlagBadInput = 1;  // status bit of a rejected lbve_set_geometry
 
 }  // namespace lbve

@@ -120,6 +120,60 @@ int launch_reduce(const InstDev* d_insts, int first_inst, int n_insts, const dou
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 
+// Default initial fields (rho = 1, u = 0, A = I) into the float64 staging
+// planes [6][stride], so that no host array is built and copied for them.
+__global__ void fill_default_fields_kernel(double* __restrict__ stage, int n, int stride) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    stage[i] = 1.0;
+    stage[(size_t)stride + i] = 0.0;
+    stage[2 * (size_t)stride + i] = 0.0;
+    stage[3 * (size_t)stride + i] = 1.0;
+    stage[4 * (size_t)stride + i] = 0.0;
+    stage[5 * (size_t)stride + i] = 1.0;
+  }
+}
+
+int launch_fill_default_fields(double* d_stage, int n, int stride, void* stream) {
+  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  if (blocks <= 0) return 0;
+  fill_default_fields_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_stage, n, stride);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
+}
+
+// Checks of the staged inputs of lbve_set_geometry, by integer tests of the
+// float64 bit patterns: every force component and initial field finite (the
+// exponent field is not all ones), every initial density in (0, +inf).  Sets
+// bit `bit` of *flag when one fails.
+__global__ void check_inputs_kernel(const double* __restrict__ force, const double* __restrict__ init,
+                                    int n, int stride, int32_t* __restrict__ flag, int bit) {
+  bool bad = false;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (force)
+      for (int c = 0; c < 2; ++c) {
+        const unsigned long long b = __double_as_longlong(force[(size_t)c * stride + i]);
+        bad |= ((b >> 52) & 0x7ffull) == 0x7ffull;
+      }
+    if (init) {
+      for (int c = 0; c < 6; ++c) {
+        const unsigned long long b = __double_as_longlong(init[(size_t)c * stride + i]);
+        bad |= ((b >> 52) & 0x7ffull) == 0x7ffull;
+      }
+      const long long r = __double_as_longlong(init[i]);
+      bad |= !(r > 0 && r < 0x7ff0000000000000ll);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1 << bit);
+}
+
+int launch_check_inputs(const double* d_force, const double* d_init, int n, int stride,
+                        int32_t* d_flag, int bit, void* stream) {
+  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  if (blocks <= 0 || (!d_force && !d_init)) return 0;
+  check_inputs_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_force, d_init, n, stride, d_flag,
+                                                               bit);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
+}
+
 template <typename R>
 __global__ void convert_force_kernel(const double* __restrict__ src, R* __restrict__ dst, int n,
                                      int stride) {

@@ -98,36 +98,50 @@ __device__ __forceinline__ void cde_moments(const R d[9], CdeM<R>& m) {
 // Rebuild the nine (deviation) populations from Hermite coefficients:
 //   d_i = w_i [ b0' + 3 e.b + 4.5 (H_xx bxx + 2 H_xy bxy + H_yy byy)
 //               + 13.5 (H_xxy bxxy + H_xyy bxyy) ]
-// with b0' the zeroth coefficient minus the rest value.  In float32 the rest
-// population is taken as b0' minus the other eight, which equals its formula
-// in exact arithmetic and keeps sum_i d_i = b0' up to unbiased rounding.
-// Evaluated from the formula, the rounded weights would scale the zeroth
-// moment by sum_i fl(w_i) = 1 + 7.5e-9 at every collision; that bias
-// accumulates over a conformation lattice's relaxation time (lambda steps)
-// into an error proportional to Wi.  In float64 the same bias is ~1e-17 and
-// the formula is kept (the float64 step is bound by the FP64 pipe).
+// with b0' the zeroth coefficient minus the rest value.
+// Float32: the products with the weights are correctly rounded, w v =
+// fmaf(v, w, v w_lo) with w + w_lo = 1/9 or 1/36 to 2^-48: multiplying by
+// the rounded weights alone scales every moment the weights carry by
+// sum_i fl(w_i) e_i e_i... = 1 + 7e-9 at every collision, a bias that the
+// momentum (and the slowly relaxing conformation moments) accumulate over
+// their relaxation times.  The rest population is taken as b0' minus the
+// other eight, which equals its formula in exact arithmetic and keeps
+// sum_i d_i = b0' up to unbiased rounding.  Float64 keeps the plain formula:
+// its weight bias is ~1e-17, and the float64 step is bound by the FP64 pipe.
+template <typename R>
+__device__ __forceinline__ R wmul(R v, R w, R wlo) {
+  if constexpr (sizeof(R) == 4)
+    return fmaf(v, w, v * wlo);
+  else
+    return w * v;
+}
+
 template <typename R>
 __device__ __forceinline__ void reconstruct(R b0p, R bx, R by, R bxx, R byy, R bxy, R bxxy,
                                             R bxyy, R out[9]) {
   const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+  // low parts of 1/9 and 1/36 below their float32 roundings
+  constexpr float kW1lo = (float)(1.0 / 9.0 - (double)(float)(1.0 / 9.0));
+  constexpr float kW5lo = (float)(1.0 / 36.0 - (double)(float)(1.0 / 36.0));
+  const R w1lo = R(kW1lo), w5lo = R(kW5lo);
   const R s = bxx + byy;
   if constexpr (sizeof(R) == 8) out[0] = w0 * (b0p - R(1.5) * s);
   const R b13 = b0p + R(3.0) * bxx - R(1.5) * byy;
   const R o13 = R(3.0) * bx - R(4.5) * bxyy;
-  out[1] = w1 * (b13 + o13);
-  out[3] = w1 * (b13 - o13);
+  out[1] = wmul<R>(b13 + o13, w1, w1lo);
+  out[3] = wmul<R>(b13 - o13, w1, w1lo);
   const R b24 = b0p - R(1.5) * bxx + R(3.0) * byy;
   const R o24 = R(3.0) * by - R(4.5) * bxxy;
-  out[2] = w1 * (b24 + o24);
-  out[4] = w1 * (b24 - o24);
+  out[2] = wmul<R>(b24 + o24, w1, w1lo);
+  out[4] = wmul<R>(b24 - o24, w1, w1lo);
   const R bd = b0p + R(3.0) * s;
   const R xy9 = R(9.0) * bxy;
   const R o57 = R(3.0) * (bx + by) + R(9.0) * (bxxy + bxyy);
   const R o68 = R(3.0) * (by - bx) + R(9.0) * (bxxy - bxyy);
-  out[5] = w5 * ((bd + xy9) + o57);
-  out[7] = w5 * ((bd + xy9) - o57);
-  out[6] = w5 * ((bd - xy9) + o68);
-  out[8] = w5 * ((bd - xy9) - o68);
+  out[5] = wmul<R>((bd + xy9) + o57, w5, w5lo);
+  out[7] = wmul<R>((bd + xy9) - o57, w5, w5lo);
+  out[6] = wmul<R>((bd - xy9) + o68, w5, w5lo);
+  out[8] = wmul<R>((bd - xy9) - o68, w5, w5lo);
   if constexpr (sizeof(R) == 4)
     out[0] = b0p - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
 }

@@ -289,3 +289,38 @@ def test_strip_mode_drift(lbve, case):
     for i, o in enumerate(orcs):
         err = parity_errors(sim32.fields(i), o.fields())
         assert err["u"] <= FP32_TOL and err["C"] <= FP32_TOL, (case, i, err)
+
+
+def test_set_geometry_rejects_bad_values(lbve):
+    """The force and initial-field values are checked on the device after
+    the upload: a NaN force, an infinite initial field or a density <= 0 is
+    LBVE_ERR_ARG and leaves the instance uninitialised (stepping is then
+    LBVE_ERR_STATE, flag bit 1 set) until a valid call sets it again; the
+    other instance of the batch is untouched."""
+    insts = [wl.frm(16, Wi=1.0, Re=1.0, Ma=0.1), wl.channel(8, nx=3, Wi=2.0)]
+    sim = lbve.Simulation(insts)
+    sim.step(5)
+    keep = sim.fields(1)
+    n = insts[0].n_nodes
+    bad_force = np.zeros((2, 16, 16))
+    bad_force[1, 3, 7] = np.nan
+    bad_init = wl.random_fields(16, 16, seed=2)
+    bad_init[4, 0, 0] = np.inf
+    bad_rho = wl.random_fields(16, 16, seed=2)
+    bad_rho[0, 5, 5] = 0.0
+    for force, init in ((bad_force, None), (None, bad_init), (None, bad_rho)):
+        with pytest.raises(lbve.LbveError) as e:
+            lbve.lbve_set_geometry(sim.h, 0, None, force, init, n_nodes=n)
+        assert e.value.code == lbve.LBVE_ERR_ARG
+        with pytest.raises(lbve.LbveError) as e:
+            sim.step(1)
+        assert e.value.code == lbve.LBVE_ERR_STATE
+        assert sim.status()[0] & 2
+    lbve.lbve_set_geometry(sim.h, 0, None, None, wl.random_fields(16, 16, seed=3), n_nodes=n)
+    assert sim.status()[0] == 0
+    sim.step(1)
+    np.testing.assert_array_equal(sim.time(1), 6)
+    o = oracle_sim(insts[1])
+    o.step(6)
+    assert_fp64_parity(sim.fields(1), o.fields())
+    assert not np.array_equal(keep, sim.fields(1))
