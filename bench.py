@@ -444,21 +444,25 @@ def run_ours(args):
     h2d = sum(t.numel() * 8 for t in pinned_init) + sum(
         t.numel() * 8 for t in pinned_force if t is not None)
     d2h = sum(t.numel() * 8 for t in pinned_out)
+    def e2e_pass():
+        t0 = time.perf_counter()
+        for j, inst in enumerate(insts):
+            lbve.lbve_set_geometry(sim.h, j, None,
+                                   None if pinned_force[j] is None else pinned_force[j].numpy(),
+                                   pinned_init[j].numpy(), n_nodes=inst.n_nodes)
+        t1 = time.perf_counter()
+        sim.step(K)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        for j in range(len(insts)):
+            lbve.lbve_fields(sim.h, j, pinned_out[j].data_ptr(), False)
+        torch.cuda.synchronize()
+        return t0, t1, t2, time.perf_counter()
+
+    e2e_pass()  # warm-up: the first touches of the pinned buffers are not timed
     torch.cuda.synchronize()
     barrier()
-    t0 = time.perf_counter()
-    for j, inst in enumerate(insts):
-        lbve.lbve_set_geometry(sim.h, j, None,
-                               None if pinned_force[j] is None else pinned_force[j].numpy(),
-                               pinned_init[j].numpy(), n_nodes=inst.n_nodes)
-    t1 = time.perf_counter()
-    sim.step(K)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    for j in range(len(insts)):
-        lbve.lbve_fields(sim.h, j, pinned_out[j].data_ptr(), False)
-    torch.cuda.synchronize()
-    t3 = time.perf_counter()
+    t0, t1, t2, t3 = e2e_pass()
     e2e_s = max_over_ranks(t3 - t0)
     e2e_value = job_value(job_nodes, K, e2e_s)
     e2e_parts = {"upload_and_init": t1 - t0, "steps": t2 - t1, "download": t3 - t2}
@@ -493,8 +497,9 @@ def run_ours(args):
     flags64 = sim64.status()
     bins = {"1-10": (1.0, 10.0), "10-100": (10.0, 100.0), "100-1e3": (100.0, 1e3),
             "1e3-1e4": (1e3, 1e4 + 1)}
-    per_bin = {k: {"u": 0.0, "C": 0.0, "instances": 0} for k in bins}
-    per_kind = {k: {"u": 0.0, "C": 0.0, "instances": 0} for k in ("channel", "frm")}
+    per_bin = {k: {"u": 0.0, "C": 0.0, "instances": 0, "within_1e-5": 0} for k in bins}
+    per_kind = {k: {"u": 0.0, "C": 0.0, "instances": 0, "within_1e-5": 0}
+                for k in ("channel", "frm")}
     err_all, err_le100 = 0.0, 0.0
     for j, inst in enumerate(insts):
         if flags64[j]:
@@ -513,11 +518,13 @@ def run_ours(args):
                 b_["u"] = max(b_["u"], eu)
                 b_["C"] = max(b_["C"], eC)
                 b_["instances"] += 1
+                b_["within_1e-5"] += int(e <= 1e-5)
         if inst.kind in per_kind:
             b_ = per_kind[inst.kind]
             b_["u"] = max(b_["u"], eu)
             b_["C"] = max(b_["C"], eC)
             b_["instances"] += 1
+            b_["within_1e-5"] += int(e <= 1e-5)
     err_all = max_over_ranks(err_all)
     err_le100 = max_over_ranks(err_le100)
 

@@ -53,7 +53,9 @@ extern "C" {
 #define LBVE_ERR_ARG (-1)       /* invalid argument or parameter            */
 #define LBVE_ERR_CUDA (-2)      /* a CUDA runtime call or launch failed     */
 #define LBVE_ERR_NONFINITE (-3) /* a field became NaN or Inf                */
-#define LBVE_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up       */
+#define LBVE_ERR_TIMEOUT (-4)   /* reserved for a bounded device-side wait;
+                                   no entry point waits on the device, so
+                                   none returns it                          */
 #define LBVE_ERR_GEOMETRY (-5)  /* geometry not supported / inconsistent    */
 #define LBVE_ERR_WORKSPACE (-6) /* workspace missing, too small, misaligned */
 #define LBVE_ERR_STATE (-7)     /* call out of order (e.g. step before init)*/

@@ -492,7 +492,8 @@ __device__ __forceinline__ void collide_cde(const InstDev& D, int k, int S, R* _
 // warp, so the final step keeps them few.
 template <typename R, int MODE>
 __device__ __forceinline__ void final_node(const InstDev& D, int k, int S, int lattice, R drho,
-                                           R rho, R ux, R uy, const R* dphi, double* part) {
+                                           R rho, R ux, R uy, const R* dphi, double* part,
+                                           double* plo) {
   double* fl = D.fields;
   bool finite = true;
   if (lattice <= 0) {
@@ -512,8 +513,17 @@ __device__ __forceinline__ void final_node(const InstDev& D, int k, int S, int l
     fl[S + k] = vx;
     fl[2 * S + k] = vy;
     part[kSumRho] = dr;
-    part[kSumJx] = to_f64(rho) * vx;
-    part[kSumJy] = to_f64(rho) * vy;
+    if constexpr (sizeof(R) == 4) {
+      // rho u exactly, as a float32 pair (product and its rounding error)
+      const float px = rho * ux, py = rho * uy;
+      part[kSumJx] = to_f64(px);
+      part[kSumJy] = to_f64(py);
+      plo[kSumJx] = to_f64(fmaf(rho, ux, -px));
+      plo[kSumJy] = to_f64(fmaf(rho, uy, -py));
+    } else {
+      part[kSumJx] = to_f64(rho) * vx;
+      part[kSumJy] = to_f64(rho) * vy;
+    }
     finite = isfinite(dr) && isfinite(vx) && isfinite(vy);
     part[kResid] = res;
   }
@@ -542,7 +552,7 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
                                              const CdeM<R>* cm, R rho, R ux, R uy, R G00, R G01,
                                              R G10, R G11, R dPx, R dPy, R dRx, R dRy, R Fx,
                                              R Fy, R So0, R So1, R So2, R uxo, R uyo,
-                                             double* part) {
+                                             double* part, double* plo) {
   // conformation tensor, constitutive function, polymer stress (eq_kramer),
   // source Phi_ab
   R Axx, Axy, Ayy, Fxx, Fxy, Fyy;
@@ -575,7 +585,7 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
 
   if (FINAL) {
     const R dphi[3] = {cm[0].dphi, cm[1].dphi, cm[2].dphi};
-    final_node<R, MODE>(D, k, S, -1, hm.drho, rho, ux, uy, dphi, part);
+    final_node<R, MODE>(D, k, S, -1, hm.drho, rho, ux, uy, dphi, part, plo);
   }
 }
 
@@ -696,28 +706,76 @@ __device__ __forceinline__ void region_rho_u(const InstDev& D, const void* src,
   node_rho_u<R, MODE>(src, force, ffield, Fx0, Fy0, S, nx, ny, py, gx, gy, rho, ux, uy);
 }
 
+// Sum of two float32 pairs (hi + lo), renormalised (Knuth's two-sum of the
+// high parts, the low parts added to its error, a fast two-sum at the end).
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  const float s = ah + bh, bv = s - ah;
+  const float e = ((ah - (s - bv)) + (bh - bv)) + (al + bl);
+  ah = s + e;
+  al = e - (ah - s);
+}
+
+// One butterfly level (fold_half) on float32 pairs.
+template <int M>
+__device__ __forceinline__ void fold_half_df(float* h, float* l, int o, bool up) {
+#pragma unroll
+  for (int j = 0; j < M / 2; ++j) {
+    const float kh = up ? h[j + M / 2] : h[j], kl = up ? l[j + M / 2] : l[j];
+    const float sh = up ? h[j] : h[j + M / 2], sl = up ? l[j] : l[j + M / 2];
+    const float rh = __shfl_xor_sync(0xffffffffu, sh, o), rl = __shfl_xor_sync(0xffffffffu, sl, o);
+    h[j] = kh;
+    l[j] = kl;
+    df_add(h[j], l[j], rh, rl);
+  }
+}
+
 // The tile's partial record of the final step in a fixed order: the 12
 // sums by a transposed butterfly per warp, the residual (>= 0 and finite, so
 // the order of its bit patterns is its numeric order) and the non-finite
 // count as integers, then the warps in order and the rest values from the
-// count of the tile's fluid nodes.  Every thread of the CTA calls it.
-template <int NT>
+// count of the tile's fluid nodes.  Every thread of the CTA calls it.  A
+// float32 instance's values are float32 numbers or exact float32 pairs
+// (part + plo), and its butterfly adds float32 pairs (a 48-bit sum; GB300
+// issues a float64 addition only every 64 cycles per warp); the warp totals
+// and everything after them are float64.
+template <int NT, bool PAIRS>
 __device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T,
-                                              const double* part, bool active,
+                                              const double* part, const double* plo, bool active,
                                               double* __restrict__ partials,
                                               double (*s_red)[kPartial]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   static_assert(kNonFinite == 13 && kResid == 12, "12 sums, then residual and flag");
-  double v[16];
+  double total;  // this lane's warp total of value slot
+  if constexpr (PAIRS) {
+    float h[16], l[16];
 #pragma unroll
-  for (int j = 0; j < 12; ++j) v[j] = part[j];
+    for (int j = 0; j < 12; ++j) {
+      h[j] = (float)part[j];  // exact: float32 values
+      l[j] = (float)plo[j];
+    }
 #pragma unroll
-  for (int j = 12; j < 16; ++j) v[j] = 0.0;
-  fold_half<16>(v, 16, (lane & 16) != 0);
-  fold_half<8>(v, 8, (lane & 8) != 0);
-  fold_half<4>(v, 4, (lane & 4) != 0);
-  fold_half<2>(v, 2, (lane & 2) != 0);
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    for (int j = 12; j < 16; ++j) h[j] = l[j] = 0.f;
+    fold_half_df<16>(h, l, 16, (lane & 16) != 0);
+    fold_half_df<8>(h, l, 8, (lane & 8) != 0);
+    fold_half_df<4>(h, l, 4, (lane & 4) != 0);
+    fold_half_df<2>(h, l, 2, (lane & 2) != 0);
+    const float rh = __shfl_xor_sync(0xffffffffu, h[0], 1);
+    const float rl = __shfl_xor_sync(0xffffffffu, l[0], 1);
+    df_add(h[0], l[0], rh, rl);
+    total = f2d_exact(h[0]) + f2d_exact(l[0]);
+  } else {
+    double v[16];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) v[j] = part[j];
+#pragma unroll
+    for (int j = 12; j < 16; ++j) v[j] = 0.0;
+    fold_half<16>(v, 16, (lane & 16) != 0);
+    fold_half<8>(v, 8, (lane & 8) != 0);
+    fold_half<4>(v, 4, (lane & 4) != 0);
+    fold_half<2>(v, 2, (lane & 2) != 0);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    total = v[0];
+  }
   long long rb = __double_as_longlong(part[kResid]);
   unsigned nf = __double_as_longlong(part[kNonFinite]) != 0 ? 1u : 0u;  // 0.0 or 1.0
 #pragma unroll
@@ -727,7 +785,7 @@ __device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T
     nf += __shfl_xor_sync(0xffffffffu, nf, o);
   }
   const int slot = (lane >> 1) & 15;
-  if ((lane & 1) == 0 && slot < 12) s_red[warp][slot] = v[0];
+  if ((lane & 1) == 0 && slot < 12) s_red[warp][slot] = total;
   if (lane == 0) {
     s_red[warp][kResid] = __longlong_as_double(rb);
     s_red[warp][kNonFinite] = (double)nf;
@@ -943,9 +1001,11 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   __syncthreads();
 
   // ---- phase B: gradients, source, collisions, stores ----------------------
-  double part[FINAL ? 14 : 1];
+  double part[FINAL ? 14 : 1], plo[FINAL ? 12 : 1];
 #pragma unroll
   for (int j = 0; j < (FINAL ? 14 : 1); ++j) part[j] = 0.0;
+#pragma unroll
+  for (int j = 0; j < (FINAL ? 12 : 1); ++j) plo[j] = 0.0;
 
   if (active) {
     // gradients: grad[g][b] = d_g u_b  (G00 = dx ux, G01 = dx uy, G10 = dy ux, G11 = dy uy)
@@ -1023,10 +1083,19 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     if (FINAL) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) part[kWallIn + j] = wall_io[j];
+      if (sizeof(R) == 4 && wcomp) {
+        // float32 pairs of the (float64) wall balances of a wall node
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const float hi = (float)wall_io[j];
+          part[kWallIn + j] = f2d_exact(hi);
+          plo[kWallIn + j] = f2d_exact((float)(wall_io[j] - f2d_exact(hi)));
+        }
+      }
     }
     collide_node<R, MODE, FINAL, MASKED>(D, k, S, dst, hist, hm, cm, rho, ux, uy, G00, G01, G10,
-                                         G11,
-                                 dPx, dPy, dRx, dRy, Fx, Fy, So[0], So[1], So[2], uxo, uyo, part);
+                                         G11, dPx, dPy, dRx, dRy, Fx, Fy, So[0], So[1], So[2], uxo,
+                                         uyo, part, plo);
   } else if (FINAL && solid) {
     // a solid node reports zero fields and adds nothing to the totals
     const int ks = y * nx + x;
@@ -1034,7 +1103,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     for (int j = 0; j < 6; ++j) D.fields[(size_t)j * S + ks] = 0.0;
   }
 
-  if (FINAL) tile_partials<NT>(D, T, part, active, partials, s_red);
+  if (FINAL) tile_partials<NT, sizeof(R) == 4>(D, T, part, plo, active, partials, s_red);
 }
 
 // One CTA of NT threads per tile (NT a multiple of 32, at least 32, with
@@ -1221,9 +1290,11 @@ __device__ __forceinline__ void process_tile_split(const InstDev* __restrict__ i
   __syncthreads();
 
   // ---- phase B: gradients, source, this warp's collision, stores ---------------
-  double part[FINAL ? 14 : 1];
+  double part[FINAL ? 14 : 1], plo[FINAL ? 12 : 1];
 #pragma unroll
   for (int j = 0; j < (FINAL ? 14 : 1); ++j) part[j] = 0.0;
+#pragma unroll
+  for (int j = 0; j < (FINAL ? 12 : 1); ++j) plo[j] = 0.0;
   if (active) {
     const R half = R(0.5);
     const R G00 = half * (s_ux[ri + 1] - s_ux[ri - 1]);
@@ -1245,7 +1316,7 @@ __device__ __forceinline__ void process_tile_split(const InstDev* __restrict__ i
       collide_hydro<R>(D, k, S, dst, hm, rho, ux, uy, dPx, dPy, txx, txy, tyy, Fx, Fy);
       hist[3 * S + k] = ux;
       hist[4 * S + k] = uy;
-      if (FINAL) final_node<R, MODE>(D, k, S, 0, hm.drho, rho, ux, uy, nullptr, part);
+      if (FINAL) final_node<R, MODE>(D, k, S, 0, hm.drho, rho, ux, uy, nullptr, part, plo);
     } else {
       const R il = coef<R>(D, kCoefInvLam);
       const R sl = source_component<R>(l, Axx, Axy, Ayy, Fxx, Fxy, Fyy, il, G00, G01, G10, G11);
@@ -1254,13 +1325,14 @@ __device__ __forceinline__ void process_tile_split(const InstDev* __restrict__ i
       hist[(size_t)l * S + k] = sl;
       if (FINAL) {
         const R dphi[3] = {s_phi[0][lane], s_phi[1][lane], s_phi[2][lane]};
-        final_node<R, MODE>(D, k, S, role, R(0), rho, ux, uy, dphi, part);
+        final_node<R, MODE>(D, k, S, role, R(0), rho, ux, uy, dphi, part, plo);
         part[kWallIn + l] = wall_in;
         part[kWallOut + l] = wall_out;
       }
     }
   }
-  if (FINAL) tile_partials<kSplitThreads>(D, T, part, active && role == 0, partials, s_red);
+  if (FINAL)
+    tile_partials<kSplitThreads, false>(D, T, part, plo, active && role == 0, partials, s_red);
 }
 
 template <bool FINAL>
