@@ -28,6 +28,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lbve_internal.h"
 
 #ifndef LBVE_FP32_MIN_BLOCKS
@@ -490,53 +492,59 @@ __device__ __forceinline__ void collide_cde(const InstDev& D, int k, int S, R* _
 // (added per tile from its node count) and the residual is scaled by 1/U_c
 // per tile: GB300 issues a float64 instruction only every 64 cycles per
 // warp, so the final step keeps them few.
+// Type of the per-node contributions to a tile's partial record: float32
+// instances keep float32 values (and exact float32 pairs) until the warp
+// totals, float64 instances float64 values.
+template <typename R>
+using PartT = typename std::conditional<sizeof(R) == 4, float, double>::type;
+
 template <typename R, int MODE>
 __device__ __forceinline__ void final_node(const InstDev& D, int k, int S, int lattice, R drho,
-                                           R rho, R ux, R uy, const R* dphi, double* part,
-                                           double* plo) {
+                                           R rho, R ux, R uy, const R* dphi, PartT<R>* part,
+                                           PartT<R>* plo) {
   double* fl = D.fields;
   bool finite = true;
   if (lattice <= 0) {
     const double dr = to_f64(drho);
     const double vx = to_f64(ux), vy = to_f64(uy);
-    // residual against the fields of the previous final step (none at init);
-    // a float32 instance's previous fields are float32 values, so its
-    // differences are taken in float32
-    double res = 0.0;
-    if (MODE == kModeStep) {
-      if constexpr (sizeof(R) == 4)
-        res = to_f64(fmaxf(fabsf(ux - (float)fl[S + k]), fabsf(uy - (float)fl[2 * S + k])));
-      else
-        res = fmax(fabs(vx - fl[S + k]), fabs(vy - fl[2 * S + k]));
-    }
     fl[k] = 1.0 + dr;
     fl[S + k] = vx;
     fl[2 * S + k] = vy;
-    part[kSumRho] = dr;
     if constexpr (sizeof(R) == 4) {
+      // residual against the fields of the previous final step (none at
+      // init), in float32: the previous fields are float32 values
+      const float res = (MODE == kModeStep)
+                            ? fmaxf(fabsf(ux - (float)fl[S + k]), fabsf(uy - (float)fl[2 * S + k]))
+                            : 0.f;
       // rho u exactly, as a float32 pair (product and its rounding error)
       const float px = rho * ux, py = rho * uy;
-      part[kSumJx] = to_f64(px);
-      part[kSumJy] = to_f64(py);
-      plo[kSumJx] = to_f64(fmaf(rho, ux, -px));
-      plo[kSumJy] = to_f64(fmaf(rho, uy, -py));
+      part[kSumRho] = drho;
+      part[kSumJx] = px;
+      part[kSumJy] = py;
+      plo[kSumJx] = fmaf(rho, ux, -px);
+      plo[kSumJy] = fmaf(rho, uy, -py);
+      part[kResid] = res;
+      finite = isfinite(drho) && isfinite(ux) && isfinite(uy);
     } else {
+      const double res =
+          (MODE == kModeStep) ? fmax(fabs(vx - fl[S + k]), fabs(vy - fl[2 * S + k])) : 0.0;
+      part[kSumRho] = dr;
       part[kSumJx] = to_f64(rho) * vx;
       part[kSumJy] = to_f64(rho) * vy;
+      part[kResid] = res;
+      finite = isfinite(dr) && isfinite(vx) && isfinite(vy);
     }
-    finite = isfinite(dr) && isfinite(vx) && isfinite(vy);
-    part[kResid] = res;
   }
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     if (lattice >= 0 && lattice != 1 + l) continue;
     const double d = to_f64(dphi[l]);
     fl[(3 + l) * S + k] = l == 1 ? d : 1.0 + d;
-    part[kSumPhi + l] = d;
-    finite = finite && isfinite(d);
+    part[kSumPhi + l] = dphi[l];
+    finite = finite && isfinite(dphi[l]);
   }
-  if (!finite) part[kResid] = 0.0;
-  part[kNonFinite] = finite ? 0.0 : 1.0;
+  if (!finite) part[kResid] = 0;
+  part[kNonFinite] = finite ? 0 : 1;
 }
 
 // Source, both collisions, stores and final-step bookkeeping of one node
@@ -552,7 +560,7 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
                                              const CdeM<R>* cm, R rho, R ux, R uy, R G00, R G01,
                                              R G10, R G11, R dPx, R dPy, R dRx, R dRy, R Fx,
                                              R Fy, R So0, R So1, R So2, R uxo, R uyo,
-                                             double* part, double* plo) {
+                                             PartT<R>* part, PartT<R>* plo) {
   // conformation tensor, constitutive function, polymer stress (eq_kramer),
   // source Phi_ab
   R Axx, Axy, Ayy, Fxx, Fxy, Fyy;
@@ -738,20 +746,21 @@ __device__ __forceinline__ void fold_half_df(float* h, float* l, int o, bool up)
 // (part + plo), and its butterfly adds float32 pairs (a 48-bit sum; GB300
 // issues a float64 addition only every 64 cycles per warp); the warp totals
 // and everything after them are float64.
-template <int NT, bool PAIRS>
-__device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T,
-                                              const double* part, const double* plo, bool active,
+template <int NT, typename P>
+__device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T, const P* part,
+                                              const P* plo, bool active,
                                               double* __restrict__ partials,
                                               double (*s_red)[kPartial]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   static_assert(kNonFinite == 13 && kResid == 12, "12 sums, then residual and flag");
   double total;  // this lane's warp total of value slot
-  if constexpr (PAIRS) {
+  double resid;  // the warp's largest residual
+  if constexpr (sizeof(P) == 4) {
     float h[16], l[16];
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
-      h[j] = (float)part[j];  // exact: float32 values
-      l[j] = (float)plo[j];
+      h[j] = part[j];
+      l[j] = plo[j];
     }
 #pragma unroll
     for (int j = 12; j < 16; ++j) h[j] = l[j] = 0.f;
@@ -763,6 +772,10 @@ __device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T
     const float rl = __shfl_xor_sync(0xffffffffu, l[0], 1);
     df_add(h[0], l[0], rh, rl);
     total = f2d_exact(h[0]) + f2d_exact(l[0]);
+    int rb = __float_as_int(part[kResid]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rb = max(rb, __shfl_xor_sync(0xffffffffu, rb, o));
+    resid = f2d_exact(__int_as_float(rb));
   } else {
     double v[16];
 #pragma unroll
@@ -775,19 +788,19 @@ __device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T
     fold_half<2>(v, 2, (lane & 2) != 0);
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
     total = v[0];
-  }
-  long long rb = __double_as_longlong(part[kResid]);
-  unsigned nf = __double_as_longlong(part[kNonFinite]) != 0 ? 1u : 0u;  // 0.0 or 1.0
+    long long rb = __double_as_longlong(part[kResid]);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long ob = __shfl_xor_sync(0xffffffffu, rb, o);
-    rb = ob > rb ? ob : rb;
-    nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ob = __shfl_xor_sync(0xffffffffu, rb, o);
+      rb = ob > rb ? ob : rb;
+    }
+    resid = __longlong_as_double(rb);
   }
+  const unsigned nf = __popc(__ballot_sync(0xffffffffu, part[kNonFinite] != P(0)));
   const int slot = (lane >> 1) & 15;
   if ((lane & 1) == 0 && slot < 12) s_red[warp][slot] = total;
   if (lane == 0) {
-    s_red[warp][kResid] = __longlong_as_double(rb);
+    s_red[warp][kResid] = resid;
     s_red[warp][kNonFinite] = (double)nf;
   }
   const int nfluid = __syncthreads_count(active);
@@ -1001,11 +1014,11 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
   __syncthreads();
 
   // ---- phase B: gradients, source, collisions, stores ----------------------
-  double part[FINAL ? 14 : 1], plo[FINAL ? 12 : 1];
+  PartT<R> part[FINAL ? 14 : 1], plo[FINAL ? 12 : 1];
 #pragma unroll
-  for (int j = 0; j < (FINAL ? 14 : 1); ++j) part[j] = 0.0;
+  for (int j = 0; j < (FINAL ? 14 : 1); ++j) part[j] = 0;
 #pragma unroll
-  for (int j = 0; j < (FINAL ? 12 : 1); ++j) plo[j] = 0.0;
+  for (int j = 0; j < (FINAL ? 12 : 1); ++j) plo[j] = 0;
 
   if (active) {
     // gradients: grad[g][b] = d_g u_b  (G00 = dx ux, G01 = dx uy, G10 = dy ux, G11 = dy uy)
@@ -1081,16 +1094,19 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
       }
     }
     if (FINAL) {
+      if constexpr (sizeof(R) == 4) {
+        if (wcomp) {
+          // float32 pairs of the (float64) wall balances of a wall node
 #pragma unroll
-      for (int j = 0; j < 6; ++j) part[kWallIn + j] = wall_io[j];
-      if (sizeof(R) == 4 && wcomp) {
-        // float32 pairs of the (float64) wall balances of a wall node
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          const float hi = (float)wall_io[j];
-          part[kWallIn + j] = f2d_exact(hi);
-          plo[kWallIn + j] = f2d_exact((float)(wall_io[j] - f2d_exact(hi)));
+          for (int j = 0; j < 6; ++j) {
+            const float hi = (float)wall_io[j];
+            part[kWallIn + j] = hi;
+            plo[kWallIn + j] = (float)(wall_io[j] - f2d_exact(hi));
+          }
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) part[kWallIn + j] = wall_io[j];
       }
     }
     collide_node<R, MODE, FINAL, MASKED>(D, k, S, dst, hist, hm, cm, rho, ux, uy, G00, G01, G10,
@@ -1103,7 +1119,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     for (int j = 0; j < 6; ++j) D.fields[(size_t)j * S + ks] = 0.0;
   }
 
-  if (FINAL) tile_partials<NT, sizeof(R) == 4>(D, T, part, plo, active, partials, s_red);
+  if (FINAL) tile_partials<NT, PartT<R>>(D, T, part, plo, active, partials, s_red);
 }
 
 // One CTA of NT threads per tile (NT a multiple of 32, at least 32, with
@@ -1290,11 +1306,11 @@ __device__ __forceinline__ void process_tile_split(const InstDev* __restrict__ i
   __syncthreads();
 
   // ---- phase B: gradients, source, this warp's collision, stores ---------------
-  double part[FINAL ? 14 : 1], plo[FINAL ? 12 : 1];
+  PartT<R> part[FINAL ? 14 : 1], plo[FINAL ? 12 : 1];
 #pragma unroll
-  for (int j = 0; j < (FINAL ? 14 : 1); ++j) part[j] = 0.0;
+  for (int j = 0; j < (FINAL ? 14 : 1); ++j) part[j] = 0;
 #pragma unroll
-  for (int j = 0; j < (FINAL ? 12 : 1); ++j) plo[j] = 0.0;
+  for (int j = 0; j < (FINAL ? 12 : 1); ++j) plo[j] = 0;
   if (active) {
     const R half = R(0.5);
     const R G00 = half * (s_ux[ri + 1] - s_ux[ri - 1]);
@@ -1332,7 +1348,7 @@ __device__ __forceinline__ void process_tile_split(const InstDev* __restrict__ i
     }
   }
   if (FINAL)
-    tile_partials<kSplitThreads, false>(D, T, part, plo, active && role == 0, partials, s_red);
+    tile_partials<kSplitThreads, double>(D, T, part, plo, active && role == 0, partials, s_red);
 }
 
 template <bool FINAL>

@@ -14,7 +14,8 @@ depend on details the paper does not state (we measure 0.887 against 0.883);
 0.015 at Wi = 10 (0.928 against 0.916) and 0.03 at Wi = 20 (0.933 against
 0.911): above Wi = 5 our values level off near 0.93 where the paper's fall
 slowly, a difference that grows with the strength of the singular stress
-layer."""
+layer.  At the stagnation point the conformation must also meet the
+steady asymptotics of eq_Aab_ana for Wi_eff < 1/2."""
 import math
 import os
 
@@ -72,6 +73,17 @@ def test_frm_effective_weissenberg_table(lbve):
                            - 0.5 * (f[2][c + 1, c] - f[2][c - 1, c])) / 2
         tol = {5.0: 0.006, 10.0: 0.015, 20.0: 0.03}.get(Wi, 0.001)
         assert abs(eps * Wi - table[Wi]) <= tol, (Wi, eps * Wi, table[Wi])
+        # eq_Aab_ana (Thomases and Shelley's steady asymptotics, Sec. 4.1) at
+        # the stagnation point itself: A_xx = 1/(1 - 2 Wi_eff), A_yy =
+        # 1/(1 + 2 Wi_eff), A_xy = 0, for Wi_eff < 1/2.  Measured: equal to
+        # 5 digits at Wi = 0.1; 2.2e-3 off at Wi = 0.5, where A_xx has a cusp
+        # |y - pi|^1.16 that the stress diffusion rounds off at the point.
+        if Wi <= 0.5:
+            We = eps * Wi
+            rtol = 1e-4 if Wi <= 0.1 else 5e-3
+            assert abs(f[3][c, c] * (1 - 2 * We) - 1) <= rtol, (Wi, f[3][c, c], 1 / (1 - 2 * We))
+            assert abs(f[5][c, c] * (1 + 2 * We) - 1) <= rtol, (Wi, f[5][c, c], 1 / (1 + 2 * We))
+            assert abs(f[4][c, c]) <= 1e-9 * f[3][c, c]
 
 
 CD_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cylinder_cd_table.txt")
