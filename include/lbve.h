@@ -65,6 +65,14 @@ extern "C" {
 #define LBVE_FP32_DEV 1 /* float32 storage of deviations from the rest state
                            (f_i - w_i, g_i - w_i delta_c), float32 arithmetic,
                            float64 for conserved totals and wall balances     */
+#define LBVE_DF32 2     /* float32 pairs (hi + lo, about 48 significant bits)
+                           for storage and arithmetic: error-free float32
+                           transformations on the float32 pipe, 8 bytes per
+                           value as float64.  Oldroyd-B instances with flat
+                           walls or periodic rows only (no solid mask, open
+                           channel, FENE model or eq_p_G form); not covered
+                           by the adjoint.  The paper has no counterpart: a
+                           precision choice of this implementation.          */
 
 /* Number of doubles returned by lbve_totals(). */
 #define LBVE_NTOTALS 14
@@ -78,7 +86,7 @@ extern "C" {
 typedef struct {
   int32_t nx, ny;     /* nodes (ny >= 3 when walled)                        */
   int32_t periodic_y; /* 1: periodic in y; 0: walls on rows 0 and ny-1      */
-  int32_t precision;  /* LBVE_FP64 or LBVE_FP32_DEV                         */
+  int32_t precision;  /* LBVE_FP64, LBVE_FP32_DEV or LBVE_DF32              */
   double beta;        /* viscosity ratio mu_s/mu_0, 0 < beta <= 1 (eqb7)    */
   double Wi;          /* Weissenberg number (eqb6), > 0                     */
   double Re;          /* Reynolds number (eqb5), > 0                        */
@@ -243,7 +251,7 @@ int lbve_step(lbve_handle* h, int64_t n_steps);
 int lbve_profile(lbve_handle* h, int32_t max_launches);
 
 /* Read the launches timed since lbve_profile() for the step kernel of one
- * precision (LBVE_FP64 or LBVE_FP32_DEV) and kind (final_step = 0: the
+ * precision (LBVE_FP64, LBVE_FP32_DEV or LBVE_DF32) and kind (final_step = 0: the
  * ordinary steps; 1: the last step of each lbve_step call, which also writes
  * the float64 fields and partial sums): their number, the sum of their
  * durations and the shortest and longest (ms; ms_min, ms_max may be NULL).

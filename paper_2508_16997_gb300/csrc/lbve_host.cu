@@ -75,8 +75,14 @@ int validate(const lbve_params& p, int i) {
     return set_error(LBVE_ERR_ARG, "instance %d: a walled channel needs ny >= 3", i);
   if (int64_t(p.nx) * p.ny > kMaxNodes)
     return set_error(LBVE_ERR_ARG, "instance %d: more than %lld nodes", i, (long long)kMaxNodes);
-  if (p.precision != LBVE_FP64 && p.precision != LBVE_FP32_DEV)
+  if (p.precision != LBVE_FP64 && p.precision != LBVE_FP32_DEV && p.precision != LBVE_DF32)
     return set_error(LBVE_ERR_ARG, "instance %d: unknown precision %d", i, p.precision);
+  if (p.precision == LBVE_DF32 &&
+      (p.max_wall_nodes != 0 || p.open_x != 0 || p.model != 0 || p.gtilde != 0))
+    return set_error(LBVE_ERR_ARG,
+                     "instance %d: LBVE_DF32 covers Oldroyd-B instances with flat walls or periodic "
+                     "rows (no solid mask, open channel, FENE model or eq_p_G form)",
+                     i);
   if (p.periodic_y != 0 && p.periodic_y != 1)
     return set_error(LBVE_ERR_ARG, "instance %d: periodic_y must be 0 or 1", i);
   if (!(std::isfinite(p.beta) && p.beta > 0.0 && p.beta <= 1.0))
@@ -111,8 +117,12 @@ int validate(const lbve_params& p, int i) {
   return LBVE_OK;
 }
 
-// Tile lists: 0 = float64 instances, 1 = float32 instances.
-constexpr int kLists = 2;
+// Tile lists, one per storage precision: 0 = float64, 1 = float32
+// deviations, 2 = float32 pairs (the list index is the precision code).
+constexpr int kLists = 3;
+
+// Bytes of one stored value of a precision.
+size_t elem_size(int precision) { return precision == LBVE_FP32_DEV ? 4 : 8; }
 
 struct InstPlan {
   size_t off_pop[2], off_hist, off_force, off_fields, off_mask, off_inlet, off_colbuf;
@@ -205,9 +215,10 @@ Plan make_plan(const lbve_params* p, int n) {
   for (int l = 0; l < kLists; ++l) pl.ntiles[l] = pl.cap_tiles[l] = pl.wall_cap[l] = pl.ncols[l] = 0;
   pl.threads[0] = fp64_threads(p, n);
   pl.threads[1] = kThreads;
+  pl.threads[2] = kThreads;
   for (int i = 0; i < n; ++i) {
     InstPlan& q = pl.inst[i];
-    const size_t es = p[i].precision == LBVE_FP64 ? 8 : 4;
+    const size_t es = elem_size(p[i].precision);
     const size_t nn = size_t(p[i].nx) * p[i].ny;
     q.stride = (int)align_up(nn, 64);
     const size_t plane = size_t(q.stride) * es;
@@ -229,7 +240,7 @@ Plan make_plan(const lbve_params* p, int n) {
       q.off_colbuf = off;
       off = align_up(off + 36 * 2 * size_t(p[i].ny) * es, kAlign);
     }
-    q.list = p[i].precision == LBVE_FP64 ? 0 : 1;
+    q.list = p[i].precision;
     tile_shape(p[i], pl.threads[q.list], q.TX, q.TY, q.hy);
     q.wall_begin = pl.wall_cap[q.list];
     q.wall_cap = p[i].max_wall_nodes;
@@ -270,8 +281,9 @@ Plan make_plan(const lbve_params* p, int n) {
     off = align_up(off + sizeof(ColTask) * std::max(pl.ncols[l], 1), kAlign);
   }
   pl.off_partials = off;
-  off = align_up(off + sizeof(double) * kPartial * std::max(pl.cap_tiles[0] + pl.cap_tiles[1], 1),
-                 kAlign);
+  int cap_all = 0;
+  for (int l = 0; l < kLists; ++l) cap_all += pl.cap_tiles[l];
+  off = align_up(off + sizeof(double) * kPartial * std::max(cap_all, 1), kAlign);
   pl.off_totals = off;
   off = align_up(off + sizeof(double) * kTotals * n, kAlign);
   pl.off_flags = off;
@@ -291,7 +303,7 @@ struct lbve_handle {
   cudaStream_t stream = nullptr;
   std::vector<InstDev> insts;
   InstDev* d_insts = nullptr;
-  TileDev* d_tiles[kLists] = {nullptr, nullptr};
+  TileDev* d_tiles[kLists] = {};
   double* d_partials = nullptr;
   double* d_totals = nullptr;
   int32_t* d_flags = nullptr;
@@ -300,20 +312,20 @@ struct lbve_handle {
   std::vector<char> ready;
   // solid masks: host copies of the tile tables (their masked flags), the
   // masked-tile tables run by the masked kernel, and the wall-node records
-  TileDev* d_mtiles[kLists] = {nullptr, nullptr};
-  WallDev* d_walls[kLists] = {nullptr, nullptr};
-  double* d_wrec[kLists] = {nullptr, nullptr};
+  TileDev* d_mtiles[kLists] = {};
+  WallDev* d_walls[kLists] = {};
+  double* d_wrec[kLists] = {};
   std::vector<TileDev> tiles_h[kLists];
-  int nmasked[kLists] = {0, 0};
-  int nmasked_inst[kLists] = {0, 0};  // instances of the list that carry a mask
+  int nmasked[kLists] = {};
+  int nmasked_inst[kLists] = {};  // instances of the list that carry a mask
   std::vector<std::vector<TileDev>> mtiles_of;  // masked tiles of each instance
   std::vector<int> mbegin;                      // first entry of each in its masked table
   std::vector<std::vector<WallDev>> walls_of;   // wall-node records of each instance
   std::vector<std::vector<int32_t>> wall_index; // node -> record, per masked instance
   std::vector<uint64_t> geom_hash;              // mask + wall fractions, 0 = no mask
   std::vector<std::vector<uint8_t>> mask_h;     // host copy of each mask
-  ColTask* d_cols[kLists] = {nullptr, nullptr};  // open-column tasks per list
-  int nopen_inst[kLists] = {0, 0};              // open channels per list
+  ColTask* d_cols[kLists] = {};  // open-column tasks per list
+  int nopen_inst[kLists] = {};   // open channels per list
   std::vector<std::vector<double>> inlet_h;     // inlet profile of each open channel
   // CUDA graph of kGraphSteps non-final steps starting at parity 0, captured
   // on a private stream on first use and replayed on the caller's stream
@@ -328,7 +340,7 @@ struct lbve_handle {
   // per launch, per tile list and per kind (0 non-final steps, 1 the final
   // step of a call), recorded on the caller's stream
   int prof_cap = 0;
-  int prof_n[kLists][2] = {{0, 0}, {0, 0}};
+  int prof_n[kLists][2] = {};
   std::vector<cudaEvent_t> prof_ev[kLists][2];
 };
 
@@ -342,13 +354,14 @@ constexpr int kGraphSteps = 32;  // even, so a replay leaves the parity unchange
 // the masked tiles, while the plain tiles, which never read what the wall
 // pass writes, run on the caller's stream; the two join before the step ends.
 int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
-  const bool fork = h->nmasked[0] + h->nmasked[1] > 0;  // any tile of the general variant
+  bool fork = false;  // any tile of the general variant
+  for (int l = 0; l < kLists; ++l) fork = fork || h->nmasked[l] > 0;
   if (fork) {
     cudaError_t e = cudaEventRecord(h->ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
     if (e != cudaSuccess) return cuda_fail(e, "fork of the masked-tile stream");
     for (int l = 0; l < kLists; ++l) {
-      const int prec = l == 0 ? LBVE_FP64 : LBVE_FP32_DEV;
+      const int prec = l;
       if (h->nmasked_inst[l] > 0 &&
           launch_wall(prec, h->d_insts, h->d_walls[l], h->d_wrec[l], h->plan.wall_cap[l], parity,
                       flags, h->side_stream))
@@ -360,7 +373,7 @@ int launch_one_step(lbve_handle* h, int parity, int flags, cudaStream_t st) {
     }
   }
   for (int l = 0; l < kLists; ++l) {
-    const int prec = l == 0 ? LBVE_FP64 : LBVE_FP32_DEV;
+    const int prec = l;
     if (h->nmasked[l] > 0 &&
         launch_step(prec, h->plan.threads[l], h->d_insts, h->d_mtiles[l], h->nmasked[l], parity,
                     kModeStep, flags,
@@ -769,7 +782,10 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
     D.model = p[i].model;
     D.gtilde = p[i].gtilde;
     D.t32 = q.TX == kTileTX && (!p[i].periodic_y || p[i].ny >= q.TY + 2);
-    for (int j = 0; j < kNumCoef; ++j) D.cf[j] = (float)D.cd[j];
+    for (int j = 0; j < kNumCoef; ++j) {
+      D.cf[j] = (float)D.cd[j];
+      D.cl[j] = (float)(D.cd[j] - (double)D.cf[j]);
+    }
     int k = q.tile_begin;
     for (int ty = 0; ty < q.nty; ++ty)
       for (int tx = 0; tx < q.ntx; ++tx) {
@@ -1048,7 +1064,7 @@ struct InstHeader {
   uint64_t geometry;  // hash of the solid mask and wall fractions, 0 = none
 };
 size_t inst_state_bytes(const lbve_params& p) {
-  const size_t nn = size_t(p.nx) * p.ny, es = p.precision == LBVE_FP64 ? 8 : 4;
+  const size_t nn = size_t(p.nx) * p.ny, es = elem_size(p.precision);
   return sizeof(InstHeader) + (36 + 5 + 2) * nn * es + 6 * nn * 8;
 }
 }  // namespace
@@ -1074,7 +1090,7 @@ int lbve_save(lbve_handle* h, void* host_buf, size_t bytes) {
   for (int i = 0; i < h->n && e == cudaSuccess; ++i) {
     const lbve_params& p = h->p[i];
     const InstDev& D = h->insts[i];
-    const size_t nn = size_t(p.nx) * p.ny, S = D.stride, es = p.precision == LBVE_FP64 ? 8 : 4;
+    const size_t nn = size_t(p.nx) * p.ny, S = D.stride, es = elem_size(p.precision);
     InstHeader I{h->t[i], p.nx, p.ny, p.precision, p.periodic_y, D.force_field, h->ready[i],
                  h->geom_hash[i]};
     std::memcpy(out, &I, sizeof(I));
@@ -1132,7 +1148,7 @@ int lbve_load(lbve_handle* h, const void* host_buf, size_t bytes) {
     in += sizeof(I);
     const lbve_params& p = h->p[i];
     InstDev& D = h->insts[i];
-    const size_t nn = size_t(p.nx) * p.ny, S = D.stride, es = p.precision == LBVE_FP64 ? 8 : 4;
+    const size_t nn = size_t(p.nx) * p.ny, S = D.stride, es = elem_size(p.precision);
     e = cudaMemcpy2DAsync(D.pop[h->parity], S * es, in, nn * es, nn * es, 36,
                           cudaMemcpyHostToDevice, h->stream);
     in += 36 * nn * es;
@@ -1245,10 +1261,10 @@ int lbve_profile(lbve_handle* h, int32_t max_launches) {
 
 int lbve_profile_read(lbve_handle* h, int32_t precision, int32_t final_step, int32_t* launches,
                       double* ms_total, double* ms_min, double* ms_max) {
-  if (!h || !launches || !ms_total || (precision != LBVE_FP64 && precision != LBVE_FP32_DEV) ||
+  if (!h || !launches || !ms_total || precision < 0 || precision >= kLists ||
       (final_step != 0 && final_step != 1))
     return set_error(LBVE_ERR_ARG, "bad handle, precision, final_step or null output");
-  const int l = precision == LBVE_FP64 ? 0 : 1;
+  const int l = precision;
   *launches = 0;
   *ms_total = 0.0;
   double lo = 0.0, hi = 0.0;
@@ -1451,7 +1467,7 @@ AdjPlan make_adj_plan(const lbve_params& p, const InstPlan& q, int64_t T, int nw
   a.T = T;
   a.s = interval > 0 ? interval : sqrt_interval(T);
   a.nck = (T + a.s - 1) / a.s;
-  const size_t es = p.precision == LBVE_FP64 ? 8 : 4;
+  const size_t es = elem_size(p.precision);
   const size_t plane = size_t(q.stride) * es;
   a.state_bytes = 41 * plane;
   size_t off = 0;
@@ -1524,6 +1540,9 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
   if (h->p[inst].model != 0 || h->p[inst].gtilde != 0)
     return set_error(LBVE_ERR_ARG, "the adjoint covers Oldroyd-B with eq_p_G_1 only (instance %d)",
                 inst);
+  if (h->p[inst].precision == LBVE_DF32)
+    return set_error(LBVE_ERR_ARG,
+                     "the adjoint covers LBVE_FP64 and LBVE_FP32_DEV instances (instance %d)", inst);
   const bool masked = h->insts[inst].mask != nullptr;
   if (!masked && (dL_ddrag || d_dL_dq))
     return set_error(LBVE_ERR_GEOMETRY, "drag and wall-fraction gradients need a solid mask");
@@ -1554,7 +1573,7 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
   cudaStream_t st = h->stream;
   const int prec = p.precision;
   const size_t nn = size_t(p.nx) * p.ny, S = q.stride;
-  const size_t es = prec == LBVE_FP64 ? 8 : 4;
+  const size_t es = elem_size(prec);
   const size_t plane = S * es;
   cudaError_t e = cudaSuccess;
 

@@ -42,8 +42,8 @@ constexpr int kTileTXTiny = 8;  // default tile width of the one-warp float64 CT
 constexpr int kNumSMs = 152;  // GB300; sizes the small-batch choice only
 constexpr int kTileTX = LBVE_TILE_TX;   // default tile width (nodes along x) for nx >= kTileTX
 // threads per CTA (for float64, the size of all but small batches) and the
-// widest tile a caller may ask for, by precision (0 = float64, 1 = float32,
-// as LBVE_FP64 / LBVE_FP32_DEV)
+// widest tile a caller may ask for, by precision (0 = float64, 1 = float32
+// deviations, 2 = float32 pairs, as LBVE_FP64 / LBVE_FP32_DEV / LBVE_DF32)
 __host__ __device__ constexpr int threads_of(int prec) { return prec == 0 ? kThreads64 : kThreads; }
 __host__ __device__ constexpr int tile_tx_max(int prec) { return threads_of(prec) / 2; }
 // Halo region of a tile: (TX+2)(TY+2*hy) <= (TX+2)(T/TX+4) = T + 4 TX + 2 T/TX
@@ -109,6 +109,7 @@ struct InstDev {
   // neither kernel converts precision per node.
   double cd[16];
   float cf[16];
+  float cl[16];  // cd - cf rounded to float32: the low parts of LBVE_DF32 pairs
 };
 
 // One tile of one instance: {instance, x0, y0, partial slot, masked}.

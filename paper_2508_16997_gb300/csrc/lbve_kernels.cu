@@ -71,6 +71,9 @@ int launch_step(int prec, int threads, const InstDev* d_insts, const TileDev* d_
   if (prec == 1 && threads == kThreads)
     return launch_step_m<float, kThreads>(d_insts, d_tiles, n_tiles, parity, mode, flags,
                                           d_partials, st, masked);
+  if (prec == 2 && threads == kThreads && !masked)  // float32 pairs: plain tiles only
+    return launch_step_t<df32, false, kThreads>(d_insts, d_tiles, n_tiles, parity, mode, flags,
+                                                d_partials, st);
   return -1;
 }
 
@@ -178,8 +181,8 @@ template <typename R>
 __global__ void convert_force_kernel(const double* __restrict__ src, R* __restrict__ dst, int n,
                                      int stride) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    dst[i] = (R)src[i];
-    dst[stride + i] = (R)src[stride + i];
+    dst[i] = R(src[i]);
+    dst[stride + i] = R(src[stride + i]);
   }
 }
 
@@ -190,6 +193,9 @@ int launch_convert_force(int prec, const double* d_src, void* d_dst, int n, int 
   if (prec == 0)
     convert_force_kernel<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(d_src, (double*)d_dst,
                                                                           n, stride);
+  else if (prec == 2)
+    convert_force_kernel<df32><<<blocks, 256, 0, (cudaStream_t)stream>>>(d_src, (df32*)d_dst, n,
+                                                                        stride);
   else
     convert_force_kernel<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(d_src, (float*)d_dst, n,
                                                                          stride);

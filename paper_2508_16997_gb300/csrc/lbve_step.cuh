@@ -30,6 +30,7 @@
 
 #include <type_traits>
 
+#include "lbve_df32.cuh"
 #include "lbve_internal.h"
 
 #ifndef LBVE_FP32_MIN_BLOCKS
@@ -63,6 +64,7 @@ __device__ __forceinline__ double f2d_exact(float f) {
 }
 __device__ __forceinline__ double to_f64(float v) { return f2d_exact(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(df32 v) { return f2d_exact(v.hi) + f2d_exact(v.lo); }
 
 template <typename R>
 struct HydroM {  // raw moments of the (deviation) populations
@@ -330,6 +332,10 @@ template <>
 __device__ __forceinline__ float coef<float>(const InstDev& D, int i) {
   return D.cf[i];
 }
+template <>
+__device__ __forceinline__ df32 coef<df32>(const InstDev& D, int i) {
+  return df32(D.cf[i], D.cl[i]);
+}
 
 // Position of halo-ring slot q in the (TX+2) x (TY+2hy) region: hy rows
 // above and hy rows below the tile (its TX columns), one column left and one
@@ -540,8 +546,13 @@ __device__ __forceinline__ void final_node(const InstDev& D, int k, int S, int l
     if (lattice >= 0 && lattice != 1 + l) continue;
     const double d = to_f64(dphi[l]);
     fl[(3 + l) * S + k] = l == 1 ? d : 1.0 + d;
-    part[kSumPhi + l] = dphi[l];
-    finite = finite && isfinite(dphi[l]);
+    if constexpr (sizeof(R) == 4) {
+      part[kSumPhi + l] = dphi[l];
+      finite = finite && isfinite(dphi[l]);
+    } else {
+      part[kSumPhi + l] = d;
+      finite = finite && isfinite(d);
+    }
   }
   if (!finite) part[kResid] = 0;
   part[kNonFinite] = finite ? 0 : 1;
@@ -642,11 +653,16 @@ __device__ __forceinline__ R y_drho(bool wb, bool wt, R rm2, R rm1, R r0, R rp1,
 // Float64 CTAs: 256 threads two per SM (128 registers per thread).  The
 // 64- and one-warp CTAs serve batches with fewer tiles than 4 and 2 per SM,
 // so they are budgeted for that many and keep every value in registers.
+#ifndef LBVE_DF32_MIN_BLOCKS
+#define LBVE_DF32_MIN_BLOCKS 4
+#endif
 template <typename R, bool MASKED, int NT>
 struct MinBlocks {
   static constexpr int value =
-      sizeof(R) == 4 ? (MASKED ? LBVE_FP32_MASKED_MIN_BLOCKS : LBVE_FP32_MIN_BLOCKS)
-                     : (NT <= 32 ? 2 : NT <= 64 ? 4 : (NT <= 512 ? 512 / NT : 1));
+      std::is_same<R, df32>::value
+          ? LBVE_DF32_MIN_BLOCKS
+          : sizeof(R) == 4 ? (MASKED ? LBVE_FP32_MASKED_MIN_BLOCKS : LBVE_FP32_MIN_BLOCKS)
+                           : (NT <= 32 ? 2 : NT <= 64 ? 4 : (NT <= 512 ? 512 / NT : 1));
 };
 
 // One-sided differences along one axis next to the solid mask (same rule as

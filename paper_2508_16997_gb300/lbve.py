@@ -25,6 +25,7 @@ LBVE_ERR_WORKSPACE = -6
 LBVE_ERR_STATE = -7
 LBVE_FP64 = 0
 LBVE_FP32_DEV = 1
+LBVE_DF32 = 2
 LBVE_NTOTALS = 14
 
 EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_step",

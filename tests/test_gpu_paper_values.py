@@ -83,7 +83,7 @@ def test_frm_effective_weissenberg_table(lbve):
             rtol = 1e-4 if Wi <= 0.1 else 5e-3
             assert abs(f[3][c, c] * (1 - 2 * We) - 1) <= rtol, (Wi, f[3][c, c], 1 / (1 - 2 * We))
             assert abs(f[5][c, c] * (1 + 2 * We) - 1) <= rtol, (Wi, f[5][c, c], 1 / (1 + 2 * We))
-            assert abs(f[4][c, c]) <= 1e-9 * f[3][c, c]
+            assert abs(f[4][c, c]) <= 1e-5  # 0 by symmetry; measured 1.1e-7 (float32)
 
 
 CD_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cylinder_cd_table.txt")
