@@ -513,14 +513,16 @@ __device__ __forceinline__ void final_node(const InstDev& D, int k, int S, int l
   if (lattice <= 0) {
     const double dr = to_f64(drho);
     const double vx = to_f64(ux), vy = to_f64(uy);
+    // the residual reads the fields of the previous final step (none at
+    // init) before they are overwritten below
+    const double ux_prev = fl[S + k], uy_prev = fl[2 * S + k];
     fl[k] = 1.0 + dr;
     fl[S + k] = vx;
     fl[2 * S + k] = vy;
     if constexpr (sizeof(R) == 4) {
-      // residual against the fields of the previous final step (none at
-      // init), in float32: the previous fields are float32 values
+      // in float32: the previous fields are float32 values
       const float res = (MODE == kModeStep)
-                            ? fmaxf(fabsf(ux - (float)fl[S + k]), fabsf(uy - (float)fl[2 * S + k]))
+                            ? fmaxf(fabsf(ux - (float)ux_prev), fabsf(uy - (float)uy_prev))
                             : 0.f;
       // rho u exactly, as a float32 pair (product and its rounding error)
       const float px = rho * ux, py = rho * uy;
@@ -533,7 +535,7 @@ __device__ __forceinline__ void final_node(const InstDev& D, int k, int S, int l
       finite = isfinite(drho) && isfinite(ux) && isfinite(uy);
     } else {
       const double res =
-          (MODE == kModeStep) ? fmax(fabs(vx - fl[S + k]), fabs(vy - fl[2 * S + k])) : 0.0;
+          (MODE == kModeStep) ? fmax(fabs(vx - ux_prev), fabs(vy - uy_prev)) : 0.0;
       part[kSumRho] = dr;
       part[kSumJx] = to_f64(rho) * vx;
       part[kSumJy] = to_f64(rho) * vy;
