@@ -425,11 +425,11 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
 
     # ---- end to end through the C ABI with host buffers --------------------
-    # One call of the public API per instance uploads its state (pinned host
+    # lbve_set_geometry_many uploads every instance's state (pinned host
     # force field and initial fields) and initialises it, lbve_step(K)
-    # advances the batch, lbve_fields copies every instance's fields back to
-    # pinned host memory.  The upload happens once per K steps: bytes are
-    # stated per call and per step (per call / K).
+    # advances the batch, lbve_fields_many copies every instance's fields
+    # back to pinned host memory.  The upload happens once per K steps: bytes
+    # are stated per call and per step (per call / K).
     pinned_force = [None if i.force_field is None else
                     torch.from_numpy(np.ascontiguousarray(i.force_field)).pin_memory()
                     for i in insts]
@@ -444,18 +444,20 @@ def run_ours(args):
     h2d = sum(t.numel() * 8 for t in pinned_init) + sum(
         t.numel() * 8 for t in pinned_force if t is not None)
     d2h = sum(t.numel() * 8 for t in pinned_out)
+    ids = list(range(len(insts)))
+    force_np = [None if t is None else t.numpy() for t in pinned_force]
+    init_np = [t.numpy() for t in pinned_init]
+    out_ptrs = [t.data_ptr() for t in pinned_out]
+    n_nodes = [i.n_nodes for i in insts]
+
     def e2e_pass():
         t0 = time.perf_counter()
-        for j, inst in enumerate(insts):
-            lbve.lbve_set_geometry(sim.h, j, None,
-                                   None if pinned_force[j] is None else pinned_force[j].numpy(),
-                                   pinned_init[j].numpy(), n_nodes=inst.n_nodes)
+        lbve.lbve_set_geometry_many(sim.h, ids, None, force_np, init_np, n_nodes=n_nodes)
         t1 = time.perf_counter()
         sim.step(K)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        for j in range(len(insts)):
-            lbve.lbve_fields(sim.h, j, pinned_out[j].data_ptr(), False)
+        lbve.lbve_fields_many(sim.h, ids, out_ptrs, False)
         torch.cuda.synchronize()
         return t0, t1, t2, time.perf_counter()
 
@@ -664,9 +666,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h / K, "h2d_bytes_per_call": h2d,
                 "d2h_bytes_per_call": d2h, "steps_per_call": K,
                 "seconds": e2e_parts,
-                "region": "once per K steps: lbve_set_geometry (pinned host force + initial "
-                          "fields) for every instance, lbve_step(K), lbve_fields of every "
-                          "instance to pinned host"},
+                "region": "once per K steps: lbve_set_geometry_many (pinned host force + "
+                          "initial fields of every instance, one synchronisation), "
+                          "lbve_step(K), lbve_fields_many (every instance to pinned host, "
+                          "one synchronisation)"},
         "flops": measured_flops(value),
         "gpu_launches": K + 1,
         "clocks": clocks,

@@ -34,8 +34,13 @@
  *     device workspace of lbve_workspace_bytes() bytes and keeps it alive
  *     until lbve_destroy(); the library carves every buffer out of it.
  *   - All device work is enqueued on the caller's CUDA stream (cudaStream_t
- *     passed as void*).  Only lbve_status, lbve_fields (host output),
- *     lbve_totals, lbve_residual and lbve_save synchronise that stream.
+ *     passed as void*).  lbve_step and lbve_fields(_many) with device output
+ *     are asynchronous.  The calls that synchronise the stream are the set-up
+ *     calls (lbve_create, lbve_set_geometry(_many), lbve_set_inlet,
+ *     lbve_set_wall_distances, lbve_autotune), the adjoint
+ *     (lbve_adjoint_step, lbve_adjoint_step_ex), the reads (lbve_status,
+ *     lbve_fields(_many) with host output, lbve_totals, lbve_residual,
+ *     lbve_profile_read), lbve_save, lbve_load and lbve_profile.
  *   - Lattice units: dx = dt = 1, rho_0 = 1, c_s^2 = 1/3.
  */
 #ifndef LBVE_H
@@ -207,6 +212,27 @@ int lbve_create(const lbve_params* p, int32_t n_instances, void* d_workspace, si
 int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
                       const double* body_force, const double* init_fields);
 
+/* lbve_set_geometry for the n instances insts[0..n-1] in one call:
+ * instance insts[j] takes solid_masks[j], body_forces[j] and init_fields[j]
+ * (each as in lbve_set_geometry; a NULL list stands for n NULL pointers).
+ * Every upload and initialisation is enqueued first and the stream is
+ * synchronised once, at the end, so that the copies of one instance overlap
+ * the host work of the next (with pinned host arrays the uploads are
+ * asynchronous DMA; the arrays may be freed when the call returns).
+ *   insts: host int32 [n], distinct instances (a repeated or out-of-range
+ *          entry returns LBVE_ERR_ARG before anything changes).
+ * Instances are enqueued in list order.  A geometry rejected on the host or
+ * a CUDA error at list position j leaves insts[j..n-1] unchanged (insts[j]
+ * uninitialised after a CUDA error) and still finishes insts[0..j-1].
+ * Values rejected on the device (as in lbve_set_geometry) leave exactly the
+ * rejected instances uninitialised; the others are set.  The return value is
+ * the error of the first failing instance in list order (LBVE_OK if none),
+ * and lbve_status bit 1 marks every instance whose values were rejected.
+ * Errors: LBVE_ERR_ARG, LBVE_ERR_GEOMETRY, LBVE_ERR_CUDA. */
+int lbve_set_geometry_many(lbve_handle* h, int32_t n, const int32_t* insts,
+                           const uint8_t* const* solid_masks, const double* const* body_forces,
+                           const double* const* init_fields);
+
 /* Inlet profile of an open channel (open_x = 1): host float64 [5][ny] =
  * u_x, u_y, A_xx, A_xy, A_yy on the inlet column, rows 0..ny-1 (e.g. the
  * fully developed Oldroyd-B channel profile of Sec. 4.3).  Takes effect from
@@ -274,6 +300,15 @@ int lbve_status(lbve_handle* h, int32_t* flags);
  * on_device = 0: out is host memory (the call synchronises the stream);
  * on_device = 1: out is device memory (asynchronous device-to-device copy). */
 int lbve_fields(lbve_handle* h, int32_t inst, double* out, int32_t on_device);
+
+/* lbve_fields for the n instances insts[0..n-1]: outs[j] (host or device
+ * as on_device says, [6][ny][nx] float64 of instance insts[j]) receives its
+ * fields.  All copies are enqueued first; with host outputs the stream is
+ * synchronised once, at the end.  The arguments are checked before any copy
+ * starts.  Errors: LBVE_ERR_ARG (null list or output, instance out of
+ * range), LBVE_ERR_STATE (an instance never initialised), LBVE_ERR_CUDA. */
+int lbve_fields_many(lbve_handle* h, int32_t n, const int32_t* insts, double* const* outs,
+                     int32_t on_device);
 
 /* Float64 totals of instance inst at its current time (synchronises):
  *   out[0..2]  sum rho, sum rho ux, sum rho uy  (rho u as in eq_ev_f0)

@@ -871,9 +871,11 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
   return LBVE_OK;
 }
 
-int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
-                      const double* body_force, const double* init_fields) {
-  if (!h || inst < 0 || inst >= h->n) return set_error(LBVE_ERR_ARG, "bad handle or instance");
+// Enqueue everything lbve_set_geometry does for one instance except the
+// final synchronisation and the read of its input check (finish_geometry).
+// The instance stays not ready until finish_geometry accepts it.
+static int enqueue_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
+                            const double* body_force, const double* init_fields) {
   {
     // the geometry is checked on the host before anything changes; the
     // values of the force and the initial fields on the device, after the
@@ -934,22 +936,76 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
     return cuda_fail(cudaGetLastError(), "masked init kernel launch");
   if (launch_reduce(h->d_insts, inst, 1, h->d_partials, h->d_totals, h->d_flags, h->stream))
     return cuda_fail(cudaGetLastError(), "reduce launch");
-  // the pageable copy of D above is staged before return; make the device
-  // state consistent before the caller reuses its arrays, and read the
-  // input check
-  int32_t flag = 0;
-  e = cudaMemcpyAsync(&flag, h->d_flags + inst, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                      h->stream);
+  return LBVE_OK;
+}
+
+// Synchronise once for the instances insts[0..n-1] enqueued by
+// enqueue_geometry (the caller's host arrays are then free), read their
+// input checks and mark the accepted ones ready at time 0.  Returns the
+// error of the first rejected instance in list order.
+static int finish_geometry(lbve_handle* h, int32_t n, const int32_t* insts) {
+  if (n <= 0) return LBVE_OK;
+  std::vector<int32_t> flags(h->n, 0);
+  cudaError_t e = cudaMemcpyAsync(flags.data(), h->d_flags, sizeof(int32_t) * h->n,
+                                  cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbve_set_geometry");
-  if (flag & (1 << kFlagBadInput))
-    return set_error(LBVE_ERR_ARG,
-                     "instance %d: a body force or initial field is not finite, or an initial "
-                     "density is not > 0; the instance is left uninitialised",
-                     inst);
-  h->t[inst] = 0;
-  h->ready[inst] = 1;
-  return LBVE_OK;
+  int rc = LBVE_OK;
+  for (int32_t j = 0; j < n; ++j) {
+    const int32_t inst = insts[j];
+    if (flags[inst] & (1 << kFlagBadInput)) {
+      if (rc == LBVE_OK)
+        rc = set_error(LBVE_ERR_ARG,
+                       "instance %d: a body force or initial field is not finite, or an initial "
+                       "density is not > 0; the instance is left uninitialised",
+                       inst);
+      continue;
+    }
+    h->t[inst] = 0;
+    h->ready[inst] = 1;
+  }
+  return rc;
+}
+
+int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
+                      const double* body_force, const double* init_fields) {
+  if (!h || inst < 0 || inst >= h->n) return set_error(LBVE_ERR_ARG, "bad handle or instance");
+  const int rc = enqueue_geometry(h, inst, solid_mask, body_force, init_fields);
+  if (rc) {
+    // what was enqueued before the error finishes before the caller's
+    // arrays are released
+    cudaStreamSynchronize(h->stream);
+    return rc;
+  }
+  return finish_geometry(h, 1, &inst);
+}
+
+int lbve_set_geometry_many(lbve_handle* h, int32_t n, const int32_t* insts,
+                           const uint8_t* const* solid_masks, const double* const* body_forces,
+                           const double* const* init_fields) {
+  if (!h || n < 0 || (n > 0 && !insts)) return set_error(LBVE_ERR_ARG, "bad argument");
+  std::vector<uint8_t> seen(h->n, 0);
+  for (int32_t j = 0; j < n; ++j) {
+    if (insts[j] < 0 || insts[j] >= h->n)
+      return set_error(LBVE_ERR_ARG, "insts[%d] = %d is not an instance", j, insts[j]);
+    if (seen[insts[j]]++)
+      return set_error(LBVE_ERR_ARG, "instance %d is listed twice", insts[j]);
+  }
+  for (int32_t j = 0; j < n; ++j) {
+    const int rc = enqueue_geometry(h, insts[j], solid_masks ? solid_masks[j] : nullptr,
+                                    body_forces ? body_forces[j] : nullptr,
+                                    init_fields ? init_fields[j] : nullptr);
+    if (rc) {
+      // the instances before j are finished (and may report an earlier
+      // error); instance j and the rest of the list are not set
+      char msg[512];
+      snprintf(msg, sizeof msg, "%s", lbve_last_error());
+      const int rc0 = finish_geometry(h, j, insts);
+      if (rc0) return rc0;
+      return set_error(rc, "%s", msg);
+    }
+  }
+  return finish_geometry(h, n, insts);
 }
 
 int lbve_step(lbve_handle* h, int64_t n_steps) {
@@ -1002,15 +1058,32 @@ int lbve_status(lbve_handle* h, int32_t* flags) {
 }
 
 int lbve_fields(lbve_handle* h, int32_t inst, double* out, int32_t on_device) {
-  if (!h || !out || inst < 0 || inst >= h->n) return set_error(LBVE_ERR_ARG, "bad argument");
-  if (!h->ready[inst]) return set_error(LBVE_ERR_STATE, "instance %d was never initialised", inst);
-  const lbve_params& p = h->p[inst];
-  const size_t nn = size_t(p.nx) * p.ny, S = h->plan.inst[inst].stride;
-  cudaError_t e = cudaMemcpy2DAsync(out, nn * 8, h->insts[inst].fields, S * 8, nn * 8, 6,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                    h->stream);
-  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "lbve_fields");
+  return lbve_fields_many(h, 1, &inst, &out, on_device);
+}
+
+int lbve_fields_many(lbve_handle* h, int32_t n, const int32_t* insts, double* const* outs,
+                     int32_t on_device) {
+  if (!h || n < 0 || (n > 0 && (!insts || !outs))) return set_error(LBVE_ERR_ARG, "bad argument");
+  for (int32_t j = 0; j < n; ++j) {
+    if (insts[j] < 0 || insts[j] >= h->n || !outs[j])
+      return set_error(LBVE_ERR_ARG, "bad instance or output at list position %d", j);
+    if (!h->ready[insts[j]])
+      return set_error(LBVE_ERR_STATE, "instance %d was never initialised", insts[j]);
+  }
+  for (int32_t j = 0; j < n; ++j) {
+    const int32_t inst = insts[j];
+    const lbve_params& p = h->p[inst];
+    const size_t nn = size_t(p.nx) * p.ny, S = h->plan.inst[inst].stride;
+    const cudaError_t e =
+        cudaMemcpy2DAsync(outs[j], nn * 8, h->insts[inst].fields, S * 8, nn * 8, 6,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbve_fields");
+  }
+  if (!on_device && n > 0) {
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbve_fields");
+  }
   return LBVE_OK;
 }
 

@@ -504,26 +504,24 @@ __device__ __forceinline__ void collide_cde(const InstDev& D, int k, int S, R* _
 template <typename R>
 using PartT = typename std::conditional<sizeof(R) == 4, float, double>::type;
 
+// ux_prev, uy_prev: the velocity fields of the previous final step at node
+// k, read by the caller before the collision (unused at init)
 template <typename R, int MODE>
 __device__ __forceinline__ void final_node(const InstDev& D, int k, int S, int lattice, R drho,
-                                           R rho, R ux, R uy, const R* dphi, PartT<R>* part,
-                                           PartT<R>* plo) {
+                                           R rho, R ux, R uy, const R* dphi, PartT<R> ux_prev,
+                                           PartT<R> uy_prev, PartT<R>* part, PartT<R>* plo) {
   double* fl = D.fields;
   bool finite = true;
   if (lattice <= 0) {
     const double dr = to_f64(drho);
     const double vx = to_f64(ux), vy = to_f64(uy);
-    // the residual reads the fields of the previous final step (none at
-    // init) before they are overwritten below
-    const double ux_prev = fl[S + k], uy_prev = fl[2 * S + k];
     fl[k] = 1.0 + dr;
     fl[S + k] = vx;
     fl[2 * S + k] = vy;
     if constexpr (sizeof(R) == 4) {
       // in float32: the previous fields are float32 values
-      const float res = (MODE == kModeStep)
-                            ? fmaxf(fabsf(ux - (float)ux_prev), fabsf(uy - (float)uy_prev))
-                            : 0.f;
+      const float res =
+          (MODE == kModeStep) ? fmaxf(fabsf(ux - ux_prev), fabsf(uy - uy_prev)) : 0.f;
       // rho u exactly, as a float32 pair (product and its rounding error)
       const float px = rho * ux, py = rho * uy;
       part[kSumRho] = drho;
@@ -560,6 +558,17 @@ __device__ __forceinline__ void final_node(const InstDev& D, int k, int S, int l
   part[kNonFinite] = finite ? 0 : 1;
 }
 
+// Final step: start the previous velocity fields of node k (the residual's
+// operands) on their way to L2 with the node's other loads; they are read
+// just before the collision.  Read only after the collision, each warp
+// stalled there for a full HBM round trip, which made the final step of a
+// large batch take 1.8 times as long; loaded with the populations, they
+// cost more registers than they save.
+__device__ __forceinline__ void prefetch_prev_u(const InstDev& D, int k, int S) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(D.fields + S + k));
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(D.fields + 2 * S + k));
+}
+
 // Source, both collisions, stores and final-step bookkeeping of one node
 // whose populations are already reduced to (wall-completed) moments:
 //   hm      raw hydro moments, cm[3] raw conformation moments
@@ -573,7 +582,8 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
                                              const CdeM<R>* cm, R rho, R ux, R uy, R G00, R G01,
                                              R G10, R G11, R dPx, R dPy, R dRx, R dRy, R Fx,
                                              R Fy, R So0, R So1, R So2, R uxo, R uyo,
-                                             PartT<R>* part, PartT<R>* plo) {
+                                             PartT<R> ux_prev, PartT<R> uy_prev, PartT<R>* part,
+                                             PartT<R>* plo) {
   // conformation tensor, constitutive function, polymer stress (eq_kramer),
   // source Phi_ab
   R Axx, Axy, Ayy, Fxx, Fxy, Fyy;
@@ -606,7 +616,7 @@ __device__ __forceinline__ void collide_node(const InstDev& D, int k, int S, R* 
 
   if (FINAL) {
     const R dphi[3] = {cm[0].dphi, cm[1].dphi, cm[2].dphi};
-    final_node<R, MODE>(D, k, S, -1, hm.drho, rho, ux, uy, dphi, part, plo);
+    final_node<R, MODE>(D, k, S, -1, hm.drho, rho, ux, uy, dphi, ux_prev, uy_prev, part, plo);
   }
 }
 
@@ -942,6 +952,7 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
       So[2] = hist[2 * S + k];
       uxo = hist[3 * S + k];
       uyo = hist[4 * S + k];
+      if (FINAL) prefetch_prev_u(D, k, S);
       if (wcomp) {
         // bottom wall: H = {4, 7, 8}; top wall: H = {2, 5, 6}
         const int h0 = wb ? 4 : 2, h1 = wb ? 7 : 5, h2 = wb ? 8 : 6;
@@ -1127,9 +1138,14 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
         for (int j = 0; j < 6; ++j) part[kWallIn + j] = wall_io[j];
       }
     }
+    PartT<R> ux_prev = 0, uy_prev = 0;
+    if (FINAL && MODE == kModeStep) {
+      ux_prev = (PartT<R>)D.fields[S + k];
+      uy_prev = (PartT<R>)D.fields[2 * S + k];
+    }
     collide_node<R, MODE, FINAL, MASKED>(D, k, S, dst, hist, hm, cm, rho, ux, uy, G00, G01, G10,
                                          G11, dPx, dPy, dRx, dRy, Fx, Fy, So[0], So[1], So[2], uxo,
-                                         uyo, part, plo);
+                                         uyo, ux_prev, uy_prev, part, plo);
   } else if (FINAL && solid) {
     // a solid node reports zero fields and adds nothing to the totals
     const int ks = y * nx + x;
@@ -1235,6 +1251,7 @@ __device__ __forceinline__ void process_tile_split(const InstDev* __restrict__ i
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     if (role == 0) {
       PopSource<R, MODE>::hydro(src, S, nx, k, y * nx, rm, rp, x, xm, xp, d);
+      if (FINAL) prefetch_prev_u(D, k, S);
     } else {
       PopSource<R, MODE>::cde(src, l, S, nx, k, y * nx, rm, rp, x, xm, xp, d);
       So = hist[(size_t)l * S + k];
@@ -1347,10 +1364,17 @@ __device__ __forceinline__ void process_tile_split(const InstDev* __restrict__ i
       const R dPx = half * (cxp - cxm);
       const R mpl = coef<R>(D, kCoefMupLam);
       const R txx = mpl * Fxx, txy = mpl * Fxy, tyy = mpl * Fyy;
+      double ux_prev = 0.0, uy_prev = 0.0;
+      if (FINAL) {
+        ux_prev = D.fields[S + k];
+        uy_prev = D.fields[2 * S + k];
+      }
       collide_hydro<R>(D, k, S, dst, hm, rho, ux, uy, dPx, dPy, txx, txy, tyy, Fx, Fy);
       hist[3 * S + k] = ux;
       hist[4 * S + k] = uy;
-      if (FINAL) final_node<R, MODE>(D, k, S, 0, hm.drho, rho, ux, uy, nullptr, part, plo);
+      if (FINAL)
+        final_node<R, MODE>(D, k, S, 0, hm.drho, rho, ux, uy, nullptr, ux_prev, uy_prev, part,
+                            plo);
     } else {
       const R il = coef<R>(D, kCoefInvLam);
       const R sl = source_component<R>(l, Axx, Axy, Ayy, Fxx, Fxy, Fyy, il, G00, G01, G10, G11);
@@ -1359,7 +1383,7 @@ __device__ __forceinline__ void process_tile_split(const InstDev* __restrict__ i
       hist[(size_t)l * S + k] = sl;
       if (FINAL) {
         const R dphi[3] = {s_phi[0][lane], s_phi[1][lane], s_phi[2][lane]};
-        final_node<R, MODE>(D, k, S, role, R(0), rho, ux, uy, dphi, part, plo);
+        final_node<R, MODE>(D, k, S, role, R(0), rho, ux, uy, dphi, 0.0, 0.0, part, plo);
         part[kWallIn + l] = wall_in;
         part[kWallOut + l] = wall_out;
       }

@@ -34,7 +34,7 @@ EXPORTED = ["lbve_workspace_bytes", "lbve_create", "lbve_set_geometry", "lbve_st
             "lbve_adjoint_workspace_bytes", "lbve_adjoint_step", "lbve_state_bytes", "lbve_save",
             "lbve_load", "lbve_autotune", "lbve_set_wall_distances", "lbve_set_inlet",
             "lbve_adjoint_step_ex", "lbve_adjoint_workspace_bytes_interval", "lbve_profile",
-            "lbve_profile_read"]
+            "lbve_profile_read", "lbve_set_geometry_many", "lbve_fields_many"]
 
 
 class lbve_params(ctypes.Structure):
@@ -75,6 +75,10 @@ def load() -> ctypes.CDLL:
         L.lbve_create.argtypes = [P, ctypes.c_int32, _vp, ctypes.c_size_t, _vp,
                                   ctypes.POINTER(_vp)]
         L.lbve_set_geometry.argtypes = [_vp, ctypes.c_int32, _vp, _dp, _dp]
+        L.lbve_set_geometry_many.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                             _vp, _vp, _vp]
+        L.lbve_fields_many.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _vp,
+                                       ctypes.c_int32]
         L.lbve_step.argtypes = [_vp, ctypes.c_int64]
         L.lbve_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
         L.lbve_fields.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32]
@@ -166,6 +170,34 @@ def lbve_set_geometry(h, inst: int, solid_mask=None, body_force=None, init_field
     _check(load().lbve_set_geometry(h, inst, mask_ptr, bf_ptr, ini_ptr), "lbve_set_geometry")
 
 
+def _ptr_list(arrays):
+    """A C array of pointers (NULL for None) to the arrays' data, or None if
+    every entry is None."""
+    if all(a is None for a in arrays):
+        return None
+    return (_vp * len(arrays))(*[None if a is None else a.ctypes.data for a in arrays])
+
+
+def lbve_set_geometry_many(h, insts, solid_masks=None, body_forces=None, init_fields=None,
+                           n_nodes=None) -> None:
+    """lbve_set_geometry for several instances with one synchronisation.
+    The lists (None = all None) are indexed like ``insts``; ``n_nodes[j]``
+    (nx * ny of insts[j]) sizes the checks of the float64 arrays."""
+    n = len(insts)
+    ids = np.ascontiguousarray(insts, dtype=np.int32)
+    masks = [None] * n if solid_masks is None else list(solid_masks)
+    forces = [None] * n if body_forces is None else list(body_forces)
+    inits = [None] * n if init_fields is None else list(init_fields)
+    if not (len(masks) == len(forces) == len(inits) == n):
+        raise ValueError("the lists must have one entry per instance")
+    masks = [None if m is None else np.ascontiguousarray(m, dtype=np.uint8) for m in masks]
+    forces = [None if f is None else _f64(f, 2 * n_nodes[j])[0] for j, f in enumerate(forces)]
+    inits = [None if a is None else _f64(a, 6 * n_nodes[j])[0] for j, a in enumerate(inits)]
+    pm, pf, pi = _ptr_list(masks), _ptr_list(forces), _ptr_list(inits)
+    _check(load().lbve_set_geometry_many(h, n, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                         pm, pf, pi), "lbve_set_geometry_many")
+
+
 def lbve_set_inlet(h, inst: int, inlet) -> None:
     """Inlet profile [5][ny] = u_x, u_y, A_xx, A_xy, A_yy of an open channel."""
     a = np.ascontiguousarray(inlet, dtype=np.float64)
@@ -215,6 +247,17 @@ def lbve_status(h, n_instances: int) -> np.ndarray:
 
 def lbve_fields(h, inst: int, out_ptr: int, on_device: bool) -> None:
     _check(load().lbve_fields(h, inst, _vp(out_ptr), 1 if on_device else 0), "lbve_fields")
+
+
+def lbve_fields_many(h, insts, out_ptrs, on_device: bool) -> None:
+    """lbve_fields for several instances; out_ptrs[j] receives insts[j]."""
+    n = len(insts)
+    if len(out_ptrs) != n:
+        raise ValueError("one output per instance")
+    ids = np.ascontiguousarray(insts, dtype=np.int32)
+    outs = (_vp * n)(*[int(p) for p in out_ptrs])
+    _check(load().lbve_fields_many(h, n, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), outs,
+                                   1 if on_device else 0), "lbve_fields_many")
 
 
 def lbve_totals(h, inst: int) -> np.ndarray:
@@ -357,10 +400,14 @@ class Simulation:
         self.tile_tx = [p.tile_tx for p in self.params]
         self.h = lbve_create(self.params, self.workspace.data_ptr(), self.nbytes,
                              self.stream.cuda_stream)
+        n = len(self.instances)
+        lbve_set_geometry_many(self.h, list(range(n)),
+                               [getattr(inst, "solid", None) for inst in self.instances],
+                               [inst.force_field for inst in self.instances],
+                               None if init_fields is None else list(init_fields),
+                               n_nodes=[inst.n_nodes for inst in self.instances])
         for i, inst in enumerate(self.instances):
-            ini = None if init_fields is None else init_fields[i]
             solid = getattr(inst, "solid", None)
-            lbve_set_geometry(self.h, i, solid, inst.force_field, ini, n_nodes=inst.n_nodes)
             if getattr(inst, "open_x", False) and getattr(inst, "inlet", None) is not None:
                 lbve_set_inlet(self.h, i, inst.inlet)
             if solid is not None and getattr(inst, "wall_q", None) is not None:

@@ -169,3 +169,18 @@ def test_empty_degenerate_and_maximum_sizes(L):
     with pytest.raises(L.LbveError) as e:
         L.lbve_workspace_bytes([big])
     assert e.value.code == L.LBVE_ERR_ARG
+
+
+def test_batched_calls_reject_bad_arguments_on_the_host(L):
+    """lbve_set_geometry_many / lbve_fields_many refuse a null handle, a
+    negative count or a missing list before touching the device; the binding
+    refuses lists of unequal length."""
+    lib = L.load()
+    ids = (ctypes.c_int32 * 2)(0, 1)
+    outs = (ctypes.c_void_p * 2)(None, None)
+    assert lib.lbve_set_geometry_many(None, 2, ids, None, None, None) == L.LBVE_ERR_ARG
+    assert lib.lbve_fields_many(None, 2, ids, outs, 0) == L.LBVE_ERR_ARG
+    with pytest.raises(ValueError):
+        L.lbve_set_geometry_many(None, [0, 1], [None], None, None, n_nodes=[4, 4])
+    with pytest.raises(ValueError):
+        L.lbve_fields_many(None, [0, 1], [0], False)

@@ -1,0 +1,145 @@
+"""lbve_set_geometry_many and lbve_fields_many: the batched forms of the
+set-up and read-back calls give the same state as one call per instance, and
+report errors per instance."""
+import numpy as np
+import pytest
+
+from paper_2508_16997_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbve():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_16997_gb300 import build, lbve as L
+    build.build()
+    return L
+
+
+def _batch():
+    a = wl.frm(24, Wi=2.0, Re=1.0, Ma=0.05)
+    b = wl.channel(12, nx=5, Wi=3.0)
+    c = wl.obstacle_box(20, 16, Wi=0.5)
+    return [a, b, c]
+
+
+def _inputs(insts):
+    inits = [wl.random_fields(i.nx, i.ny, seed=11 + k) for k, i in enumerate(insts)]
+    forces = [wl.random_force(i.nx, i.ny, seed=5 + k, amp=2e-5) if k != 1 else None
+              for k, i in enumerate(insts)]
+    masks = [getattr(i, "solid", None) for i in insts]
+    return masks, forces, inits
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_geometry_many_equals_single_calls(lbve, precision):
+    """One lbve_set_geometry_many call over the batch (masks, per-node forces,
+    initial fields; instances listed out of order) leaves the same state as
+    one lbve_set_geometry per instance: fields bit-identical at t = 0 and
+    after 40 steps."""
+    insts = _batch()
+    masks, forces, inits = _inputs(insts)
+    n = [i.n_nodes for i in insts]
+    a = lbve.Simulation(insts, precision=precision)
+    b = lbve.Simulation(insts, precision=precision)
+    a.step(3)
+    b.step(7)
+    order = [2, 0, 1]
+    lbve.lbve_set_geometry_many(a.h, order, [masks[j] for j in order],
+                                [forces[j] for j in order], [inits[j] for j in order],
+                                n_nodes=[n[j] for j in order])
+    for j in range(3):
+        lbve.lbve_set_geometry(b.h, j, masks[j], forces[j], inits[j], n_nodes=n[j])
+    for j in range(3):
+        assert a.time(j) == b.time(j) == 0
+        np.testing.assert_array_equal(a.fields(j), b.fields(j))
+    a.step(40)
+    b.step(40)
+    for j in range(3):
+        np.testing.assert_array_equal(a.fields(j), b.fields(j))
+        np.testing.assert_array_equal(a.totals(j), b.totals(j))
+    assert not np.any(a.status())
+
+
+def test_set_geometry_many_partial_list_and_errors(lbve):
+    """A list naming some instances leaves the others running; a value
+    rejected on the device leaves exactly that instance uninitialised (flag
+    bit 1) and the rest of the list set; a geometry rejected on the host
+    stops the list there; a repeated instance changes nothing."""
+    insts = _batch()
+    masks, forces, inits = _inputs(insts)
+    n = [i.n_nodes for i in insts]
+    sim = lbve.Simulation(insts)
+    sim.step(5)
+    keep0 = sim.fields(0)
+
+    # only instance 1 is reset
+    lbve.lbve_set_geometry_many(sim.h, [1], None, None, [inits[1]], n_nodes=[n[1]])
+    assert sim.time(0) == 5 and sim.time(1) == 0 and sim.time(2) == 5
+    np.testing.assert_array_equal(sim.fields(0), keep0)
+
+    # a repeated instance: refused before anything changes
+    with pytest.raises(lbve.LbveError) as e:
+        lbve.lbve_set_geometry_many(sim.h, [0, 0], None, None, None, n_nodes=[n[0], n[0]])
+    assert e.value.code == lbve.LBVE_ERR_ARG
+    assert sim.time(0) == 5
+    np.testing.assert_array_equal(sim.fields(0), keep0)
+
+    # a NaN in the middle instance's initial fields
+    bad = inits[1].copy()
+    bad[2, 3, 1] = np.nan
+    with pytest.raises(lbve.LbveError) as e:
+        lbve.lbve_set_geometry_many(sim.h, [0, 1, 2], masks, forces, [inits[0], bad, inits[2]],
+                                    n_nodes=n)
+    assert e.value.code == lbve.LBVE_ERR_ARG
+    assert "instance 1" in str(e.value)
+    flags = sim.status()
+    assert flags[1] & 2 and not flags[0] & 2 and not flags[2] & 2
+    assert sim.time(0) == 0 and sim.time(2) == 0
+    with pytest.raises(lbve.LbveError) as e:
+        sim.step(1)
+    assert e.value.code == lbve.LBVE_ERR_STATE
+
+    # a mask with no fluid at list position 1: instance 0 (position 0) is
+    # set, instances 1 and 2 are not touched
+    lbve.lbve_set_geometry_many(sim.h, [1], None, None, [inits[1]], n_nodes=[n[1]])
+    sim.step(2)
+    keep2 = sim.fields(2)
+    full = np.ones((insts[2].ny, insts[2].nx), np.uint8)
+    with pytest.raises(lbve.LbveError) as e:
+        lbve.lbve_set_geometry_many(sim.h, [0, 2, 1], [None, full, None], None, None,
+                                    n_nodes=[n[0], n[2], n[1]])
+    assert e.value.code == lbve.LBVE_ERR_GEOMETRY
+    assert sim.time(0) == 0 and sim.time(1) == 2 and sim.time(2) == 2
+    np.testing.assert_array_equal(sim.fields(2), keep2)
+    sim.step(1)
+    assert not np.any(sim.status())
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_fields_many_equals_single_calls(lbve, on_device):
+    """lbve_fields_many writes what lbve_fields writes, to host or device
+    outputs in any order; a bad instance is refused before any copy."""
+    import torch
+    insts = _batch()
+    sim = lbve.Simulation(insts, precision=1)
+    sim.step(9)
+    order = [1, 2, 0]
+    dev = "cuda" if on_device else "cpu"
+    outs = [torch.full((6, insts[j].ny, insts[j].nx), -7.0, dtype=torch.float64, device=dev)
+            for j in order]
+    lbve.lbve_fields_many(sim.h, order, [t.data_ptr() for t in outs], on_device)
+    torch.cuda.synchronize()
+    for t, j in zip(outs, order):
+        np.testing.assert_array_equal(t.cpu().numpy(), sim.fields(j))
+    for t in outs:
+        t.fill_(-7.0)
+    with pytest.raises(lbve.LbveError) as e:
+        lbve.lbve_fields_many(sim.h, [0, 3], [outs[0].data_ptr(), outs[1].data_ptr()],
+                              on_device)
+    assert e.value.code == lbve.LBVE_ERR_ARG
+    torch.cuda.synchronize()
+    assert bool((outs[0] == -7.0).all())
