@@ -136,7 +136,7 @@ struct InstPlan {
 
 struct Plan {
   std::vector<InstPlan> inst;
-  size_t off_insts, off_tiles[kLists], off_partials, off_totals, off_flags, total;
+  size_t off_insts, off_tiles[kLists], off_partials, off_totals, off_flags, off_geo, total;
   int ntiles[kLists], nslots;
   int cap_tiles[kLists];  // tile-table capacity: the most tiles any tile width gives
   int threads[kLists];    // CTA size of each list's step launches
@@ -288,6 +288,8 @@ Plan make_plan(const lbve_params* p, int n) {
   off = align_up(off + sizeof(double) * kTotals * n, kAlign);
   pl.off_flags = off;
   off = align_up(off + sizeof(int32_t) * n, kAlign);
+  pl.off_geo = off;  // list of a batched lbve_set_geometry: ids[n], what[n]
+  off = align_up(off + sizeof(int32_t) * 2 * n, kAlign);
   pl.total = off;
   return pl;
 }
@@ -307,6 +309,7 @@ struct lbve_handle {
   double* d_partials = nullptr;
   double* d_totals = nullptr;
   int32_t* d_flags = nullptr;
+  int32_t* d_geo = nullptr;  // [2][n]: instance ids and staged inputs of a geometry call
   int parity = 0;
   std::vector<int64_t> t;
   std::vector<char> ready;
@@ -732,6 +735,7 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
   h->d_partials = (double*)(h->ws + pl.off_partials);
   h->d_totals = (double*)(h->ws + pl.off_totals);
   h->d_flags = (int32_t*)(h->ws + pl.off_flags);
+  h->d_geo = (int32_t*)(h->ws + pl.off_geo);
 
   h->insts.resize(n);
   h->c.resize(n);
@@ -871,80 +875,102 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
   return LBVE_OK;
 }
 
-// Enqueue everything lbve_set_geometry does for one instance except the
-// final synchronisation and the read of its input check (finish_geometry).
-// The instance stays not ready until finish_geometry accepts it.
-static int enqueue_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
-                            const double* body_force, const double* init_fields) {
+// Host part of lbve_set_geometry for one instance: check and install the
+// geometry, and start the uploads of the staged inputs (float64 force into
+// pop[parity], float64 initial fields into pop[parity ^ 1]).  *what gets bit
+// 0 for a staged force and bit 1 for staged fields.  From the first upload
+// on, the instance is not ready until finish_geometry accepts it.
+static int stage_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
+                          const double* body_force, const double* init_fields, int32_t* what) {
+  *what = 0;
   {
     // the geometry is checked on the host before anything changes; the
     // values of the force and the initial fields on the device, after the
-    // upload (below)
+    // upload (init_geometry)
     const int rc = install_mask(h, inst, solid_mask);
     if (rc) return rc;
   }
   const lbve_params& p = h->p[inst];
-  const InstPlan& q = h->plan.inst[inst];
   const size_t nn = size_t(p.nx) * p.ny;
-  const size_t S = q.stride;
+  const size_t S = h->plan.inst[inst].stride;
   const int P = h->parity;
   InstDev& D = h->insts[inst];
-  cudaError_t e = cudaSuccess;
-
-  // from here on the instance's state is being replaced: it counts as
-  // initialised again only when the call succeeds
   h->ready[inst] = 0;
-  e = cudaMemsetAsync(h->d_flags + inst, 0, sizeof(int32_t), h->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "flag reset");
-  double* fstage = nullptr;
+  D.force_field = body_force ? 1 : 0;
   if (body_force) {
-    fstage = (double*)D.pop[P];  // staging: float64 [2][S]
-    e = cudaMemcpy2DAsync(fstage, S * 8, body_force, nn * 8, nn * 8, 2, cudaMemcpyHostToDevice,
-                          h->stream);
+    const cudaError_t e = cudaMemcpy2DAsync(D.pop[P], S * 8, body_force, nn * 8, nn * 8, 2,
+                                            cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "force upload");
-    if (launch_convert_force(p.precision, fstage, D.force, (int)nn, (int)S, h->stream))
-      return cuda_fail(cudaGetLastError(), "force conversion launch");
-    D.force_field = 1;
-  } else {
-    D.force_field = 0;
+    *what |= 1;
   }
-
-  // staged initial fields, float64 [6][S], in the buffer the init kernel reads
-  double* stage = (double*)D.pop[P ^ 1];
   if (init_fields) {
-    e = cudaMemcpy2DAsync(stage, S * 8, init_fields, nn * 8, nn * 8, 6, cudaMemcpyHostToDevice,
-                          h->stream);
+    const cudaError_t e = cudaMemcpy2DAsync(D.pop[P ^ 1], S * 8, init_fields, nn * 8, nn * 8, 6,
+                                            cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "initial field upload");
-  } else if (launch_fill_default_fields(stage, (int)nn, (int)S, h->stream)) {
-    return cuda_fail(cudaGetLastError(), "default field launch");
+    *what |= 2;
   }
-  if (launch_check_inputs(fstage, init_fields ? stage : nullptr, (int)nn, (int)S,
-                          h->d_flags + inst, kFlagBadInput, h->stream))
+  return LBVE_OK;
+}
+
+// Device part for the staged list entries j < n (instance ids[j], inputs
+// what[j]), a few launches for the whole list: the list and the descriptors
+// are uploaded; one kernel checks the staged values, converts the forces and
+// writes default fields; the equilibrium state of t = 0 is collided (one
+// launch per precision when the list holds every instance of it); one
+// reduction gives the totals.
+static int init_geometry(lbve_handle* h, int32_t n, const int32_t* ids, const int32_t* what) {
+  if (n <= 0) return LBVE_OK;
+  std::vector<int32_t> geo(2 * (size_t)n);
+  int max_nodes = 1;
+  int in_list[kLists] = {0}, of_list[kLists] = {0};
+  for (int32_t j = 0; j < n; ++j) {
+    geo[j] = ids[j];
+    geo[n + j] = what[j];
+    max_nodes = std::max(max_nodes, h->p[ids[j]].nx * h->p[ids[j]].ny);
+    ++in_list[h->plan.inst[ids[j]].list];
+  }
+  for (int i = 0; i < h->n; ++i) ++of_list[h->plan.inst[i].list];
+  // pageable sources: both copies are staged before the calls return
+  cudaError_t e = cudaMemcpyAsync(h->d_geo, geo.data(), sizeof(int32_t) * geo.size(),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_insts, h->insts.data(), sizeof(InstDev) * h->n,
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "geometry list upload");
+  const int P = h->parity;
+  if (launch_geometry_inputs(h->d_insts, h->d_geo, h->d_geo + n, n, max_nodes, P, h->d_flags,
+                             kFlagBadInput, h->stream))
     return cuda_fail(cudaGetLastError(), "input check launch");
-  e = cudaMemcpyAsync(h->d_insts + inst, &D, sizeof(InstDev), cudaMemcpyHostToDevice, h->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "descriptor upload");
   // collide the equilibrium state of t = 0: reads pop[P^1] (staging), writes pop[P]
-  if (launch_step(p.precision, h->plan.threads[q.list], h->d_insts,
-                  h->d_tiles[q.list] + q.tile_begin, q.ntiles, P ^ 1,
-                  kModeInit, kFinal, h->d_partials, h->stream))
-    return cuda_fail(cudaGetLastError(), "init kernel launch");
-  if (!h->mtiles_of[inst].empty() &&
-      launch_step(p.precision, h->plan.threads[q.list], h->d_insts,
-                  h->d_mtiles[q.list] + h->mbegin[inst],
-                  (int)h->mtiles_of[inst].size(), P ^ 1, kModeInit, kFinal, h->d_partials,
-                  h->stream, 1))
-    return cuda_fail(cudaGetLastError(), "masked init kernel launch");
-  if (launch_reduce(h->d_insts, inst, 1, h->d_partials, h->d_totals, h->d_flags, h->stream))
+  for (int l = 0; l < kLists; ++l)
+    if (in_list[l] > 0 && in_list[l] == of_list[l] &&
+        launch_step(l, h->plan.threads[l], h->d_insts, h->d_tiles[l], h->plan.ntiles[l], P ^ 1,
+                    kModeInit, kFinal, h->d_partials, h->stream))
+      return cuda_fail(cudaGetLastError(), "init kernel launch");
+  for (int32_t j = 0; j < n; ++j) {
+    const int32_t inst = ids[j];
+    const InstPlan& q = h->plan.inst[inst];
+    const int prec = h->p[inst].precision;
+    if (in_list[q.list] != of_list[q.list] &&
+        launch_step(prec, h->plan.threads[q.list], h->d_insts, h->d_tiles[q.list] + q.tile_begin,
+                    q.ntiles, P ^ 1, kModeInit, kFinal, h->d_partials, h->stream))
+      return cuda_fail(cudaGetLastError(), "init kernel launch");
+    if (!h->mtiles_of[inst].empty() &&
+        launch_step(prec, h->plan.threads[q.list], h->d_insts,
+                    h->d_mtiles[q.list] + h->mbegin[inst], (int)h->mtiles_of[inst].size(), P ^ 1,
+                    kModeInit, kFinal, h->d_partials, h->stream, 1))
+      return cuda_fail(cudaGetLastError(), "masked init kernel launch");
+  }
+  if (launch_reduce(h->d_insts, 0, n, h->d_partials, h->d_totals, h->d_flags, h->stream, h->d_geo))
     return cuda_fail(cudaGetLastError(), "reduce launch");
   return LBVE_OK;
 }
 
-// Synchronise once for the instances insts[0..n-1] enqueued by
-// enqueue_geometry (the caller's host arrays are then free), read their
-// input checks and mark the accepted ones ready at time 0.  Returns the
-// error of the first rejected instance in list order.
-static int finish_geometry(lbve_handle* h, int32_t n, const int32_t* insts) {
-  if (n <= 0) return LBVE_OK;
+// Synchronise once for the list entries ids[0..n-1] (the caller's host
+// arrays are then free), read their input checks and mark the accepted
+// instances ready at time 0.  Returns the error of the first rejected
+// instance in list order.
+static int finish_geometry(lbve_handle* h, int32_t n, const int32_t* ids) {
   std::vector<int32_t> flags(h->n, 0);
   cudaError_t e = cudaMemcpyAsync(flags.data(), h->d_flags, sizeof(int32_t) * h->n,
                                   cudaMemcpyDeviceToHost, h->stream);
@@ -952,7 +978,7 @@ static int finish_geometry(lbve_handle* h, int32_t n, const int32_t* insts) {
   if (e != cudaSuccess) return cuda_fail(e, "lbve_set_geometry");
   int rc = LBVE_OK;
   for (int32_t j = 0; j < n; ++j) {
-    const int32_t inst = insts[j];
+    const int32_t inst = ids[j];
     if (flags[inst] & (1 << kFlagBadInput)) {
       if (rc == LBVE_OK)
         rc = set_error(LBVE_ERR_ARG,
@@ -969,15 +995,7 @@ static int finish_geometry(lbve_handle* h, int32_t n, const int32_t* insts) {
 
 int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
                       const double* body_force, const double* init_fields) {
-  if (!h || inst < 0 || inst >= h->n) return set_error(LBVE_ERR_ARG, "bad handle or instance");
-  const int rc = enqueue_geometry(h, inst, solid_mask, body_force, init_fields);
-  if (rc) {
-    // what was enqueued before the error finishes before the caller's
-    // arrays are released
-    cudaStreamSynchronize(h->stream);
-    return rc;
-  }
-  return finish_geometry(h, 1, &inst);
+  return lbve_set_geometry_many(h, 1, &inst, &solid_mask, &body_force, &init_fields);
 }
 
 int lbve_set_geometry_many(lbve_handle* h, int32_t n, const int32_t* insts,
@@ -991,21 +1009,33 @@ int lbve_set_geometry_many(lbve_handle* h, int32_t n, const int32_t* insts,
     if (seen[insts[j]]++)
       return set_error(LBVE_ERR_ARG, "instance %d is listed twice", insts[j]);
   }
+  if (n == 0) return LBVE_OK;
+  std::vector<int32_t> what(n, 0);
+  int32_t staged = n;  // entries 0..staged-1 go through the device part
+  int rc_stage = LBVE_OK;
+  char msg[512] = "";
   for (int32_t j = 0; j < n; ++j) {
-    const int rc = enqueue_geometry(h, insts[j], solid_masks ? solid_masks[j] : nullptr,
-                                    body_forces ? body_forces[j] : nullptr,
-                                    init_fields ? init_fields[j] : nullptr);
-    if (rc) {
-      // the instances before j are finished (and may report an earlier
-      // error); instance j and the rest of the list are not set
-      char msg[512];
+    rc_stage = stage_geometry(h, insts[j], solid_masks ? solid_masks[j] : nullptr,
+                              body_forces ? body_forces[j] : nullptr,
+                              init_fields ? init_fields[j] : nullptr, &what[j]);
+    if (rc_stage) {
+      // entries before j are still initialised (and may report an earlier
+      // error); entry j and the rest of the list are not set
       snprintf(msg, sizeof msg, "%s", lbve_last_error());
-      const int rc0 = finish_geometry(h, j, insts);
-      if (rc0) return rc0;
-      return set_error(rc, "%s", msg);
+      staged = j;
+      break;
     }
   }
-  return finish_geometry(h, n, insts);
+  int rc = init_geometry(h, staged, insts, what.data());
+  if (rc) {
+    // what was enqueued finishes before the caller's arrays are released
+    cudaStreamSynchronize(h->stream);
+    return rc;
+  }
+  rc = finish_geometry(h, staged, insts);
+  if (rc) return rc;
+  if (rc_stage) return set_error(rc_stage, "%s", msg);
+  return LBVE_OK;
 }
 
 int lbve_step(lbve_handle* h, int64_t n_steps) {

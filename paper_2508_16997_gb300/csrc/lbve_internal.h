@@ -184,16 +184,20 @@ struct AdjArgsRaw {
 // kAdjFields, kAdjInit (lbve_adjoint.cuh).
 int launch_adjoint(int prec, int mode, int pass, const InstDev* d_desc, const AdjArgsRaw& a,
                    int n_nodes, void* stream);
+// Totals of n_insts instances: ids[0..n_insts-1] (device), or first_inst..
+// first_inst + n_insts - 1 when d_ids is null.
 int launch_reduce(const InstDev* d_insts, int first_inst, int n_insts, const double* d_partials,
-                  double* d_totals, int32_t* d_flags, void* stream);
-int launch_convert_force(int prec, const double* d_src, void* d_dst, int n, int stride,
-                         void* stream);
-// Default initial fields (rho = 1, u = 0, A = I) into float64 staging planes.
-int launch_fill_default_fields(double* d_stage, int n, int stride, void* stream);
-// Set bit `bit` of *d_flag if a staged force component or initial field is
-// not finite or an initial density is not in (0, inf) (either may be null).
-int launch_check_inputs(const double* d_force, const double* d_init, int n, int stride,
-                        int32_t* d_flag, int bit, void* stream);
+                  double* d_totals, int32_t* d_flags, void* stream,
+                  const int32_t* d_ids = nullptr);
+// Staged inputs of the list entries j < n_list (instance d_ids[j], d_what[j]
+// bit 0 force staged in pop[parity], bit 1 initial fields staged in
+// pop[parity ^ 1]): zero the instances' flags, check the staged values (bit
+// `bit` of the flag on failure), convert the force to the instance's
+// precision, write default fields where none are staged.  max_nodes: the
+// largest nx * ny of the list.
+int launch_geometry_inputs(const InstDev* d_insts, const int32_t* d_ids, const int32_t* d_what,
+                           int n_list, int max_nodes, int parity, int32_t* d_flags, int bit,
+                           void* stream);
 constexpr int kFlagBadInput = 1;  // status bit of a rejected lbve_set_geometry
 
 }  // namespace lbve

@@ -79,14 +79,16 @@ int launch_step(int prec, int threads, const InstDev* d_insts, const TileDev* d_
 
 // One CTA per instance: sum (max for the residual) the partial records of the
 // instance's tiles, and the wall-pass records of its mask walls, in a fixed
-// order, so totals are bit-reproducible.
+// order, so totals are bit-reproducible.  CTA b takes instance ids[b], or
+// first_inst + b without a list.
 __global__ void __launch_bounds__(256) reduce_kernel(const InstDev* __restrict__ insts,
                                                      int first_inst,
+                                                     const int32_t* __restrict__ ids,
                                                      const double* __restrict__ partials,
                                                      double* __restrict__ totals,
                                                      int32_t* __restrict__ flags) {
   __shared__ double s[256];
-  const int inst = first_inst + blockIdx.x;
+  const int inst = ids ? ids[blockIdx.x] : first_inst + blockIdx.x;
   const InstDev& D = insts[inst];
   for (int j = 0; j < kDrag + 2; ++j) {
     double v = 0.0;
@@ -116,89 +118,97 @@ __global__ void __launch_bounds__(256) reduce_kernel(const InstDev* __restrict__
 }
 
 int launch_reduce(const InstDev* d_insts, int first_inst, int n_insts, const double* d_partials,
-                  double* d_totals, int32_t* d_flags, void* stream) {
+                  double* d_totals, int32_t* d_flags, void* stream, const int32_t* d_ids) {
   if (n_insts <= 0) return 0;
-  reduce_kernel<<<n_insts, 256, 0, (cudaStream_t)stream>>>(d_insts, first_inst, d_partials,
+  reduce_kernel<<<n_insts, 256, 0, (cudaStream_t)stream>>>(d_insts, first_inst, d_ids, d_partials,
                                                            d_totals, d_flags);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 
-// Default initial fields (rho = 1, u = 0, A = I) into the float64 staging
-// planes [6][stride], so that no host array is built and copied for them.
-__global__ void fill_default_fields_kernel(double* __restrict__ stage, int n, int stride) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    stage[i] = 1.0;
-    stage[(size_t)stride + i] = 0.0;
-    stage[2 * (size_t)stride + i] = 0.0;
-    stage[3 * (size_t)stride + i] = 1.0;
-    stage[4 * (size_t)stride + i] = 0.0;
-    stage[5 * (size_t)stride + i] = 1.0;
-  }
+// Staged inputs of a list of lbve_set_geometry calls, one grid row
+// (blockIdx.y) per list entry j, instance ids[j]:
+//   what[j] bit 0: a float64 body force is staged in pop[parity] ([2][stride]):
+//                  checked and converted to the instance's precision into
+//                  its force planes;
+//   what[j] bit 1: float64 initial fields are staged in pop[parity ^ 1]
+//                  ([6][stride]): checked; without it the default fields
+//                  (rho = 1, u = 0, A = I) are written there.
+// The checks test the float64 bit patterns as integers: every force
+// component and initial field finite (exponent field not all ones), every
+// initial density in (0, +inf).  A failure sets bit `bit` of flags[ids[j]],
+// which clear_flags_kernel has zeroed.
+template <typename R>
+__device__ __forceinline__ void store_force(void* dst, size_t i, double v) {
+  ((R*)dst)[i] = R(v);
 }
 
-int launch_fill_default_fields(double* d_stage, int n, int stride, void* stream) {
-  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
-  if (blocks <= 0) return 0;
-  fill_default_fields_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_stage, n, stride);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
-}
-
-// Checks of the staged inputs of lbve_set_geometry, by integer tests of the
-// float64 bit patterns: every force component and initial field finite (the
-// exponent field is not all ones), every initial density in (0, +inf).  Sets
-// bit `bit` of *flag when one fails.
-__global__ void check_inputs_kernel(const double* __restrict__ force, const double* __restrict__ init,
-                                    int n, int stride, int32_t* __restrict__ flag, int bit) {
+__global__ void __launch_bounds__(256) geometry_inputs_kernel(const InstDev* __restrict__ insts,
+                                                               const int32_t* __restrict__ ids,
+                                                               const int32_t* __restrict__ what,
+                                                               int parity,
+                                                               int32_t* __restrict__ flags,
+                                                               int bit) {
+  const int j = blockIdx.y;
+  const InstDev& D = insts[ids[j]];
+  const int n = D.nx * D.ny, S = D.stride, w = what[j], prec = D.prec;
+  const double* __restrict__ fstage = (const double*)D.pop[parity];
+  double* __restrict__ stage = (double*)D.pop[parity ^ 1];
   bool bad = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (force)
+    if (w & 1) {
+#pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const unsigned long long b = __double_as_longlong(force[(size_t)c * stride + i]);
-        bad |= ((b >> 52) & 0x7ffull) == 0x7ffull;
+        const double v = fstage[(size_t)c * S + i];
+        bad |= ((__double_as_longlong(v) >> 52) & 0x7ff) == 0x7ff;
+        if (prec == 0)
+          store_force<double>(D.force, (size_t)c * S + i, v);
+        else if (prec == 2)
+          store_force<df32>(D.force, (size_t)c * S + i, v);
+        else
+          store_force<float>(D.force, (size_t)c * S + i, v);
       }
-    if (init) {
+    }
+    if (w & 2) {
+#pragma unroll
       for (int c = 0; c < 6; ++c) {
-        const unsigned long long b = __double_as_longlong(init[(size_t)c * stride + i]);
-        bad |= ((b >> 52) & 0x7ffull) == 0x7ffull;
+        const long long b = __double_as_longlong(stage[(size_t)c * S + i]);
+        bad |= ((b >> 52) & 0x7ff) == 0x7ff;
       }
-      const long long r = __double_as_longlong(init[i]);
+      const long long r = __double_as_longlong(stage[i]);
       bad |= !(r > 0 && r < 0x7ff0000000000000ll);
+    } else {
+      stage[i] = 1.0;
+      stage[(size_t)S + i] = 0.0;
+      stage[2 * (size_t)S + i] = 0.0;
+      stage[3 * (size_t)S + i] = 1.0;
+      stage[4 * (size_t)S + i] = 0.0;
+      stage[5 * (size_t)S + i] = 1.0;
     }
   }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1 << bit);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&flags[ids[j]], 1 << bit);
 }
 
-int launch_check_inputs(const double* d_force, const double* d_init, int n, int stride,
-                        int32_t* d_flag, int bit, void* stream) {
-  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
-  if (blocks <= 0 || (!d_force && !d_init)) return 0;
-  check_inputs_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_force, d_init, n, stride, d_flag,
-                                                               bit);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
+__global__ void clear_flags_kernel(const int32_t* __restrict__ ids, int n,
+                                   int32_t* __restrict__ flags) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    flags[ids[j]] = 0;
 }
 
-template <typename R>
-__global__ void convert_force_kernel(const double* __restrict__ src, R* __restrict__ dst, int n,
-                                     int stride) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    dst[i] = R(src[i]);
-    dst[stride + i] = R(src[stride + i]);
+int launch_geometry_inputs(const InstDev* d_insts, const int32_t* d_ids, const int32_t* d_what,
+                           int n_list, int max_nodes, int parity, int32_t* d_flags, int bit,
+                           void* stream) {
+  if (n_list <= 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  clear_flags_kernel<<<(n_list + 255) / 256, 256, 0, st>>>(d_ids, n_list, d_flags);
+  // about eight nodes per thread for the largest instance, at most 64 CTAs per entry
+  int gx = (max_nodes + 2047) / 2048;
+  gx = gx < 1 ? 1 : (gx > 64 ? 64 : gx);
+  constexpr int kMaxRows = 65535;  // grid y limit
+  for (int j0 = 0; j0 < n_list; j0 += kMaxRows) {
+    const int rows = n_list - j0 < kMaxRows ? n_list - j0 : kMaxRows;
+    geometry_inputs_kernel<<<dim3(gx, rows), 256, 0, st>>>(d_insts, d_ids + j0, d_what + j0, parity,
+                                                           d_flags, bit);
   }
-}
-
-int launch_convert_force(int prec, const double* d_src, void* d_dst, int n, int stride,
-                         void* stream) {
-  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
-  if (blocks <= 0) return 0;
-  if (prec == 0)
-    convert_force_kernel<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(d_src, (double*)d_dst,
-                                                                          n, stride);
-  else if (prec == 2)
-    convert_force_kernel<df32><<<blocks, 256, 0, (cudaStream_t)stream>>>(d_src, (df32*)d_dst, n,
-                                                                        stride);
-  else
-    convert_force_kernel<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(d_src, (float*)d_dst, n,
-                                                                         stride);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 
