@@ -370,9 +370,11 @@ int lbve_adjoint_workspace_bytes_interval(lbve_handle* h, int32_t inst, int64_t 
  * (the reverse of each stage of the coupled step of Secs. 3.1-3.3: collisions,
  * source, finite-difference gradients, Zou-He and CNEBB completions, pull
  * streaming) with sqrt(n_steps) checkpointing and recomputation.
- * Instances open in x are refused (LBVE_ERR_GEOMETRY), and so are models
- * other than Oldroyd-B and the eq_p_G form (LBVE_ERR_ARG); a solid mask is
- * covered (see lbve_adjoint_step_ex).
+ * Open channels (Sec. 4.3 set-up) are covered: the inlet and outlet columns'
+ * completion from the neighbouring column is reversed too, with the inlet
+ * profile held fixed.  Models other than Oldroyd-B and the eq_p_G form are
+ * refused (LBVE_ERR_ARG); a solid mask is covered (see
+ * lbve_adjoint_step_ex).
  * The trajectory is the one that lbve_set_geometry(h, inst, NULL, <current
  * force of inst>, init_fields) followed by lbve_step(n_steps) produces; the
  * forward states are recomputed in the adjoint workspace (the instance's own

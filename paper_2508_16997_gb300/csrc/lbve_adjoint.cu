@@ -37,6 +37,7 @@ static void run_pass(int pass, const InstDev* d, const AdjArgs<R>& A, int blocks
     case 0: adj_moments<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
     case 1: adj_local<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
     case 2: adj_gather<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
+    case 4: adj_column<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
     default: adj_pull<R><<<blocks, 256, 0, st>>>(d, A); break;
   }
 }

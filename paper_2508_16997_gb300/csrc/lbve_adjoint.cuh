@@ -20,7 +20,10 @@
 //               writes lambda of the hydro pulls, accumulates dL/dF
 //   adj_pull    reverse pull into lambda_t's populations
 // A fourth kernel (adj_moments) recomputes rho, u of the forward state so the
-// gather can read its neighbours.  Modes: a normal step; the final fields
+// gather can read its neighbours.  Open channels add a fifth between the
+// gather and the pull (adj_column): the inlet and outlet nodes' completed
+// populations are built from the neighbouring column, so their lambda goes
+// back to that column's pulled populations, moments and force.  Modes: a normal step; the final fields
 // (the loss enters through rho, u, A of the last step); the initial collision
 // (equilibrium populations do not depend on F; history = current values).
 #pragma once
@@ -84,6 +87,7 @@ __device__ __forceinline__ int adj_wrap(int v, int n) {
 // Node index of (x, y), x and y at most two nodes outside the domain, with
 // the periodic wraps; -1 outside a walled domain.
 __device__ __forceinline__ int adj_node(const InstDev& D, int x, int y) {
+  if (D.open_x && (x < 0 || x >= D.nx)) return -1;  // beyond the inlet / outlet
   x = adj_wrap(x, D.nx);
   if (D.periodic_y) y = adj_wrap(y, D.ny);
   else if (y < 0 || y >= D.ny) return -1;
@@ -109,8 +113,9 @@ __device__ __forceinline__ void diff_coefs(const InstDev& D, const uint8_t* M, i
     }
     return;
   }
-  const bool sp = adj_solid(M, adj_node(D, x + dx, y + dy));
-  const bool sm = adj_solid(M, adj_node(D, x - dx, y - dy));
+  // beyond an open channel's inlet or outlet column counts as blocked
+  const bool sp = adj_solid(M, adj_node(D, x + dx, y + dy)) || (dx && D.open_x && x == D.nx - 1);
+  const bool sm = adj_solid(M, adj_node(D, x - dx, y - dy)) || (dx && D.open_x && x == 0);
   if (!sp && !sm) {
     c[1] = -0.5; c[3] = 0.5;
   } else if (sp && sm) {
@@ -149,6 +154,136 @@ __device__ __forceinline__ R bouzidi(const InstDev& D, const R* X, const WallDev
   return (R)a * fb + (R)(1.0 - a) * X[(size_t)i * S + k];
 }
 
+// Open channels: the inlet (x = 0) and outlet (x = nx - 1) nodes' completed
+// populations come from the neighbouring column x_f = 1 or nx - 2, as the
+// forward column pass builds them: the neighbour's pull, Zou-He and CNEBB on
+// wall rows, its rho, u and phi, then
+//   inlet:  f = f_f + f^eq(rho_f, u_in) - f^eq(rho_f, u_f),
+//           g = g_f + g^eq(A_in, u_in) - g^eq(phi_f, u_f);
+//   outlet: f = f_f + f^eq(1, u_f) - f^eq(rho_f, u_f), g = g_f
+// (the equilibrium differences as Hermite coefficient differences).
+__device__ __forceinline__ bool adj_open_column(const InstDev& D, int x) {
+  return D.open_x && (x == 0 || x == D.nx - 1);
+}
+
+template <typename R>
+struct ColState {
+  R dp[9], d[9];        // the neighbour's pulled and completed hydro populations
+  R gp[3][9], g[3][9];  // the same for the conformation lattices
+  R post[3][3];         // the neighbour's own outgoing-to-wall slots (wall rows)
+  R Fx, Fy, rho, ux, uy;
+  R phi[3];             // delta + sum of the completed g
+  bool wb, wt;
+  int kf;               // the neighbour's node index
+};
+
+template <typename R>
+__device__ __forceinline__ void adj_column_state(const InstDev& D, const R* X, const R* force,
+                                                 int side, int y, ColState<R>& C) {
+  const int nx = D.nx, ny = D.ny, S = D.stride;
+  const bool py = D.periodic_y != 0;
+  const int xf = side == 0 ? 1 : nx - 2, rc = y * nx;
+  C.kf = rc + xf;
+  int rm, rp;
+  neighbour_rows(y, nx, ny, py, rm, rp);
+  C.wb = !py && y == 0;
+  C.wt = !py && y == ny - 1;
+  C.Fx = force ? force[C.kf] : coef<R>(D, kCoefFx);
+  C.Fy = force ? force[S + C.kf] : coef<R>(D, kCoefFy);
+  pull9<R>(X, S, rc, rm, rp, xf, xf - 1, xf + 1, C.dp);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) C.d[i] = C.dp[i];
+  if (C.wb || C.wt) zou_he<R>(C.d, C.Fx, C.Fy, C.wb);
+  HydroM<R> hm;
+  hydro_moments<R>(C.d, hm);
+  C.rho = R(1) + hm.drho;
+  C.ux = (hm.jx + R(0.5) * C.Fx) / C.rho;
+  C.uy = (hm.jy + R(0.5) * C.Fy) / C.rho;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    pull9<R>(X + (size_t)(9 + 9 * l) * S, S, rc, rm, rp, xf, xf - 1, xf + 1, C.gp[l]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) C.g[l][i] = C.gp[l][i];
+    C.post[l][0] = C.post[l][1] = C.post[l][2] = R(0);
+    if (C.wb || C.wt) {
+      const R* own = X + (size_t)(9 + 9 * l) * S + C.kf;
+      C.post[l][0] = own[(C.wb ? 4 : 2) * S];
+      C.post[l][1] = own[(C.wb ? 7 : 5) * S];
+      C.post[l][2] = own[(C.wb ? 8 : 6) * S];
+      double wi, wo;
+      cnebb<R>(C.g[l], C.post[l][0], C.post[l][1], C.post[l][2], (l == 1) ? R(0) : R(1), C.ux,
+               C.uy, C.wb, wi, wo);
+    }
+    CdeM<R> m;
+    cde_moments<R>(C.g[l], m);
+    C.phi[l] = ((l == 1) ? R(0) : R(1)) + m.dphi;
+  }
+}
+
+// The open node's completed populations from the column state.
+template <typename R>
+__device__ __forceinline__ void column_complete(const InstDev& D, int side, int y,
+                                                const ColState<R>& C, R d[9], R g[3][9]) {
+  const int ny = D.ny;
+  const R rho = C.rho, ux = C.ux, uy = C.uy;
+  R e[9];
+  if (side == 0) {
+    const double* in = D.inlet;
+    const R bx = (R)in[y], by = (R)in[ny + y];
+    reconstruct<R>(R(0), rho * (bx - ux), rho * (by - uy), rho * (bx * bx - ux * ux),
+                   rho * (by * by - uy * uy), rho * (bx * by - ux * uy),
+                   rho * (bx * bx * by - ux * ux * uy), rho * (bx * by * by - ux * uy * uy), e);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = C.d[i] + e[i];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const R phif = C.phi[l], phib = (R)in[(2 + l) * ny + y];
+      reconstruct<R>(phib - phif, phib * bx - phif * ux, phib * by - phif * uy,
+                     phib * bx * bx - phif * ux * ux, phib * by * by - phif * uy * uy,
+                     phib * bx * by - phif * ux * uy, R(0), R(0), e);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[l][i] = C.g[l][i] + e[i];
+    }
+  } else {
+    const R dr = R(1) - rho;
+    reconstruct<R>(dr, dr * ux, dr * uy, dr * ux * ux, dr * uy * uy, dr * ux * uy,
+                   dr * ux * ux * uy, dr * ux * uy * uy, e);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = C.d[i] + e[i];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[l][i] = C.g[l][i];
+  }
+}
+
+// Reverse of zou_he(): lambda of the completed populations ld (in place) to
+// lambda of the pulled ones, and the force's share.
+template <typename R>
+__device__ __forceinline__ void zou_he_T(R ld[9], R& lFx, R& lFy, bool bottom) {
+  if (bottom) {
+    // d2 = d4; d5 = d7 - h - Fx/4 - Fy/4; d6 = d8 + h + Fx/4 - Fy/4, h = (d1 - d3)/2
+    ld[4] += ld[2];
+    ld[7] += ld[5];
+    ld[8] += ld[6];
+    ld[1] += R(0.5) * (ld[6] - ld[5]);
+    ld[3] += R(0.5) * (ld[5] - ld[6]);
+    lFx += R(0.25) * (ld[6] - ld[5]);
+    lFy += R(-0.25) * (ld[5] + ld[6]);
+    ld[2] = ld[5] = ld[6] = R(0);
+  } else {
+    // d4 = d2; d7 = d5 + h + Fx/4 + Fy/4; d8 = d6 - h - Fx/4 + Fy/4
+    ld[2] += ld[4];
+    ld[5] += ld[7];
+    ld[6] += ld[8];
+    ld[1] += R(0.5) * (ld[7] - ld[8]);
+    ld[3] += R(0.5) * (ld[8] - ld[7]);
+    lFx += R(0.25) * (ld[7] - ld[8]);
+    lFy += R(0.25) * (ld[7] + ld[8]);
+    ld[4] = ld[7] = ld[8] = R(0);
+  }
+}
+
 // Forward recompute at one node: completed hydro populations (deviations),
 // force, raw moments and rho, u.  kAdjInit takes the equilibria of the
 // staged initial fields instead of a pull and completes no wall.
@@ -166,6 +301,11 @@ __device__ __forceinline__ void adj_hydro_node(const InstDev& D, const AdjArgs<R
   Fy = A.force ? A.force[S + k] : coef<R>(D, kCoefFy);
   if (MODE == kAdjInit) {
     PopSource<R, kModeInit>::hydro(A.init, S, nx, k, y * nx, rm, rp, x, xm, xp, d);
+  } else if (adj_open_column(D, x)) {
+    ColState<R> C;
+    adj_column_state<R>(D, A.X, A.force, x == 0 ? 0 : 1, y, C);
+    R g[3][9];
+    column_complete<R>(D, x == 0 ? 0 : 1, y, C, d, g);
   } else {
     pull9<R>(A.X, S, y * nx, rm, rp, x, xm, xp, d);
     if (!py && (y == 0 || y == ny - 1)) zou_he<R>(d, Fx, Fy, y == 0);
@@ -376,7 +516,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   const int x = k % nx, y = k / nx;
   const bool py = D.periodic_y != 0;
   const bool wb = !py && y == 0, wt = !py && y == ny - 1;
-  const bool walls = (MODE != kAdjInit) && (wb || wt);
+  // an open column's node takes completed populations (no wall completion)
+  const bool ocol = MODE != kAdjInit && adj_open_column(D, x);
+  const bool walls = (MODE != kAdjInit) && (wb || wt) && !ocol;
   if (A.mask && A.mask[k]) {
     // a solid node takes no part: every lambda it would carry is zero
 #pragma unroll
@@ -405,11 +547,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   R g[3][9], gp[3][9], post[3][3], pm[3][9];
   CdeM<R> cm[3];
+  if (ocol) {
+    ColState<R> C;
+    adj_column_state<R>(D, A.X, A.force, x == 0 ? 0 : 1, y, C);
+    R dd[9];
+    column_complete<R>(D, x == 0 ? 0 : 1, y, C, dd, g);
+  }
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     if (MODE == kAdjInit) {
       PopSource<R, kModeInit>::cde(A.init, l, S, nx, k, y * nx, rm, rp, x, xm, xp, g[l]);
-    } else {
+    } else if (!ocol) {
       pull9<R>(A.X + (size_t)(9 + 9 * l) * S, S, y * nx, rm, rp, x, xm, xp, g[l]);
     }
 #pragma unroll
@@ -463,7 +611,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     const R* My = A.M + 2 * S;
     // the step's difference rules (central, wall rows, next to solids)
     R G00 = R(0), G01 = R(0), dPx = R(0), G10 = R(0), G11 = R(0), dPy = R(0);
-    if (!A.mask && !wb && !wt) {
+    if (!A.mask && !wb && !wt && !adj_open_column(D, x)) {
       // central differences along both axes: the general rule's result, term
       // by term in the same order, without looking the rule up
       const int kxm = y * nx + adj_wrap(x - 1, nx), kxp = y * nx + adj_wrap(x + 1, nx);
@@ -734,7 +882,7 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   // along an axis whose difference reads this node with coefficient c
   {
     R lcx = R(0), lcy = R(0);
-    if (!A.mask && (py || (y >= 3 && y <= ny - 4))) {
+    if (!A.mask && (py || (y >= 3 && y <= ny - 4)) && !(D.open_x && (x < 3 || x > nx - 4))) {
       // every stencil reaching this node is central (no mask, no wall row
       // within two rows): the general loop's terms in the same order
       const int kxp = y * nx + adj_wrap(x + 1, nx), kxm = y * nx + adj_wrap(x - 1, nx);
@@ -758,7 +906,7 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
 #pragma unroll
       for (int j = -2; j <= 2; ++j) {
         const int xk = x - (axis == 0 ? j : 0), yk = y - (axis == 1 ? j : 0);
-        const int kk = adj_node(D, xk, yk);
+        const int kk = adj_node(D, xk, yk);  // -1 beyond a wall or an open end
         if (kk < 0 || (A.mask && A.mask[kk])) continue;
         double c[5];
         diff_coefs(D, A.mask, adj_wrap(xk, nx), kk / nx, axis, c);
@@ -791,28 +939,10 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   if (MODE != kAdjInit) {
     R ld[9];
     moments_T<R>(lm[0], lm[1], lm[2], lm[3], lm[4], lm[5], lm[6], lm[7], ld);
+    // Zou-He on wall rows; an open column's node is completed by the column
+    // pass instead (adj_column takes its lambda back to the neighbour)
     const bool wb = !py && y == 0, wt = !py && y == ny - 1;
-    if (wb) {
-      // d2 = d4; d5 = d7 - h - Fx/4 - Fy/4; d6 = d8 + h + Fx/4 - Fy/4, h = (d1 - d3)/2
-      ld[4] += ld[2];
-      ld[7] += ld[5];
-      ld[8] += ld[6];
-      ld[1] += R(0.5) * (ld[6] - ld[5]);
-      ld[3] += R(0.5) * (ld[5] - ld[6]);
-      lFx += R(0.25) * (ld[6] - ld[5]);
-      lFy += R(-0.25) * (ld[5] + ld[6]);
-      ld[2] = ld[5] = ld[6] = R(0);
-    } else if (wt) {
-      // d4 = d2; d7 = d5 + h + Fx/4 + Fy/4; d8 = d6 - h - Fx/4 + Fy/4
-      ld[2] += ld[4];
-      ld[5] += ld[7];
-      ld[6] += ld[8];
-      ld[1] += R(0.5) * (ld[7] - ld[8]);
-      ld[3] += R(0.5) * (ld[8] - ld[7]);
-      lFx += R(0.25) * (ld[7] - ld[8]);
-      lFy += R(0.25) * (ld[7] + ld[8]);
-      ld[4] = ld[7] = ld[8] = R(0);
-    }
+    if ((wb || wt) && !adj_open_column(D, x)) zou_he_T<R>(ld, lFx, lFy, wb);
     if (A.final_pass && A.widx && A.widx[k] >= 0) {
       // the loss's share of the final step's force on the solid: e_ib (f^dagger_ib +
       // f_i) over the wall links (eq_F_x); here the f_i part (the completed links)
@@ -826,6 +956,116 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   }
   A.dF[k] += (double)lFx;
   A.dF[n + k] += (double)lFy;
+}
+
+// Pass 2b (open channels, after the gather): reverse of the column pass.
+// One thread per open-column node (side, y).  The gather and the local pass
+// left there lambda of the node's completed populations; they go back to the
+// neighbour x_f's pulled populations (the unknown slots of a wall row carry
+// lambda of its own outgoing-to-wall slots, as in adj_local), and through the
+// neighbour's rho, u and phi to its moments and force.  The open node's own
+// entries are then cleared: it pulls nothing.
+template <typename R, int MODE>
+__global__ void adj_column(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
+  const InstDev& D = *Dp;
+  const int nx = D.nx, ny = D.ny, S = D.stride, n = nx * ny;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!D.open_x || t >= 2 * ny) return;
+  const int side = t / ny, y = t % ny;
+  const int kc = y * nx + (side == 0 ? 0 : nx - 1);
+  R lc[36];
+#pragma unroll
+  for (int q = 0; q < 36; ++q) {
+    lc[q] = A.lam_pulled[(size_t)q * S + kc];
+    A.lam_pulled[(size_t)q * S + kc] = R(0);
+  }
+  ColState<R> C;
+  adj_column_state<R>(D, A.X, A.force, side, y, C);
+  const R rho = C.rho, ux = C.ux, uy = C.uy;
+  R lrho = R(0), lux = R(0), luy = R(0);
+  R ld[9], lg[3][9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) ld[i] = lc[i];
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) lg[l][i] = lc[9 + 9 * l + i];
+  R b0, b1, b2, b3, b4, b5, b6, b7;
+  reconstruct_T<R>(lc, b0, b1, b2, b3, b4, b5, b6, b7);
+  if (side == 0) {
+    const double* in = D.inlet;
+    const R bx = (R)in[y], by = (R)in[ny + y];
+    // coefficients rho (b - u) ... of the hydrodynamic equilibrium difference
+    lrho += (bx - ux) * b1 + (by - uy) * b2 + (bx * bx - ux * ux) * b3 + (by * by - uy * uy) * b4 +
+            (bx * by - ux * uy) * b5 + (bx * bx * by - ux * ux * uy) * b6 +
+            (bx * by * by - ux * uy * uy) * b7;
+    lux += -rho * b1 - R(2) * rho * ux * b3 - rho * uy * b5 - R(2) * rho * ux * uy * b6 -
+           rho * uy * uy * b7;
+    luy += -rho * b2 - R(2) * rho * uy * b4 - rho * ux * b5 - rho * ux * ux * b6 -
+           R(2) * rho * ux * uy * b7;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      R m0, m1, m2, m3, m4, m5, m6, m7;
+      reconstruct_T<R>(lc + 9 + 9 * l, m0, m1, m2, m3, m4, m5, m6, m7);
+      const R phif = C.phi[l];
+      // coefficients phi_b b - phi_f u ...: d/dphi_f and d/du
+      const R lphif = -m0 - ux * m1 - uy * m2 - ux * ux * m3 - uy * uy * m4 - ux * uy * m5;
+      lux += -phif * m1 - R(2) * phif * ux * m3 - phif * uy * m5;
+      luy += -phif * m2 - R(2) * phif * uy * m4 - phif * ux * m5;
+      // phi_f = delta + sum of the completed g_f
+#pragma unroll
+      for (int i = 0; i < 9; ++i) lg[l][i] += lphif;
+    }
+  } else {
+    // coefficients (1 - rho) (1, u, u u, u u u) of the outlet's difference
+    const R dr = R(1) - rho;
+    const R ldr = b0 + ux * b1 + uy * b2 + ux * ux * b3 + uy * uy * b4 + ux * uy * b5 +
+                  ux * ux * uy * b6 + ux * uy * uy * b7;
+    lrho += -ldr;
+    lux += dr * (b1 + R(2) * ux * b3 + uy * b5 + R(2) * ux * uy * b6 + uy * uy * b7);
+    luy += dr * (b2 + R(2) * uy * b4 + ux * b5 + ux * ux * b6 + R(2) * ux * uy * b7);
+  }
+  // the neighbour's CNEBB on wall rows (u_b = its u)
+  R lgp[3][9];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    if (C.wb || C.wt) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) lgp[l][i] = R(0);
+      R lpost[3] = {R(0), R(0), R(0)};
+      cnebb_T<R>(C.gp[l], C.post[l][0], C.post[l][1], C.post[l][2], (l == 1) ? R(0) : R(1), ux,
+                 uy, C.wb, lg[l], lgp[l], lpost, lux, luy);
+      if (C.wb) {  // U = {2, 5, 6} <- H = {4, 7, 8}
+        lgp[l][2] = lpost[0];
+        lgp[l][5] = lpost[1];
+        lgp[l][6] = lpost[2];
+      } else {     // U = {4, 7, 8} <- H = {2, 5, 6}
+        lgp[l][4] = lpost[0];
+        lgp[l][7] = lpost[1];
+        lgp[l][8] = lpost[2];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) lgp[l][i] = lg[l][i];
+    }
+  }
+  // u = (j + F/2) / rho, rho = 1 + drho, moments of the completed d_f
+  R lFx = R(0.5) * lux / rho, lFy = R(0.5) * luy / rho;
+  R lm[9];
+  moments_T<R>(lrho - (ux * lux + uy * luy) / rho, lux / rho, luy / rho, R(0), R(0), R(0), R(0),
+               R(0), lm);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) ld[i] += lm[i];
+  if (C.wb || C.wt) zou_he_T<R>(ld, lFx, lFy, C.wb);
+  const int kf = C.kf;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) A.lam_pulled[(size_t)i * S + kf] += ld[i];
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) A.lam_pulled[(size_t)(9 + 9 * l + i) * S + kf] += lgp[l][i];
+  A.dF[kf] += (double)lFx;
+  A.dF[n + kf] += (double)lFy;
 }
 
 // Pass 3: reverse pull.  lambda_t(y, i) = lambda_pulled(y + e_i, i).  A
@@ -865,7 +1105,9 @@ __global__ void adj_pull(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
       const int kd = adj_node(D, x + aex(i), y + aey(i));
       const R* lp = A.lam_pulled + (size_t)(9 * l) * S;
       R v = R(0);
-      if (kd >= 0 && !(A.mask && A.mask[kd])) {
+      if (D.open_x && (x + aex(i) < 0 || x + aex(i) >= D.nx)) {
+        // leaves through the inlet or outlet: pulled by nobody
+      } else if (kd >= 0 && !(A.mask && A.mask[kd])) {
         v = lp[(size_t)i * S + kd];
       } else if (l > 0) {
         v = lp[(size_t)aopp(i) * S + k];  // CNEBB's own slot

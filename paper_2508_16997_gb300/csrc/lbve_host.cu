@@ -1551,6 +1551,7 @@ struct AdjPlan {
   // records and final-step records, each node's record, the masked tiles
   int nwall, nmtiles;
   size_t off_scratch, off_walls, off_wrec, off_widx, off_mtiles;
+  size_t off_cols;  // open channels: the column tasks of the instance (2 ny)
 };
 
 // The square-root checkpoint interval: ceil(sqrt(T)).
@@ -1594,14 +1595,15 @@ AdjPlan make_adj_plan(const lbve_params& p, const InstPlan& q, int64_t T, int nw
   a.off_mh = take(8 * plane);
   a.off_M = take(3 * plane);
   a.off_zero = take(sizeof(double) * 6 * q.stride);
-  a.off_scratch = a.off_walls = a.off_wrec = a.off_widx = a.off_mtiles = off;
+  a.off_scratch = a.off_walls = a.off_wrec = a.off_widx = a.off_mtiles = a.off_cols = off;
   if (nwall > 0) {
     a.off_scratch = take(36 * plane);
     a.off_walls = take(sizeof(WallDev) * nwall);
     a.off_wrec = take(sizeof(double) * kWallRec * nwall);
     a.off_widx = take(sizeof(int32_t) * q.stride);
-    a.off_mtiles = take(sizeof(TileDev) * std::max(nmtiles, 1));
   }
+  if (nmtiles > 0) a.off_mtiles = take(sizeof(TileDev) * nmtiles);
+  if (p.open_x) a.off_cols = take(sizeof(ColTask) * 2 * size_t(p.ny));
   a.total = off;
   return a;
 }
@@ -1638,8 +1640,6 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
     return set_error(LBVE_ERR_ARG, "bad handle, instance, pointer or step count");
   if (!d_dL_dfields && !dL_ddrag) return set_error(LBVE_ERR_ARG, "no loss: dL/dfields and dL/ddrag are null");
   if (!h->ready[inst]) return set_error(LBVE_ERR_STATE, "instance %d was never initialised", inst);
-  if (h->p[inst].open_x)
-    return set_error(LBVE_ERR_GEOMETRY, "the adjoint does not cover open channels (instance %d)", inst);
   if (h->p[inst].model != 0 || h->p[inst].gtilde != 0)
     return set_error(LBVE_ERR_ARG, "the adjoint covers Oldroyd-B with eq_p_G_1 only (instance %d)",
                 inst);
@@ -1647,6 +1647,7 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
     return set_error(LBVE_ERR_ARG,
                      "the adjoint covers LBVE_FP64 and LBVE_FP32_DEV instances (instance %d)", inst);
   const bool masked = h->insts[inst].mask != nullptr;
+  const bool open = h->p[inst].open_x != 0;
   if (!masked && (dL_ddrag || d_dL_dq))
     return set_error(LBVE_ERR_GEOMETRY, "drag and wall-fraction gradients need a solid mask");
   if (dL_ddrag && !(std::isfinite(dL_ddrag[0]) && std::isfinite(dL_ddrag[1])))
@@ -1657,7 +1658,9 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
   const std::vector<TileDev>& mtiles_h = h->mtiles_of[inst];
   // the shortest checkpoint interval whose plan fits the workspace given
   // (the square-root interval needs the least)
-  const int nw = masked ? (int)walls_h.size() : 0, nm = masked ? (int)mtiles_h.size() : 0;
+  // masked tiles: those of a mask and of an open channel's columns
+  const int nw = masked ? (int)walls_h.size() : 0;
+  const int nm = (masked || open) ? (int)mtiles_h.size() : 0;
   const int64_t s_max = sqrt_interval(n_steps);
   AdjPlan a = make_adj_plan(p, q, n_steps, nw, nm, s_max);
   for (int64_t s = 1; s < s_max; ++s) {
@@ -1690,7 +1693,7 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
   for (int ty = 0, k = 0; ty < q.nty; ++ty)
     for (int tx = 0; tx < q.ntx; ++tx, ++k) {
       // the handle's masked flags of this instance's tiles (same order)
-      const int mk = masked ? h->tiles_h[q.list][q.tile_begin + k].masked : 0;
+      const int mk = (masked || open) ? h->tiles_h[q.list][q.tile_begin + k].masked : 0;
       tiles[k] = TileDev{0, tx * q.TX, ty * q.TY, k, mk};
       if (mk) mtiles.push_back(tiles[k]);
     }
@@ -1707,6 +1710,20 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
   char* scratch = ws + a.off_scratch;
   std::vector<WallDev> wcopy;
   std::vector<int32_t> widx;
+  if (open) {
+    // the column pass of instance 0 (the inlet profile is the instance's)
+    std::vector<ColTask> cols(2 * size_t(p.ny));
+    for (int side = 0; side < 2; ++side)
+      for (int y = 0; y < p.ny; ++y) cols[side * p.ny + y] = ColTask{0, y, side, 0};
+    e = cudaMemcpyAsync(ws + a.off_cols, cols.data(), sizeof(ColTask) * cols.size(),
+                        cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint column tasks");
+    if (!mtiles.empty() && !masked) {
+      e = cudaMemcpyAsync(ws + a.off_mtiles, mtiles.data(), sizeof(TileDev) * mtiles.size(),
+                          cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "adjoint masked tiles");
+    }
+  }
   if (masked) {
     wcopy = walls_h;
     widx.assign(q.stride, -1);
@@ -1781,6 +1798,8 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
         launch_wall(prec, d_desc, d_walls, (double*)(ws + a.off_wrec), (int)wcopy.size(), 0, 0,
                     st))
       return cuda_fail(cudaGetLastError(), "adjoint wall pass");
+    if (open && launch_column(prec, d_desc, (const ColTask*)(ws + a.off_cols), 2 * p.ny, 0, st))
+      return cuda_fail(cudaGetLastError(), "adjoint column pass");
     if (!launch_tiles(kModeStep, 0)) return cuda_fail(cudaGetLastError(), "adjoint forward step");
     return LBVE_OK;
   };
@@ -1878,6 +1897,8 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
       int rc = pass(mode, 0);
       if (!rc) rc = pass(mode, 1);
       if (!rc) rc = pass(mode, 2);
+      if (!rc && open && launch_adjoint(prec, mode, 4, d_desc, A, 2 * p.ny, st))
+        rc = cuda_fail(cudaGetLastError(), "adjoint column reverse launch");
       if (!rc) rc = pass(mode, 3);
       if (rc) return rc;
       li ^= 1;

@@ -180,8 +180,9 @@ struct AdjArgsRaw {
   double drag_w[2];
   int final_pass;
 };
-// pass: 0 moments, 1 local reverse, 2 gather, 3 reverse pull; mode: kAdjStep,
-// kAdjFields, kAdjInit (lbve_adjoint.cuh).
+// pass: 0 moments, 1 local reverse, 2 gather, 3 reverse pull, 4 reverse of an
+// open channel's column pass (n_nodes = 2 ny: one thread per open-column
+// node); mode: kAdjStep, kAdjFields, kAdjInit (lbve_adjoint.cuh).
 int launch_adjoint(int prec, int mode, int pass, const InstDev* d_desc, const AdjArgsRaw& a,
                    int n_nodes, void* stream);
 // Totals of n_insts instances: ids[0..n_insts-1] (device), or first_inst..
