@@ -168,7 +168,7 @@ def measured_peaks():
 def kernel_sources_sha256() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("lbve_step.cuh", "lbve_kernels.cu", "lbve_internal.h"):
+    for f in ("lbve_step.cuh", "lbve_df32.cuh", "lbve_kernels.cu", "lbve_internal.h"):
         with open(os.path.join(ROOT, "paper_2508_16997_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

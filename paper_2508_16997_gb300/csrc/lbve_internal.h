@@ -85,38 +85,45 @@ enum : int {
 // Everything a CTA needs about its instance.  Pointers are device addresses
 // inside the caller's workspace.  Coefficients are derived in float64 on
 // the host (Sec. 3.1-3.2 relaxation-time relations) and rounded once.
-struct InstDev {
+// Layout: 16-byte aligned, the fields the step kernel reads first (buffers,
+// geometry, flags, float32 coefficients) in the leading 16-byte groups, so
+// that each CTA's prologue loads them as a few 16-byte vectors.
+struct alignas(16) InstDev {
   void* pop[2];        // [36][stride] post-collision populations, ping-pong
   void* hist;          // [5][stride]  S_xx, S_xy, S_yy, ux, uy of the last step
   void* force;         // [2][stride]  per-node body force (if force_field)
-  double* fields;      // [6][stride]  rho, ux, uy, Axx, Axy, Ayy (float64)
   int32_t nx, ny, stride, periodic_y;
   int32_t TX, TY, hy, force_field;
-  int32_t slot_begin, slot_end;  // partial-record slots of this instance
-  int32_t prec, wall_cap;        // wall_cap: wall-node records of this instance
-  const uint8_t* mask;           // [stride] 1 = solid node, or null (no mask)
-  double* wall_rec;              // [wall_cap][kWallRec] final-step wall sums
-  int32_t open_x;                // inlet column x = 0, outlet x = nx - 1
   int32_t t32;                   // tiles are kTileTX wide and rows wrap at most once
                                  // inside a tile's halo region (plain tiles specialise)
+  int32_t open_x;                // inlet column x = 0, outlet x = nx - 1
   int32_t model, gtilde;         // constitutive model (0 Oldroyd-B, 1 FENE-P, 2 FENE-CR);
                                  // G~ form (0 eq_p_G_1, 1 eq_p_G)
+  int32_t slot_begin, slot_end;  // partial-record slots of this instance
+  int32_t prec, wall_cap;        // wall_cap: wall-node records of this instance
+  // Collision coefficients rounded once to float32 (cf), their float64
+  // values (cd) and the low parts of the LBVE_DF32 pairs (cl = cd - cf), so
+  // that no kernel converts precision per node.
+  float cf[16];
+  double* fields;                // [6][stride]  rho, ux, uy, Axx, Axy, Ayy (float64)
+  const uint8_t* mask;           // [stride] 1 = solid node, or null (no mask)
+  double* wall_rec;              // [wall_cap][kWallRec] final-step wall sums
   void* colbuf;                  // [36][2 ny] completed populations of the two open
                                  // columns (inlet rows, then outlet rows), deviations
   const double* inlet;           // [5][ny] u_x, u_y, A_xx, A_xy, A_yy at the inlet
   double inv_Uc;
-  // Collision coefficients, in float64 and rounded once to float32, so that
-  // neither kernel converts precision per node.
   double cd[16];
-  float cf[16];
-  float cl[16];  // cd - cf rounded to float32: the low parts of LBVE_DF32 pairs
+  float cl[16];
 };
+static_assert(sizeof(InstDev) % 16 == 0, "descriptor size");
 
 // One tile of one instance: {instance, x0, y0, partial slot, masked}.
 // masked: the tile holds a solid node or a node with a solid neighbour along
 // x or y; such tiles are run by the masked variant of the step kernel.
-struct TileDev {
-  int32_t inst, x0, y0, slot, masked;
+// Padded to 32 bytes and aligned to 16, so that a CTA reads its entry with
+// vector loads.
+struct alignas(16) TileDev {
+  int32_t inst, x0, y0, slot, masked, pad0, pad1, pad2;
 };
 
 // One fluid node next to the solid mask (the compact link list of the wall
