@@ -31,23 +31,33 @@ static AdjArgs<R> cast_args(const AdjArgsRaw& a) {
   return A;
 }
 
-template <typename R, int MODE>
+// OPEN: the node passes' variant with an open channel's inlet and outlet
+// columns (one-sided x-differences there in every mode, the column pass's
+// completion in the step modes).
+template <typename R, int MODE, bool OPEN>
 static void run_pass(int pass, const InstDev* d, const AdjArgs<R>& A, int blocks, cudaStream_t st) {
   switch (pass) {
-    case 0: adj_moments<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
-    case 1: adj_local<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
-    case 2: adj_gather<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
+    case 0: adj_moments<R, MODE, OPEN><<<blocks, 256, 0, st>>>(d, A); break;
+    case 1: adj_local<R, MODE, OPEN><<<blocks, 256, 0, st>>>(d, A); break;
+    case 2: adj_gather<R, MODE, OPEN><<<blocks, 256, 0, st>>>(d, A); break;
     case 4: adj_column<R, MODE><<<blocks, 256, 0, st>>>(d, A); break;
     default: adj_pull<R><<<blocks, 256, 0, st>>>(d, A); break;
   }
 }
 
 template <typename R>
-static void run_mode(int mode, int pass, const InstDev* d, const AdjArgs<R>& A, int blocks,
-                     cudaStream_t st) {
-  if (mode == kAdjStep) run_pass<R, kAdjStep>(pass, d, A, blocks, st);
-  else if (mode == kAdjFields) run_pass<R, kAdjFields>(pass, d, A, blocks, st);
-  else run_pass<R, kAdjInit>(pass, d, A, blocks, st);
+static void run_mode(int mode, int pass, bool open, const InstDev* d, const AdjArgs<R>& A,
+                     int blocks, cudaStream_t st) {
+  if (mode == kAdjStep) {
+    if (open) run_pass<R, kAdjStep, true>(pass, d, A, blocks, st);
+    else run_pass<R, kAdjStep, false>(pass, d, A, blocks, st);
+  } else if (mode == kAdjFields) {
+    if (open) run_pass<R, kAdjFields, true>(pass, d, A, blocks, st);
+    else run_pass<R, kAdjFields, false>(pass, d, A, blocks, st);
+  } else {
+    if (open) run_pass<R, kAdjInit, true>(pass, d, A, blocks, st);
+    else run_pass<R, kAdjInit, false>(pass, d, A, blocks, st);
+  }
 }
 
 int launch_adjoint(int prec, int mode, int pass, const InstDev* d_desc, const AdjArgsRaw& a,
@@ -55,8 +65,9 @@ int launch_adjoint(int prec, int mode, int pass, const InstDev* d_desc, const Ad
   const int blocks = (n_nodes + 255) / 256;
   if (blocks <= 0) return 0;
   cudaStream_t st = (cudaStream_t)stream;
-  if (prec == 0) run_mode<double>(mode, pass, d_desc, cast_args<double>(a), blocks, st);
-  else run_mode<float>(mode, pass, d_desc, cast_args<float>(a), blocks, st);
+  const bool open = a.open != 0;
+  if (prec == 0) run_mode<double>(mode, pass, open, d_desc, cast_args<double>(a), blocks, st);
+  else run_mode<float>(mode, pass, open, d_desc, cast_args<float>(a), blocks, st);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 

@@ -86,8 +86,11 @@ __device__ __forceinline__ int adj_wrap(int v, int n) {
 
 // Node index of (x, y), x and y at most two nodes outside the domain, with
 // the periodic wraps; -1 outside a walled domain.
+// In an open channel x still wraps: the wrapped node is the far open column,
+// whose lambda of pulled populations adj_column has cleared and whose
+// difference coefficients toward the wrap are zero, so nothing flows
+// through the open ends.
 __device__ __forceinline__ int adj_node(const InstDev& D, int x, int y) {
-  if (D.open_x && (x < 0 || x >= D.nx)) return -1;  // beyond the inlet / outlet
   x = adj_wrap(x, D.nx);
   if (D.periodic_y) y = adj_wrap(y, D.ny);
   else if (y < 0 || y >= D.ny) return -1;
@@ -287,7 +290,7 @@ __device__ __forceinline__ void zou_he_T(R ld[9], R& lFx, R& lFy, bool bottom) {
 // Forward recompute at one node: completed hydro populations (deviations),
 // force, raw moments and rho, u.  kAdjInit takes the equilibria of the
 // staged initial fields instead of a pull and completes no wall.
-template <typename R, int MODE>
+template <typename R, int MODE, bool OPEN>
 __device__ __forceinline__ void adj_hydro_node(const InstDev& D, const AdjArgs<R>& A, int x, int y,
                                                R d[9], R& Fx, R& Fy, HydroM<R>& hm, R& rho, R& ux,
                                                R& uy) {
@@ -301,7 +304,7 @@ __device__ __forceinline__ void adj_hydro_node(const InstDev& D, const AdjArgs<R
   Fy = A.force ? A.force[S + k] : coef<R>(D, kCoefFy);
   if (MODE == kAdjInit) {
     PopSource<R, kModeInit>::hydro(A.init, S, nx, k, y * nx, rm, rp, x, xm, xp, d);
-  } else if (adj_open_column(D, x)) {
+  } else if (OPEN && adj_open_column(D, x)) {
     ColState<R> C;
     adj_column_state<R>(D, A.X, A.force, x == 0 ? 0 : 1, y, C);
     R g[3][9];
@@ -324,7 +327,7 @@ __device__ __forceinline__ void adj_hydro_node(const InstDev& D, const AdjArgs<R
 }
 
 // rho, u of every node of the forward state (for the neighbours' gradients).
-template <typename R, int MODE>
+template <typename R, int MODE, bool OPEN>
 __global__ void adj_moments(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   const InstDev& D = *Dp;
   const int n = D.nx * D.ny;
@@ -338,7 +341,7 @@ __global__ void adj_moments(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   }
   R d[9], Fx, Fy, rho, ux, uy;
   HydroM<R> hm;
-  adj_hydro_node<R, MODE>(D, A, x, y, d, Fx, Fy, hm, rho, ux, uy);
+  adj_hydro_node<R, MODE, OPEN>(D, A, x, y, d, Fx, Fy, hm, rho, ux, uy);
   A.M[k] = rho;
   A.M[S + k] = ux;
   A.M[2 * S + k] = uy;
@@ -506,7 +509,7 @@ __device__ __forceinline__ void cnebb_mask_T(const R gp[9], const R pm[9], R del
 // Pass 1: local reverse of the collision, source, history and CNEBB.
 // float32: a budget of 128 registers (two CTAs per SM) trades a few spills
 // for twice the warps in flight; float64 keeps its full register file.
-template <typename R, int MODE>
+template <typename R, int MODE, bool OPEN>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     adj_local(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   const InstDev& D = *Dp;
@@ -517,7 +520,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   const bool py = D.periodic_y != 0;
   const bool wb = !py && y == 0, wt = !py && y == ny - 1;
   // an open column's node takes completed populations (no wall completion)
-  const bool ocol = MODE != kAdjInit && adj_open_column(D, x);
+  const bool ocol = OPEN && MODE != kAdjInit && adj_open_column(D, x);
   const bool walls = (MODE != kAdjInit) && (wb || wt) && !ocol;
   if (A.mask && A.mask[k]) {
     // a solid node takes no part: every lambda it would carry is zero
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   // ---- forward recompute ----
   R d[9], Fx, Fy, rho, ux, uy;
   HydroM<R> hm;
-  adj_hydro_node<R, MODE>(D, A, x, y, d, Fx, Fy, hm, rho, ux, uy);
+  adj_hydro_node<R, MODE, OPEN>(D, A, x, y, d, Fx, Fy, hm, rho, ux, uy);
   int rm, rp;
   neighbour_rows(y, nx, ny, py, rm, rp);
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
@@ -611,7 +614,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     const R* My = A.M + 2 * S;
     // the step's difference rules (central, wall rows, next to solids)
     R G00 = R(0), G01 = R(0), dPx = R(0), G10 = R(0), G11 = R(0), dPy = R(0);
-    if (!A.mask && !wb && !wt && !adj_open_column(D, x)) {
+    if (!A.mask && !wb && !wt && !(OPEN && adj_open_column(D, x))) {
       // central differences along both axes: the general rule's result, term
       // by term in the same order, without looking the rule up
       const int kxm = y * nx + adj_wrap(x - 1, nx), kxp = y * nx + adj_wrap(x + 1, nx);
@@ -863,7 +866,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
 // Pass 2: gather the transposed gradient stencils, reverse u = (j + F/2)/rho
 // and the hydro moments, reverse Zou-He; writes lambda of the hydro pulls and
 // accumulates dL/dF.
-template <typename R, int MODE>
+template <typename R, int MODE, bool OPEN>
 __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   const InstDev& D = *Dp;
   const int nx = D.nx, ny = D.ny, S = D.stride, n = nx * ny;
@@ -882,7 +885,7 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   // along an axis whose difference reads this node with coefficient c
   {
     R lcx = R(0), lcy = R(0);
-    if (!A.mask && (py || (y >= 3 && y <= ny - 4)) && !(D.open_x && (x < 3 || x > nx - 4))) {
+    if (!A.mask && (py || (y >= 3 && y <= ny - 4)) && !(OPEN && (x < 3 || x > nx - 4))) {
       // every stencil reaching this node is central (no mask, no wall row
       // within two rows): the general loop's terms in the same order
       const int kxp = y * nx + adj_wrap(x + 1, nx), kxm = y * nx + adj_wrap(x - 1, nx);
@@ -906,7 +909,7 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
 #pragma unroll
       for (int j = -2; j <= 2; ++j) {
         const int xk = x - (axis == 0 ? j : 0), yk = y - (axis == 1 ? j : 0);
-        const int kk = adj_node(D, xk, yk);  // -1 beyond a wall or an open end
+        const int kk = adj_node(D, xk, yk);
         if (kk < 0 || (A.mask && A.mask[kk])) continue;
         double c[5];
         diff_coefs(D, A.mask, adj_wrap(xk, nx), kk / nx, axis, c);
@@ -942,7 +945,7 @@ __global__ void adj_gather(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
     // Zou-He on wall rows; an open column's node is completed by the column
     // pass instead (adj_column takes its lambda back to the neighbour)
     const bool wb = !py && y == 0, wt = !py && y == ny - 1;
-    if ((wb || wt) && !adj_open_column(D, x)) zou_he_T<R>(ld, lFx, lFy, wb);
+    if ((wb || wt) && !(OPEN && adj_open_column(D, x))) zou_he_T<R>(ld, lFx, lFy, wb);
     if (A.final_pass && A.widx && A.widx[k] >= 0) {
       // the loss's share of the final step's force on the solid: e_ib (f^dagger_ib +
       // f_i) over the wall links (eq_F_x); here the f_i part (the completed links)
@@ -1079,7 +1082,8 @@ __global__ void adj_column(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
 // The interpolation's other operands add 1 - 1/(2q) (the own post in the
 // same direction, q >= 1/2) and 1 - 2q (the next node's post, q < 1/2), and
 // each wall link adds lambda of its completed population times dv/dq to
-// dL/dq.
+// dL/dq.  A population that leaves an open channel through its inlet or
+// outlet reads the (cleared) entries of the far open column: zero.
 template <typename R>
 __global__ void adj_pull(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
   const InstDev& D = *Dp;
@@ -1105,9 +1109,7 @@ __global__ void adj_pull(const InstDev* __restrict__ Dp, AdjArgs<R> A) {
       const int kd = adj_node(D, x + aex(i), y + aey(i));
       const R* lp = A.lam_pulled + (size_t)(9 * l) * S;
       R v = R(0);
-      if (D.open_x && (x + aex(i) < 0 || x + aex(i) >= D.nx)) {
-        // leaves through the inlet or outlet: pulled by nobody
-      } else if (kd >= 0 && !(A.mask && A.mask[kd])) {
+      if (kd >= 0 && !(A.mask && A.mask[kd])) {
         v = lp[(size_t)i * S + kd];
       } else if (l > 0) {
         v = lp[(size_t)aopp(i) * S + k];  // CNEBB's own slot

@@ -1846,6 +1846,7 @@ extern "C" int lbve_adjoint_step_ex(lbve_handle* h, int32_t inst, const double* 
     A.drag_w[0] = dL_ddrag[0];
     A.drag_w[1] = dL_ddrag[1];
   }
+  A.open = open ? 1 : 0;
   // without a field loss the final pass reads zeros
   const double* fields_seed = d_dL_dfields;
   if (!fields_seed) {

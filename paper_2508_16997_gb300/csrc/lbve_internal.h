@@ -186,6 +186,7 @@ struct AdjArgsRaw {
   double* dq;
   double drag_w[2];
   int final_pass;
+  int open;  // open channel: the node passes are the variants with the open columns
 };
 // pass: 0 moments, 1 local reverse, 2 gather, 3 reverse pull, 4 reverse of an
 // open channel's column pass (n_nodes = 2 ny: one thread per open-column
