@@ -930,12 +930,20 @@ static int init_geometry(lbve_handle* h, int32_t n, const int32_t* ids, const in
     ++in_list[h->plan.inst[ids[j]].list];
   }
   for (int i = 0; i < h->n; ++i) ++of_list[h->plan.inst[i].list];
-  // pageable sources: both copies are staged before the calls return
+  // pageable sources: the copies are staged before the calls return.  The
+  // descriptors go up as one array when the list covers much of the handle,
+  // else one by one (a single instance of a large batch moves 400 bytes)
   cudaError_t e = cudaMemcpyAsync(h->d_geo, geo.data(), sizeof(int32_t) * geo.size(),
                                   cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->d_insts, h->insts.data(), sizeof(InstDev) * h->n,
-                        cudaMemcpyHostToDevice, h->stream);
+  if ((size_t)n * 8 >= (size_t)h->n) {
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->d_insts, h->insts.data(), sizeof(InstDev) * h->n,
+                          cudaMemcpyHostToDevice, h->stream);
+  } else {
+    for (int32_t j = 0; j < n && e == cudaSuccess; ++j)
+      e = cudaMemcpyAsync(h->d_insts + ids[j], &h->insts[ids[j]], sizeof(InstDev),
+                          cudaMemcpyHostToDevice, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "geometry list upload");
   const int P = h->parity;
   if (launch_geometry_inputs(h->d_insts, h->d_geo, h->d_geo + n, n, max_nodes, P, h->d_flags,

@@ -143,3 +143,24 @@ def test_fields_many_equals_single_calls(lbve, on_device):
     assert e.value.code == lbve.LBVE_ERR_ARG
     torch.cuda.synchronize()
     assert bool((outs[0] == -7.0).all())
+
+
+def test_single_instance_set_geometry_in_a_large_batch(lbve):
+    """lbve_set_geometry on one instance of a twelve-instance handle (its
+    descriptor goes up alone) resets exactly that instance: it then evolves
+    as in a handle created with the same initial fields, and its neighbours
+    in the batch continue undisturbed."""
+    insts = [wl.frm(12 + (j % 3), Wi=1.0 + j, Re=1.0, Ma=0.05) for j in range(12)]
+    init5 = wl.random_fields(insts[5].nx, insts[5].ny, seed=55)
+    a = lbve.Simulation(insts, precision=0)
+    a.step(3)
+    lbve.lbve_set_geometry(a.h, 5, None, insts[5].force_field, init5, n_nodes=insts[5].n_nodes)
+    assert a.time(5) == 0 and a.time(4) == 3
+    a.step(7)
+    b = lbve.Simulation(insts, precision=0,
+                        init_fields=[init5 if j == 5 else None for j in range(12)])
+    b.step(7)
+    np.testing.assert_array_equal(a.fields(5), b.fields(5))
+    b.step(3)
+    for j in (4, 6, 11):
+        np.testing.assert_array_equal(a.fields(j), b.fields(j))
