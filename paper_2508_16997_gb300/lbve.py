@@ -191,8 +191,12 @@ def lbve_set_geometry_many(h, insts, solid_masks=None, body_forces=None, init_fi
     if not (len(masks) == len(forces) == len(inits) == n):
         raise ValueError("the lists must have one entry per instance")
     masks = [None if m is None else np.ascontiguousarray(m, dtype=np.uint8) for m in masks]
-    forces = [None if f is None else _f64(f, 2 * n_nodes[j])[0] for j, f in enumerate(forces)]
-    inits = [None if a is None else _f64(a, 6 * n_nodes[j])[0] for j, a in enumerate(inits)]
+
+    def planes(a, j, k):  # float64, contiguous, k planes of n_nodes[j] values (if given)
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        return a if n_nodes is None else _f64(a, k * n_nodes[j])[0]
+    forces = [None if f is None else planes(f, j, 2) for j, f in enumerate(forces)]
+    inits = [None if a is None else planes(a, j, 6) for j, a in enumerate(inits)]
     pm, pf, pi = _ptr_list(masks), _ptr_list(forces), _ptr_list(inits)
     _check(load().lbve_set_geometry_many(h, n, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                          pm, pf, pi), "lbve_set_geometry_many")
