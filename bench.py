@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--cylinder-steps", type=int, default=2000)
     ap.add_argument("--frm64-steps", type=int, default=2000)
+    ap.add_argument("--frm-large-steps", type=int, default=20,
+                    help="timed steps of the four-roll mill at 2048^2 and 4096^2 (0: skip)")
     ap.add_argument("--error-steps", type=int, default=2000)
     return ap.parse_args()
 
@@ -637,6 +639,11 @@ def run_ours(args):
     if args.frm64_steps > 0:
         c1, c1_fields = bench_frm64(args.frm64_steps, stream)
 
+    # ---- the same four-roll mill on large grids: roofline of one instance --
+    frm_large = None
+    if args.frm_large_steps > 0:
+        frm_large = bench_frm_large(args.frm_large_steps, stream)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -696,6 +703,8 @@ def run_ours(args):
         line["cylinder"] = cyl
     if c1 is not None:
         line["frm64"] = c1
+    if frm_large is not None:
+        line["frm_large"] = frm_large
     if world == 1 and not args.no_cpu_baseline:
         sample, nodes = cpu_sample(insts, 50000)
         steps_cpu = 200
@@ -763,6 +772,46 @@ def bench_frm64(steps: int, stream):
            "unit": UNIT, "ms": ms, "us_per_step": ms * 1e3 / steps,
            "finite": not bool(sim.status()[0])}
     return out, fields
+
+
+def bench_frm_large(steps: int, stream) -> dict:
+    """The small configuration's four-roll mill (beta 0.5, Wi 5, Re 0.01,
+    Sc 1e5, Ma 1e-3) on 2048^2 and 4096^2 grids, one instance per handle, in
+    FP32 deviations and FP64: per-launch step-kernel time (lbve_profile) over
+    `steps` ordinary steps after a warm-up, MLUPS, and the kernel against its
+    bound (HBM for FP32, the FP64 pipe for FP64)."""
+    import torch
+    from paper_2508_16997_gb300 import lbve, workloads as wl
+    peak, peak_kind = measured_peaks()
+    out = {"workload": "four-roll mill N^2, beta 0.5, Wi 5, Re 0.01, Sc 1e5, Ma 1e-3, from rest",
+           "steps": steps}
+    for N in (2048, 4096):
+        inst = wl.frm(N)
+        row = {}
+        for name, prec in (("fp32", lbve.LBVE_FP32_DEV), ("fp64", lbve.LBVE_FP64)):
+            sim = lbve.Simulation([inst], precision=prec)
+            sim.step(5)
+            torch.cuda.synchronize()
+            lbve.lbve_profile(sim.h, steps + 1)
+            sim.step(steps + 1)  # steps ordinary launches, then the final one
+            n, tot, lo, hi = lbve.lbve_profile_read(sim.h, prec)
+            lbve.lbve_profile(sim.h, 0)
+            kms = tot / max(n, 1)
+            mlups = inst.n_nodes / (kms / 1e3) / 1e6
+            r = {"kernel_ms": kms, "kernel_ms_min": lo, "kernel_ms_max": hi, "launches": n,
+                 "MLUPS": mlups, "finite": not bool(sim.status()[0])}
+            if prec == lbve.LBVE_FP32_DEV:
+                b = inst.n_nodes * bytes_per_lu(inst, 4)
+                r["roofline"] = {"bound": "hbm", "achieved": b / (kms / 1e3) / 1e9, "peak": peak,
+                                 "unit": "GB/s", "frac": b / (kms / 1e3) / 1e9 / peak,
+                                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": b}
+            else:
+                r["roofline"] = measured_fp64_pipe(mlups)
+            row[name] = r
+            del sim
+            torch.cuda.empty_cache()
+        out[str(N)] = row
+    return out
 
 
 def bench_cylinder(steps: int, stream) -> dict:
