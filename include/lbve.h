@@ -223,7 +223,9 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
  *          entry returns LBVE_ERR_ARG before anything changes).
  * Instances are enqueued in list order.  A geometry rejected on the host or
  * a CUDA error at list position j leaves insts[j..n-1] unchanged (insts[j]
- * uninitialised after a CUDA error) and still finishes insts[0..j-1].
+ * uninitialised after a CUDA error) and still finishes insts[0..j-1]; a
+ * CUDA error in the launches that follow the uploads leaves every staged
+ * instance uninitialised.
  * Values rejected on the device (as in lbve_set_geometry) leave exactly the
  * rejected instances uninitialised; the others are set.  The return value is
  * the error of the first failing instance in list order (LBVE_OK if none),
