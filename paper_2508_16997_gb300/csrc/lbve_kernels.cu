@@ -80,48 +80,49 @@ int launch_step(int prec, int threads, const InstDev* d_insts, const TileDev* d_
 // One CTA per instance: sum (max for the residual) the partial records of the
 // instance's tiles, and the wall-pass records of its mask walls, in a fixed
 // order, so totals are bit-reproducible.  CTA b takes instance ids[b], or
-// first_inst + b without a list.
-__global__ void __launch_bounds__(256) reduce_kernel(const InstDev* __restrict__ insts,
-                                                     int first_inst,
-                                                     const int32_t* __restrict__ ids,
-                                                     const double* __restrict__ partials,
-                                                     double* __restrict__ totals,
-                                                     int32_t* __restrict__ flags) {
-  __shared__ double s[256];
+// first_inst + b without a list.  Warp j of the 16 reduces total j: each lane
+// runs over every 32nd record, then the warp folds its lanes by shuffles
+// (no block-wide barrier: GB300 issues float64 additions slowly, so the
+// sums are spread over warps instead of levels of a shared-memory tree).
+constexpr int kReduceThreads = 32 * kTotals;
+static_assert(kTotals == kDrag + 2, "one warp per total");
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const InstDev* __restrict__ insts,
+                                                                int first_inst,
+                                                                const int32_t* __restrict__ ids,
+                                                                const double* __restrict__ partials,
+                                                                double* __restrict__ totals,
+                                                                int32_t* __restrict__ flags) {
   const int inst = ids ? ids[blockIdx.x] : first_inst + blockIdx.x;
   const InstDev& D = insts[inst];
-  for (int j = 0; j < kDrag + 2; ++j) {
-    double v = 0.0;
-    if (j < kDrag)
-      for (int q = D.slot_begin + threadIdx.x; q < D.slot_end; q += blockDim.x) {
-        const double p = partials[(size_t)q * kPartial + j];
-        v = (j == kResid) ? fmax(v, p) : v + p;
-      }
-    // wall record layout: drag x, drag y, in x3, out x3
-    const int r = (j >= kDrag) ? j - kDrag : (j >= kWallIn && j < kResid) ? 2 + (j - kWallIn) : -1;
-    if (r >= 0)
-      for (int q = threadIdx.x; q < D.wall_cap; q += blockDim.x) v += D.wall_rec[(size_t)q * kWallRec + r];
-    s[threadIdx.x] = v;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w)
-        s[threadIdx.x] = (j == kResid) ? fmax(s[threadIdx.x], s[threadIdx.x + w])
-                                       : s[threadIdx.x] + s[threadIdx.x + w];
-      __syncthreads();
+  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool is_max = j == kResid;
+  double v = 0.0;
+  if (j < kDrag)
+    for (int q = D.slot_begin + lane; q < D.slot_end; q += 32) {
+      const double p = partials[(size_t)q * kPartial + j];
+      v = is_max ? fmax(v, p) : v + p;
     }
-    if (threadIdx.x == 0) {
-      totals[(size_t)inst * kTotals + j] = s[0];
-      if (j == kNonFinite && s[0] > 0.0) flags[inst] |= 1;
-    }
-    __syncthreads();
+  // wall record layout: drag x, drag y, in x3, out x3
+  const int r = (j >= kDrag) ? j - kDrag : (j >= kWallIn && j < kResid) ? 2 + (j - kWallIn) : -1;
+  if (r >= 0)
+    for (int q = lane; q < D.wall_cap; q += 32) v += D.wall_rec[(size_t)q * kWallRec + r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmax(v, w) : v + w;
+  }
+  if (lane == 0) {
+    totals[(size_t)inst * kTotals + j] = v;
+    if (j == kNonFinite && v > 0.0) flags[inst] |= 1;
   }
 }
 
 int launch_reduce(const InstDev* d_insts, int first_inst, int n_insts, const double* d_partials,
                   double* d_totals, int32_t* d_flags, void* stream, const int32_t* d_ids) {
   if (n_insts <= 0) return 0;
-  reduce_kernel<<<n_insts, 256, 0, (cudaStream_t)stream>>>(d_insts, first_inst, d_ids, d_partials,
-                                                           d_totals, d_flags);
+  reduce_kernel<<<n_insts, kReduceThreads, 0, (cudaStream_t)stream>>>(d_insts, first_inst, d_ids,
+                                                                      d_partials, d_totals,
+                                                                      d_flags);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears it
 }
 

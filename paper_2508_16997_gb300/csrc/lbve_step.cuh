@@ -773,7 +773,9 @@ __device__ __forceinline__ void fold_half_df(float* h, float* l, int o, bool up)
 // float32 instance's values are float32 numbers or exact float32 pairs
 // (part + plo), and its butterfly adds float32 pairs (a 48-bit sum; GB300
 // issues a float64 addition only every 64 cycles per warp); the warp totals
-// and everything after them are float64.
+// and everything after them are float64.  A float32 warp whose nodes carry no
+// wall balance folds only the first 6 values (the order of the sum is fixed
+// by the tile's own data, so totals stay reproducible).
 template <int NT, typename P>
 __device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T, const P* part,
                                               const P* plo, bool active,
@@ -783,23 +785,56 @@ __device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T
   static_assert(kNonFinite == 13 && kResid == 12, "12 sums, then residual and flag");
   double total;  // this lane's warp total of value slot
   double resid;  // the warp's largest residual
+  int slot;   // the value slot this lane's total belongs to
+  bool write;  // whether this lane writes it
   if constexpr (sizeof(P) == 4) {
-    float h[16], l[16];
+    // a warp without wall nodes has zero wall balances (slots 6..11): its
+    // butterfly sums the first 6 values only
+    bool wall = false;
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
-      h[j] = part[j];
-      l[j] = plo[j];
+    for (int j = kWallIn; j < kResid; ++j) wall = wall || part[j] != 0.f || plo[j] != 0.f;
+    if (__any_sync(0xffffffffu, wall)) {
+      float h[16], l[16];
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        h[j] = part[j];
+        l[j] = plo[j];
+      }
+#pragma unroll
+      for (int j = 12; j < 16; ++j) h[j] = l[j] = 0.f;
+      fold_half_df<16>(h, l, 16, (lane & 16) != 0);
+      fold_half_df<8>(h, l, 8, (lane & 8) != 0);
+      fold_half_df<4>(h, l, 4, (lane & 4) != 0);
+      fold_half_df<2>(h, l, 2, (lane & 2) != 0);
+      const float rh = __shfl_xor_sync(0xffffffffu, h[0], 1);
+      const float rl = __shfl_xor_sync(0xffffffffu, l[0], 1);
+      df_add(h[0], l[0], rh, rl);
+      total = f2d_exact(h[0]) + f2d_exact(l[0]);
+      slot = (lane >> 1) & 15;
+      write = (lane & 1) == 0 && slot < 12;
+    } else {
+      float h[8], l[8];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        h[j] = part[j];
+        l[j] = plo[j];
+      }
+      h[6] = h[7] = l[6] = l[7] = 0.f;
+      fold_half_df<8>(h, l, 16, (lane & 16) != 0);
+      fold_half_df<4>(h, l, 8, (lane & 8) != 0);
+      fold_half_df<2>(h, l, 4, (lane & 4) != 0);
+#pragma unroll
+      for (int o = 2; o > 0; o >>= 1) {
+        const float rh = __shfl_xor_sync(0xffffffffu, h[0], o);
+        const float rl = __shfl_xor_sync(0xffffffffu, l[0], o);
+        df_add(h[0], l[0], rh, rl);
+      }
+      // value (lane >> 2) & 7; lanes 4m write it, lanes 4m + 1 the zero of wall slot 6 + m
+      const int s8 = (lane >> 2) & 7;
+      total = (lane & 3) == 1 ? 0.0 : f2d_exact(h[0]) + f2d_exact(l[0]);
+      slot = (lane & 3) == 1 ? kWallIn + s8 : s8;
+      write = (lane & 3) <= 1 && s8 < 6;
     }
-#pragma unroll
-    for (int j = 12; j < 16; ++j) h[j] = l[j] = 0.f;
-    fold_half_df<16>(h, l, 16, (lane & 16) != 0);
-    fold_half_df<8>(h, l, 8, (lane & 8) != 0);
-    fold_half_df<4>(h, l, 4, (lane & 4) != 0);
-    fold_half_df<2>(h, l, 2, (lane & 2) != 0);
-    const float rh = __shfl_xor_sync(0xffffffffu, h[0], 1);
-    const float rl = __shfl_xor_sync(0xffffffffu, l[0], 1);
-    df_add(h[0], l[0], rh, rl);
-    total = f2d_exact(h[0]) + f2d_exact(l[0]);
     int rb = __float_as_int(part[kResid]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rb = max(rb, __shfl_xor_sync(0xffffffffu, rb, o));
@@ -816,6 +851,8 @@ __device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T
     fold_half<2>(v, 2, (lane & 2) != 0);
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
     total = v[0];
+    slot = (lane >> 1) & 15;
+    write = (lane & 1) == 0 && slot < 12;
     long long rb = __double_as_longlong(part[kResid]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -825,8 +862,7 @@ __device__ __forceinline__ void tile_partials(const InstDev& D, const TileDev& T
     resid = __longlong_as_double(rb);
   }
   const unsigned nf = __popc(__ballot_sync(0xffffffffu, part[kNonFinite] != P(0)));
-  const int slot = (lane >> 1) & 15;
-  if ((lane & 1) == 0 && slot < 12) s_red[warp][slot] = total;
+  if (write) s_red[warp][slot] = total;
   if (lane == 0) {
     s_red[warp][kResid] = resid;
     s_red[warp][kNonFinite] = (double)nf;
