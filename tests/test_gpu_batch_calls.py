@@ -164,3 +164,22 @@ def test_single_instance_set_geometry_in_a_large_batch(lbve):
     b.step(3)
     for j in (4, 6, 11):
         np.testing.assert_array_equal(a.fields(j), b.fields(j))
+
+
+def test_set_geometry_many_mixed_precisions(lbve):
+    """One handle holding a float64, a float32 and a float32-pair instance,
+    set by one lbve_set_geometry_many (each precision's equilibrium launch
+    covers its whole list), steps exactly as three one-instance handles."""
+    insts = [wl.frm(20, Wi=2.0, Re=1.0, Ma=0.05), wl.channel(10, nx=7, Wi=5.0),
+             wl.frm(18, Wi=1.0, Re=1.0, Ma=0.05)]
+    precs = [0, 1, 2]
+    inits = [wl.random_fields(i.nx, i.ny, seed=70 + k) for k, i in enumerate(insts)]
+    mixed = lbve.Simulation(insts, precision=precs, init_fields=inits)
+    mixed.step(25)
+    for j in range(3):
+        one = lbve.Simulation([insts[j]], precision=precs[j], init_fields=[inits[j]])
+        one.step(25)
+        np.testing.assert_array_equal(mixed.fields(j), one.fields(0))
+        # the float64 tile shape may differ with the batch: totals agree to
+        # the summation order's round-off
+        np.testing.assert_allclose(mixed.totals(j), one.totals(0), rtol=1e-12, atol=1e-12)
