@@ -218,7 +218,10 @@ int lbve_set_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
  * Every upload and initialisation is enqueued first and the stream is
  * synchronised once, at the end, so that the copies of one instance overlap
  * the host work of the next (with pinned host arrays the uploads are
- * asynchronous DMA; the arrays may be freed when the call returns).
+ * asynchronous DMA; the arrays may be freed when the call returns).  Lists
+ * of 16 or more instances are uploaded in chunks on the handle's internal
+ * side stream, which waits for the caller's stream first; each chunk's
+ * launches run on the caller's stream once its uploads are done.
  *   insts: host int32 [n], distinct instances (a repeated or out-of-range
  *          entry returns LBVE_ERR_ARG before anything changes).
  * Instances are enqueued in list order.  A geometry rejected on the host or

@@ -337,6 +337,10 @@ struct lbve_handle {
   // nodes, shared read-only source), joined before the step ends
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // chunked geometry set-up: the uploads of chunk c on the side stream, its
+  // launches on the caller's stream once geo_ev[c] has passed
+  static constexpr int kGeoChunks = 8;
+  cudaEvent_t geo_ev[kGeoChunks] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   // per-launch timing of the plain step kernels (lbve_profile): two events
@@ -881,7 +885,8 @@ int lbve_create(const lbve_params* p, int32_t n, void* d_workspace, size_t bytes
 // 0 for a staged force and bit 1 for staged fields.  From the first upload
 // on, the instance is not ready until finish_geometry accepts it.
 static int stage_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mask,
-                          const double* body_force, const double* init_fields, int32_t* what) {
+                          const double* body_force, const double* init_fields, int32_t* what,
+                          cudaStream_t cs) {
   *what = 0;
   {
     // the geometry is checked on the host before anything changes; the
@@ -899,13 +904,13 @@ static int stage_geometry(lbve_handle* h, int32_t inst, const uint8_t* solid_mas
   D.force_field = body_force ? 1 : 0;
   if (body_force) {
     const cudaError_t e = cudaMemcpy2DAsync(D.pop[P], S * 8, body_force, nn * 8, nn * 8, 2,
-                                            cudaMemcpyHostToDevice, h->stream);
+                                            cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "force upload");
     *what |= 1;
   }
   if (init_fields) {
     const cudaError_t e = cudaMemcpy2DAsync(D.pop[P ^ 1], S * 8, init_fields, nn * 8, nn * 8, 6,
-                                            cudaMemcpyHostToDevice, h->stream);
+                                            cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "initial field upload");
     *what |= 2;
   }
@@ -922,14 +927,11 @@ static int init_geometry(lbve_handle* h, int32_t n, const int32_t* ids, const in
   if (n <= 0) return LBVE_OK;
   std::vector<int32_t> geo(2 * (size_t)n);
   int max_nodes = 1;
-  int in_list[kLists] = {0}, of_list[kLists] = {0};
   for (int32_t j = 0; j < n; ++j) {
     geo[j] = ids[j];
     geo[n + j] = what[j];
     max_nodes = std::max(max_nodes, h->p[ids[j]].nx * h->p[ids[j]].ny);
-    ++in_list[h->plan.inst[ids[j]].list];
   }
-  for (int i = 0; i < h->n; ++i) ++of_list[h->plan.inst[i].list];
   // pageable sources: the copies are staged before the calls return.  The
   // descriptors go up as one array when the list covers much of the handle,
   // else one by one (a single instance of a large batch moves 400 bytes)
@@ -949,20 +951,25 @@ static int init_geometry(lbve_handle* h, int32_t n, const int32_t* ids, const in
   if (launch_geometry_inputs(h->d_insts, h->d_geo, h->d_geo + n, n, max_nodes, P, h->d_flags,
                              kFlagBadInput, h->stream))
     return cuda_fail(cudaGetLastError(), "input check launch");
-  // collide the equilibrium state of t = 0: reads pop[P^1] (staging), writes pop[P]
-  for (int l = 0; l < kLists; ++l)
-    if (in_list[l] > 0 && in_list[l] == of_list[l] &&
-        launch_step(l, h->plan.threads[l], h->d_insts, h->d_tiles[l], h->plan.ntiles[l], P ^ 1,
+  // collide the equilibrium state of t = 0: reads pop[P^1] (staging), writes
+  // pop[P].  One launch per run of consecutive instances of one precision:
+  // their tiles are contiguous in that precision's table
+  for (int32_t j = 0; j < n;) {
+    const int32_t first = ids[j];
+    const int l = h->plan.inst[first].list;
+    int32_t last = first, k = j + 1;
+    while (k < n && ids[k] == last + 1 && h->plan.inst[ids[k]].list == l) last = ids[k++];
+    const int t0 = h->plan.inst[first].tile_begin;
+    const int t1 = h->plan.inst[last].tile_begin + h->plan.inst[last].ntiles;
+    if (launch_step(l, h->plan.threads[l], h->d_insts, h->d_tiles[l] + t0, t1 - t0, P ^ 1,
                     kModeInit, kFinal, h->d_partials, h->stream))
       return cuda_fail(cudaGetLastError(), "init kernel launch");
+    j = k;
+  }
   for (int32_t j = 0; j < n; ++j) {
     const int32_t inst = ids[j];
     const InstPlan& q = h->plan.inst[inst];
     const int prec = h->p[inst].precision;
-    if (in_list[q.list] != of_list[q.list] &&
-        launch_step(prec, h->plan.threads[q.list], h->d_insts, h->d_tiles[q.list] + q.tile_begin,
-                    q.ntiles, P ^ 1, kModeInit, kFinal, h->d_partials, h->stream))
-      return cuda_fail(cudaGetLastError(), "init kernel launch");
     if (!h->mtiles_of[inst].empty() &&
         launch_step(prec, h->plan.threads[q.list], h->d_insts,
                     h->d_mtiles[q.list] + h->mbegin[inst], (int)h->mtiles_of[inst].size(), P ^ 1,
@@ -1019,24 +1026,52 @@ int lbve_set_geometry_many(lbve_handle* h, int32_t n, const int32_t* insts,
   }
   if (n == 0) return LBVE_OK;
   std::vector<int32_t> what(n, 0);
-  int32_t staged = n;  // entries 0..staged-1 go through the device part
-  int rc_stage = LBVE_OK;
-  char msg[512] = "";
-  for (int32_t j = 0; j < n; ++j) {
-    rc_stage = stage_geometry(h, insts[j], solid_masks ? solid_masks[j] : nullptr,
-                              body_forces ? body_forces[j] : nullptr,
-                              init_fields ? init_fields[j] : nullptr, &what[j]);
-    if (rc_stage) {
-      // entries before j are still initialised (and may report an earlier
-      // error); entry j and the rest of the list are not set
-      snprintf(msg, sizeof msg, "%s", lbve_last_error());
-      staged = j;
-      break;
-    }
+  // Lists of 16 or more instances go in up to kGeoChunks chunks: the uploads
+  // on the side stream (after the caller's stream has reached this call),
+  // each chunk's launches on the caller's stream after its uploads, so that
+  // the launches of one chunk overlap the uploads of the next.
+  const int nchunk = n >= 16 ? lbve_handle::kGeoChunks : 1;
+  const int32_t per = (n + nchunk - 1) / nchunk;
+  cudaStream_t cs = h->stream;
+  if (nchunk > 1) {
+    int rc = ensure_side_stream(h);
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < nchunk && rc == LBVE_OK && e == cudaSuccess; ++c)
+      if (!h->geo_ev[c]) e = cudaEventCreateWithFlags(&h->geo_ev[c], cudaEventDisableTiming);
+    if (e == cudaSuccess && rc == LBVE_OK) e = cudaEventRecord(h->ev_fork, h->stream);
+    if (e == cudaSuccess && rc == LBVE_OK) e = cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "geometry upload stream");
+    cs = h->side_stream;
   }
-  int rc = init_geometry(h, staged, insts, what.data());
+  int32_t staged = n;  // entries 0..staged-1 go through the device part
+  int rc_stage = LBVE_OK, rc = LBVE_OK;
+  char msg[512] = "";
+  for (int32_t j0 = 0, c = 0; j0 < staged && rc == LBVE_OK; j0 += per, ++c) {
+    const int32_t j1 = std::min(n, j0 + per);
+    int32_t j = j0;
+    for (; j < j1; ++j) {
+      rc_stage = stage_geometry(h, insts[j], solid_masks ? solid_masks[j] : nullptr,
+                                body_forces ? body_forces[j] : nullptr,
+                                init_fields ? init_fields[j] : nullptr, &what[j], cs);
+      if (rc_stage) {
+        // entries before j are still initialised (and may report an earlier
+        // error); entry j and the rest of the list are not set
+        snprintf(msg, sizeof msg, "%s", lbve_last_error());
+        staged = j;
+        break;
+      }
+    }
+    if (cs != h->stream) {
+      cudaError_t e = cudaEventRecord(h->geo_ev[c], cs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->geo_ev[c], 0);
+      if (e != cudaSuccess) rc = cuda_fail(e, "geometry upload stream");
+    }
+    if (rc == LBVE_OK) rc = init_geometry(h, j - j0, insts + j0, what.data() + j0);
+  }
   if (rc) {
     // what was enqueued finishes before the caller's arrays are released
+    if (cs != h->stream) cudaStreamSynchronize(cs);
     cudaStreamSynchronize(h->stream);
     return rc;
   }
@@ -1410,6 +1445,8 @@ void lbve_destroy(lbve_handle* h) {
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  for (cudaEvent_t ev : h->geo_ev)
+    if (ev) cudaEventDestroy(ev);
   delete h;
 }
 
