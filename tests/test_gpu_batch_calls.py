@@ -183,3 +183,32 @@ def test_set_geometry_many_mixed_precisions(lbve):
         # the float64 tile shape may differ with the batch: totals agree to
         # the summation order's round-off
         np.testing.assert_allclose(mixed.totals(j), one.totals(0), rtol=1e-12, atol=1e-12)
+
+
+def test_chunked_set_geometry_many(lbve):
+    """A list of 24 instances (uploaded in chunks on the side stream) leaves
+    the same state as 24 single calls, and a NaN in one instance of a later
+    chunk leaves exactly that instance uninitialised."""
+    insts = [wl.frm(10 + (j % 4), Wi=0.5 + j, Re=1.0, Ma=0.05) if j % 2 else
+             wl.channel(6 + (j % 5), nx=3 + (j % 3), Wi=1.0 + j) for j in range(24)]
+    inits = [wl.random_fields(i.nx, i.ny, seed=300 + j) for j, i in enumerate(insts)]
+    n = [i.n_nodes for i in insts]
+    ids = list(range(24))
+    a = lbve.Simulation(insts, precision=1)
+    b = lbve.Simulation(insts, precision=1)
+    a.step(4)
+    lbve.lbve_set_geometry_many(a.h, ids, None, [i.force_field for i in insts], inits, n_nodes=n)
+    for j in ids:
+        lbve.lbve_set_geometry(b.h, j, None, insts[j].force_field, inits[j], n_nodes=n[j])
+    a.step(30)
+    b.step(30)
+    for j in ids:
+        np.testing.assert_array_equal(a.fields(j), b.fields(j))
+    bad = [x.copy() for x in inits]
+    bad[19][5, 1, 1] = np.inf
+    with pytest.raises(lbve.LbveError) as e:
+        lbve.lbve_set_geometry_many(a.h, ids, None, [i.force_field for i in insts], bad, n_nodes=n)
+    assert e.value.code == lbve.LBVE_ERR_ARG and "instance 19" in str(e.value)
+    flags = a.status()
+    assert [j for j in ids if flags[j] & 2] == [19]
+    assert all(a.time(j) == 0 for j in ids if j != 19)
