@@ -11,7 +11,7 @@
 //        unrenormalised: |lo| stays within about 1.5 ulp(hi), which the
 //        two-sum of the next addition absorbs (4 operations instead of 7;
 //        10 % off the step on the batched mix);
-//   div: a float32 quotient refined by one correction step.
+//   div: a float32 quotient from one reciprocal, refined by one correction step.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -47,9 +47,14 @@ __device__ __forceinline__ df32 operator*(df32 a, df32 b) {
   return df32(p, e);
 }
 __device__ __forceinline__ df32 operator/(df32 a, df32 b) {
-  const float q = a.hi / b.hi;
-  const df32 r = a - b * df32(q, 0.f);  // remainder
-  return df_renorm(q, r.hi / b.hi);
+  // one correctly rounded reciprocal serves both quotients; the correction
+  // takes the first quotient's extra rounding (about 47 bits in all)
+  const float rb = 1.f / b.hi;
+  const float q = a.hi * rb;
+  const float p = b.hi * q;  // b * q exactly as a pair (b.hi q + b.lo q)
+  const df32 bq(p, fmaf(b.lo, q, fmaf(b.hi, q, -p)));
+  const df32 r = a - bq;  // remainder
+  return df_renorm(q, r.hi * rb);
 }
 __device__ __forceinline__ df32& operator+=(df32& a, df32 b) { return a = a + b; }
 

@@ -665,8 +665,10 @@ __device__ __forceinline__ R y_drho(bool wb, bool wt, R rm2, R rm1, R r0, R rp1,
 // Float64 CTAs: 256 threads two per SM (128 registers per thread).  The
 // 64- and one-warp CTAs serve batches with fewer tiles than 4 and 2 per SM,
 // so they are budgeted for that many and keep every value in registers.
+// Float32 pairs: 3 CTAs per SM keep their registers (227 at most) without
+// spills; 4 per SM spill a little and ran 1.4 % slower on the batched mix.
 #ifndef LBVE_DF32_MIN_BLOCKS
-#define LBVE_DF32_MIN_BLOCKS 4
+#define LBVE_DF32_MIN_BLOCKS 3
 #endif
 template <typename R, bool MASKED, int NT>
 struct MinBlocks {
@@ -1176,8 +1178,9 @@ __device__ __forceinline__ void process_tile(const InstDev* __restrict__ insts, 
     }
     PartT<R> ux_prev = 0, uy_prev = 0;
     if (FINAL && MODE == kModeStep) {
-      ux_prev = (PartT<R>)D.fields[S + k];
-      uy_prev = (PartT<R>)D.fields[2 * S + k];
+      // prefetched into L2 above; read past L1 (nothing else touches these lines)
+      ux_prev = (PartT<R>)__ldcg(D.fields + S + k);
+      uy_prev = (PartT<R>)__ldcg(D.fields + 2 * S + k);
     }
     collide_node<R, MODE, FINAL, MASKED>(D, k, S, dst, hist, hm, cm, rho, ux, uy, G00, G01, G10,
                                          G11, dPx, dPy, dRx, dRy, Fx, Fy, So[0], So[1], So[2], uxo,
